@@ -1,0 +1,99 @@
+/*
+ * mplobpcg_steps.h -- the individual steps of one LOBPCG iteration
+ * (Algorithm 3), exposed on an existing handle so that each step can be run
+ * and checked on its own.  They are the same routines mpl_solve() calls.
+ *
+ * Conventions: every pointer is DEVICE memory unless named *_host; matrices
+ * are column-major with leading dimension n (the order of A) for n-row
+ * blocks and the row count for small matrices; element type is the handle's
+ * working type (double or interleaved complex double) unless stated.
+ * Vectors live in the permuted ordering Pi of the handle (Pi = I for dense).
+ * Block widths must not exceed the handle's m (ncol <= 3m).  Every call is
+ * synchronous on the handle's stream and returns an mpl_status.
+ */
+#ifndef MPLOBPCG_STEPS_H
+#define MPLOBPCG_STEPS_H
+
+#include "mplobpcg.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Block product Y = (Pi^* A Pi) X, ncols columns (Algorithm 3: "R <- AX - X
+ * Theta", "A_p <- S^* A S"; Table 1 mat-vec).  lower = 1 uses the FP32 copy
+ * of A with X, Y in the lower type (float / interleaved complex float). */
+mpl_status mpl_step_apply_A(mpl_handle h, const void* X, void* Y, int ncols, int lower);
+
+/* Residual R = AX - X diag(theta) and the squared column norms
+ * norms2_host[0..m) = ||r_j||^2, norms2_host[m..2m) = ||x_j||^2
+ * (Algorithm 3 lines "Compute residual", "Determine n_c"; Eq. (stop)).
+ * theta_host: m doubles. */
+mpl_status mpl_step_residual(mpl_handle h, const void* AX, const void* X,
+                             const double* theta_host, int m, void* R, double* norms2_host);
+
+/* Preconditioner W = double(f_T(single(R))) with f_T = L^-* L^-1 (Section
+ * 5.1, two triangular solves in the factor's precision), m columns.  scale = 1
+ * first divides each column of R by its 2-norm.  Requires mpl_factor(). */
+mpl_status mpl_step_precond(mpl_handle h, const void* R, void* W, int m, int scale);
+
+/* Algorithm 2 on W (n x m, in place): W <- Q with W = QR.  lower_qr = 1 runs
+ * step 1 (Householder QR) in FP32, 0 in working precision.  info is set to the
+ * failing column if the Cholesky of V^* V breaks down (MPL_ERANK). */
+mpl_status mpl_step_mixed_qr(mpl_handle h, void* W, int m, int lower_qr);
+
+/* Orthogonalise W (n x m) against B (n x nb, orthonormal columns) twice:
+ * W <- W - B (B^* W) (Algorithm 3, "Orthogonalize W against [X, P] twice"). */
+mpl_status mpl_step_project(mpl_handle h, const void* B, int nb, void* W, int m);
+
+/* The m smallest eigenpairs of the Hermitian N x N matrix Ap (destroyed):
+ * lam_host (m doubles, ascending) and C1 (N x m eigenvectors). */
+mpl_status mpl_step_small_eig(mpl_handle h, void* Ap, int N, int m, double* lam_host, void* C1);
+
+/* Rayleigh-Ritz of Algorithm 3 on S = [X, P, W] (n x ncol) and AS = A S:
+ * A_p = S^* A S, A_p C = C D, and the coefficient block Ccoef (ncol x 2m)
+ * = [C(:, 1:m), V_P] where S V_P spans the part of the old X orthogonal to the
+ * new Ritz vectors (the improved Hetmaniuk-Lehoucq step).  lam_host: the m
+ * smallest Ritz values. */
+mpl_status mpl_step_rayleigh_ritz(mpl_handle h, const void* S, const void* AS, int ncol, int m,
+                                  double* lam_host, void* Ccoef);
+
+/* Copy the factor L (n x n lower, column-major) into a device buffer of the
+ * factor's type: float / complex float for the schol policies, double /
+ * complex double for MPL_D_DCHOL.  Dense handles only. */
+mpl_status mpl_get_factor_dense(mpl_handle h, void* L);
+
+/* The ordering Pi (perm[new] = old) into a host array of n int64. */
+mpl_status mpl_get_permutation(mpl_handle h, int64_t* perm_host);
+
+/* Sparse handles: sizes of the symbolic analysis (after mpl_factor or
+ * mpl_analyze): nsuper_host = number of supernodes, nnzl_host = entries of L
+ * (including the diagonal), nrows_host = total supernode row-index count. */
+mpl_status mpl_analyze(mpl_handle h);
+mpl_status mpl_get_symbolic_sizes(mpl_handle h, int64_t* nsuper_host, int64_t* nnzl_host,
+                                  int64_t* nrows_host);
+
+/* Sparse handles: the symbolic structure (host arrays): parent (n int64,
+ * elimination tree, -1 for roots), colcount (n int64, |L(:, j)| including the
+ * diagonal), sn_start (nsuper + 1 int64, first column of each supernode),
+ * sn_rowptr (nsuper + 1 int64) and sn_rows (nrows int64, the row indices of
+ * each supernode, its own columns first), sn_level (nsuper int64).  Any
+ * pointer may be NULL. */
+mpl_status mpl_get_symbolic(mpl_handle h, int64_t* parent, int64_t* colcount, int64_t* sn_start,
+                            int64_t* sn_rowptr, int64_t* sn_rows, int64_t* sn_level);
+
+/* Host-only ordering + symbolic analysis of a CSR pattern (host arrays; no
+ * GPU is touched).  The returned handle answers mpl_get_permutation,
+ * mpl_get_symbolic_sizes and mpl_get_symbolic only; release it with
+ * mpl_destroy.  grid_dims as for mpl_create_csr. */
+mpl_status mpl_analyze_host(mpl_handle* h, int64_t n, int64_t nnz, const int64_t* rowptr,
+                            const int32_t* colind, const int32_t* grid_dims, int ndims);
+
+/* Sparse handles: L applied to a block, Y = L X (n x ncols, float), for
+ * checking the numeric factor without materialising it. */
+mpl_status mpl_step_apply_L(mpl_handle h, const float* X, float* Y, int ncols);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPLOBPCG_STEPS_H */

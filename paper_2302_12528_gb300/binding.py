@@ -1,0 +1,274 @@
+"""ctypes binding of libmplobpcg.so (argument marshalling only).
+
+Layout convention: a column-major n x m block is passed as a C-contiguous
+array/tensor of shape (m, n) (its transpose); a dense matrix A is passed as the
+C-contiguous array holding A^T (for real symmetric A that is A itself; for
+complex Hermitian A it is conj(A)).  ``Handle.from_dense`` accepts the
+mathematical matrix and does that conversion.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmplobpcg.so")
+
+MPL_R64, MPL_C128 = 0, 1
+MPL_D_DCHOL, MPL_D_SCHOL, MPL_MP_SCHOL = 0, 1, 2
+POLICIES = {"dchol": MPL_D_DCHOL, "schol": MPL_D_SCHOL, "mp": MPL_MP_SCHOL}
+STATUS = {0: "MPL_OK", 1: "MPL_EINVAL", 2: "MPL_ENOT_HPD", 3: "MPL_ERANK", 4: "MPL_ENOT_CONVERGED",
+          5: "MPL_ENUMERICAL", 6: "MPL_ENOMEM", 7: "MPL_ECUDA", 8: "MPL_ESTATE"}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"CUDA library {LIB_PATH} is missing: build it with "
+        "`python -c \"import __graft_entry__ as g; g.build()\"` (there is no CPU fallback)")
+lib = C.CDLL(LIB_PATH)
+
+_h = C.c_void_p
+_p = C.c_void_p
+_i = C.c_int
+_i64 = C.c_int64
+_d = C.c_double
+
+
+class Stats(C.Structure):
+    _fields_ = [("t_create_ms", _d), ("t_symbolic_ms", _d), ("t_factor_ms", _d), ("t_stage1_ms", _d),
+                ("t_stage2_ms", _d), ("iters_stage1", _i), ("iters_stage2", _i), ("factor_tries", _i),
+                ("factor_shift", _d), ("norm_est", _d), ("qr_fallbacks", _i), ("explicit_checks", _i),
+                ("nnz_L", _i64), ("nsuper", _i64), ("max_rel_resid", _d)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _sig(name, res, args):
+    f = getattr(lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_create_dense = _sig("mpl_create_dense", _i, [C.POINTER(_h), _i, _i64, _p, _i64, _i, _i, _i, _d, _i, _p, _i, _i, _p])
+_create_csr = _sig("mpl_create_csr", _i, [C.POINTER(_h), _i64, _i64, _p, _p, _p, _i, _p, _i, _i, _i, _d, _i, _p, _i,
+                                          _i, _p])
+_factor = _sig("mpl_factor", _i, [_h])
+_solve = _sig("mpl_solve", _i, [_h, _p, _i, _i, _p, _p, _i, _p, _i, _p, _p])
+_stats = _sig("mpl_get_stats", _i, [_h, C.POINTER(Stats)])
+_last_error = _sig("mpl_last_error", C.c_char_p, [_h])
+_last_info = _sig("mpl_last_info", _i64, [_h])
+_destroy = _sig("mpl_destroy", None, [_h])
+_apply_A = _sig("mpl_step_apply_A", _i, [_h, _p, _p, _i, _i])
+_residual = _sig("mpl_step_residual", _i, [_h, _p, _p, _p, _i, _p, _p])
+_precond = _sig("mpl_step_precond", _i, [_h, _p, _p, _i, _i])
+_mixed_qr = _sig("mpl_step_mixed_qr", _i, [_h, _p, _i, _i])
+_project = _sig("mpl_step_project", _i, [_h, _p, _i, _p, _i])
+_small_eig = _sig("mpl_step_small_eig", _i, [_h, _p, _i, _i, _p, _p])
+_rr = _sig("mpl_step_rayleigh_ritz", _i, [_h, _p, _p, _i, _i, _p, _p])
+_get_factor = _sig("mpl_get_factor_dense", _i, [_h, _p])
+_get_perm = _sig("mpl_get_permutation", _i, [_h, _p])
+_sym_sizes = _sig("mpl_get_symbolic_sizes", _i, [_h, _p, _p, _p])
+_get_sym = _sig("mpl_get_symbolic", _i, [_h, _p, _p, _p, _p, _p, _p])
+_apply_L = _sig("mpl_step_apply_L", _i, [_h, _p, _p, _i])
+_analyze_host = _sig("mpl_analyze_host", _i, [C.POINTER(_h), _i64, _i64, _p, _p, _p, _i])
+
+
+class MplError(RuntimeError):
+    def __init__(self, status, msg, info):
+        super().__init__(f"{STATUS.get(status, status)}: {msg} (info={info})")
+        self.status = status
+        self.info = info
+
+
+def _ptr(x):
+    """Raw pointer of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _is_dev(x):
+    return 0 if isinstance(x, np.ndarray) else int(getattr(x, "is_cuda", False))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class Handle:
+    """Owns an ``mpl_handle``; methods map one-to-one onto the C ABI."""
+
+    def __init__(self, raw, dtype, n, k, m, keep=()):
+        self._h = raw
+        self.dtype = dtype
+        self.n, self.k, self.m = n, k, m
+        self._keep = keep
+
+    def _check(self, st, allow=(0,)):
+        if st not in allow:
+            raise MplError(st, self.last_error(), self.last_info())
+        return st
+
+    def last_error(self):
+        return _last_error(self._h).decode()
+
+    def last_info(self):
+        return int(_last_info(self._h))
+
+    def factor(self):
+        self._check(_factor(self._h))
+
+    def solve(self, X0, maxit=2000, X_out=None, hist_cap=4096, allow_not_converged=False):
+        """Algorithm 3.  X0: (m, n) array/tensor (column-major n x m).
+        X_out: optional (k, n) tensor/array receiving the eigenvectors.
+        Returns (lambda (k,), X_out, hist list, (it1, it2), status)."""
+        lam = np.zeros(self.k)
+        hist = np.zeros(max(hist_cap, 1))
+        hl = C.c_int(0)
+        its = (C.c_int * 2)()
+        st = _solve(self._h, _ptr(X0), _is_dev(X0), maxit, lam.ctypes.data, _ptr(X_out),
+                    _is_dev(X_out) if X_out is not None else 0, hist.ctypes.data, hist_cap,
+                    C.byref(hl), its)
+        self._check(st, (0, 4) if allow_not_converged else (0,))
+        return lam, X_out, hist[: hl.value].tolist(), (its[0], its[1]), st
+
+    def stats(self):
+        s = Stats()
+        self._check(_stats(self._h, C.byref(s)))
+        return s.as_dict()
+
+    # ---- steps (device tensors) ----
+    def apply_A(self, X, Y, ncols, lower=False):
+        self._check(_apply_A(self._h, _ptr(X), _ptr(Y), ncols, int(lower)))
+
+    def residual(self, AX, X, theta, m, R):
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        out = np.zeros(2 * m)
+        self._check(_residual(self._h, _ptr(AX), _ptr(X), th.ctypes.data, m, _ptr(R), out.ctypes.data))
+        return out[:m], out[m:]
+
+    def precond(self, R, W, m, scale=False):
+        self._check(_precond(self._h, _ptr(R), _ptr(W), m, int(scale)))
+
+    def mixed_qr(self, W, m, lower_qr=True):
+        return self._check(_mixed_qr(self._h, _ptr(W), m, int(lower_qr)), (0, 3))
+
+    def project(self, B, nb, W, m):
+        self._check(_project(self._h, _ptr(B), nb, _ptr(W), m))
+
+    def small_eig(self, Ap, N, m, C1):
+        lam = np.zeros(m)
+        self._check(_small_eig(self._h, _ptr(Ap), N, m, lam.ctypes.data, _ptr(C1)))
+        return lam
+
+    def rayleigh_ritz(self, S, AS, ncol, m, Ccoef):
+        lam = np.zeros(m)
+        self._check(_rr(self._h, _ptr(S), _ptr(AS), ncol, m, lam.ctypes.data, _ptr(Ccoef)))
+        return lam
+
+    def get_factor_dense(self, L):
+        self._check(_get_factor(self._h, _ptr(L)))
+
+    def permutation(self):
+        p = np.zeros(self.n, dtype=np.int64)
+        self._check(_get_perm(self._h, p.ctypes.data))
+        return p
+
+    def symbolic(self):
+        ns, nl, nr = C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(_sym_sizes(self._h, C.byref(ns), C.byref(nl), C.byref(nr)))
+        n, nsup = self.n, ns.value
+        out = dict(parent=np.zeros(n, np.int64), colcount=np.zeros(n, np.int64),
+                   sn_start=np.zeros(nsup + 1, np.int64), sn_rowptr=np.zeros(nsup + 1, np.int64),
+                   sn_rows=np.zeros(max(nr.value, 1), np.int64), sn_level=np.zeros(max(nsup, 1), np.int64))
+        self._check(_get_sym(self._h, *[out[k].ctypes.data for k in
+                                        ("parent", "colcount", "sn_start", "sn_rowptr", "sn_rows", "sn_level")]))
+        out["sn_rows"] = out["sn_rows"][: nr.value]
+        out["sn_level"] = out["sn_level"][:nsup]
+        out["nsuper"] = nsup
+        out["nnz_L"] = nl.value
+        return out
+
+    def apply_L(self, X, Y, ncols):
+        self._check(_apply_L(self._h, _ptr(X), _ptr(Y), ncols))
+
+    def close(self):
+        if self._h:
+            _destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _raise_create(st, what):
+    raise MplError(st, f"{what} failed", 0)
+
+
+def create_dense(A_colmajor, k, m, tol=1e-12, policy="mp", Omega=None, stream=None):
+    """Dense Hermitian PD matrix.  ``A_colmajor``: C-contiguous (n, n) array or
+    tensor holding A^T (float64 or complex128).  ``Omega``: (m_omega, n)
+    C-contiguous sketch (column-major n x m_omega), same dtype."""
+    n = A_colmajor.shape[0]
+    cplx = (A_colmajor.dtype == np.complex128) if isinstance(A_colmajor, np.ndarray) else A_colmajor.is_complex()
+    dtype = MPL_C128 if cplx else MPL_R64
+    if Omega is None:
+        raise ValueError("Omega (the norm-estimate sketch) is required")
+    h = _h()
+    st = _create_dense(C.byref(h), dtype, n, _ptr(A_colmajor), n, _is_dev(A_colmajor), k, m, tol,
+                       POLICIES.get(policy, policy), _ptr(Omega), Omega.shape[0], _is_dev(Omega),
+                       _stream_ptr(stream))
+    if st != 0:
+        _raise_create(st, "mpl_create_dense")
+    return Handle(h, dtype, n, k, m)
+
+
+def create_csr(rowptr, colind, vals, k, m, tol=1e-12, policy="mp", Omega=None, grid_dims=None,
+               stream=None):
+    """Sparse real SPD CSR matrix (numpy int64 rowptr, int32 colind, float64
+    vals, host or device).  ``grid_dims``: (nx, ny[, nz]) for the grid
+    nested-dissection ordering, or None."""
+    n = len(rowptr) - 1
+    nnz = len(colind)
+    if Omega is None:
+        raise ValueError("Omega (the norm-estimate sketch) is required")
+    gd = None if grid_dims is None else np.ascontiguousarray(grid_dims, dtype=np.int32)
+    h = _h()
+    st = _create_csr(C.byref(h), n, nnz, _ptr(rowptr), _ptr(colind), _ptr(vals), _is_dev(vals),
+                     _ptr(gd), 0 if gd is None else len(gd), k, m, tol, POLICIES.get(policy, policy),
+                     _ptr(Omega), Omega.shape[0], _is_dev(Omega), _stream_ptr(stream))
+    if st != 0:
+        _raise_create(st, "mpl_create_csr")
+    return Handle(h, MPL_R64, n, k, m)
+
+
+def analyze_host(rowptr, colind, grid_dims=None):
+    """Host-only ordering + symbolic analysis (no GPU needed).  Returns a
+    Handle on which ``permutation()`` and ``symbolic()`` work."""
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray(colind, dtype=np.int32)
+    n = len(rp) - 1
+    gd = None if grid_dims is None else np.ascontiguousarray(grid_dims, dtype=np.int32)
+    h = _h()
+    st = _analyze_host(C.byref(h), n, len(ci), rp.ctypes.data, ci.ctypes.data, _ptr(gd),
+                       0 if gd is None else len(gd))
+    if st != 0:
+        _raise_create(st, "mpl_analyze_host")
+    return Handle(h, MPL_R64, n, 1, 1)

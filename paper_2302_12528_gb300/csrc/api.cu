@@ -1,0 +1,760 @@
+// C ABI (include/mplobpcg.h, include/mplobpcg_steps.h): handle lifetime,
+// the precision policies of Section 5.1 and the two stages of Algorithm 3.
+#include <chrono>
+#include <cstdio>
+
+#include "engine.cuh"
+#include "mplobpcg_steps.h"
+#include "sparse.cuh"
+
+namespace mpl {
+
+template <typename TV, typename T>
+void spmm_csr(cudaStream_t st, int n, int m, const long long* rowptr, const int* colind,
+              const TV* vals, const T* X, long long ldx, T* Y, long long ldy);
+
+// ---- operators ---------------------------------------------------------
+template <typename T>
+struct DenseOp : Op<T> {
+  const T* A = nullptr;
+  long long lda = 0;
+  int n = 0;
+  Scratch scr;
+  void apply(cudaStream_t st, const T* X, long long ldx, T* Y, long long ldy, int ncols) override {
+    gemm<T>(st, false, false, n, ncols, n, 1, A, lda, X, ldx, 0, Y, ldy, false, scr);
+  }
+};
+
+template <typename T>
+struct CsrOp : Op<T> {
+  const long long* rowptr = nullptr;
+  const int* colind = nullptr;
+  const T* vals = nullptr;
+  int n = 0;
+  void apply(cudaStream_t st, const T* X, long long ldx, T* Y, long long ldy, int ncols) override {
+    spmm_csr<T, T>(st, n, ncols, rowptr, colind, vals, X, ldx, Y, ldy);
+  }
+};
+
+template <typename TF>
+struct DenseFactorSolve : FactorSolve<TF> {
+  DenseFactor<TF> F;
+  void solve(cudaStream_t st, TF* B, long long ldb, int m) override { dense_precond<TF>(st, F, B, ldb, m); }
+};
+
+// ---- engine ------------------------------------------------------------
+struct EngineBase {
+  virtual ~EngineBase() {}
+  virtual void factor() = 0;
+  virtual mpl_status solve(const void* X0, int x0_dev, int maxit, double* lambda, void* X, int x_dev,
+                           double* hist, int hist_cap, int* hist_len, int* iters) = 0;
+  virtual void step_apply_A(const void* X, void* Y, int ncols, int lower) = 0;
+  virtual void step_residual(const void* AX, const void* X, const double* theta, int m, void* R,
+                             double* norms2) = 0;
+  virtual void step_precond(const void* R, void* W, int m, int scale) = 0;
+  virtual bool step_mixed_qr(void* W, int m, int lower) = 0;
+  virtual void step_project(const void* B, int nb, void* W, int m) = 0;
+  virtual void step_small_eig(void* Ap, int N, int m, double* lam, void* C1) = 0;
+  virtual void step_rr(const void* S, const void* AS, int ncol, int m, double* lam, void* Ccoef) = 0;
+  virtual void get_factor_dense(void* L) = 0;
+  virtual void step_apply_L(const float* X, float* Y, int ncols) = 0;
+  virtual void analyze() = 0;
+  virtual SparseSymbolic* symbolic() = 0;
+};
+
+}  // namespace mpl
+
+struct mpl_ctx {
+  int dtype = 0, policy = 0, k = 0, m = 0;
+  long long n = 0;
+  double tol = 0.0, norm_est = 0.0;
+  bool sparse = false, factored = false;
+  cudaStream_t stream = nullptr;
+  std::vector<long long> perm;  // perm[new] = old
+  mpl_stats stats{};
+  std::string err;
+  long long info = 0;
+  std::unique_ptr<mpl::EngineBase> eng;
+};
+
+namespace mpl {
+
+static double elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  return (double)ms;
+}
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaStream_t st;
+  explicit Timer(cudaStream_t s) : st(s) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+  }
+  double stop() {
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    return elapsed_ms(a, b);
+  }
+  ~Timer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+template <typename TW>
+class Engine : public EngineBase {
+  using TL = typename tr<TW>::low;
+
+ public:
+  Engine(mpl_ctx* c) : c_(c) {}
+
+  // ---- setup ----
+  void create_dense(const void* A, long long lda, int is_dev, const void* Om, int mo, int om_dev) {
+    const long long n = c_->n;
+    cudaStream_t st = c_->stream;
+    Aw_.alloc(sizeof(TW) * n * n);
+    MPL_CUDA(cudaMemcpy2DAsync(Aw_.ptr(), sizeof(TW) * n, A, sizeof(TW) * lda, sizeof(TW) * n, n,
+                               is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    scr_mem_.alloc((size_t)48 << 20);
+    scr_.ptr = scr_mem_.ptr();
+    scr_.bytes = scr_mem_.bytes();
+    dense_op_.A = Aw_.as<TW>();
+    dense_op_.lda = n;
+    dense_op_.n = (int)n;
+    dense_op_.scr = scr_;
+    opw_ = &dense_op_;
+    if (c_->policy == MPL_MP_SCHOL) {
+      Al_.alloc(sizeof(TL) * n * n);
+      cast<TL, TW>(st, (int)n, (int)n, Aw_.as<TW>(), n, Al_.as<TL>(), n);
+      dense_op_l_.A = Al_.as<TL>();
+      dense_op_l_.lda = n;
+      dense_op_l_.n = (int)n;
+      dense_op_l_.scr = scr_;
+      opl_ = &dense_op_l_;
+    }
+    norm_estimate(Om, mo, om_dev);
+    check_launch("create_dense");
+    MPL_CUDA(cudaStreamSynchronize(st));
+  }
+
+  void create_csr(const long long* rowptr, const int* colind, const double* vals, long long nnz,
+                  int is_dev, const int* dims, int ndims, const void* Om, int mo, int om_dev);
+
+  void norm_estimate(const void* Om, int mo, int om_dev) {
+    // ||Omega A||_F / ||Omega||_F = ||A conj(Omega^T)||_F / ||Omega||_F for Hermitian A
+    const long long n = c_->n;
+    cudaStream_t st = c_->stream;
+    DevMem O(sizeof(TW) * n * mo), Y(sizeof(TW) * n * mo), part(sizeof(double) * (ceil_div(n, 2048) + 1) * mo),
+        out(sizeof(double) * mo);
+    MPL_CUDA(cudaMemcpyAsync(O.ptr(), Om, sizeof(TW) * n * mo,
+                             om_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    conj_inplace<TW>(st, (int)n, mo, O.as<TW>(), n);
+    opw_->apply(st, O.as<TW>(), n, Y.as<TW>(), n, mo);
+    std::vector<double> a(mo), b(mo);
+    col_norms2<TW>(st, (int)n, mo, Y.as<TW>(), n, part.as<double>(), out.as<double>());
+    MPL_CUDA(cudaMemcpyAsync(a.data(), out.ptr(), sizeof(double) * mo, cudaMemcpyDeviceToHost, st));
+    MPL_CUDA(cudaStreamSynchronize(st));
+    col_norms2<TW>(st, (int)n, mo, O.as<TW>(), n, part.as<double>(), out.as<double>());
+    MPL_CUDA(cudaMemcpyAsync(b.data(), out.ptr(), sizeof(double) * mo, cudaMemcpyDeviceToHost, st));
+    MPL_CUDA(cudaStreamSynchronize(st));
+    double sa = 0, sb = 0;
+    for (int j = 0; j < mo; ++j) { sa += a[j]; sb += b[j]; }
+    c_->norm_est = std::sqrt(sa / sb);
+    c_->stats.norm_est = c_->norm_est;
+  }
+
+  // ---- factor ----
+  void factor() override {
+    cudaStream_t st = c_->stream;
+    const bool dchol = c_->policy == MPL_D_DCHOL;
+    Timer t(st);
+    if (c_->sparse) {
+      sparse_factor(dchol);
+    } else if (dchol) {
+      dense_factor<TW>(fw_);
+    } else {
+      dense_factor<TL>(fl_);
+    }
+    c_->stats.t_factor_ms = t.stop();
+    c_->factored = true;
+  }
+
+  template <typename TF>
+  void dense_factor(DenseFactorSolve<TF>& FS) {
+    cudaStream_t st = c_->stream;
+    const long long n = c_->n;
+    constexpr int NB = CholBlock<TF>::NB;
+    const int nblk = ceil_div(n, NB);
+    DenseFactor<TF>& F = FS.F;
+    if (!F.L) {
+      Lbuf_.alloc(sizeof(TF) * n * n);
+      Dbuf_.alloc(sizeof(TF) * (size_t)nblk * NB * NB);
+      tmp_.alloc(sizeof(TF) * n * NB);
+      info_.alloc(16);
+      F.L = Lbuf_.as<TF>();
+      F.Dinv = Dbuf_.as<TF>();
+      F.ldl = n;
+      F.n = (int)n;
+    }
+    const double u = (sizeof(real_t<TF>) == 4) ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
+    double sigma = 0.0;
+    for (int j = 0; j <= 8; ++j) {
+      cast<TF, TW>(st, (int)n, (int)n, Aw_.as<TW>(), n, F.L, n);
+      if (sigma != 0.0) add_diag<TF>(st, (int)n, F.L, n, sigma);
+      dense_cholesky<TF>(st, F, tmp_.as<TF>(), info_.as<int>(), scr_);
+      int info = 0;
+      MPL_CUDA(cudaMemcpyAsync(&info, info_.ptr(), sizeof(int), cudaMemcpyDeviceToHost, st));
+      MPL_CUDA(cudaStreamSynchronize(st));
+      check_launch("dense_cholesky");
+      c_->stats.factor_tries = j + 1;
+      if (info == 0) {
+        c_->stats.factor_shift = sigma;
+        c_->stats.nnz_L = n * (n + 1) / 2;
+        return;
+      }
+      c_->info = info;
+      sigma = std::ldexp(1.0, j) * u * c_->norm_est;
+    }
+    throw MplError{MPL_ENOT_HPD, "Cholesky factorisation broke down for every shift", c_->info};
+  }
+
+  void sparse_factor(bool dchol);
+
+  // ---- solve ----
+  template <typename TF, typename TQ>
+  Progress stage2(FactorSolve<TF>* FS, const TW* X0, int maxit, bool qr_low) {
+    PreFromFactor<TW, TF> pre;
+    pre.F = FS;
+    pre.n = (int)c_->n;
+    auto& stg = stage_w<TQ>();
+    return stg.run(c_->stream, opw_, &pre, X0, c_->k, c_->tol, c_->norm_est, maxit, false, qr_low, true);
+  }
+
+  template <typename TQ>
+  Stage<TW, TQ>& stage_w();
+
+  FactorSolve<TL>* factor_low() {
+    if constexpr (std::is_same<TL, float>::value) {
+      if (c_->sparse) return sparse_low_.get();
+    }
+    return &fl_;
+  }
+  FactorSolve<TW>* factor_work();
+
+  mpl_status solve(const void* X0, int x0_dev, int maxit, double* lambda, void* X, int x_dev,
+                   double* hist, int hist_cap, int* hist_len, int* iters) override {
+    if (!c_->factored) throw MplError{MPL_ESTATE, "mpl_solve before mpl_factor", 0};
+    cudaStream_t st = c_->stream;
+    const long long n = c_->n;
+    const int m = c_->m, k = c_->k;
+    X0_.ensure(sizeof(TW) * n * m);
+    TW* x0 = X0_.as<TW>();
+    if (c_->sparse && !c_->perm.empty()) {
+      tmpx_.ensure(sizeof(TW) * n * m);
+      MPL_CUDA(cudaMemcpyAsync(tmpx_.ptr(), X0, sizeof(TW) * n * m,
+                               x0_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+      permute_rows<TW>(st, (int)n, m, perm_dev_.as<long long>(), false, tmpx_.as<TW>(), n, x0, n);
+    } else {
+      MPL_CUDA(cudaMemcpyAsync(x0, X0, sizeof(TW) * n * m,
+                               x0_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    }
+    std::vector<double> h;
+    Progress p1;
+    const TW* start = x0;
+    if (c_->policy == MPL_MP_SCHOL) {
+      // Algorithm 3 line 1: lower-precision LOBPCG from single(X0)
+      Timer t1(st);
+      x0l_.ensure(sizeof(TL) * n * m);
+      cast<TL, TW>(st, (int)n, m, x0, n, x0l_.as<TL>(), n);
+      PreFromFactor<TL, TL> pre1;
+      pre1.F = factor_low();
+      pre1.n = (int)n;
+      if (!stage1_) stage1_.reset(new Stage<TL, TL>((int)n, m));
+      p1 = stage1_->run(st, opl_, &pre1, x0l_.as<TL>(), k, 5e-6, c_->norm_est, maxit, true, true, false);
+      cast<TW, TL>(st, (int)n, m, stage1_->X(), n, x0, n);
+      c_->stats.t_stage1_ms = t1.stop();
+      h = p1.hist;
+    } else {
+      c_->stats.t_stage1_ms = 0.0;
+    }
+    Timer t2(st);
+    Progress p2;
+    TW* Xfin = nullptr;
+    const double* th = nullptr;
+    if (c_->policy == MPL_D_DCHOL) {
+      p2 = stage2<TW, TW>(factor_work(), start, maxit, false);
+      Xfin = stage_w<TW>().X();
+      th = stage_w<TW>().theta_host();
+    } else if (c_->policy == MPL_D_SCHOL) {
+      p2 = stage2<TL, TW>(factor_low(), start, maxit, false);
+      Xfin = stage_w<TW>().X();
+      th = stage_w<TW>().theta_host();
+    } else {
+      p2 = stage2<TL, TL>(factor_low(), start, maxit, true);
+      Xfin = stage_w<TL>().X();
+      th = stage_w<TL>().theta_host();
+    }
+    c_->stats.t_stage2_ms = t2.stop();
+    h.insert(h.end(), p2.hist.begin(), p2.hist.end());
+    c_->stats.iters_stage1 = p1.iters;
+    c_->stats.iters_stage2 = p2.iters;
+    c_->stats.qr_fallbacks = p1.qr_fallbacks + p2.qr_fallbacks;
+    c_->stats.explicit_checks = p2.explicit_checks;
+    c_->stats.max_rel_resid = p2.max_rel;
+    if (lambda) for (int j = 0; j < k; ++j) lambda[j] = th[j];
+    if (X) {
+      TW* src = Xfin;
+      if (c_->sparse && !c_->perm.empty()) {
+        tmpx_.ensure(sizeof(TW) * n * m);
+        permute_rows<TW>(st, (int)n, k, perm_dev_.as<long long>(), true, Xfin, n, tmpx_.as<TW>(), n);
+        src = tmpx_.as<TW>();
+      }
+      MPL_CUDA(cudaMemcpyAsync(X, src, sizeof(TW) * n * k, x_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    }
+    MPL_CUDA(cudaStreamSynchronize(st));
+    if (hist) for (int i = 0; i < (int)h.size() && i < hist_cap; ++i) hist[i] = h[i];
+    if (hist_len) *hist_len = (int)h.size();
+    if (iters) { iters[0] = p1.iters; iters[1] = p2.iters; }
+    check_launch("solve");
+    return p2.converged ? MPL_OK : MPL_ENOT_CONVERGED;
+  }
+
+  // ---- steps ----
+  Stage<TW, TW>& step_stage() { return stage_w<TW>(); }
+
+  void step_apply_A(const void* X, void* Y, int ncols, int lower) override {
+    const long long n = c_->n;
+    if (lower) {
+      if (!opl_) make_low_op();
+      opl_->apply(c_->stream, static_cast<const TL*>(X), n, static_cast<TL*>(Y), n, ncols);
+    } else {
+      opw_->apply(c_->stream, static_cast<const TW*>(X), n, static_cast<TW*>(Y), n, ncols);
+    }
+    sync("apply_A");
+  }
+  void step_residual(const void* AX, const void* X, const double* theta, int m, void* R,
+                     double* norms2) override {
+    const long long n = c_->n;
+    auto& s = step_stage();
+    s.prepare();
+    MPL_CUDA(cudaMemcpyAsync(s.vec() + 2 * c_->m, theta, sizeof(double) * m, cudaMemcpyHostToDevice, c_->stream));
+    DevMem part(sizeof(double) * (ceil_div(n, 2048) + 1) * 2 * m);
+    DevMem out(sizeof(double) * 2 * m);
+    residual<TW>(c_->stream, (int)n, m, static_cast<const TW*>(AX), n, static_cast<const TW*>(X), n,
+                 s.vec() + 2 * c_->m, static_cast<TW*>(R), n, part.as<double>(), out.as<double>());
+    MPL_CUDA(cudaMemcpyAsync(norms2, out.ptr(), sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, c_->stream));
+    sync("residual");
+  }
+  void step_precond(const void* R, void* W, int m, int scale) override {
+    if (!c_->factored) throw MplError{MPL_ESTATE, "preconditioner before mpl_factor", 0};
+    const long long n = c_->n;
+    DevMem nr;
+    const double* rn2 = nullptr;
+    if (scale) {
+      nr.alloc(sizeof(double) * m);
+      DevMem part(sizeof(double) * (ceil_div(n, 2048) + 1) * m);
+      col_norms2<TW>(c_->stream, (int)n, m, static_cast<const TW*>(R), n, part.as<double>(), nr.as<double>());
+      rn2 = nr.as<double>();
+      MPL_CUDA(cudaStreamSynchronize(c_->stream));
+    }
+    if (c_->policy == MPL_D_DCHOL) {
+      PreFromFactor<TW, TW> pre;
+      pre.F = factor_work();
+      pre.n = (int)n;
+      pre.apply(c_->stream, static_cast<const TW*>(R), n, rn2, static_cast<TW*>(W), n, m);
+      sync("precond");
+    } else {
+      PreFromFactor<TW, TL> pre;
+      pre.F = factor_low();
+      pre.n = (int)n;
+      pre.apply(c_->stream, static_cast<const TW*>(R), n, rn2, static_cast<TW*>(W), n, m);
+      sync("precond");
+    }
+  }
+  bool step_mixed_qr(void* W, int m, int lower) override {
+    bool ok;
+    if (lower) ok = stage_w<TL>().mixed_qr(c_->stream, static_cast<TW*>(W), m, true);
+    else ok = stage_w<TW>().mixed_qr(c_->stream, static_cast<TW*>(W), m, false);
+    sync("mixed_qr");
+    return ok;
+  }
+  void step_project(const void* B, int nb, void* W, int m) override {
+    auto& s = step_stage();
+    s.prepare();
+    s.project(c_->stream, static_cast<const TW*>(B), nb, static_cast<TW*>(W), m);
+    sync("project");
+  }
+  void step_small_eig(void* Ap, int N, int m, double* lam, void* C1) override {
+    auto& s = step_stage();
+    s.prepare();
+    eig_small<TW>(c_->stream, N, m, static_cast<TW*>(Ap), s.vec() + 2 * c_->m, static_cast<TW*>(C1),
+                  eig_ws(N, m));
+    MPL_CUDA(cudaMemcpyAsync(lam, s.vec() + 2 * c_->m, sizeof(double) * m, cudaMemcpyDeviceToHost, c_->stream));
+    sync("small_eig");
+  }
+  void step_rr(const void* S, const void* AS, int ncol, int m, double* lam, void* Ccoef) override {
+    auto& s = step_stage();
+    s.prepare();
+    s.rayleigh_ritz(c_->stream, static_cast<const TW*>(S), static_cast<const TW*>(AS), ncol, m, true);
+    MPL_CUDA(cudaMemcpyAsync(lam, s.vec() + 2 * c_->m, sizeof(double) * m, cudaMemcpyDeviceToHost, c_->stream));
+    MPL_CUDA(cudaMemcpyAsync(Ccoef, s.Ccoef(), sizeof(TW) * ncol * 2 * m, cudaMemcpyDeviceToDevice, c_->stream));
+    sync("rayleigh_ritz");
+  }
+  void get_factor_dense(void* L) override {
+    if (c_->sparse || !c_->factored) throw MplError{MPL_ESTATE, "no dense factor", 0};
+    const long long n = c_->n;
+    const size_t es = (c_->policy == MPL_D_DCHOL) ? sizeof(TW) : sizeof(TL);
+    MPL_CUDA(cudaMemcpyAsync(L, Lbuf_.ptr(), es * n * n, cudaMemcpyDeviceToDevice, c_->stream));
+    sync("get_factor");
+  }
+  void step_apply_L(const float* X, float* Y, int ncols) override;
+  void analyze() override;
+  SparseSymbolic* symbolic() override { return sym_.get(); }
+
+ private:
+  void sync(const char* where) {
+    check_launch(where);
+    MPL_CUDA(cudaStreamSynchronize(c_->stream));
+  }
+  void* eig_ws(int N, int m) {
+    eigws_.ensure(eig_ws_bytes(N, m, sizeof(TW)));
+    return eigws_.ptr();
+  }
+  void make_low_op();
+
+  mpl_ctx* c_;
+  DevMem Aw_, Al_, Lbuf_, Dbuf_, tmp_, info_, scr_mem_, X0_, x0l_, tmpx_, eigws_, perm_dev_;
+  DevMem rp_, ci_, vw_, vl_;
+  long long csr_nnz_ = 0;
+  Scratch scr_;
+  DenseOp<TW> dense_op_;
+  DenseOp<TL> dense_op_l_;
+  CsrOp<double> csr_op_;
+  CsrOp<float> csr_op_l_;
+  Op<TW>* opw_ = nullptr;
+  Op<TL>* opl_ = nullptr;
+  DenseFactorSolve<TL> fl_;
+  DenseFactorSolve<TW> fw_;
+  std::unique_ptr<SparseFactorSolve<float>> sparse_low_;
+  std::unique_ptr<SparseFactorSolve<double>> sparse_work_;
+  std::unique_ptr<SparseSymbolic> sym_;
+  std::unique_ptr<Stage<TL, TL>> stage1_;
+  std::unique_ptr<Stage<TW, TL>> stage_mp_;
+  std::unique_ptr<Stage<TW, TW>> stage_d_;
+  friend struct EngineAccess;
+};
+
+template <typename TW>
+template <typename TQ>
+Stage<TW, TQ>& Engine<TW>::stage_w() {
+  if constexpr (std::is_same<TQ, TW>::value) {
+    if (!stage_d_) stage_d_.reset(new Stage<TW, TW>((int)c_->n, c_->m));
+    return *stage_d_;
+  } else {
+    if (!stage_mp_) stage_mp_.reset(new Stage<TW, TL>((int)c_->n, c_->m));
+    return *stage_mp_;
+  }
+}
+
+template <typename TW>
+FactorSolve<TW>* Engine<TW>::factor_work() {
+  if constexpr (std::is_same<TW, double>::value) {
+    if (c_->sparse) return sparse_work_.get();
+  }
+  return &fw_;
+}
+
+template <typename TW>
+void Engine<TW>::make_low_op() {
+  const long long n = c_->n;
+  cudaStream_t st = c_->stream;
+  if (c_->sparse) {
+    if constexpr (std::is_same<TW, double>::value) {
+      vl_.alloc(sizeof(float) * csr_nnz_);
+      cast<float, double>(st, (int)csr_nnz_, 1, vw_.as<double>(), csr_nnz_, vl_.as<float>(), csr_nnz_);
+      csr_op_l_.rowptr = rp_.as<long long>();
+      csr_op_l_.colind = ci_.as<int>();
+      csr_op_l_.vals = vl_.as<float>();
+      csr_op_l_.n = (int)n;
+      opl_ = reinterpret_cast<Op<TL>*>(&csr_op_l_);
+    }
+  } else {
+    Al_.alloc(sizeof(TL) * n * n);
+    cast<TL, TW>(st, (int)n, (int)n, Aw_.as<TW>(), n, Al_.as<TL>(), n);
+    dense_op_l_.A = Al_.as<TL>();
+    dense_op_l_.lda = n;
+    dense_op_l_.n = (int)n;
+    dense_op_l_.scr = scr_;
+    opl_ = &dense_op_l_;
+  }
+}
+
+// Symbolic analysis only (no device state).
+struct HostSymEngine : EngineBase {
+  std::unique_ptr<SparseSymbolic> sym;
+  [[noreturn]] static void no() { throw MplError{MPL_ESTATE, "host-only symbolic handle", 0}; }
+  void factor() override { no(); }
+  mpl_status solve(const void*, int, int, double*, void*, int, double*, int, int*, int*) override { no(); }
+  void step_apply_A(const void*, void*, int, int) override { no(); }
+  void step_residual(const void*, const void*, const double*, int, void*, double*) override { no(); }
+  void step_precond(const void*, void*, int, int) override { no(); }
+  bool step_mixed_qr(void*, int, int) override { no(); }
+  void step_project(const void*, int, void*, int) override { no(); }
+  void step_small_eig(void*, int, int, double*, void*) override { no(); }
+  void step_rr(const void*, const void*, int, int, double*, void*) override { no(); }
+  void get_factor_dense(void*) override { no(); }
+  void step_apply_L(const float*, float*, int) override { no(); }
+  void analyze() override {}
+  SparseSymbolic* symbolic() override { return sym.get(); }
+};
+
+}  // namespace mpl
+
+#include "api_sparse.inl"
+
+// ------------------------------------------------------------------------
+// extern "C" entry points
+// ------------------------------------------------------------------------
+using mpl::MplError;
+
+template <typename F>
+static mpl_status guarded(mpl_ctx* c, F&& f) {
+  try {
+    mpl_status s = f();
+    if (c && s == MPL_OK) { c->err.clear(); c->info = 0; }
+    return s;
+  } catch (const MplError& e) {
+    if (c) { c->err = e.msg; c->info = e.info; }
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    if (c) c->err = "host allocation failed";
+    return MPL_ENOMEM;
+  } catch (...) {
+    if (c) c->err = "unexpected exception";
+    return MPL_ECUDA;
+  }
+}
+
+static bool valid_common(int k, int m, long long n, double tol, int policy) {
+  return n > 0 && k >= 1 && m >= k && 3LL * m <= n && tol > 0.0 && policy >= MPL_D_DCHOL &&
+         policy <= MPL_MP_SCHOL && m <= 1024;
+}
+
+extern "C" mpl_status mpl_create_dense(mpl_handle* h, int dtype, int64_t n, const void* A, int64_t lda,
+                                       int is_device, int k, int m, double tol, int policy,
+                                       const void* Omega, int m_omega, int omega_is_device, void* stream) {
+  if (!h) return MPL_EINVAL;
+  *h = nullptr;
+  if (!A || !Omega || m_omega < 1 || lda < n || (dtype != MPL_R64 && dtype != MPL_C128) ||
+      !valid_common(k, m, n, tol, policy) || n > (1LL << 31) - 1)
+    return MPL_EINVAL;
+  mpl_ctx* c = new (std::nothrow) mpl_ctx();
+  if (!c) return MPL_ENOMEM;
+  c->dtype = dtype; c->n = n; c->k = k; c->m = m; c->tol = tol; c->policy = policy;
+  c->stream = static_cast<cudaStream_t>(stream);
+  mpl_status s = guarded(c, [&]() {
+    auto t0 = std::chrono::steady_clock::now();
+    if (dtype == MPL_R64) {
+      auto* e = new mpl::Engine<double>(c);
+      c->eng.reset(e);
+      e->create_dense(A, lda, is_device, Omega, m_omega, omega_is_device);
+    } else {
+      auto* e = new mpl::Engine<mpl::zd>(c);
+      c->eng.reset(e);
+      e->create_dense(A, lda, is_device, Omega, m_omega, omega_is_device);
+    }
+    c->stats.t_create_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return MPL_OK;
+  });
+  if (s != MPL_OK) {
+    delete c;
+    return s;
+  }
+  *h = c;
+  return MPL_OK;
+}
+
+extern "C" mpl_status mpl_create_csr(mpl_handle* h, int64_t n, int64_t nnz, const int64_t* rowptr,
+                                     const int32_t* colind, const double* vals, int is_device,
+                                     const int32_t* grid_dims, int ndims, int k, int m, double tol,
+                                     int policy, const double* Omega, int m_omega, int omega_is_device,
+                                     void* stream) {
+  if (!h) return MPL_EINVAL;
+  *h = nullptr;
+  if (!rowptr || !colind || !vals || !Omega || m_omega < 1 || nnz < n || !valid_common(k, m, n, tol, policy) ||
+      n > (1LL << 31) - 1 || (grid_dims && ndims != 2 && ndims != 3))
+    return MPL_EINVAL;
+  mpl_ctx* c = new (std::nothrow) mpl_ctx();
+  if (!c) return MPL_ENOMEM;
+  c->dtype = MPL_R64; c->n = n; c->k = k; c->m = m; c->tol = tol; c->policy = policy;
+  c->sparse = true;
+  c->stream = static_cast<cudaStream_t>(stream);
+  mpl_status s = guarded(c, [&]() {
+    auto t0 = std::chrono::steady_clock::now();
+    auto* e = new mpl::Engine<double>(c);
+    c->eng.reset(e);
+    e->create_csr(reinterpret_cast<const long long*>(rowptr), colind, vals, nnz, is_device, grid_dims,
+                  grid_dims ? ndims : 0, Omega, m_omega, omega_is_device);
+    c->stats.t_create_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return MPL_OK;
+  });
+  if (s != MPL_OK) {
+    delete c;
+    return s;
+  }
+  *h = c;
+  return MPL_OK;
+}
+
+extern "C" mpl_status mpl_factor(mpl_handle h) {
+  if (!h) return MPL_EINVAL;
+  return guarded(h, [&]() { h->eng->factor(); return MPL_OK; });
+}
+
+extern "C" mpl_status mpl_solve(mpl_handle h, const void* X0, int x0_is_device, int maxit, double* lambda,
+                                void* X, int x_is_device, double* resid_hist, int hist_cap, int* hist_len,
+                                int* iters) {
+  if (!h || !X0 || maxit < 0 || (resid_hist && hist_cap < 0)) return MPL_EINVAL;
+  mpl_status s = guarded(h, [&]() {
+    return h->eng->solve(X0, x0_is_device, maxit, lambda, X, x_is_device, resid_hist, hist_cap, hist_len, iters);
+  });
+  if (s == MPL_ENOT_CONVERGED) h->err = "maximum number of iterations reached";
+  return s;
+}
+
+extern "C" mpl_status mpl_get_stats(mpl_handle h, mpl_stats* s) {
+  if (!h || !s) return MPL_EINVAL;
+  *s = h->stats;
+  return MPL_OK;
+}
+
+extern "C" const char* mpl_last_error(mpl_handle h) { return h ? h->err.c_str() : "null handle"; }
+extern "C" int64_t mpl_last_info(mpl_handle h) { return h ? h->info : 0; }
+
+extern "C" void mpl_destroy(mpl_handle h) {
+  if (!h) return;
+  if (!h->factored && !h->eng) {
+    delete h;
+    return;
+  }
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else if (dynamic_cast<mpl::HostSymEngine*>(h->eng.get()) == nullptr) cudaDeviceSynchronize();
+  delete h;
+}
+
+// ---- steps ----
+static bool width_ok(mpl_handle h, int w, int cap) { return h && w >= 1 && w <= cap; }
+
+extern "C" mpl_status mpl_step_apply_A(mpl_handle h, const void* X, void* Y, int ncols, int lower) {
+  if (!width_ok(h, ncols, h ? 3 * h->m : 0) || !X || !Y) return MPL_EINVAL;
+  return guarded(h, [&]() { h->eng->step_apply_A(X, Y, ncols, lower); return MPL_OK; });
+}
+extern "C" mpl_status mpl_step_residual(mpl_handle h, const void* AX, const void* X, const double* theta_host,
+                                        int m, void* R, double* norms2_host) {
+  if (!width_ok(h, m, h ? h->m : 0) || !AX || !X || !theta_host || !R || !norms2_host) return MPL_EINVAL;
+  return guarded(h, [&]() { h->eng->step_residual(AX, X, theta_host, m, R, norms2_host); return MPL_OK; });
+}
+extern "C" mpl_status mpl_step_precond(mpl_handle h, const void* R, void* W, int m, int scale) {
+  if (!width_ok(h, m, h ? h->m : 0) || !R || !W) return MPL_EINVAL;
+  return guarded(h, [&]() { h->eng->step_precond(R, W, m, scale); return MPL_OK; });
+}
+extern "C" mpl_status mpl_step_mixed_qr(mpl_handle h, void* W, int m, int lower_qr) {
+  if (!width_ok(h, m, h ? h->m : 0) || !W) return MPL_EINVAL;
+  return guarded(h, [&]() {
+    return h->eng->step_mixed_qr(W, m, lower_qr) ? MPL_OK : MPL_ERANK;
+  });
+}
+extern "C" mpl_status mpl_step_project(mpl_handle h, const void* B, int nb, void* W, int m) {
+  if (!width_ok(h, m, h ? h->m : 0) || !width_ok(h, nb, h ? 2 * h->m : 0) || !B || !W) return MPL_EINVAL;
+  return guarded(h, [&]() { h->eng->step_project(B, nb, W, m); return MPL_OK; });
+}
+extern "C" mpl_status mpl_step_small_eig(mpl_handle h, void* Ap, int N, int m, double* lam_host, void* C1) {
+  if (!width_ok(h, N, h ? 3 * h->m : 0) || m < 1 || m > N || m > h->m || !Ap || !lam_host || !C1) return MPL_EINVAL;
+  return guarded(h, [&]() { h->eng->step_small_eig(Ap, N, m, lam_host, C1); return MPL_OK; });
+}
+extern "C" mpl_status mpl_step_rayleigh_ritz(mpl_handle h, const void* S, const void* AS, int ncol, int m,
+                                             double* lam_host, void* Ccoef) {
+  if (!h || m < 1 || m > h->m || ncol < 2 * m || ncol > 3 * h->m || !S || !AS || !lam_host || !Ccoef)
+    return MPL_EINVAL;
+  return guarded(h, [&]() { h->eng->step_rr(S, AS, ncol, m, lam_host, Ccoef); return MPL_OK; });
+}
+extern "C" mpl_status mpl_get_factor_dense(mpl_handle h, void* L) {
+  if (!h || !L) return MPL_EINVAL;
+  return guarded(h, [&]() { h->eng->get_factor_dense(L); return MPL_OK; });
+}
+extern "C" mpl_status mpl_get_permutation(mpl_handle h, int64_t* perm) {
+  if (!h || !perm) return MPL_EINVAL;
+  for (long long i = 0; i < h->n; ++i) perm[i] = h->perm.empty() ? i : h->perm[i];
+  return MPL_OK;
+}
+extern "C" mpl_status mpl_step_apply_L(mpl_handle h, const float* X, float* Y, int ncols) {
+  if (!h || !h->sparse || !X || !Y || ncols < 1 || ncols > 3 * h->m) return MPL_EINVAL;
+  return guarded(h, [&]() { h->eng->step_apply_L(X, Y, ncols); return MPL_OK; });
+}
+extern "C" mpl_status mpl_analyze(mpl_handle h) {
+  if (!h || !h->sparse) return MPL_EINVAL;
+  return guarded(h, [&]() { h->eng->analyze(); return MPL_OK; });
+}
+extern "C" mpl_status mpl_get_symbolic_sizes(mpl_handle h, int64_t* nsuper, int64_t* nnzl, int64_t* nrows) {
+  if (!h || !h->sparse) return MPL_EINVAL;
+  return guarded(h, [&]() {
+    mpl::SparseSymbolic* s = h->eng->symbolic();
+    if (!s) throw MplError{MPL_ESTATE, "no symbolic analysis yet", 0};
+    if (nsuper) *nsuper = s->nsuper;
+    if (nnzl) *nnzl = s->nnz_L;
+    if (nrows) *nrows = (int64_t)s->sn_rows.size();
+    return MPL_OK;
+  });
+}
+extern "C" mpl_status mpl_get_symbolic(mpl_handle h, int64_t* parent, int64_t* colcount, int64_t* sn_start,
+                                       int64_t* sn_rowptr, int64_t* sn_rows, int64_t* sn_level) {
+  if (!h || !h->sparse) return MPL_EINVAL;
+  return guarded(h, [&]() {
+    mpl::SparseSymbolic* s = h->eng->symbolic();
+    if (!s) throw MplError{MPL_ESTATE, "no symbolic analysis yet", 0};
+    auto cp = [](int64_t* d, const std::vector<long long>& v) {
+      if (d) std::memcpy(d, v.data(), v.size() * sizeof(long long));
+    };
+    cp(parent, s->parent);
+    cp(colcount, s->colcount);
+    cp(sn_start, s->sn_start);
+    cp(sn_rowptr, s->sn_rowptr);
+    cp(sn_rows, s->sn_rows);
+    cp(sn_level, s->sn_level);
+    return MPL_OK;
+  });
+}
+
+extern "C" mpl_status mpl_analyze_host(mpl_handle* h, int64_t n, int64_t nnz, const int64_t* rowptr,
+                                       const int32_t* colind, const int32_t* grid_dims, int ndims) {
+  if (!h) return MPL_EINVAL;
+  *h = nullptr;
+  if (n <= 0 || nnz < 0 || !rowptr || !colind || (grid_dims && ndims != 2 && ndims != 3)) return MPL_EINVAL;
+  mpl_ctx* c = new (std::nothrow) mpl_ctx();
+  if (!c) return MPL_ENOMEM;
+  c->n = n;
+  c->sparse = true;
+  mpl_status s = guarded(c, [&]() {
+    if (rowptr[0] != 0 || rowptr[n] != nnz) throw MplError{MPL_EINVAL, "rowptr inconsistent with nnz", 0};
+    for (int64_t i = 0; i < n; ++i)
+      if (rowptr[i + 1] < rowptr[i]) throw MplError{MPL_EINVAL, "rowptr not monotone", i};
+    for (int64_t q = 0; q < nnz; ++q)
+      if (colind[q] < 0 || colind[q] >= n) throw MplError{MPL_EINVAL, "column index out of range", q};
+    auto* e = new mpl::HostSymEngine();
+    c->eng.reset(e);
+    e->sym.reset(new mpl::SparseSymbolic());
+    mpl::analyze_csr(n, reinterpret_cast<const long long*>(rowptr), colind, nullptr, grid_dims,
+                     grid_dims ? ndims : 0, *e->sym);
+    c->perm = e->sym->perm;
+    return MPL_OK;
+  });
+  if (s != MPL_OK) {
+    delete c;
+    return s;
+  }
+  *h = c;
+  return MPL_OK;
+}

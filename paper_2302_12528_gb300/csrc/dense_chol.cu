@@ -1,0 +1,234 @@
+// Dense lower-precision Cholesky factor and the multi-right-hand-side
+// triangular sweeps that apply T = L^-* L^-1 (Section 5.1: "solving two
+// triangular systems in single precision").
+//
+// Factor: blocked right-looking.  Per NB-column step k one CTA factors the
+// diagonal block in shared memory and also writes its inverse Dinv_k; the
+// panel L_ik = A_ik Dinv_k^* and the lower-triangular trailing update
+// A_ij -= L_ik L_jk^* are GEMMs.  Dinv is kept for the sweeps.
+//
+// Sweeps: one launch per block row.  Forward step k subtracts L_ik Y_k from
+// every block row i > k (all m right-hand sides at once, staged in shared
+// memory) and the CTA that owns row block k+1 finishes Y_{k+1} = Dinv_{k+1}
+// B_{k+1} in the same launch.  The backward sweep does the same with
+// (L_ki)^* and Dinv^*.
+#include "dense_chol.cuh"
+
+namespace mpl {
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(256)
+potrf_diag_kernel(int kb, T* A, long long lda, T* Dinv, int col0, int* info) {
+  using R = real_t<T>;
+  extern __shared__ unsigned char sm[];
+  constexpr int LD = NB + 1;
+  T* S = reinterpret_cast<T*>(sm);      // factor, [c * LD + r]
+  T* Si = S + NB * LD;                  // inverse
+  __shared__ R piv;
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    const int r = e % NB, c = e / NB;
+    S[c * LD + r] = (r < kb && c < kb && r >= c) ? A[r + (long long)c * lda] : zero_<T>();
+  }
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    if (tid == 0) {
+      R d = re_(S[j * LD + j]);
+      if (!(d > R(0)) || !isfinite((double)d)) {
+        if (bad == 0) bad = j + 1;
+        d = R(1);
+      }
+      d = (sizeof(R) == 8) ? (R)sqrt((double)d) : (R)sqrtf((float)d);
+      S[j * LD + j] = from_real<T>(d);
+      piv = R(1) / d;
+    }
+    __syncthreads();
+    const R rs = piv;
+    for (int i = j + 1 + tid; i < kb; i += blockDim.x) S[j * LD + i] = S[j * LD + i] * rs;
+    __syncthreads();
+    const int w = kb - j - 1;
+    for (int e = tid; e < w * w; e += blockDim.x) {
+      const int i = j + 1 + e % w, l = j + 1 + e / w;
+      if (i >= l) S[l * LD + i] = S[l * LD + i] - S[j * LD + i] * conj_(S[j * LD + l]);
+    }
+    __syncthreads();
+  }
+  // inverse of the lower-triangular block, one column per thread
+  for (int c = tid; c < NB; c += blockDim.x) {
+    for (int i = 0; i < NB; ++i) {
+      T s = zero_<T>();
+      if (c < kb && i >= c && i < kb) {
+        s = (i == c) ? from_real<T>(R(1)) : zero_<T>();
+        for (int l = c; l < i; ++l) s = s - S[l * LD + i] * Si[c * LD + l];
+        const R dii = re_(S[i * LD + i]);
+        s = s * (R(1) / dii);
+      }
+      Si[c * LD + i] = s;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    const int r = e % NB, c = e / NB;
+    if (r < kb && c < kb) A[r + (long long)c * lda] = (r >= c) ? S[c * LD + r] : zero_<T>();
+    Dinv[r + c * NB] = Si[c * LD + r];
+  }
+  if (tid == 0 && bad != 0) atomicCAS(info, 0, col0 + bad);
+}
+
+template <typename T>
+__global__ void copy_block_kernel(int rows, int cols, const T* __restrict__ S, long long lds,
+                                  T* __restrict__ D, long long ldd) {
+  const long long total = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e % rows), c = (int)(e / rows);
+    D[r + c * ldd] = S[r + c * lds];
+  }
+}
+
+template <typename T>
+void dense_cholesky(cudaStream_t st, DenseFactor<T>& F, T* tmp, int* info, Scratch scr) {
+  constexpr int NB = CholBlock<T>::NB;
+  const int n = F.n;
+  F.nb = NB;
+  F.nblk = ceil_div(n, NB);
+  const long long lda = F.ldl;
+  const size_t sm = 2 * (size_t)NB * (NB + 1) * sizeof(T);
+  cudaFuncSetAttribute(potrf_diag_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaMemsetAsync(info, 0, sizeof(int), st);
+  zero_upper<T>(st, n, F.L, lda);
+  for (int b = 0; b < F.nblk; ++b) {
+    const int k = b * NB;
+    const int kb = (n - k < NB) ? (n - k) : NB;
+    T* Akk = F.L + k + (long long)k * lda;
+    T* Db = F.Dinv + (size_t)b * NB * NB;
+    potrf_diag_kernel<T, NB><<<1, 256, sm, st>>>(kb, Akk, lda, Db, k, info);
+    const int rest = n - k - kb;
+    if (rest <= 0) continue;
+    T* Aik = F.L + (k + kb) + (long long)k * lda;
+    // panel: L_ik = A_ik Dinv^*  (out of place, then copied back)
+    gemm<T>(st, false, true, rest, kb, kb, real_t<T>(1), Aik, lda, Db, NB, real_t<T>(0), tmp, rest,
+            false, scr);
+    long long tot = (long long)rest * kb;
+    int blocks = (int)((tot + 255) / 256);
+    if (blocks > 8 * NUM_SMS) blocks = 8 * NUM_SMS;
+    copy_block_kernel<T><<<blocks, 256, 0, st>>>(rest, kb, tmp, rest, Aik, lda);
+    // trailing update, lower triangle only
+    T* Att = F.L + (k + kb) + (long long)(k + kb) * lda;
+    gemm<T>(st, false, true, rest, rest, kb, real_t<T>(-1), Aik, lda, Aik, lda, real_t<T>(1), Att,
+            lda, true, scr);
+  }
+}
+
+// ------------------------------------------------------------------------
+// triangular sweeps
+// ------------------------------------------------------------------------
+constexpr int SWEEP_CT = 32;  // right-hand sides per CTA
+
+template <typename T, int NB, bool BACK>
+__global__ void __launch_bounds__(256)
+trsm_step_kernel(int n, int nblk, int k, const T* __restrict__ L, long long ldl,
+                 const T* __restrict__ Dinv, T* B, long long ldb, int m, int only_diag) {
+  constexpr int CT = SWEEP_CT;
+  constexpr int LDS = NB + 1;
+  constexpr int CG = 256 / NB;
+  constexpr int CPT = CT / CG;
+  extern __shared__ unsigned char sm[];
+  T* Ls = reinterpret_cast<T*>(sm);  // Ls[kk * LDS + r]
+  T* Ys = Ls + NB * LDS;             // Ys[kk * CT + c]
+  const int tid = threadIdx.x;
+  int i;
+  if (only_diag) i = BACK ? nblk - 1 : 0;
+  else i = BACK ? (k - 1 - (int)blockIdx.x) : (k + 1 + (int)blockIdx.x);
+  const int ct0 = blockIdx.y * CT;
+  const int cw = min(CT, m - ct0);
+  const int r0 = i * NB, rb = min(NB, n - r0);
+  const int r = tid % NB, cg = tid / NB;
+
+  T acc[CPT];
+#pragma unroll
+  for (int q = 0; q < CPT; ++q) {
+    const int c = cg * CPT + q;
+    acc[q] = (r < rb && c < cw) ? B[(r0 + r) + (long long)(ct0 + c) * ldb] : zero_<T>();
+  }
+  if (!only_diag) {
+    const int rk0 = k * NB, kb = min(NB, n - rk0);
+    for (int e = tid; e < NB * CT; e += 256) {
+      const int kk = e % NB, c = e / NB;
+      Ys[kk * CT + c] = (kk < kb && c < cw) ? B[(rk0 + kk) + (long long)(ct0 + c) * ldb] : zero_<T>();
+    }
+    for (int e = tid; e < NB * NB; e += 256) {
+      const int a = e % NB, b = e / NB;
+      if (!BACK) {  // L_ik(r = a, kk = b)
+        Ls[b * LDS + a] = (a < rb && b < kb) ? L[(r0 + a) + (long long)(rk0 + b) * ldl] : zero_<T>();
+      } else {      // (L_ki)^*(r = b, kk = a) = conj(L_ki(a, b))
+        Ls[a * LDS + b] = (a < kb && b < rb) ? conj_(L[(rk0 + a) + (long long)(r0 + b) * ldl]) : zero_<T>();
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < NB; ++kk) {
+      const T a = Ls[kk * LDS + r];
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) acc[q] = acc[q] - a * Ys[kk * CT + cg * CPT + q];
+    }
+    __syncthreads();
+  }
+  const bool diag = only_diag || (BACK ? (i == k - 1) : (i == k + 1));
+  if (diag) {
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) Ys[r * CT + cg * CPT + q] = acc[q];
+    const T* Di = Dinv + (size_t)i * NB * NB;
+    for (int e = tid; e < NB * NB; e += 256) {
+      const int a = e % NB, b = e / NB;
+      if (!BACK) Ls[b * LDS + a] = Di[a + b * NB];           // Dinv(r = a, kk = b)
+      else Ls[a * LDS + b] = conj_(Di[a + b * NB]);          // Dinv^*(r = b, kk = a)
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) acc[q] = zero_<T>();
+#pragma unroll 4
+    for (int kk = 0; kk < NB; ++kk) {
+      const T a = Ls[kk * LDS + r];
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) fma_(acc[q], a, Ys[kk * CT + cg * CPT + q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < CPT; ++q) {
+    const int c = cg * CPT + q;
+    if (r < rb && c < cw) B[(r0 + r) + (long long)(ct0 + c) * ldb] = acc[q];
+  }
+}
+
+template <typename T>
+void dense_precond(cudaStream_t st, const DenseFactor<T>& F, T* B, long long ldb, int m) {
+  constexpr int NB = CholBlock<T>::NB;
+  const int nblk = F.nblk;
+  const int n = F.n;
+  const size_t sm = ((size_t)NB * (NB + 1) + (size_t)NB * SWEEP_CT) * sizeof(T);
+  cudaFuncSetAttribute(trsm_step_kernel<T, NB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(trsm_step_kernel<T, NB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const int cty = ceil_div(m, SWEEP_CT);
+  // forward: L Y = B
+  trsm_step_kernel<T, NB, false><<<dim3(1, cty), 256, sm, st>>>(n, nblk, -1, F.L, F.ldl, F.Dinv, B, ldb, m, 1);
+  for (int k = 0; k + 1 < nblk; ++k)
+    trsm_step_kernel<T, NB, false><<<dim3(nblk - 1 - k, cty), 256, sm, st>>>(n, nblk, k, F.L, F.ldl, F.Dinv, B, ldb, m, 0);
+  // backward: L^* Z = Y
+  trsm_step_kernel<T, NB, true><<<dim3(1, cty), 256, sm, st>>>(n, nblk, nblk, F.L, F.ldl, F.Dinv, B, ldb, m, 1);
+  for (int k = nblk - 1; k >= 1; --k)
+    trsm_step_kernel<T, NB, true><<<dim3(k, cty), 256, sm, st>>>(n, nblk, k, F.L, F.ldl, F.Dinv, B, ldb, m, 0);
+}
+
+#define MPL_INST_CHOL(T)                                                                      \
+  template void dense_cholesky<T>(cudaStream_t, DenseFactor<T>&, T*, int*, Scratch);         \
+  template void dense_precond<T>(cudaStream_t, const DenseFactor<T>&, T*, long long, int);
+MPL_INST_CHOL(float)
+MPL_INST_CHOL(double)
+MPL_INST_CHOL(zf)
+MPL_INST_CHOL(zd)
+#undef MPL_INST_CHOL
+
+}  // namespace mpl

@@ -1,0 +1,31 @@
+// Dense Cholesky factor and its two triangular sweeps (the preconditioner
+// T = Pi L^-* L^-1 Pi^* of Section 5.1 with Pi = I for dense A).
+#pragma once
+#include "blas.cuh"
+
+namespace mpl {
+
+template <typename T> struct CholBlock { static constexpr int NB = 64; };
+template <> struct CholBlock<float> { static constexpr int NB = 128; };
+
+// Factor storage: L (n x n, ld = ldl, lower; strict upper zeroed) and the
+// inverses of its NB x NB diagonal blocks (nblk blocks of NB x NB, ld NB).
+template <typename T>
+struct DenseFactor {
+  T* L = nullptr;
+  long long ldl = 0;
+  T* Dinv = nullptr;
+  int n = 0, nb = 0, nblk = 0;
+};
+
+// In-place blocked Cholesky of the lower triangle of F.L.  ``tmp`` holds
+// n * NB elements of T.  info (device int) = 0 or the 1-based global column
+// of the first pivot that is not positive.  Asynchronous on ``st``.
+template <typename T>
+void dense_cholesky(cudaStream_t st, DenseFactor<T>& F, T* tmp, int* info, Scratch scr);
+
+// B <- L^-* L^-1 B for B n x m (ld ldb), in place, two blocked sweeps.
+template <typename T>
+void dense_precond(cudaStream_t st, const DenseFactor<T>& F, T* B, long long ldb, int m);
+
+}  // namespace mpl

@@ -1,0 +1,59 @@
+// Sparse lower-precision Cholesky (Section 5.1: Pi^* A Pi = L L^* with a
+// fill-reducing permutation, the paper's CHOLMOD factor) for real SPD CSR
+// matrices: host ordering + symbolic analysis, GPU multifrontal supernodal
+// numeric factorisation and level-scheduled multi-RHS triangular solves.
+#pragma once
+#include <vector>
+
+#include "engine.cuh"
+
+namespace mpl {
+
+// Host symbolic structure of L for the permuted matrix B = Pi^* A Pi.
+struct SparseSymbolic {
+  long long n = 0, nsuper = 0, nnz_L = 0;
+  std::vector<long long> perm;       // perm[new] = old
+  std::vector<long long> parent;     // elimination tree (per column), -1 = root
+  std::vector<long long> colcount;   // |L(:, j)| including the diagonal
+  std::vector<long long> sn_start;   // nsuper + 1 first columns
+  std::vector<long long> sn_rowptr;  // nsuper + 1
+  std::vector<long long> sn_rows;    // per supernode: its columns, then struct below, ascending
+  std::vector<long long> sn_parent;  // supernodal tree
+  std::vector<long long> sn_level;   // 0 = leaf, 1 + max(child levels)
+  // permuted lower-triangular CSR of B (row j holds B(j, i) for i <= j)
+  std::vector<long long> b_rowptr;
+  std::vector<int> b_colind;
+  std::vector<double> b_vals;
+  // full permuted CSR (for the operator)
+  std::vector<long long> p_rowptr;
+  std::vector<int> p_colind;
+  std::vector<double> p_vals;
+};
+
+// Grid nested dissection (x fastest; see the reading in the docs):
+// perm[new] = old.
+std::vector<long long> nd_grid_order(const int* dims, int ndims, int leaf);
+
+// Ordering + symbolic analysis.  ``dims`` may be null (natural order).
+void analyze_csr(long long n, const long long* rowptr, const int* colind, const double* vals,
+                 const int* dims, int ndims, SparseSymbolic& S);
+
+// Numeric factor on the GPU.
+template <typename T>
+class SparseFactorSolve : public FactorSolve<T> {
+ public:
+  SparseFactorSolve(const SparseSymbolic& S, cudaStream_t st);
+  ~SparseFactorSolve() override;
+  // Factor (B + sigma I) from the permuted values (device, double, full CSR
+  // of B).  Returns 0 or the 1-based column of the first bad pivot.
+  int factorize(cudaStream_t st, double sigma);
+  void solve(cudaStream_t st, T* B, long long ldb, int m) override;
+  // Y = L X (for checks)
+  void apply_L(cudaStream_t st, const T* X, T* Y, int m);
+
+ private:
+  struct Impl;
+  Impl* p_;
+};
+
+}  // namespace mpl
