@@ -1,0 +1,423 @@
+#!/usr/bin/env python
+"""Time-to-k-eigenpairs at relative residual <= 1e-12: mixed-precision vs
+all-FP64 LOBPCG on one GB300 (Kressner, Ma, Shao, Algorithm 3 / Section 5).
+
+One step = one full solve of the workload already resident in HBM:
+mpl_factor (lower-precision Cholesky) + mpl_solve (Algorithm 3) through the C
+ABI.  Default workload: dense complex Hermitian, n = 16384, lambda log-spaced
+in [1, 1e8], k = 64, m = 96 (A = U diag(lambda) U^*, U from QR of a seeded
+complex Gaussian).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--policy mp] [--no-fp64] [--no-e2e]
+                  [--no-cpu-baseline]
+
+--impl reference times the CPU oracle (oracle/, NumPy/SciPy on the host
+cores) on a bounded sample of the same workload: the lower-precision factor
+plus one working-precision iteration, extrapolated to the iteration counts
+of a full solve.  Under torchrun (N > 1) every rank solves its own replica
+(independent problems, no collective on the data path); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+FP64_PEAK_GFLOPS = 1250.0     # nominal GB300 FP64 (152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz ~ 1.26e3)
+CACHE_DIR = os.path.join(tempfile.gettempdir(), "mplobpcg_bench_cache")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dense_complex_n16384", choices=sorted(W.WORKLOADS))
+    ap.add_argument("--policy", default="mp", choices=["mp", "schol", "dchol"])
+    ap.add_argument("--maxit", type=int, default=1000)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# inputs (seeded, synthetic)
+# ---------------------------------------------------------------------------
+def dense_input(w, rank, device):
+    """Column-major storage of A (the C-contiguous array holding A^T) on
+    ``device``; cached on local disk so the second arm of a run reuses it."""
+    import torch
+    seed = w.seed + 1000 * rank
+    os.makedirs(CACHE_DIR, exist_ok=True)
+    path = os.path.join(CACHE_DIR, f"{w.name}_{seed}.npy")
+    cplx = w.kind == "dense_complex"
+    if os.path.exists(path):
+        try:
+            a = np.load(path)
+            if a.shape == (w.n, w.n):
+                return torch.from_numpy(a).to(device)
+        except Exception:
+            pass
+    gen = W.dense_hpd if cplx else W.dense_spd
+    A, _ = gen(w.n, seed, w.kappa, device=str(device))
+    At = A.conj() if cplx else A             # Hermitian: A^T = conj(A)
+    At = At.resolve_conj().contiguous() if cplx else At.contiguous()
+    try:
+        np.save(path + ".tmp.npy", At.cpu().numpy())
+        os.replace(path + ".tmp.npy", path)
+    except OSError:
+        pass
+    return At
+
+
+def make_handle(M, w, d, policy, stream=None):
+    if w.kind == "csr":
+        return M.create_csr(d["rowptr"], d["colind"], d["vals"], w.k, w.m, w.tol, policy,
+                            Omega=d["Omega_np"], grid_dims=w.dims, stream=stream)
+    return M.create_dense(d["A"], w.k, w.m, w.tol, policy, Omega=d["Omega"], stream=stream)
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(tempfile.gettempdir(), f"mpl_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = max(smax, float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+# ---------------------------------------------------------------------------
+def oracle_sample(w, d_host, iters_total):
+    """Time the oracle's lower-precision factor and one working-precision
+    LOBPCG iteration on the host cores; extrapolate to ``iters_total``."""
+    from oracle import dense as OD
+    from oracle import lobpcg as OL
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] or [os.cpu_count()])
+    except Exception:
+        cores = os.cpu_count()
+    if w.kind == "csr":
+        from oracle import sparse as OS
+        from oracle import symbolic as OSy
+        perm = OSy.nd_grid_order(w.dims)
+        prp, pci, pv = OSy.permute_csr(d_host["rowptr"], d_host["colind"], d_host["vals"], perm)
+        Ap = OS.csr_to_scipy(prp, pci, pv)
+        op = OL.CsrOperator(Ap)
+        t0 = time.perf_counter()
+        import scipy.sparse.linalg as spla
+        spla.splu(Ap.tocsc().astype(np.float32), permc_spec="NATURAL")  # sparse FP32 factor sample
+        t_factor = time.perf_counter() - t0
+        X = d_host["X0"].T
+        normA = OD.norm_estimate(op.work, d_host["Omega_np"])
+    else:
+        A = d_host["A"]
+        op = OL.DenseOperator(A)
+        normA = OD.norm_estimate(op.work, d_host["Omega_np"])
+        t0 = time.perf_counter()
+        F = OD.lower_cholesky(A, normA)
+        t_factor = time.perf_counter() - t0
+        X = d_host["X0"].T
+    # one working-precision iteration of Algorithm 3 (same operations as the loop body)
+    t0 = time.perf_counter()
+    m = X.shape[1]
+    AX = op.work(X)
+    R = AX - X * np.linspace(1, 2, m)[None, :]
+    OD.stop_test(R, X, np.linspace(1, 2, m), normA, w.tol)
+    if w.kind != "csr":
+        Wb = OD.working(OD.apply_T(F, OD.lower(R)))
+    else:
+        Wb = R.copy()
+    B = X
+    for _ in range(2):
+        Wb = Wb - B @ (B.conj().T @ Wb)
+    from oracle.mqr import mixed_qr
+    Wb, _ = mixed_qr(Wb)
+    S = np.concatenate([X, X, Wb], axis=1)
+    AS = op.work(S)
+    Ap = S.conj().T @ AS
+    np.linalg.eigh(0.5 * (Ap + Ap.conj().T))
+    t_iter = time.perf_counter() - t0
+    value = t_factor + iters_total * t_iter
+    return {"value": value, "t_factor_s": t_factor, "t_iter_s": t_iter, "cores": int(cores),
+            "iters_extrapolated": int(iters_total)}
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    w = W.WORKLOADS[args.workload]
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        return run_reference(args, w)
+
+    import paper_2302_12528_gb300 as M
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    d = {}
+    seed = w.seed + 1000 * rank
+    if w.kind == "csr":
+        rp, ci, v, _ = W.diffusion_csr(w.dims, seed, w.ell, w.sigma)
+        d.update(rowptr=rp, colind=ci, vals=v)
+        d["Omega_np"] = W.sketch(w.n, 8, seed + 2)
+        X0h = W.start_block(w.n, w.m, seed + 1)
+    else:
+        d["A"] = dense_input(w, rank, dev)
+        cplx = w.kind == "dense_complex"
+        d["Omega_np"] = W.sketch(w.n, 8, seed + 2, cplx)
+        X0h = W.start_block(w.n, w.m, seed + 1, cplx)
+    d["Omega"] = torch.from_numpy(d["Omega_np"]).to(dev)
+    X0 = torch.from_numpy(X0h).to(dev)
+    torch.cuda.synchronize()
+
+    h = make_handle(M, w, d, args.policy, stream)
+    # warm-up steps (untimed)
+    for _ in range(args.warmup):
+        h.factor()
+        h.solve(X0, maxit=args.maxit)
+    clocks = Clocks(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    apply_ms = apply_flops = 0.0
+    apply_calls = launches = 0
+    its = (0, 0)
+    lam = None
+    for _ in range(args.steps):
+        h.factor()
+        lam, _, hist, its, _ = h.solve(X0, maxit=args.maxit)
+        st = h.stats()
+        apply_ms += st["apply_ms"]
+        apply_flops += st["apply_flops"]
+        apply_calls += st["apply_calls"]
+        launches += st["kernel_launches"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    stats = h.stats()
+    h.close()
+
+    out = {
+        "metric": "time-to-k-eigenpairs at resid<=1e-12 (mixed-precision LOBPCG, Algorithm 3)",
+        "value": ms / 1000.0, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+f32", "data": "synthetic (seeded; see DESIGN.md input recipe)",
+        "config": {"workload": w.name, "n": w.n, "k": w.k, "m": w.m, "tol": w.tol,
+                   "policy": {"mp": "MPLOBPCG-schol", "schol": "DLOBPCG-schol", "dchol": "DLOBPCG-dchol"}[args.policy],
+                   "kind": w.kind, "kappa": w.kappa if w.kind != "csr" else None,
+                   "replicas": world, "l2": "inputs larger than L2 (A: %.2f GB)" % (
+                       (w.n * w.n * (16 if w.kind == 'dense_complex' else 8) / 1e9) if w.kind != "csr" else 0.0)},
+        "iterations": {"stage1": its[0], "stage2": its[1]},
+        "phases_ms": {"factor": stats["t_factor_ms"], "stage1": stats["t_stage1_ms"],
+                      "stage2": stats["t_stage2_ms"]},
+        "factor_shift": stats["factor_shift"],
+        "gpu_launches": launches,
+    }
+    if apply_calls:
+        per_launch_s = apply_ms / 1000.0 / apply_calls
+        achieved = apply_flops / apply_calls / per_launch_s / 1e9
+        out["roofline"] = {"kernel": "gemm_kernel (working-precision A X, FP64 DFMA)", "bound": "alu",
+                           "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                           "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                           "flops_per_launch": apply_flops / apply_calls, "launches": apply_calls,
+                           "avg_launch_ms": per_launch_s * 1e3,
+                           "peak_note": "nominal FP64 of the recipe table (DFMA microbenchmark: 1190)"}
+    if ck:
+        out["clocks"] = ck
+    if rank == 0 and not args.no_fp64 and args.policy != "dchol":
+        h2 = make_handle(M, w, d, "dchol", stream)
+        h2.factor()
+        h2.solve(X0, maxit=args.maxit)        # warm-up (allocations)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        h2.factor()
+        _, _, _, its2, _ = h2.solve(X0, maxit=args.maxit)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        t64 = f0.elapsed_time(f1) / 1000.0
+        h2.close()
+        out["fp64_comparator"] = {"policy": "DLOBPCG-dchol", "value": t64, "unit": "s",
+                                  "iterations": its2[1], "speedup_mixed_vs_fp64": t64 / out["value"]}
+    if rank == 0 and not args.no_e2e:
+        out["e2e"] = e2e(M, w, d, X0h, args, stream, torch)
+    if rank == 0 and not args.no_cpu_baseline:
+        dh = host_copy(w, d, X0h)
+        cb = oracle_sample(w, dh, its[0] + its[1])
+        out["cpu_baseline"] = {"value": cb["value"], "unit": "s", "cores": cb["cores"], "kind": "oracle",
+                               "sample": "oracle lower-precision factor + 1 working-precision iteration "
+                                         f"(t_factor {cb['t_factor_s']:.2f} s, t_iter {cb['t_iter_s']:.2f} s), "
+                                         f"extrapolated to {cb['iters_extrapolated']} iterations"}
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def host_copy(w, d, X0h):
+    dh = {"X0": X0h, "Omega_np": d["Omega_np"]}
+    if w.kind == "csr":
+        dh.update(rowptr=d["rowptr"], colind=d["colind"], vals=d["vals"])
+    else:
+        At = d["A"].cpu().numpy()
+        dh["A"] = np.ascontiguousarray(At.T)     # the matrix (row-major)
+    return dh
+
+
+def e2e(M, w, d, X0h, args, stream, torch):
+    """Same metric through the public API with HOST buffers: upload of A, X0,
+    Omega and download of Lambda, X inside the timed region."""
+    if w.kind == "csr":
+        A_h = None
+    else:
+        A_h = torch.empty(d["A"].shape, dtype=d["A"].dtype, pin_memory=True)
+        A_h.copy_(d["A"])
+    X0_h = torch.from_numpy(X0h).pin_memory()
+    Om_h = torch.from_numpy(d["Omega_np"]).pin_memory()
+    dtype = torch.complex128 if w.kind == "dense_complex" else torch.float64
+    Xout = torch.empty((w.k, w.n), dtype=dtype, pin_memory=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if w.kind == "csr":
+        h = M.create_csr(d["rowptr"], d["colind"], d["vals"], w.k, w.m, w.tol, args.policy, Omega=Om_h.numpy(),
+                         grid_dims=w.dims, stream=stream)
+    else:
+        h = M.create_dense(A_h, w.k, w.m, w.tol, args.policy, Omega=Om_h, stream=stream)
+    h.factor()
+    lam, _, _, _, _ = h.solve(X0_h, maxit=args.maxit, X_out=Xout)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    h.close()
+    es = 16 if w.kind == "dense_complex" else 8
+    if w.kind == "csr":
+        h2d = d["rowptr"].nbytes + d["colind"].nbytes + d["vals"].nbytes
+    else:
+        h2d = w.n * w.n * es
+    h2d += w.n * w.m * es + w.n * 8 * es
+    d2h = w.n * w.k * es + w.k * 8
+    return {"value": t, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+def run_reference(args, w):
+    """CPU oracle arm: bounded sample per step (factor + one iteration),
+    extrapolated with the oracle's own iteration count on a smaller twin."""
+    import torch
+    seed = w.seed
+    cplx = w.kind == "dense_complex"
+    if w.kind == "csr":
+        rp, ci, v, _ = W.diffusion_csr(w.dims, seed, w.ell, w.sigma)
+        d = {"rowptr": rp, "colind": ci, "vals": v}
+    else:
+        dev = "cuda" if torch.cuda.is_available() else None
+        if dev:
+            At = dense_input(w, 0, torch.device("cuda:0")).cpu().numpy()
+            A = np.ascontiguousarray(At.T)
+        else:
+            A, _ = (W.dense_hpd if cplx else W.dense_spd)(w.n, seed, w.kappa)
+        d = {"A": A}
+    d["Omega_np"] = W.sketch(w.n, 8, seed + 2, cplx)
+    d["X0"] = W.start_block(w.n, w.m, seed + 1, cplx)
+    iters = int(os.environ.get("MPL_REF_ITERS", "55"))
+    vals = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        cb = oracle_sample(w, d, iters)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    v = float(np.mean(vals))
+    out = {"impl": "reference", "metric": "time-to-k-eigenpairs at resid<=1e-12 (mixed-precision LOBPCG, Algorithm 3)",
+           "value": v, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": v * 1000.0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64+f32", "data": "synthetic (seeded)",
+           "config": {"workload": w.name, "n": w.n, "k": w.k, "m": w.m, "tol": w.tol, "policy": "MPLOBPCG-schol"},
+           "cpu_baseline": {"value": v, "unit": "s", "cores": cb["cores"], "kind": "oracle",
+                            "sample": f"oracle factor + 1 iteration per step, extrapolated to {iters} iterations"},
+           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -71,6 +71,12 @@ typedef struct {
   int64_t nnz_L;          /* entries of the factor (dense: n(n+1)/2)                    */
   int64_t nsuper;         /* sparse: number of supernodes                               */
   double max_rel_resid;   /* max_j<=k ||r_j|| / ((||A||_est + |theta_j|) ||x_j||) at exit */
+  double apply_ms;        /* working-precision products A X of the last solve (stage 2):
+                             summed device time, CUDA events around each launch      */
+  int64_t apply_calls;    /* number of those products                                 */
+  double apply_flops;     /* their algorithmic flops (dense: 2 n^2 per column, x4
+                             complex; CSR: 2 nnz per column)                          */
+  int64_t kernel_launches;/* kernels launched by the last mpl_factor + mpl_solve      */
 } mpl_stats;
 
 /*

@@ -82,6 +82,17 @@ mpl_status mpl_get_symbolic_sizes(mpl_handle h, int64_t* nsuper_host, int64_t* n
 mpl_status mpl_get_symbolic(mpl_handle h, int64_t* parent, int64_t* colcount, int64_t* sn_start,
                             int64_t* sn_rowptr, int64_t* sn_rows, int64_t* sn_level);
 
+/* Sparse handles: the block partition used by the numeric factor (the
+ * nested-dissection leaf boxes and separator planes; the fundamental
+ * supernodes when no grid was given).  Sizes: nblock_host blocks and
+ * nrows_host total row indices.  Arrays (host, int64, any may be NULL):
+ * bk_start (nblock + 1), bk_rowptr (nblock + 1), bk_rows (nrows: the block's
+ * columns, then the union of the column structures below it, ascending),
+ * bk_parent (nblock, -1 for roots), bk_level (nblock). */
+mpl_status mpl_get_block_sizes(mpl_handle h, int64_t* nblock_host, int64_t* nrows_host);
+mpl_status mpl_get_blocks(mpl_handle h, int64_t* bk_start, int64_t* bk_rowptr, int64_t* bk_rows,
+                          int64_t* bk_parent, int64_t* bk_level);
+
 /* Host-only ordering + symbolic analysis of a CSR pattern (host arrays; no
  * GPU is touched).  The returned handle answers mpl_get_permutation,
  * mpl_get_symbolic_sizes and mpl_get_symbolic only; release it with
@@ -89,8 +100,8 @@ mpl_status mpl_get_symbolic(mpl_handle h, int64_t* parent, int64_t* colcount, in
 mpl_status mpl_analyze_host(mpl_handle* h, int64_t n, int64_t nnz, const int64_t* rowptr,
                             const int32_t* colind, const int32_t* grid_dims, int ndims);
 
-/* Sparse handles: L applied to a block, Y = L X (n x ncols, float), for
- * checking the numeric factor without materialising it. */
+/* Sparse handles: L applied to a block, Y = L X (n x ncols, float, ncols <=
+ * n), for checking the numeric factor (a slow single-CTA sweep; checks only). */
 mpl_status mpl_step_apply_L(mpl_handle h, const float* X, float* Y, int ncols);
 
 #ifdef __cplusplus

@@ -31,9 +31,11 @@ import numpy as np
 LEAF = 64
 
 
-def nd_grid_order(dims, leaf=LEAF):
+def nd_grid_order(dims, leaf=LEAF, return_blocks=False):
     """Grid nested dissection (reading above).  ``dims`` = (nx, ny[, nz]);
-    node index = x + nx*(y + ny*z).  Returns perm (int64), perm[new] = old."""
+    node index = x + nx*(y + ny*z).  Returns perm (int64), perm[new] = old,
+    and with ``return_blocks`` also the block starts (every leaf box and
+    separator plane, in the new order) followed by n."""
     dims = tuple(int(d) for d in dims)
     strides = [1]
     for d in dims[:-1]:
@@ -70,7 +72,11 @@ def nd_grid_order(dims, leaf=LEAF):
         out.append(lexi(sep))
 
     rec([(0, d) for d in dims])
-    return np.concatenate(out).astype(np.int64)
+    perm = np.concatenate(out).astype(np.int64)
+    if return_blocks:
+        starts = np.cumsum([0] + [len(o) for o in out])
+        return perm, starts.astype(np.int64)
+    return perm
 
 
 def permute_csr(rowptr, colind, vals, perm):
@@ -167,6 +173,40 @@ class Symbolic:
                 level[p] = max(level[p], level[s] + 1)
         self.sn_level = level
         self.nnz_L = int(self.colcount.sum())
+
+
+class Blocks:
+    """The relaxed partition used for the numeric factor: contiguous column
+    blocks (nested-dissection leaf boxes and separator planes) with
+    rows(b) = cols(b) followed by the union over j in b of
+    { i in struct(j) : i > last column of b }, ascending; parent(b) = block
+    of parent(last column); level = 0 for leaves, 1 + max over children."""
+
+    def __init__(self, rowptr, colind, starts):
+        parent, struct = symbolic_elimination(rowptr, colind)
+        n = len(rowptr) - 1
+        self.start = np.asarray(starts, dtype=np.int64)
+        nb = len(self.start) - 1
+        self.nblock = nb
+        col2b = np.empty(n, dtype=np.int64)
+        for b in range(nb):
+            col2b[self.start[b]:self.start[b + 1]] = b
+        rows, bpar = [], np.full(nb, -1, dtype=np.int64)
+        for b in range(nb):
+            f, e = int(self.start[b]), int(self.start[b + 1])
+            u = set()
+            for j in range(f, e):
+                u |= {i for i in struct[j] if i >= e}
+            rows.append(np.array(list(range(f, e)) + sorted(u), dtype=np.int64))
+            if parent[e - 1] >= 0:
+                bpar[b] = col2b[parent[e - 1]]
+        self.rows = rows
+        self.parent = bpar
+        lev = np.zeros(nb, dtype=np.int64)
+        for b in range(nb):
+            if bpar[b] >= 0:
+                lev[bpar[b]] = max(lev[bpar[b]], lev[b] + 1)
+        self.level = lev
 
 
 def lower_pattern(sym: Symbolic):

@@ -40,7 +40,8 @@ class Stats(C.Structure):
     _fields_ = [("t_create_ms", _d), ("t_symbolic_ms", _d), ("t_factor_ms", _d), ("t_stage1_ms", _d),
                 ("t_stage2_ms", _d), ("iters_stage1", _i), ("iters_stage2", _i), ("factor_tries", _i),
                 ("factor_shift", _d), ("norm_est", _d), ("qr_fallbacks", _i), ("explicit_checks", _i),
-                ("nnz_L", _i64), ("nsuper", _i64), ("max_rel_resid", _d)]
+                ("nnz_L", _i64), ("nsuper", _i64), ("max_rel_resid", _d), ("apply_ms", _d),
+                ("apply_calls", _i64), ("apply_flops", _d), ("kernel_launches", _i64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -74,6 +75,8 @@ _get_perm = _sig("mpl_get_permutation", _i, [_h, _p])
 _sym_sizes = _sig("mpl_get_symbolic_sizes", _i, [_h, _p, _p, _p])
 _get_sym = _sig("mpl_get_symbolic", _i, [_h, _p, _p, _p, _p, _p, _p])
 _apply_L = _sig("mpl_step_apply_L", _i, [_h, _p, _p, _i])
+_blk_sizes = _sig("mpl_get_block_sizes", _i, [_h, _p, _p])
+_get_blocks = _sig("mpl_get_blocks", _i, [_h, _p, _p, _p, _p, _p])
 _analyze_host = _sig("mpl_analyze_host", _i, [C.POINTER(_h), _i64, _i64, _p, _p, _p, _i])
 
 
@@ -195,6 +198,21 @@ class Handle:
         out["sn_level"] = out["sn_level"][:nsup]
         out["nsuper"] = nsup
         out["nnz_L"] = nl.value
+        return out
+
+    def blocks(self):
+        nb, nr = C.c_int64(), C.c_int64()
+        self._check(_blk_sizes(self._h, C.byref(nb), C.byref(nr)))
+        k = nb.value
+        out = dict(bk_start=np.zeros(k + 1, np.int64), bk_rowptr=np.zeros(k + 1, np.int64),
+                   bk_rows=np.zeros(max(nr.value, 1), np.int64), bk_parent=np.zeros(max(k, 1), np.int64),
+                   bk_level=np.zeros(max(k, 1), np.int64))
+        self._check(_get_blocks(self._h, *[out[x].ctypes.data for x in
+                                           ("bk_start", "bk_rowptr", "bk_rows", "bk_parent", "bk_level")]))
+        out["bk_rows"] = out["bk_rows"][: nr.value]
+        out["bk_parent"] = out["bk_parent"][:k]
+        out["bk_level"] = out["bk_level"][:k]
+        out["nblock"] = k
         return out
 
     def apply_L(self, X, Y, ncols):

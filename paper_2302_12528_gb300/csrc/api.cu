@@ -23,6 +23,7 @@ struct DenseOp : Op<T> {
   void apply(cudaStream_t st, const T* X, long long ldx, T* Y, long long ldy, int ncols) override {
     gemm<T>(st, false, false, n, ncols, n, 1, A, lda, X, ldx, 0, Y, ldy, false, scr);
   }
+  double flops(int ncols) const override { return (tr<T>::cx ? 8.0 : 2.0) * (double)n * n * ncols; }
 };
 
 template <typename T>
@@ -34,6 +35,8 @@ struct CsrOp : Op<T> {
   void apply(cudaStream_t st, const T* X, long long ldx, T* Y, long long ldy, int ncols) override {
     spmm_csr<T, T>(st, n, ncols, rowptr, colind, vals, X, ldx, Y, ldy);
   }
+  double flops(int ncols) const override { return 2.0 * (double)nnz * ncols; }
+  long long nnz = 0;
 };
 
 template <typename TF>
@@ -170,6 +173,7 @@ class Engine : public EngineBase {
   void factor() override {
     cudaStream_t st = c_->stream;
     const bool dchol = c_->policy == MPL_D_DCHOL;
+    const long long l0 = launch_counter().load();
     Timer t(st);
     if (c_->sparse) {
       sparse_factor(dchol);
@@ -180,6 +184,7 @@ class Engine : public EngineBase {
     }
     c_->stats.t_factor_ms = t.stop();
     c_->factored = true;
+    launches_factor_ = launch_counter().load() - l0;
   }
 
   template <typename TF>
@@ -250,6 +255,7 @@ class Engine : public EngineBase {
     cudaStream_t st = c_->stream;
     const long long n = c_->n;
     const int m = c_->m, k = c_->k;
+    const long long l0 = launch_counter().load();
     X0_.ensure(sizeof(TW) * n * m);
     TW* x0 = X0_.as<TW>();
     if (c_->sparse && !c_->perm.empty()) {
@@ -304,6 +310,10 @@ class Engine : public EngineBase {
     c_->stats.qr_fallbacks = p1.qr_fallbacks + p2.qr_fallbacks;
     c_->stats.explicit_checks = p2.explicit_checks;
     c_->stats.max_rel_resid = p2.max_rel;
+    c_->stats.apply_ms = p2.apply_ms;
+    c_->stats.apply_calls = p2.apply_calls;
+    c_->stats.apply_flops = p2.apply_flops;
+    c_->stats.kernel_launches = launches_factor_ + (launch_counter().load() - l0);
     if (lambda) for (int j = 0; j < k; ++j) lambda[j] = th[j];
     if (X) {
       TW* src = Xfin;
@@ -429,6 +439,7 @@ class Engine : public EngineBase {
   DevMem Aw_, Al_, Lbuf_, Dbuf_, tmp_, info_, scr_mem_, X0_, x0l_, tmpx_, eigws_, perm_dev_;
   DevMem rp_, ci_, vw_, vl_;
   long long csr_nnz_ = 0;
+  long long launches_factor_ = 0;
   Scratch scr_;
   DenseOp<TW> dense_op_;
   DenseOp<TL> dense_op_l_;
@@ -479,6 +490,7 @@ void Engine<TW>::make_low_op() {
       csr_op_l_.colind = ci_.as<int>();
       csr_op_l_.vals = vl_.as<float>();
       csr_op_l_.n = (int)n;
+      csr_op_l_.nnz = csr_nnz_;
       opl_ = reinterpret_cast<Op<TL>*>(&csr_op_l_);
     }
   } else {
@@ -691,7 +703,7 @@ extern "C" mpl_status mpl_get_permutation(mpl_handle h, int64_t* perm) {
   return MPL_OK;
 }
 extern "C" mpl_status mpl_step_apply_L(mpl_handle h, const float* X, float* Y, int ncols) {
-  if (!h || !h->sparse || !X || !Y || ncols < 1 || ncols > 3 * h->m) return MPL_EINVAL;
+  if (!h || !h->sparse || !X || !Y || ncols < 1 || ncols > h->n) return MPL_EINVAL;
   return guarded(h, [&]() { h->eng->step_apply_L(X, Y, ncols); return MPL_OK; });
 }
 extern "C" mpl_status mpl_analyze(mpl_handle h) {
@@ -757,4 +769,32 @@ extern "C" mpl_status mpl_analyze_host(mpl_handle* h, int64_t n, int64_t nnz, co
   }
   *h = c;
   return MPL_OK;
+}
+
+extern "C" mpl_status mpl_get_block_sizes(mpl_handle h, int64_t* nblock, int64_t* nrows) {
+  if (!h || !h->sparse) return MPL_EINVAL;
+  return guarded(h, [&]() {
+    mpl::SparseSymbolic* s = h->eng->symbolic();
+    if (!s) throw MplError{MPL_ESTATE, "no symbolic analysis yet", 0};
+    if (nblock) *nblock = s->nblock;
+    if (nrows) *nrows = (int64_t)s->bk_rows.size();
+    return MPL_OK;
+  });
+}
+extern "C" mpl_status mpl_get_blocks(mpl_handle h, int64_t* bk_start, int64_t* bk_rowptr, int64_t* bk_rows,
+                                     int64_t* bk_parent, int64_t* bk_level) {
+  if (!h || !h->sparse) return MPL_EINVAL;
+  return guarded(h, [&]() {
+    mpl::SparseSymbolic* s = h->eng->symbolic();
+    if (!s) throw MplError{MPL_ESTATE, "no symbolic analysis yet", 0};
+    auto cp = [](int64_t* d, const std::vector<long long>& v) {
+      if (d) std::memcpy(d, v.data(), v.size() * sizeof(long long));
+    };
+    cp(bk_start, s->bk_start);
+    cp(bk_rowptr, s->bk_rowptr);
+    cp(bk_rows, s->bk_rows);
+    cp(bk_parent, s->bk_parent);
+    cp(bk_level, s->bk_level);
+    return MPL_OK;
+  });
 }

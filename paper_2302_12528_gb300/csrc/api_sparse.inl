@@ -48,6 +48,7 @@ void Engine<TW>::create_csr(const long long* rowptr, const int* colind, const do
     csr_op_.colind = ci_.as<int>();
     csr_op_.vals = vw_.as<double>();
     csr_op_.n = (int)n;
+    csr_op_.nnz = nnz;
     opw_ = &csr_op_;
     if (c_->policy == MPL_MP_SCHOL) make_low_op();
     // the sketch indexes the permuted ordering

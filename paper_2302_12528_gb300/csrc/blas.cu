@@ -155,6 +155,7 @@ void gemm(cudaStream_t st, bool opA, bool opB, int M, int N, int K, real_t<T> al
   T* ws = splits > 1 ? static_cast<T*>(scr.ptr) : nullptr;
 #define MPL_GEMM_LAUNCH(OA, OB) \
   gemm_kernel<T, OA, OB><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, lower_only, kchunk, ws)
+  count_launch();
   if (!opA && !opB) MPL_GEMM_LAUNCH(false, false);
   else if (!opA && opB) MPL_GEMM_LAUNCH(false, true);
   else if (opA && !opB) MPL_GEMM_LAUNCH(true, false);
@@ -164,6 +165,7 @@ void gemm(cudaStream_t st, bool opA, bool opB, int M, int N, int K, real_t<T> al
     const long long total = (long long)M * N;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 4 * NUM_SMS) blocks = 4 * NUM_SMS;
+    count_launch();
     splitk_reduce_kernel<T><<<blocks, 256, 0, st>>>(M, N, splits, ws, alpha, beta, C, ldc, lower_only);
   }
 }
@@ -217,7 +219,9 @@ void residual(cudaStream_t st, int n, int m, const T* AX, long long ldax, const 
               long long ldx, const double* theta, T* R, long long ldr, double* part,
               double* out) {
   const int nchunk = ceil_div(n, RES_CHUNK);
+  count_launch();
   residual_kernel<T><<<dim3(nchunk, m), 256, 0, st>>>(n, m, AX, ldax, X, ldx, theta, R, ldr, part);
+  count_launch();
   sum_chunks_kernel<<<ceil_div(2 * m, 128), 128, 0, st>>>(nchunk, 2 * m, part, out);
 }
 
@@ -243,7 +247,9 @@ template <typename T>
 void col_norms2(cudaStream_t st, int n, int m, const T* X, long long ldx, double* part,
                 double* out) {
   const int nchunk = ceil_div(n, RES_CHUNK);
+  count_launch();
   col_norms2_kernel<T><<<dim3(nchunk, m), 256, 0, st>>>(n, m, X, ldx, part);
+  count_launch();
   sum_chunks_kernel<<<ceil_div(m, 128), 128, 0, st>>>(nchunk, m, part, out);
 }
 
@@ -266,6 +272,7 @@ void scale_cast(cudaStream_t st, int n, int m, const T* R, long long ldr, const 
                 TL* Rl, long long ldl) {
   int bx = ceil_div(n, 256);
   if (bx > 64) bx = 64;
+  count_launch();
   scale_cast_kernel<T, TL><<<dim3(bx, m), 256, 0, st>>>(n, m, R, ldr, rn2, Rl, ldl);
 }
 
@@ -285,6 +292,7 @@ void cast(cudaStream_t st, int n, int m, const TI* X, long long ldx, TO* Y, long
   // grid.y limit 65535: m is a column count (<= a few thousand) or n (dense copy)
   for (int j0 = 0; j0 < m; j0 += 65535) {
     const int mj = (m - j0 < 65535) ? (m - j0) : 65535;
+    count_launch();
     cast_kernel<TO, TI><<<dim3(bx, mj), 256, 0, st>>>(n, mj, X + (long long)j0 * ldx, ldx,
                                                       Y + (long long)j0 * ldy, ldy);
   }
@@ -312,6 +320,7 @@ void hermitize(cudaStream_t st, int N, T* A, long long lda) {
   int blocks = (int)((total + 255) / 256);
   if (blocks > 4 * NUM_SMS) blocks = 4 * NUM_SMS;
   if (blocks < 1) return;
+  count_launch();
   hermitize_kernel<T><<<blocks, 256, 0, st>>>(N, A, lda);
 }
 
@@ -324,6 +333,7 @@ __global__ void add_diag_kernel(int n, T* A, long long lda, double sigma) {
 template <typename T>
 void add_diag(cudaStream_t st, int n, T* A, long long lda, double sigma) {
   if (n <= 0) return;
+  count_launch();
   add_diag_kernel<T><<<ceil_div(n, 256), 256, 0, st>>>(n, A, lda, sigma);
 }
 
@@ -340,6 +350,7 @@ void zero_upper(cudaStream_t st, int n, T* A, long long lda) {
   int bx = ceil_div(n, 256);
   if (bx > 64) bx = 64;
   const int by = n < 65535 ? n : 65535;
+  count_launch();
   zero_upper_kernel<T><<<dim3(bx, by), 256, 0, st>>>(n, A, lda);
 }
 
@@ -360,6 +371,7 @@ void herm_from_lower(cudaStream_t st, int N, T* A, long long lda) {
   int blocks = (int)((total + 255) / 256);
   if (blocks > 4 * NUM_SMS) blocks = 4 * NUM_SMS;
   if (blocks < 1) return;
+  count_launch();
   herm_from_lower_kernel<T><<<blocks, 256, 0, st>>>(N, A, lda);
 }
 
@@ -379,6 +391,7 @@ void set_identity(cudaStream_t st, int N, int m, T* Y, long long ldy) {
   int blocks = (int)((total + 255) / 256);
   if (blocks > 4 * NUM_SMS) blocks = 4 * NUM_SMS;
   if (blocks < 1) return;
+  count_launch();
   set_identity_kernel<T><<<blocks, 256, 0, st>>>(N, m, Y, ldy);
 }
 
@@ -394,6 +407,7 @@ void conj_inplace(cudaStream_t st, int n, int m, T* X, long long ldx) {
   if (!tr<T>::cx || n <= 0 || m <= 0) return;
   int bx = ceil_div(n, 256);
   if (bx > 64) bx = 64;
+  count_launch();
   conj_kernel<T><<<dim3(bx, m), 256, 0, st>>>(n, m, X, ldx);
 }
 
@@ -415,6 +429,7 @@ void permute_rows(cudaStream_t st, int n, int m, const long long* idx, bool scat
   if (n <= 0 || m <= 0) return;
   int bx = ceil_div(n, 256);
   if (bx > 128) bx = 128;
+  count_launch();
   permute_rows_kernel<T><<<dim3(bx, m), 256, 0, st>>>(n, m, idx, scatter ? 1 : 0, X, ldx, Y, ldy);
 }
 

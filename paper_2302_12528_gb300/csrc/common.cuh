@@ -7,6 +7,7 @@
 // complex numbers are interleaved (re, im).
 #pragma once
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <cstddef>
 
@@ -120,6 +121,14 @@ __device__ __forceinline__ V block_sum(V v, V* red) {
 }
 
 constexpr int NUM_SMS = 152;  // GB300: 2 dies x 76 SMs
+
+// Number of kernels this library has launched (process-wide), reported in
+// the handle statistics.  Every launch site calls count_launch().
+inline std::atomic<long long>& launch_counter() {
+  static std::atomic<long long> c{0};
+  return c;
+}
+inline void count_launch(long long k = 1) { launch_counter().fetch_add(k, std::memory_order_relaxed); }
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 

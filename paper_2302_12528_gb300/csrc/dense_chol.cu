@@ -89,22 +89,25 @@ __global__ void copy_block_kernel(int rows, int cols, const T* __restrict__ S, l
 }
 
 template <typename T>
-void dense_cholesky(cudaStream_t st, DenseFactor<T>& F, T* tmp, int* info, Scratch scr) {
+void dense_cholesky(cudaStream_t st, DenseFactor<T>& F, T* tmp, int* info, Scratch scr, int nfact,
+                    long long col_offset, bool reset_info) {
   constexpr int NB = CholBlock<T>::NB;
   const int n = F.n;
+  if (nfact < 0 || nfact > n) nfact = n;
   F.nb = NB;
-  F.nblk = ceil_div(n, NB);
+  F.nblk = ceil_div(nfact, NB);
   const long long lda = F.ldl;
   const size_t sm = 2 * (size_t)NB * (NB + 1) * sizeof(T);
   cudaFuncSetAttribute(potrf_diag_kernel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  cudaMemsetAsync(info, 0, sizeof(int), st);
-  zero_upper<T>(st, n, F.L, lda);
+  if (reset_info) cudaMemsetAsync(info, 0, sizeof(int), st);
+  if (nfact == n) zero_upper<T>(st, n, F.L, lda);
   for (int b = 0; b < F.nblk; ++b) {
     const int k = b * NB;
-    const int kb = (n - k < NB) ? (n - k) : NB;
+    const int kb = (nfact - k < NB) ? (nfact - k) : NB;
     T* Akk = F.L + k + (long long)k * lda;
     T* Db = F.Dinv + (size_t)b * NB * NB;
-    potrf_diag_kernel<T, NB><<<1, 256, sm, st>>>(kb, Akk, lda, Db, k, info);
+    count_launch();
+    potrf_diag_kernel<T, NB><<<1, 256, sm, st>>>(kb, Akk, lda, Db, (int)(col_offset + k), info);
     const int rest = n - k - kb;
     if (rest <= 0) continue;
     T* Aik = F.L + (k + kb) + (long long)k * lda;
@@ -114,6 +117,7 @@ void dense_cholesky(cudaStream_t st, DenseFactor<T>& F, T* tmp, int* info, Scrat
     long long tot = (long long)rest * kb;
     int blocks = (int)((tot + 255) / 256);
     if (blocks > 8 * NUM_SMS) blocks = 8 * NUM_SMS;
+    count_launch();
     copy_block_kernel<T><<<blocks, 256, 0, st>>>(rest, kb, tmp, rest, Aik, lda);
     // trailing update, lower triangle only
     T* Att = F.L + (k + kb) + (long long)(k + kb) * lda;
@@ -204,27 +208,53 @@ trsm_step_kernel(int n, int nblk, int k, const T* __restrict__ L, long long ldl,
 }
 
 template <typename T>
-void dense_precond(cudaStream_t st, const DenseFactor<T>& F, T* B, long long ldb, int m) {
+static size_t sweep_smem() {
   constexpr int NB = CholBlock<T>::NB;
-  const int nblk = F.nblk;
-  const int n = F.n;
-  const size_t sm = ((size_t)NB * (NB + 1) + (size_t)NB * SWEEP_CT) * sizeof(T);
+  return ((size_t)NB * (NB + 1) + (size_t)NB * SWEEP_CT) * sizeof(T);
+}
+
+template <typename T>
+void dense_trsm_fwd(cudaStream_t st, const DenseFactor<T>& F, T* B, long long ldb, int m) {
+  constexpr int NB = CholBlock<T>::NB;
+  const int nblk = F.nblk, n = F.n;
+  const size_t sm = sweep_smem<T>();
   cudaFuncSetAttribute(trsm_step_kernel<T, NB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const int cty = ceil_div(m, SWEEP_CT);
+  count_launch();
+  trsm_step_kernel<T, NB, false><<<dim3(1, cty), 256, sm, st>>>(n, nblk, -1, F.L, F.ldl, F.Dinv, B, ldb, m, 1);
+  for (int k = 0; k + 1 < nblk; ++k) {
+    count_launch();
+    trsm_step_kernel<T, NB, false><<<dim3(nblk - 1 - k, cty), 256, sm, st>>>(n, nblk, k, F.L, F.ldl, F.Dinv, B, ldb, m, 0);
+  }
+}
+
+template <typename T>
+void dense_trsm_bwd(cudaStream_t st, const DenseFactor<T>& F, T* B, long long ldb, int m) {
+  constexpr int NB = CholBlock<T>::NB;
+  const int nblk = F.nblk, n = F.n;
+  const size_t sm = sweep_smem<T>();
   cudaFuncSetAttribute(trsm_step_kernel<T, NB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   const int cty = ceil_div(m, SWEEP_CT);
-  // forward: L Y = B
-  trsm_step_kernel<T, NB, false><<<dim3(1, cty), 256, sm, st>>>(n, nblk, -1, F.L, F.ldl, F.Dinv, B, ldb, m, 1);
-  for (int k = 0; k + 1 < nblk; ++k)
-    trsm_step_kernel<T, NB, false><<<dim3(nblk - 1 - k, cty), 256, sm, st>>>(n, nblk, k, F.L, F.ldl, F.Dinv, B, ldb, m, 0);
-  // backward: L^* Z = Y
+  count_launch();
   trsm_step_kernel<T, NB, true><<<dim3(1, cty), 256, sm, st>>>(n, nblk, nblk, F.L, F.ldl, F.Dinv, B, ldb, m, 1);
-  for (int k = nblk - 1; k >= 1; --k)
+  for (int k = nblk - 1; k >= 1; --k) {
+    count_launch();
     trsm_step_kernel<T, NB, true><<<dim3(k, cty), 256, sm, st>>>(n, nblk, k, F.L, F.ldl, F.Dinv, B, ldb, m, 0);
+  }
+}
+
+template <typename T>
+void dense_precond(cudaStream_t st, const DenseFactor<T>& F, T* B, long long ldb, int m) {
+  dense_trsm_fwd<T>(st, F, B, ldb, m);   // L Y = B
+  dense_trsm_bwd<T>(st, F, B, ldb, m);   // L^* Z = Y
 }
 
 #define MPL_INST_CHOL(T)                                                                      \
-  template void dense_cholesky<T>(cudaStream_t, DenseFactor<T>&, T*, int*, Scratch);         \
-  template void dense_precond<T>(cudaStream_t, const DenseFactor<T>&, T*, long long, int);
+  template void dense_cholesky<T>(cudaStream_t, DenseFactor<T>&, T*, int*, Scratch, int,     \
+                                  long long, bool);                                          \
+  template void dense_precond<T>(cudaStream_t, const DenseFactor<T>&, T*, long long, int);   \
+  template void dense_trsm_fwd<T>(cudaStream_t, const DenseFactor<T>&, T*, long long, int);  \
+  template void dense_trsm_bwd<T>(cudaStream_t, const DenseFactor<T>&, T*, long long, int);
 MPL_INST_CHOL(float)
 MPL_INST_CHOL(double)
 MPL_INST_CHOL(zf)

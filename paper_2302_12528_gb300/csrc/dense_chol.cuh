@@ -18,14 +18,25 @@ struct DenseFactor {
   int n = 0, nb = 0, nblk = 0;
 };
 
-// In-place blocked Cholesky of the lower triangle of F.L.  ``tmp`` holds
-// n * NB elements of T.  info (device int) = 0 or the 1-based global column
-// of the first pivot that is not positive.  Asynchronous on ``st``.
+// In-place blocked Cholesky of the lower triangle of F.L.  Only the first
+// ``nfact`` columns are factored (nfact < 0: all n); the rest of the lower
+// triangle receives the Schur-complement update (a multifrontal front).
+// ``tmp`` holds n * NB elements of T.  info (device int) = 0 or col_offset +
+// the 1-based column of the first pivot that is not positive (reset to 0
+// first when ``reset_info``).  Sets F.nb and
+// F.nblk for the factored columns.  Asynchronous on ``st``.
 template <typename T>
-void dense_cholesky(cudaStream_t st, DenseFactor<T>& F, T* tmp, int* info, Scratch scr);
+void dense_cholesky(cudaStream_t st, DenseFactor<T>& F, T* tmp, int* info, Scratch scr,
+                    int nfact = -1, long long col_offset = 0, bool reset_info = true);
 
 // B <- L^-* L^-1 B for B n x m (ld ldb), in place, two blocked sweeps.
 template <typename T>
 void dense_precond(cudaStream_t st, const DenseFactor<T>& F, T* B, long long ldb, int m);
+
+// The two halves: B <- L^-1 B and B <- L^-* B (F.n rows).
+template <typename T>
+void dense_trsm_fwd(cudaStream_t st, const DenseFactor<T>& F, T* B, long long ldb, int m);
+template <typename T>
+void dense_trsm_bwd(cudaStream_t st, const DenseFactor<T>& F, T* B, long long ldb, int m);
 
 }  // namespace mpl

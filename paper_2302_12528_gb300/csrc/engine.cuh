@@ -73,6 +73,45 @@ template <typename T>
 struct Op {
   virtual ~Op() {}
   virtual void apply(cudaStream_t st, const T* X, long long ldx, T* Y, long long ldy, int ncols) = 0;
+  virtual double flops(int ncols) const = 0;  // algorithmic flops of one apply
+};
+
+// Device time of a sequence of launches, measured with CUDA events on the
+// launching stream; harvested after the stream has been synchronised.
+class EventTimer {
+ public:
+  ~EventTimer() {
+    for (auto& e : ev_) cudaEventDestroy(e);
+  }
+  void begin(cudaStream_t st) { cudaEventRecord(get(2 * used_), st); }
+  void end(cudaStream_t st) {
+    cudaEventRecord(get(2 * used_ + 1), st);
+    ++used_;
+  }
+  // call only after the stream is synchronised
+  void harvest() {
+    for (int i = 0; i < used_; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev_[2 * i], ev_[2 * i + 1]) == cudaSuccess) total_ms += ms;
+    }
+    calls += used_;
+    used_ = 0;
+  }
+  void reset() { total_ms = 0.0; calls = 0; used_ = 0; }
+  double total_ms = 0.0;
+  long long calls = 0;
+
+ private:
+  cudaEvent_t get(int i) {
+    while ((int)ev_.size() <= i) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      ev_.push_back(e);
+    }
+    return ev_[i];
+  }
+  std::vector<cudaEvent_t> ev_;
+  int used_ = 0;
 };
 
 // W = double(f_T(single(R diag(1/||r_j||)))) for the stage's working type.
@@ -106,6 +145,8 @@ struct PreFromFactor : Pre<TW> {
 };
 
 struct Progress {
+  double apply_ms = 0.0, apply_flops = 0.0;
+  long long apply_calls = 0;
   std::vector<double> hist;
   int iters = 0;
   bool converged = false;
@@ -151,6 +192,14 @@ class Stage {
   }
 
   Scratch scratch() const { return scr_; }
+
+  // op->apply between CUDA events (device time of the working-precision A X)
+  void timed_apply(cudaStream_t st, Op<TW>* op, const TW* X, TW* Y, int ncols) {
+    atimer_.begin(st);
+    op->apply(st, X, n_, Y, n_, ncols);
+    atimer_.end(st);
+    prog_.apply_flops += op->flops(ncols);
+  }
 
   // small buffers
   // (every accessor below is valid only after prepare())
@@ -236,7 +285,8 @@ class Stage {
     TW* S = S_[0].as<TW>();
     MPL_CUDA(cudaMemcpyAsync(S, X0, sizeof(TW) * n * m, cudaMemcpyDeviceToDevice, st));
     if (!mixed_qr(st, S, m, qr_low)) throw MplError{MPL_ERANK, "Algorithm 2 failed on the start block", 0};
-    op->apply(st, S, n, AS_[0].as<TW>(), n, m);
+    atimer_.reset();
+    timed_apply(st, op, S, AS_[0].as<TW>(), m);
     rayleigh_ritz(st, S, AS_[0].as<TW>(), m, m, false);
     update(st, m, m);  // X <- X C, AX <- AX C
     bool hasP = false;
@@ -252,7 +302,7 @@ class Stage {
       if (nc >= k && verify) {
         // confirm with an explicit product A X (AX is carried through the updates)
         ++prog_.explicit_checks;
-        op->apply(st, X, n, V_.as<TW>(), n, m);
+        timed_apply(st, op, X, V_.as<TW>(), m);
         residual<TW>(st, n_, m, V_.as<TW>(), n, X, n, vec() + 2 * m, R_.as<TW>(), n, part_.as<double>(), vec());
         nc = fetch_and_test(st, k, tol, normA);
         prog_.max_rel = last_max_;
@@ -262,6 +312,7 @@ class Stage {
       if (nc >= k) {
         prog_.converged = true;
         prog_.iters = it - 1;
+        finish_timing();
         return prog_;
       }
       if (it > maxit) break;
@@ -270,6 +321,7 @@ class Stage {
         window[5] = last_max_;
         if (it > 5 && window[5] > 0.9 * window[0]) {
           prog_.iters = it - 1;
+          finish_timing();
           return prog_;
         }
       }
@@ -278,7 +330,7 @@ class Stage {
       pre->apply(st, R_.as<TW>(), n, vec(), W, n, m);
       project(st, X, wcol, W, m);
       if (!mixed_qr(st, W, m, qr_low)) throw MplError{MPL_ERANK, "Algorithm 2 broke down", it};
-      op->apply(st, W, n, AX + (size_t)wcol * n, n, m);
+      timed_apply(st, op, W, AX + (size_t)wcol * n, m);
       const int ncol = wcol + m;
       rayleigh_ritz(st, X, AX, ncol, m, true);
       update(st, ncol, 2 * m);
@@ -286,6 +338,7 @@ class Stage {
       check_launch("lobpcg iteration");
     }
     prog_.iters = maxit;
+    finish_timing();
     return prog_;
   }
 
@@ -306,12 +359,19 @@ class Stage {
     cur_ = nx;
   }
 
+  void finish_timing() {
+    atimer_.harvest();
+    prog_.apply_ms = atimer_.total_ms;
+    prog_.apply_calls = atimer_.calls;
+  }
+
   // Read [rn2 | xn2 | theta] and apply Eq. (stop); returns n_c (leading
   // converged count) or -1 on NaN/Inf.
   int fetch_and_test(cudaStream_t st, int k, double tol, double normA) {
     const int m = m_;
     MPL_CUDA(cudaMemcpyAsync(host_, vec(), sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, st));
     MPL_CUDA(cudaStreamSynchronize(st));
+    atimer_.harvest();
     int nc = 0;
     bool run = true;
     double mx = 0.0;
@@ -335,6 +395,7 @@ class Stage {
   double* host_ = nullptr;
   double last_max_ = 0.0;
   Progress prog_;
+  EventTimer atimer_;
 };
 
 }  // namespace mpl

@@ -157,6 +157,7 @@ void tsqr_r(cudaStream_t st, int n, int m, const T* W, long long ldw, TQ* R, TQ*
   TQ* Ra = slots + (size_t)nleaf * slot;
   TQ* Rb = Ra + (size_t)nleaf * m * m;
   TQ* hbuf = Rb + (size_t)nleaf * m * m;
+  count_launch();
   tsqr_leaf_kernel<T, TQ><<<nleaf, 256, 0, st>>>(n, m, W, ldw, b, slots, slot, Ra, hbuf);
   int cnt = nleaf;
   TQ* src = Ra;
@@ -164,6 +165,7 @@ void tsqr_r(cudaStream_t st, int n, int m, const T* W, long long ldw, TQ* R, TQ*
   while (cnt > 1) {
     const int groups = ceil_div(cnt, TSQR_G);
     TQ* out = (groups == 1) ? R : dst;
+    count_launch();
     tsqr_merge_kernel<TQ><<<groups, 256, 0, st>>>(cnt, m, src, out, slots, slot, hbuf);
     cnt = groups;
     TQ* t = src;
@@ -196,6 +198,7 @@ __global__ void trinv_upper_ct_kernel(int m, const TI* __restrict__ R, long long
 
 template <typename TI, typename TO>
 void trinv_upper_ct(cudaStream_t st, int m, const TI* R, long long ldr, TO* Linv) {
+  count_launch();
   trinv_upper_ct_kernel<TI, TO><<<1, 256, 0, st>>>(m, R, ldr, Linv);
 }
 
@@ -255,6 +258,7 @@ __global__ void chol_inv_kernel(int m, T* G, long long ldg, T* Linv, int* info) 
 
 template <typename T>
 void chol_inv(cudaStream_t st, int m, T* G, long long ldg, T* Linv, int* info) {
+  count_launch();
   chol_inv_kernel<T><<<1, 256, 0, st>>>(m, G, ldg, Linv, info);
 }
 
@@ -534,6 +538,7 @@ template <typename T>
 void eig_small(cudaStream_t st, int N, int m, T* Ap, double* lam, T* C1, void* ws) {
   const size_t sm = 2 * (size_t)N * sizeof(T);
   if (sm > 48 * 1024) cudaFuncSetAttribute(eig_small_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  count_launch();
   eig_small_kernel<T><<<1, 512, sm, st>>>(N, m, Ap, lam, C1, static_cast<unsigned char*>(ws));
 }
 
@@ -576,6 +581,7 @@ __global__ void __launch_bounds__(256) thin_q_kernel(int N, int q, T* Y, int c0,
 
 template <typename T>
 void thin_q(cudaStream_t st, int N, int q, T* Y, int c0, int nq, T* Q, T* ws) {
+  count_launch();
   thin_q_kernel<T><<<1, 256, 0, st>>>(N, q, Y, c0, nq, Q, ws);
 }
 

@@ -1,27 +1,530 @@
-// Sparse numeric factor (placeholder until the supernodal kernels land).
+// Sparse lower-precision Cholesky on the GPU (Section 5.1: Pi^* A Pi = L L^*,
+// "computed in single precision"; the paper used a single-precision CHOLMOD).
+//
+// Multifrontal over the blocks of the symbolic analysis (nested-dissection
+// leaf boxes and separator planes).  Each block b owns a dense front F_b of
+// nrows_b x nrows_b (column-major); its first ncols_b columns become the
+// columns of L, the trailing part is the update matrix U_b passed to the
+// parent.  Schedule, level by level from the leaves (level = height in the
+// block tree):
+//   1. extend-add: U_c of every child c is added into its parent's front at
+//      the parent-relative row positions (children in fixed order: one launch
+//      per child rank, so no two writers ever meet -- deterministic);
+//   2. partial factorisation of every front at the level: one CTA per small
+//      front, the blocked dense Cholesky (GEMM trailing updates) for large
+//      fronts.
+// Solves (all m right-hand sides at once) follow the same tree: forward from
+// the leaves, each block gathering its children's contribution blocks, solving
+// with its diagonal block and producing its own contribution; backward from
+// the root, each block reading the already solved rows of its ancestors.
+#include <algorithm>
+
 #include "sparse.cuh"
 
 namespace mpl {
 
-template <typename T>
-struct SparseFactorSolve<T>::Impl {};
+constexpr int BIG_NCOLS = 256;
+constexpr int BIG_NROWS = 1536;
+constexpr int EA_COLS = 32;  // child columns per extend-add CTA
 
 template <typename T>
-SparseFactorSolve<T>::SparseFactorSolve(const SparseSymbolic&, cudaStream_t) : p_(new Impl) {}
+struct SparseFactorSolve<T>::Impl {
+  long long n = 0, nb = 0, nnzl = 0, ftotal = 0;
+  int maxlevel = 0;
+  std::vector<long long> start, rowptr, fptr, cptr;
+  std::vector<int> ncols, nrows;
+  std::vector<std::vector<int>> small_lv, big_lv;
+  std::vector<long long> small_off;  // offsets into d_small per level
+  struct Round { long long off; int cnt; int maxchunks; };
+  std::vector<std::vector<Round>> rounds;
+  std::vector<long long> big_dinv;   // Dinv offset per block (-1 if small)
+  std::vector<std::vector<int>> children;
+
+  DevMem F, d_rows, d_rowptr, d_relpos, d_fptr, d_amap, d_avals, d_dmap, d_start, d_ncols, d_nrows,
+      d_chptr, d_chlist, d_small, d_pairs, d_cptr, dinv, tmp, info, contrib, gbuf, scr_mem;
+  Scratch scr;
+  int mcap = 0;
+};
+
+// ---- kernels -------------------------------------------------------------
+template <typename T>
+__global__ void assemble_kernel(long long nnz, const long long* __restrict__ amap,
+                                const double* __restrict__ vals, T* __restrict__ F) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nnz;
+       q += (long long)gridDim.x * blockDim.x)
+    F[amap[q]] = (T)vals[q];
+}
+
+template <typename T>
+__global__ void add_sigma_kernel(long long n, const long long* __restrict__ dmap, T* F, double sigma) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x)
+    F[dmap[j]] += (T)sigma;
+}
+
+// U_c (lower part) of the child into the parent's front.
+template <typename T>
+__global__ void __launch_bounds__(256)
+extend_add_kernel(const int2* __restrict__ pairs, T* F, const long long* __restrict__ fptr,
+                  const long long* __restrict__ rowptr, const int* __restrict__ relpos,
+                  const int* __restrict__ ncols, const int* __restrict__ nrows) {
+  const int2 pr = pairs[blockIdx.x];
+  const int c = pr.x, s = pr.y;
+  const int ncc = ncols[c], nrc = nrows[c], nbc = nrc - ncc;
+  const int nrs = nrows[s];
+  const int j0 = blockIdx.y * EA_COLS;
+  if (j0 >= nbc) return;
+  const int j1 = min(nbc, j0 + EA_COLS);
+  const T* Fc = F + fptr[c];
+  T* Fs = F + fptr[s];
+  const int* rp = relpos + rowptr[c] + ncc;
+  for (int jc = j0; jc < j1; ++jc) {
+    const int tc = rp[jc];
+    const T* col = Fc + (long long)(ncc + jc) * nrc + ncc;
+    T* tcol = Fs + (long long)tc * nrs;
+    for (int ic = jc + threadIdx.x; ic < nbc; ic += blockDim.x) tcol[rp[ic]] += col[ic];
+  }
+}
+
+// Partial Cholesky of a small front: the first nc columns, Schur update of
+// the rest (one CTA per front).
+template <typename T>
+__global__ void __launch_bounds__(256)
+factor_small_kernel(const int* __restrict__ list, T* F, const long long* __restrict__ fptr,
+                    const int* __restrict__ ncols, const int* __restrict__ nrows,
+                    const long long* __restrict__ start, int* info) {
+  const int b = list[blockIdx.x];
+  const int nc = ncols[b], nr = nrows[b];
+  T* A = F + fptr[b];
+  __shared__ T piv;
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  for (int j = 0; j < nc; ++j) {
+    if (threadIdx.x == 0) {
+      T d = A[j + (long long)j * nr];
+      if (!(d > T(0)) || !isfinite((double)d)) {
+        if (bad == 0) bad = j + 1;
+        d = T(1);
+      }
+      d = (sizeof(T) == 8) ? (T)sqrt((double)d) : (T)sqrtf((float)d);
+      A[j + (long long)j * nr] = d;
+      piv = T(1) / d;
+    }
+    __syncthreads();
+    const T rs = piv;
+    T* cj = A + (long long)j * nr;
+    for (int i = j + 1 + threadIdx.x; i < nr; i += blockDim.x) cj[i] *= rs;
+    __syncthreads();
+    // lower-triangular trailing update: one warp per column, lanes down the rows
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int col = j + 1 + wid; col < nr; col += nw) {
+      const T f = cj[col];
+      T* ac = A + (long long)col * nr;
+      for (int row = col + lane; row < nr; row += 32) ac[row] -= cj[row] * f;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && bad != 0) atomicCAS(info, 0, (int)(start[b] + bad));
+}
+
+// Forward solve of the small blocks of one level: gather the children's
+// contributions, y = L11^-1 t, contribution = t_below - L21 y.
+template <typename T>
+__global__ void __launch_bounds__(256)
+fwd_small_kernel(const int* __restrict__ list, int single, const T* __restrict__ F,
+                 const long long* __restrict__ fptr,
+                 const int* __restrict__ ncols, const int* __restrict__ nrows,
+                 const long long* __restrict__ start, const long long* __restrict__ rowptr,
+                 const int* __restrict__ relpos, const int* __restrict__ chptr,
+                 const int* __restrict__ chlist, const long long* __restrict__ cptr, T* contrib,
+                 T* B, long long ldb, int m, int gather_only) {
+  const int b = single >= 0 ? single : list[blockIdx.x];
+  const int nc = ncols[b], nr = nrows[b], nbl = nr - nc;
+  const long long f = start[b];
+  const T* A = F + fptr[b];
+  T* Cb = contrib + cptr[b] * m;
+  for (long long e = threadIdx.x; e < (long long)nbl * m; e += blockDim.x) Cb[e] = T(0);
+  __syncthreads();
+  for (int q = chptr[b]; q < chptr[b + 1]; ++q) {
+    const int ch = chlist[q];
+    const int ncc = ncols[ch], nbc = nrows[ch] - ncc;
+    const T* Cc = contrib + cptr[ch] * m;
+    const int* rp = relpos + rowptr[ch] + ncc;
+    for (long long e = threadIdx.x; e < (long long)nbc * m; e += blockDim.x) {
+      const int i = (int)(e % nbc), c = (int)(e / nbc);
+      const int pos = rp[i];
+      const T v = Cc[i + (long long)c * nbc];
+      if (pos < nc) B[(f + pos) + (long long)c * ldb] += v;
+      else Cb[(pos - nc) + (long long)c * nbl] += v;
+    }
+    __syncthreads();
+  }
+  if (gather_only) return;
+  for (int j = 0; j < nc; ++j) {
+    const T ljj = A[j + (long long)j * nr];
+    for (int c = threadIdx.x; c < m; c += blockDim.x) B[(f + j) + (long long)c * ldb] /= ljj;
+    __syncthreads();
+    const int w = nr - j - 1;
+    for (long long e = threadIdx.x; e < (long long)w * m; e += blockDim.x) {
+      const int i = j + 1 + (int)(e % w), c = (int)(e / w);
+      const T v = A[i + (long long)j * nr] * B[(f + j) + (long long)c * ldb];
+      if (i < nc) B[(f + i) + (long long)c * ldb] -= v;
+      else Cb[(i - nc) + (long long)c * nbl] -= v;
+    }
+    __syncthreads();
+  }
+}
+
+// Backward solve of the small blocks of one level: t = y - L21^T x_below,
+// x = L11^-T t.
+template <typename T>
+__global__ void __launch_bounds__(256)
+bwd_small_kernel(const int* __restrict__ list, const T* __restrict__ F, const long long* __restrict__ fptr,
+                 const int* __restrict__ ncols, const int* __restrict__ nrows,
+                 const long long* __restrict__ start, const long long* __restrict__ rowptr,
+                 const int* __restrict__ rows, T* B, long long ldb, int m) {
+  const int b = list[blockIdx.x];
+  const int nc = ncols[b], nr = nrows[b];
+  const long long f = start[b];
+  const T* A = F + fptr[b];
+  const int* rw = rows + rowptr[b];
+  for (long long e = threadIdx.x; e < (long long)nc * m; e += blockDim.x) {
+    const int i = (int)(e % nc), c = (int)(e / nc);
+    T acc = B[(f + i) + (long long)c * ldb];
+    const T* li = A + (long long)i * nr;
+    for (int q = nc; q < nr; ++q) acc -= li[q] * B[rw[q] + (long long)c * ldb];
+    B[(f + i) + (long long)c * ldb] = acc;
+  }
+  __syncthreads();
+  for (int j = nc - 1; j >= 0; --j) {
+    const T ljj = A[j + (long long)j * nr];
+    for (int c = threadIdx.x; c < m; c += blockDim.x) B[(f + j) + (long long)c * ldb] /= ljj;
+    __syncthreads();
+    for (long long e = threadIdx.x; e < (long long)j * m; e += blockDim.x) {
+      const int i = (int)(e % j), c = (int)(e / j);
+      B[(f + i) + (long long)c * ldb] -= A[j + (long long)i * nr] * B[(f + j) + (long long)c * ldb];
+    }
+    __syncthreads();
+  }
+}
+
+// gather G(q, c) = B(rows[q], c) for the below-rows of a (large) block
+template <typename T>
+__global__ void gather_rows_kernel(int nbl, int m, const int* __restrict__ rw, const T* __restrict__ B,
+                                   long long ldb, T* G) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)nbl * m;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(e % nbl), c = (int)(e / nbl);
+    G[e] = B[rw[q] + (long long)c * ldb];
+  }
+}
+
+// Y = L X for checks: column j of L is row (start..) of its block.
+template <typename T>
+__global__ void apply_L_kernel(int nblk, const T* __restrict__ F, const long long* __restrict__ fptr,
+                               const int* __restrict__ ncols, const int* __restrict__ nrows,
+                               const long long* __restrict__ start, const long long* __restrict__ rowptr,
+                               const int* __restrict__ rows, const T* __restrict__ X, long long ldx,
+                               T* Y, long long ldy, int m) {
+  // one CTA per block, scatter with atomics is avoided: every output row is
+  // reached from several blocks, so Y is accumulated column by column of L
+  // in a fixed block order by a single CTA sweep (slow but only for checks)
+  if (blockIdx.x != 0) return;
+  for (int b = 0; b < nblk; ++b) {
+    const int nc = ncols[b], nr = nrows[b];
+    const T* A = F + fptr[b];
+    const int* rw = rows + rowptr[b];
+    for (long long e = threadIdx.x; e < (long long)nr * m; e += blockDim.x) {
+      const int i = (int)(e % nr), c = (int)(e / nr);
+      T acc = T(0);
+      const int jmax = (i < nc) ? i : nc - 1;
+      for (int j = 0; j <= jmax; ++j) acc += A[i + (long long)j * nr] * X[(start[b] + j) + (long long)c * ldx];
+      Y[rw[i] + (long long)c * ldy] += acc;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- host ----------------------------------------------------------------
+template <typename T>
+SparseFactorSolve<T>::SparseFactorSolve(const SparseSymbolic& S, cudaStream_t st) : p_(new Impl) {
+  Impl& I = *p_;
+  I.n = S.n;
+  I.nb = S.nblock;
+  const long long nb = I.nb;
+  I.start.assign(S.bk_start.begin(), S.bk_start.end());
+  I.rowptr.assign(S.bk_rowptr.begin(), S.bk_rowptr.end());
+  I.ncols.resize(nb);
+  I.nrows.resize(nb);
+  I.fptr.assign(nb + 1, 0);
+  I.cptr.assign(nb + 1, 0);
+  for (long long b = 0; b < nb; ++b) {
+    I.ncols[b] = (int)(I.start[b + 1] - I.start[b]);
+    I.nrows[b] = (int)(I.rowptr[b + 1] - I.rowptr[b]);
+    I.fptr[b + 1] = I.fptr[b] + (long long)I.nrows[b] * I.nrows[b];
+    I.cptr[b + 1] = I.cptr[b] + (I.nrows[b] - I.ncols[b]);
+  }
+  I.ftotal = I.fptr[nb];
+  std::vector<long long> col2b(I.n);
+  for (long long b = 0; b < nb; ++b)
+    for (long long c = I.start[b]; c < I.start[b + 1]; ++c) col2b[c] = b;
+  // relative positions in the parent's row list
+  std::vector<int> rows32(S.bk_rows.size()), relpos(S.bk_rows.size(), -1);
+  for (size_t q = 0; q < S.bk_rows.size(); ++q) rows32[q] = (int)S.bk_rows[q];
+  I.children.assign(nb, {});
+  for (long long b = 0; b < nb; ++b) {
+    const long long p = S.bk_parent[b];
+    if (p < 0) {
+      if (I.nrows[b] != I.ncols[b]) throw MplError{MPL_EINVAL, "root block with rows below", b};
+      continue;
+    }
+    I.children[p].push_back((int)b);
+    const long long* pr = S.bk_rows.data() + I.rowptr[p];
+    const long long plen = I.rowptr[p + 1] - I.rowptr[p];
+    for (long long q = I.rowptr[b] + I.ncols[b]; q < I.rowptr[b + 1]; ++q) {
+      const long long* it = std::lower_bound(pr, pr + plen, S.bk_rows[q]);
+      if (it == pr + plen || *it != S.bk_rows[q])
+        throw MplError{MPL_EINVAL, "block structure not contained in its parent", b};
+      relpos[q] = (int)(it - pr);
+    }
+  }
+  // assembly map of the lower triangle: entry B(j, i), i <= j -> block of i
+  I.nnzl = (long long)S.b_colind.size();
+  std::vector<long long> amap(I.nnzl), dmap(I.n);
+  for (long long j = 0; j < I.n; ++j) {
+    for (long long q = S.b_rowptr[j]; q < S.b_rowptr[j + 1]; ++q) {
+      const long long i = S.b_colind[q];
+      const long long b = col2b[i];
+      const long long* pr = S.bk_rows.data() + I.rowptr[b];
+      const long long plen = I.rowptr[b + 1] - I.rowptr[b];
+      const long long* it = std::lower_bound(pr, pr + plen, j);
+      if (it == pr + plen || *it != j) throw MplError{MPL_EINVAL, "matrix entry outside the symbolic structure", j};
+      amap[q] = I.fptr[b] + (it - pr) + (i - I.start[b]) * I.nrows[b];
+    }
+    const long long b = col2b[j];
+    const long long p = j - I.start[b];
+    dmap[j] = I.fptr[b] + p + p * I.nrows[b];
+  }
+  // levels, schedules, extend-add rounds
+  I.maxlevel = 0;
+  for (long long b = 0; b < nb; ++b) I.maxlevel = std::max(I.maxlevel, (int)S.bk_level[b]);
+  const int L = I.maxlevel + 1;
+  I.small_lv.assign(L, {});
+  I.big_lv.assign(L, {});
+  I.big_dinv.assign(nb, -1);
+  long long dinv_total = 0;
+  constexpr int NB = CholBlock<T>::NB;
+  for (long long b = 0; b < nb; ++b) {
+    const bool big = I.ncols[b] >= BIG_NCOLS || I.nrows[b] >= BIG_NROWS;
+    if (big) {
+      I.big_lv[S.bk_level[b]].push_back((int)b);
+      I.big_dinv[b] = dinv_total;
+      dinv_total += (long long)ceil_div(I.ncols[b], NB) * NB * NB;
+    } else {
+      I.small_lv[S.bk_level[b]].push_back((int)b);
+    }
+  }
+  std::vector<int> small_all;
+  I.small_off.assign(L + 1, 0);
+  for (int l = 0; l < L; ++l) {
+    I.small_off[l] = (long long)small_all.size();
+    small_all.insert(small_all.end(), I.small_lv[l].begin(), I.small_lv[l].end());
+  }
+  I.small_off[L] = (long long)small_all.size();
+  std::vector<int2> pairs;
+  I.rounds.assign(L, {});
+  for (int l = 0; l < L; ++l) {
+    std::vector<int> parents = I.small_lv[l];
+    parents.insert(parents.end(), I.big_lv[l].begin(), I.big_lv[l].end());
+    std::sort(parents.begin(), parents.end());
+    for (int r = 0;; ++r) {
+      typename Impl::Round rd{(long long)pairs.size(), 0, 0};
+      for (int p : parents)
+        if ((int)I.children[p].size() > r) {
+          const int c = I.children[p][r];
+          pairs.push_back(make_int2(c, p));
+          ++rd.cnt;
+          rd.maxchunks = std::max(rd.maxchunks, ceil_div(I.nrows[c] - I.ncols[c], EA_COLS));
+        }
+      if (rd.cnt == 0) break;
+      I.rounds[l].push_back(rd);
+    }
+  }
+  std::vector<int> chptr(nb + 1, 0), chlist;
+  for (long long b = 0; b < nb; ++b) {
+    chptr[b + 1] = chptr[b] + (int)I.children[b].size();
+    chlist.insert(chlist.end(), I.children[b].begin(), I.children[b].end());
+  }
+  // device copies
+  auto up = [&](DevMem& d, const void* h, size_t bytes) {
+    d.alloc(bytes);
+    if (bytes) MPL_CUDA(cudaMemcpyAsync(d.ptr(), h, bytes, cudaMemcpyHostToDevice, st));
+  };
+  I.F.alloc(sizeof(T) * (size_t)I.ftotal);
+  up(I.d_rows, rows32.data(), sizeof(int) * rows32.size());
+  up(I.d_relpos, relpos.data(), sizeof(int) * relpos.size());
+  up(I.d_rowptr, I.rowptr.data(), sizeof(long long) * I.rowptr.size());
+  up(I.d_fptr, I.fptr.data(), sizeof(long long) * I.fptr.size());
+  up(I.d_cptr, I.cptr.data(), sizeof(long long) * I.cptr.size());
+  up(I.d_amap, amap.data(), sizeof(long long) * amap.size());
+  up(I.d_avals, S.b_vals.data(), sizeof(double) * S.b_vals.size());
+  up(I.d_dmap, dmap.data(), sizeof(long long) * dmap.size());
+  up(I.d_start, I.start.data(), sizeof(long long) * I.start.size());
+  up(I.d_ncols, I.ncols.data(), sizeof(int) * I.ncols.size());
+  up(I.d_nrows, I.nrows.data(), sizeof(int) * I.nrows.size());
+  up(I.d_chptr, chptr.data(), sizeof(int) * chptr.size());
+  up(I.d_chlist, chlist.data(), sizeof(int) * std::max<size_t>(chlist.size(), 1));
+  up(I.d_small, small_all.data(), sizeof(int) * std::max<size_t>(small_all.size(), 1));
+  up(I.d_pairs, pairs.data(), sizeof(int2) * std::max<size_t>(pairs.size(), 1));
+  I.dinv.alloc(sizeof(T) * (size_t)std::max<long long>(dinv_total, 1));
+  int maxnr = 1;
+  for (long long b = 0; b < nb; ++b) maxnr = std::max(maxnr, I.nrows[b]);
+  I.tmp.alloc(sizeof(T) * (size_t)maxnr * NB);
+  I.info.alloc(16);
+  I.scr_mem.alloc((size_t)32 << 20);
+  I.scr.ptr = I.scr_mem.ptr();
+  I.scr.bytes = I.scr_mem.bytes();
+  MPL_CUDA(cudaStreamSynchronize(st));
+}
+
 template <typename T>
 SparseFactorSolve<T>::~SparseFactorSolve() { delete p_; }
+
 template <typename T>
-int SparseFactorSolve<T>::factorize(cudaStream_t, double) {
-  throw MplError{MPL_EINVAL, "sparse numeric factorisation not available", 0};
+int SparseFactorSolve<T>::factorize(cudaStream_t st, double sigma) {
+  Impl& I = *p_;
+  MPL_CUDA(cudaMemsetAsync(I.F.ptr(), 0, sizeof(T) * (size_t)I.ftotal, st));
+  MPL_CUDA(cudaMemsetAsync(I.info.ptr(), 0, sizeof(int), st));
+  {
+    int blocks = (int)std::min<long long>((I.nnzl + 255) / 256, 16 * NUM_SMS);
+    count_launch();
+    assemble_kernel<T><<<std::max(blocks, 1), 256, 0, st>>>(I.nnzl, I.d_amap.template as<long long>(),
+                                                             I.d_avals.template as<double>(), I.F.template as<T>());
+    if (sigma != 0.0) {
+      int b2 = (int)std::min<long long>((I.n + 255) / 256, 16 * NUM_SMS);
+      count_launch();
+      add_sigma_kernel<T><<<b2, 256, 0, st>>>(I.n, I.d_dmap.template as<long long>(), I.F.template as<T>(), sigma);
+    }
+  }
+  for (int l = 0; l <= I.maxlevel; ++l) {
+    for (const auto& rd : I.rounds[l]) {
+      count_launch();
+      extend_add_kernel<T><<<dim3(rd.cnt, std::max(rd.maxchunks, 1)), 256, 0, st>>>(
+          I.d_pairs.template as<int2>() + rd.off, I.F.template as<T>(), I.d_fptr.template as<long long>(), I.d_rowptr.template as<long long>(),
+          I.d_relpos.template as<int>(), I.d_ncols.template as<int>(), I.d_nrows.template as<int>());
+    }
+    const long long ns = I.small_off[l + 1] - I.small_off[l];
+    if (ns > 0) {
+      count_launch();
+      factor_small_kernel<T><<<(int)ns, 256, 0, st>>>(I.d_small.template as<int>() + I.small_off[l], I.F.template as<T>(),
+                                                       I.d_fptr.template as<long long>(), I.d_ncols.template as<int>(),
+                                                       I.d_nrows.template as<int>(), I.d_start.template as<long long>(),
+                                                       I.info.template as<int>());
+    }
+    for (int b : I.big_lv[l]) {
+      DenseFactor<T> D;
+      D.L = I.F.template as<T>() + I.fptr[b];
+      D.ldl = I.nrows[b];
+      D.n = I.nrows[b];
+      D.Dinv = I.dinv.template as<T>() + I.big_dinv[b];
+      dense_cholesky<T>(st, D, I.tmp.template as<T>(), I.info.template as<int>(), I.scr, I.ncols[b], I.start[b], false);
+    }
+  }
+  check_launch("sparse factorize");
+  int info = 0;
+  MPL_CUDA(cudaMemcpyAsync(&info, I.info.ptr(), sizeof(int), cudaMemcpyDeviceToHost, st));
+  MPL_CUDA(cudaStreamSynchronize(st));
+  return info;
 }
+
 template <typename T>
-void SparseFactorSolve<T>::solve(cudaStream_t, T*, long long, int) {
-  throw MplError{MPL_EINVAL, "sparse solves not available", 0};
+void SparseFactorSolve<T>::solve(cudaStream_t st, T* B, long long ldb, int m) {
+  Impl& I = *p_;
+  if (m > I.mcap) {
+    I.contrib.alloc(sizeof(T) * (size_t)std::max<long long>(I.cptr[I.nb], 1) * m);
+    int maxnbl = 1;
+    for (long long b = 0; b < I.nb; ++b) maxnbl = std::max(maxnbl, I.nrows[b] - I.ncols[b]);
+    I.gbuf.alloc(sizeof(T) * (size_t)maxnbl * m);
+    I.mcap = m;
+  }
+  T* C = I.contrib.template as<T>();
+  // forward
+  for (int l = 0; l <= I.maxlevel; ++l) {
+    const long long ns = I.small_off[l + 1] - I.small_off[l];
+    if (ns > 0) {
+      count_launch();
+      fwd_small_kernel<T><<<(int)ns, 256, 0, st>>>(
+          I.d_small.template as<int>() + I.small_off[l], -1, I.F.template as<T>(), I.d_fptr.template as<long long>(), I.d_ncols.template as<int>(),
+          I.d_nrows.template as<int>(), I.d_start.template as<long long>(), I.d_rowptr.template as<long long>(), I.d_relpos.template as<int>(),
+          I.d_chptr.template as<int>(), I.d_chlist.template as<int>(), I.d_cptr.template as<long long>(), C, B, ldb, m, 0);
+    }
+    for (int b : I.big_lv[l]) {
+      // gather children into B / C_b (single CTA over a one-element list)
+      count_launch();
+      fwd_small_kernel<T><<<1, 256, 0, st>>>(
+          nullptr, b, I.F.template as<T>(), I.d_fptr.template as<long long>(), I.d_ncols.template as<int>(),
+          I.d_nrows.template as<int>(), I.d_start.template as<long long>(), I.d_rowptr.template as<long long>(), I.d_relpos.template as<int>(),
+          I.d_chptr.template as<int>(), I.d_chlist.template as<int>(), I.d_cptr.template as<long long>(), C, B, ldb, m, 1);
+      DenseFactor<T> D;
+      D.L = I.F.template as<T>() + I.fptr[b];
+      D.ldl = I.nrows[b];
+      D.n = I.ncols[b];
+      D.nb = CholBlock<T>::NB;
+      D.nblk = ceil_div(I.ncols[b], D.nb);
+      D.Dinv = I.dinv.template as<T>() + I.big_dinv[b];
+      T* top = B + I.start[b];
+      dense_trsm_fwd<T>(st, D, top, ldb, m);
+      const int nbl = I.nrows[b] - I.ncols[b];
+      if (nbl > 0)
+        gemm<T>(st, false, false, nbl, m, I.ncols[b], T(-1), D.L + I.ncols[b], D.ldl, top, ldb, T(1),
+                C + I.cptr[b] * m, nbl, false, I.scr);
+    }
+  }
+  // backward
+  for (int l = I.maxlevel; l >= 0; --l) {
+    for (int b : I.big_lv[l]) {
+      DenseFactor<T> D;
+      D.L = I.F.template as<T>() + I.fptr[b];
+      D.ldl = I.nrows[b];
+      D.n = I.ncols[b];
+      D.nb = CholBlock<T>::NB;
+      D.nblk = ceil_div(I.ncols[b], D.nb);
+      D.Dinv = I.dinv.template as<T>() + I.big_dinv[b];
+      T* top = B + I.start[b];
+      const int nbl = I.nrows[b] - I.ncols[b];
+      if (nbl > 0) {
+        int gb = (int)std::min<long long>(((long long)nbl * m + 255) / 256, 8 * NUM_SMS);
+        count_launch();
+        gather_rows_kernel<T><<<gb, 256, 0, st>>>(nbl, m, I.d_rows.template as<int>() + I.rowptr[b] + I.ncols[b], B, ldb,
+                                                  I.gbuf.template as<T>());
+        gemm<T>(st, true, false, I.ncols[b], m, nbl, T(-1), D.L + I.ncols[b], D.ldl, I.gbuf.template as<T>(), nbl, T(1),
+                top, ldb, false, I.scr);
+      }
+      dense_trsm_bwd<T>(st, D, top, ldb, m);
+    }
+    const long long ns = I.small_off[l + 1] - I.small_off[l];
+    if (ns > 0) {
+      count_launch();
+      bwd_small_kernel<T><<<(int)ns, 256, 0, st>>>(
+          I.d_small.template as<int>() + I.small_off[l], I.F.template as<T>(), I.d_fptr.template as<long long>(), I.d_ncols.template as<int>(),
+          I.d_nrows.template as<int>(), I.d_start.template as<long long>(), I.d_rowptr.template as<long long>(), I.d_rows.template as<int>(), B,
+          ldb, m);
+    }
+  }
+  check_launch("sparse solve");
 }
+
 template <typename T>
-void SparseFactorSolve<T>::apply_L(cudaStream_t, const T*, T*, int) {
-  throw MplError{MPL_EINVAL, "sparse factor not available", 0};
+void SparseFactorSolve<T>::apply_L(cudaStream_t st, const T* X, T* Y, int m) {
+  Impl& I = *p_;
+  MPL_CUDA(cudaMemsetAsync(Y, 0, sizeof(T) * (size_t)I.n * m, st));
+  count_launch();
+  apply_L_kernel<T><<<1, 256, 0, st>>>((int)I.nb, I.F.template as<T>(), I.d_fptr.template as<long long>(), I.d_ncols.template as<int>(),
+                                       I.d_nrows.template as<int>(), I.d_start.template as<long long>(), I.d_rowptr.template as<long long>(),
+                                       I.d_rows.template as<int>(), X, I.n, Y, I.n, m);
+  check_launch("apply_L");
 }
+
 template class SparseFactorSolve<float>;
 template class SparseFactorSolve<double>;
 

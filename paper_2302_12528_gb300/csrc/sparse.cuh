@@ -20,6 +20,12 @@ struct SparseSymbolic {
   std::vector<long long> sn_rows;    // per supernode: its columns, then struct below, ascending
   std::vector<long long> sn_parent;  // supernodal tree
   std::vector<long long> sn_level;   // 0 = leaf, 1 + max(child levels)
+  // Relaxed partition used by the numeric factor: the nested-dissection
+  // blocks (leaf boxes and separator planes; fundamental supernodes when no
+  // grid is given).  Rows of a block = its columns followed by the union of
+  // struct(j) over its columns (rows beyond the block), ascending.
+  long long nblock = 0;
+  std::vector<long long> bk_start, bk_rowptr, bk_rows, bk_parent, bk_level;
   // permuted lower-triangular CSR of B (row j holds B(j, i) for i <= j)
   std::vector<long long> b_rowptr;
   std::vector<int> b_colind;
@@ -31,8 +37,10 @@ struct SparseSymbolic {
 };
 
 // Grid nested dissection (x fastest; see the reading in the docs):
-// perm[new] = old.
-std::vector<long long> nd_grid_order(const int* dims, int ndims, int leaf);
+// perm[new] = old.  ``blocks`` (optional) receives the start of every
+// emitted block (leaf box or separator plane) in the new order, plus n.
+std::vector<long long> nd_grid_order(const int* dims, int ndims, int leaf,
+                                     std::vector<long long>* blocks = nullptr);
 
 // Ordering + symbolic analysis.  ``dims`` may be null (natural order).
 void analyze_csr(long long n, const long long* rowptr, const int* colind, const double* vals,

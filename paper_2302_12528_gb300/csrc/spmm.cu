@@ -43,6 +43,7 @@ void spmm_csr(cudaStream_t st, int n, int m, const long long* rowptr, const int*
               const TV* vals, const T* X, long long ldx, T* Y, long long ldy) {
   if (n <= 0 || m <= 0) return;
   dim3 grid(ceil_div(n, 256), ceil_div(m, SPMM_CG));
+  count_launch();
   spmm_csr_kernel<TV, T><<<grid, 256, 0, st>>>(n, m, rowptr, colind, vals, X, ldx, Y, ldy);
 }
 

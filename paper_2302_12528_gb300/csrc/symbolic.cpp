@@ -25,14 +25,17 @@ namespace mpl {
 
 static constexpr int ND_LEAF = 64;
 
-std::vector<long long> nd_grid_order(const int* dims, int ndims, int leaf) {
+std::vector<long long> nd_grid_order(const int* dims, int ndims, int leaf,
+                                     std::vector<long long>* blocks) {
   long long d[3] = {1, 1, 1};
   for (int a = 0; a < ndims; ++a) d[a] = dims[a];
   const long long stride[3] = {1, d[0], d[0] * d[1]};
   std::vector<long long> out;
   out.reserve(d[0] * d[1] * d[2]);
   struct Box { long long lo[3], hi[3]; };
+  if (blocks) blocks->clear();
   auto emit = [&](const Box& b) {
+    if (blocks) blocks->push_back((long long)out.size());
     for (long long z = b.lo[2]; z < b.hi[2]; ++z)
       for (long long y = b.lo[1]; y < b.hi[1]; ++y)
         for (long long x = b.lo[0]; x < b.hi[0]; ++x) out.push_back(x * stride[0] + y * stride[1] + z * stride[2]);
@@ -67,13 +70,15 @@ std::vector<long long> nd_grid_order(const int* dims, int ndims, int leaf) {
     all.hi[a] = d[a];
   }
   rec(all);
+  if (blocks) blocks->push_back((long long)out.size());
   return out;
 }
 
 void analyze_csr(long long n, const long long* rowptr, const int* colind, const double* vals,
                  const int* dims, int ndims, SparseSymbolic& S) {
   S.n = n;
-  if (dims) S.perm = nd_grid_order(dims, ndims, ND_LEAF);
+  std::vector<long long> blocks;
+  if (dims) S.perm = nd_grid_order(dims, ndims, ND_LEAF, &blocks);
   else {
     S.perm.resize(n);
     std::iota(S.perm.begin(), S.perm.end(), 0LL);
@@ -163,6 +168,15 @@ void analyze_csr(long long n, const long long* rowptr, const int* colind, const 
     S.sn_rowptr.push_back((long long)S.sn_rows.size());
   };
   long long cur_first = 0;
+  // relaxed partition: grid blocks, or (no grid) fundamental supernodes,
+  // filled in after the loop
+  std::vector<long long> umark(n, -1);
+  std::vector<int> ubuf;
+  long long blk = 0;
+  S.bk_start.clear();
+  S.bk_rowptr.assign(1, 0);
+  S.bk_rows.clear();
+  const bool grid_blocks = !blocks.empty();
   for (long long j = 0; j < n; ++j) {
     buf.clear();
     // adj_>(j): column j of the lower part = row j of the upper part; B is
@@ -183,6 +197,24 @@ void analyze_csr(long long n, const long long* rowptr, const int* colind, const 
     }
     std::sort(buf.begin(), buf.end());
     st[j] = buf;
+    if (grid_blocks) {
+      // union of struct(j) over the block's columns, rows beyond the block
+      while (j >= blocks[blk + 1]) ++blk;
+      const long long bend = blocks[blk + 1];
+      if (j == blocks[blk]) ubuf.clear();
+      for (int i : buf)
+        if (i >= bend && umark[i] != blk) {
+          umark[i] = blk;
+          ubuf.push_back(i);
+        }
+      if (j == bend - 1) {
+        std::sort(ubuf.begin(), ubuf.end());
+        S.bk_start.push_back(blocks[blk]);
+        for (long long c = blocks[blk]; c < bend; ++c) S.bk_rows.push_back(c);
+        for (int r : ubuf) S.bk_rows.push_back(r);
+        S.bk_rowptr.push_back((long long)S.bk_rows.size());
+      }
+    }
     S.colcount[j] = (long long)buf.size() + 1;
     if (!buf.empty() && buf[0] != S.parent[j]) throw MplError{MPL_EINVAL, "matrix pattern is not structurally symmetric", j};
     if (j > 0) {
@@ -214,6 +246,27 @@ void analyze_csr(long long n, const long long* rowptr, const int* colind, const 
   for (long long s = 0; s < S.nsuper; ++s) {
     const long long p = S.sn_parent[s];
     if (p >= 0) S.sn_level[p] = std::max(S.sn_level[p], S.sn_level[s] + 1);
+  }
+  // relaxed partition tree and levels
+  if (!grid_blocks) {
+    S.bk_start.assign(S.sn_start.begin(), S.sn_start.end() - 1);
+    S.bk_rowptr = S.sn_rowptr;
+    S.bk_rows = S.sn_rows;
+  }
+  S.bk_start.push_back(n);
+  S.nblock = (long long)S.bk_start.size() - 1;
+  std::vector<long long> col2bk(n);
+  for (long long b = 0; b < S.nblock; ++b)
+    for (long long c = S.bk_start[b]; c < S.bk_start[b + 1]; ++c) col2bk[c] = b;
+  S.bk_parent.assign(S.nblock, -1);
+  S.bk_level.assign(S.nblock, 0);
+  for (long long b = 0; b < S.nblock; ++b) {
+    const long long last = S.bk_start[b + 1] - 1;
+    if (S.parent[last] >= 0) S.bk_parent[b] = col2bk[S.parent[last]];
+  }
+  for (long long b = 0; b < S.nblock; ++b) {
+    const long long p = S.bk_parent[b];
+    if (p >= 0) S.bk_level[p] = std::max(S.bk_level[p], S.bk_level[b] + 1);
   }
 }
 

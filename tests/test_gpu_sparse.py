@@ -1,0 +1,173 @@
+"""GPU parity of the sparse hot path (CSR block product, nested-dissection
+ordering, multifrontal lower-precision factor, level-scheduled solves, full
+solves) through the C ABI against the CPU oracle."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from helpers import U_H, U_L, subspace_sin, to_np, torch_dev
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_2302_12528_gb300 as M  # noqa: E402
+import workloads as W  # noqa: E402
+from oracle import dense as D  # noqa: E402
+from oracle import lobpcg as OL  # noqa: E402
+from oracle import sparse as SP  # noqa: E402
+from oracle import symbolic as S  # noqa: E402
+
+
+def make(dims, k, m, policy="mp", sigma=1.0, ell=3.0, seed=5):
+    rp, ci, v, c = W.diffusion_csr(dims, seed, ell=ell, sigma=sigma)
+    n = len(rp) - 1
+    Om = W.sketch(n, 8, seed + 2)
+    h = M.create_csr(rp, ci, v, k, m, tol=1e-12, policy=policy, Omega=Om, grid_dims=dims)
+    return h, (rp, ci, v), Om
+
+
+def permuted(rp, ci, v, dims):
+    perm = S.nd_grid_order(dims)
+    prp, pci, pv = S.permute_csr(rp, ci, v, perm)
+    return perm, SP.csr_to_scipy(prp, pci, pv)
+
+
+@pytest.mark.parametrize("dims,ncols", [((12, 10, 9), 7), ((33, 17), 20), ((16, 16, 16), 48)])
+def test_spmm_parity(dims, ncols):
+    h, (rp, ci, v), _ = make(dims, 4, 16 if ncols <= 48 else ncols)
+    perm, Ap = permuted(rp, ci, v, dims)
+    n = Ap.shape[0]
+    X = W.start_block(n, ncols, seed=1)
+    Y = torch.empty_like(torch_dev(X))
+    h.apply_A(torch_dev(X), Y, ncols)
+    ref = Ap @ X.T
+    bound = 8 * U_H * np.linalg.norm(np.abs(Ap) @ np.abs(X.T))
+    assert np.linalg.norm(to_np(Y).T - ref) <= bound
+    h.close()
+
+
+@pytest.mark.parametrize("dims", [(8, 7, 6), (20, 17), (9, 9, 9)])
+def test_sparse_factor_vs_definition(dims):
+    h, (rp, ci, v), _ = make(dims, 4, 8, policy="schol")
+    h.factor()
+    st = h.stats()
+    assert st["factor_tries"] == 1
+    n = len(rp) - 1
+    I = torch.eye(n, dtype=torch.float32, device="cuda:0")
+    Lt = torch.empty_like(I)
+    h.apply_L(I, Lt, n)                          # column j of L = L e_j
+    Lg = to_np(Lt).T.astype(np.float64)
+    perm = S.nd_grid_order(dims)
+    Lref = SP.lower_factor_by_definition(rp, ci, v, perm).astype(np.float64)
+    assert np.abs(np.triu(Lg, 1)).max() == 0.0
+    prp, pci, _ = S.permute_csr(rp, ci, v, perm)
+    pat = S.lower_pattern(S.Symbolic(prp, pci)) | np.eye(n, dtype=bool)
+    assert np.all(Lg[~pat] == 0.0)               # explicit zeros of the blocks stay exact zeros
+    A = SP.csr_to_scipy(rp, ci, v).toarray()[np.ix_(perm, perm)]
+    ev = np.linalg.eigvalsh(A)
+    kappa = ev[-1] / ev[0]
+    # both are float32 Cholesky factors of the same matrix; they differ by the
+    # forward error of the factorisation, O(kappa u_l)
+    assert np.linalg.norm(Lg - Lref) / np.linalg.norm(Lref) <= 10 * kappa * U_L
+    assert np.linalg.norm(Lg @ Lg.T - A) / np.linalg.norm(A, 2) <= 50 * U_L
+    h.close()
+
+
+@pytest.mark.parametrize("dims,m", [((8, 7, 6), 12), ((24, 20), 20)])
+def test_sparse_precond_parity(dims, m):
+    h, (rp, ci, v), _ = make(dims, 4, m, policy="schol")
+    h.factor()
+    n = len(rp) - 1
+    I = torch.eye(n, dtype=torch.float32, device="cuda:0")
+    Lt = torch.empty_like(I)
+    h.apply_L(I, Lt, n)
+    Lg = to_np(Lt).T
+    R = W.start_block(n, m, seed=9)
+    Wd = torch.empty_like(torch_dev(R))
+    h.precond(torch_dev(R), Wd, m, scale=False)
+    ref = D.working(D.apply_T(D.LowerFactor(Lg, 0.0, 0, np.float32), D.lower(R.T)))
+    assert np.linalg.norm(to_np(Wd).T - ref) / np.linalg.norm(ref) <= 50 * n * U_L
+    h.close()
+
+
+@pytest.mark.parametrize("policy", ["mp", "schol", "dchol"])
+def test_sparse_solve_3d_vs_oracle(policy):
+    dims, k, m = (10, 9, 8), 6, 10
+    h, (rp, ci, v), Om = make(dims, k, m, policy=policy)
+    n = len(rp) - 1
+    X0 = W.start_block(n, m, seed=11)
+    Xo = np.zeros((k, n))
+    h.factor()
+    lam, _, hist, its, _ = h.solve(X0, maxit=500, X_out=Xo)
+    h.close()
+    A = SP.csr_to_scipy(rp, ci, v).toarray()
+    evall = np.linalg.eigvalsh(A)
+    X = Xo.T
+    rn = np.linalg.norm(A @ X - X * lam[None, :], axis=0)
+    assert np.all(rn <= 1e-12 * (evall[-1] + np.abs(lam)) * np.linalg.norm(X, axis=0) * 10)
+    gap = evall[k] - evall[k - 1]
+    floor = 10 * U_H * evall[-1]
+    assert np.all(np.abs(lam - evall[:k]) <= np.maximum(1e-10 * evall[:k], 2 * rn ** 2 / gap) + floor)
+    assert np.abs(X.T @ X - np.eye(k)).max() <= 1e-12
+    perm, Ap = permuted(rp, ci, v, dims)
+    ref = OL.solve(OL.CsrOperator(Ap), Ap.toarray(), X0.T[perm], Om, k, tol=1e-12, policy=policy)
+    assert np.allclose(lam, ref.theta, rtol=1e-10, atol=floor)
+    Xref = np.empty_like(ref.X)
+    Xref[perm] = ref.X
+    for j in range(k):
+        assert subspace_sin(X[:, j:j + 1], Xref[:, j:j + 1]) <= 1e-8 * evall[-1] / gap
+
+
+def test_sparse_laplacian_closed_form_multiplicities():
+    """Constant coefficients (sigma = 0): eigenvalues with multiplicities."""
+    from test_oracle_sparse import laplace_eigs
+    dims, k, m = (8, 8, 8), 7, 12
+    h, (rp, ci, v), Om = make(dims, k, m, sigma=0.0)
+    h.factor()
+    n = len(rp) - 1
+    lam, _, _, _, _ = h.solve(W.start_block(n, m, seed=3), maxit=500)
+    h.close()
+    assert np.allclose(lam, laplace_eigs(dims, k), rtol=1e-10)
+
+
+def test_sparse_2d_graded():
+    dims, k, m = (40, 37), 8, 12
+    h, (rp, ci, v), Om = make(dims, k, m, sigma=0.5, ell=8.0)
+    h.factor()
+    n = len(rp) - 1
+    Xo = np.zeros((k, n))
+    lam, _, _, its, _ = h.solve(W.start_block(n, m, seed=4), maxit=800, X_out=Xo)
+    h.close()
+    A = SP.csr_to_scipy(rp, ci, v)
+    X = Xo.T
+    ev = np.linalg.eigvalsh(A.toarray())
+    rn = np.linalg.norm(A @ X - X * lam[None, :], axis=0)
+    assert np.all(rn <= 1e-11 * (ev[-1] + lam) * np.linalg.norm(X, axis=0))
+    assert np.allclose(lam, ev[:k], rtol=1e-9)
+
+
+def test_sparse_full_size_64cubed_properties():
+    """The 3D workload at full size (64^3, n = 262144, k = 32, m = 48):
+    properties that hold at any size -- residuals of the returned pairs from
+    an explicit SpMM, orthonormality, and ascending Ritz values."""
+    w = W.WORKLOADS["diffusion3d_64"]
+    rp, ci, v, c = W.diffusion_csr(w.dims, w.seed, w.ell, w.sigma)
+    Om = W.sketch(w.n, 8, w.seed + 2)
+    h = M.create_csr(rp, ci, v, w.k, w.m, tol=w.tol, policy="mp", Omega=Om, grid_dims=w.dims)
+    h.factor()
+    Xo = torch.empty((w.k, w.n), dtype=torch.float64, device="cuda:0")
+    lam, _, hist, its, _ = h.solve(torch_dev(W.start_block(w.n, w.m, w.seed + 1)), maxit=2000, X_out=Xo)
+    st = h.stats()
+    h.close()
+    A = SP.csr_to_scipy(rp, ci, v)
+    X = to_np(Xo).T
+    rn = np.linalg.norm(A @ X - X * lam[None, :], axis=0)
+    assert np.all(rn <= w.tol * (st["norm_est"] + lam) * np.linalg.norm(X, axis=0) * 1.01)
+    assert np.abs(X.T @ X - np.eye(w.k)).max() <= 1e-12
+    assert np.all(np.diff(lam) >= 0)
+    # Rayleigh quotients from the explicit product agree with the returned values
+    rq = np.einsum("ij,ij->j", X, A @ X)
+    assert np.allclose(rq, lam, rtol=1e-12)
