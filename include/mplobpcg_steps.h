@@ -104,6 +104,31 @@ mpl_status mpl_analyze_host(mpl_handle* h, int64_t n, int64_t nnz, const int64_t
  * n), for checking the numeric factor (a slow single-CTA sweep; checks only). */
 mpl_status mpl_step_apply_L(mpl_handle h, const float* X, float* Y, int ncols);
 
+/* Residual without device allocation (the paper has no counterpart).
+ *
+ * For callers that cannot call cudaMalloc: code that runs while a stream is
+ * being captured into a CUDA graph, code under a memory manager that owns the
+ * whole device, or latency-critical code that must not wait on the driver's
+ * allocator.  Same result as mpl_step_residual, without a handle:
+ *   R = AX - X diag(theta), norms2[0..m) = ||r_j||^2, norms2[m..2m) = ||x_j||^2.
+ * dtype: MPL_R64 or MPL_C128.  AX, X, R: n x m column-major (leading dimension
+ * n), theta (m doubles) and norms2 (2m doubles) -- all DEVICE pointers owned by
+ * the caller.  stream: a cudaStream_t or NULL.  Asynchronous: returns after the
+ * launches; the results are ready when the stream reaches them.
+ *
+ * Scratch: the partial sums, ceil(n / 2048) * 2m doubles, live in one static
+ * device array of 1,048,576 doubles (8 MiB) that every GPU loading this
+ * library holds until the process exits.  Larger n * m returns MPL_EINVAL
+ * (e.g. n <= 262,144 allows m <= 4,096; n <= 16,777,216 allows m <= 64).
+ * The first call on each device looks up that device's address of the array
+ * (cudaGetSymbolAddress, with the device current); make that first call
+ * before any stream capture.  Every call shares the one array: calls whose
+ * kernels overlap on the GPU (different streams, no ordering between them)
+ * race and give wrong norms.  Nothing in the array needs clearing; each call
+ * writes every partial it reads. */
+mpl_status mpl_residual_noalloc(int dtype, int64_t n, int m, const void* AX, const void* X,
+                                const double* theta, void* R, double* norms2, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,5 +10,5 @@ Import fails loudly when the CUDA library has not been built
 """
 from .binding import (  # noqa: F401
     LIB_PATH, MPL_C128, MPL_D_DCHOL, MPL_D_SCHOL, MPL_MP_SCHOL, MPL_R64, POLICIES, MplError,
-    Stats, Handle, analyze_host, create_csr, create_dense, lib,
+    Stats, Handle, analyze_host, create_csr, create_dense, lib, residual_noalloc,
 )

@@ -78,6 +78,7 @@ _apply_L = _sig("mpl_step_apply_L", _i, [_h, _p, _p, _i])
 _blk_sizes = _sig("mpl_get_block_sizes", _i, [_h, _p, _p])
 _get_blocks = _sig("mpl_get_blocks", _i, [_h, _p, _p, _p, _p, _p])
 _analyze_host = _sig("mpl_analyze_host", _i, [C.POINTER(_h), _i64, _i64, _p, _p, _p, _i])
+_residual_noalloc = _sig("mpl_residual_noalloc", _i, [_i, _i64, _i, _p, _p, _p, _p, _p, _p])
 
 
 class MplError(RuntimeError):
@@ -290,3 +291,11 @@ def analyze_host(rowptr, colind, grid_dims=None):
     if st != 0:
         _raise_create(st, "mpl_analyze_host")
     return Handle(h, MPL_R64, n, 1, 1)
+
+def residual_noalloc(dtype, n, m, AX, X, theta, R, norms2, stream=None):
+    """mpl_residual_noalloc: every argument a device tensor (theta: m float64,
+    norms2: 2m float64).  Allocates nothing on the device; see the header."""
+    st = _residual_noalloc(dtype, n, m, _ptr(AX), _ptr(X), _ptr(theta), _ptr(R), _ptr(norms2),
+                           _stream_ptr(stream))
+    if st != 0:
+        raise MplError(st, "mpl_residual_noalloc failed", 0)

@@ -225,6 +225,10 @@ void residual(cudaStream_t st, int n, int m, const T* AX, long long ldax, const 
   sum_chunks_kernel<<<ceil_div(2 * m, 128), 128, 0, st>>>(nchunk, 2 * m, part, out);
 }
 
+long long residual_scratch_doubles(long long n, int m) {
+  return (long long)ceil_div(n, RES_CHUNK) * 2LL * m;
+}
+
 template <typename T>
 __global__ void col_norms2_kernel(int n, int m, const T* __restrict__ X, long long ldx,
                                   double* __restrict__ part) {

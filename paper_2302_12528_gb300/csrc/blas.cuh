@@ -30,6 +30,9 @@ void residual(cudaStream_t st, int n, int m, const T* AX, long long ldax, const 
               long long ldx, const double* theta, T* R, long long ldr, double* part,
               double* out);
 
+// Number of doubles ``residual`` needs in ``part`` for an n x m block.
+long long residual_scratch_doubles(long long n, int m);
+
 // Rl = single(R diag(1 / sqrt(rn2)))  (scaled cast of Section 3's single()).
 template <typename T, typename TL>
 void scale_cast(cudaStream_t st, int n, int m, const T* R, long long ldr, const double* rn2,
