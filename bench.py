@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="profiling runs only: cap the iterations (result may be unconverged)")
     return ap.parse_args()
 
 
@@ -241,10 +243,13 @@ def main():
     torch.cuda.synchronize()
 
     h = make_handle(M, w, d, args.policy, stream)
+    unconv = args.profile_iters > 0
+    if unconv:
+        args.maxit = args.profile_iters
     # warm-up steps (untimed)
     for _ in range(args.warmup):
         h.factor()
-        h.solve(X0, maxit=args.maxit)
+        h.solve(X0, maxit=args.maxit, allow_not_converged=unconv)
     clocks = Clocks(local)
     if dist is not None:
         dist.barrier()
@@ -259,7 +264,7 @@ def main():
     lam = None
     for _ in range(args.steps):
         h.factor()
-        lam, _, hist, its, _ = h.solve(X0, maxit=args.maxit)
+        lam, _, hist, its, _ = h.solve(X0, maxit=args.maxit, allow_not_converged=unconv)
         st = h.stats()
         apply_ms += st["apply_ms"]
         apply_flops += st["apply_flops"]
@@ -304,7 +309,9 @@ def main():
                            "peak_note": "nominal FP64 of the recipe table (DFMA microbenchmark: 1190)"}
     if ck:
         out["clocks"] = ck
-    if rank == 0 and not args.no_fp64 and args.policy != "dchol":
+    if unconv:
+        out["profile_run"] = f"iterations capped at {args.profile_iters}; not a bench value"
+    if rank == 0 and not args.no_fp64 and args.policy != "dchol" and not unconv:
         h2 = make_handle(M, w, d, "dchol", stream)
         h2.factor()
         h2.solve(X0, maxit=args.maxit)        # warm-up (allocations)

@@ -77,6 +77,11 @@ typedef struct {
   double apply_flops;     /* their algorithmic flops (dense: 2 n^2 per column, x4
                              complex; CSR: 2 nnz per column)                          */
   int64_t kernel_launches;/* kernels launched by the last mpl_factor + mpl_solve      */
+  double phase_ms[10];    /* device time of the working-precision loop by phase (CUDA
+                             events): 0 A X/A W products, 1 residual + test, 2
+                             preconditioner, 3 projections, 4 Algorithm 2, 5 Gram
+                             S^*AS, 6 small eigenproblem, 7 HL coefficients, 8 basis
+                             update, 9 explicit check                                */
 } mpl_stats;
 
 /*

@@ -41,10 +41,14 @@ class Stats(C.Structure):
                 ("t_stage2_ms", _d), ("iters_stage1", _i), ("iters_stage2", _i), ("factor_tries", _i),
                 ("factor_shift", _d), ("norm_est", _d), ("qr_fallbacks", _i), ("explicit_checks", _i),
                 ("nnz_L", _i64), ("nsuper", _i64), ("max_rel_resid", _d), ("apply_ms", _d),
-                ("apply_calls", _i64), ("apply_flops", _d), ("kernel_launches", _i64)]
+                ("apply_calls", _i64), ("apply_flops", _d), ("kernel_launches", _i64),
+                ("phase_ms", _d * 10)]
+    PHASES = ("apply", "residual", "precond", "project", "alg2", "gram", "eig", "hl", "update", "check")
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "phase_ms"}
+        d["phase_ms"] = {name: float(self.phase_ms[i]) for i, name in enumerate(self.PHASES)}
+        return d
 
 
 def _sig(name, res, args):
@@ -291,6 +295,7 @@ def analyze_host(rowptr, colind, grid_dims=None):
     if st != 0:
         _raise_create(st, "mpl_analyze_host")
     return Handle(h, MPL_R64, n, 1, 1)
+
 
 def residual_noalloc(dtype, n, m, AX, X, theta, R, norms2, stream=None):
     """mpl_residual_noalloc: every argument a device tensor (theta: m float64,

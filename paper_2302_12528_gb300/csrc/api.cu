@@ -313,6 +313,7 @@ class Engine : public EngineBase {
     c_->stats.apply_ms = p2.apply_ms;
     c_->stats.apply_calls = p2.apply_calls;
     c_->stats.apply_flops = p2.apply_flops;
+    for (int q = 0; q < PH_N; ++q) c_->stats.phase_ms[q] = p2.phase_ms[q];
     c_->stats.kernel_launches = launches_factor_ + (launch_counter().load() - l0);
     if (lambda) for (int j = 0; j < k; ++j) lambda[j] = th[j];
     if (X) {
@@ -400,8 +401,11 @@ class Engine : public EngineBase {
   void step_small_eig(void* Ap, int N, int m, double* lam, void* C1) override {
     auto& s = step_stage();
     s.prepare();
-    eig_small<TW>(c_->stream, N, m, static_cast<TW*>(Ap), s.vec() + 2 * c_->m, static_cast<TW*>(C1),
-                  eig_ws(N, m));
+    DevMem fl(16);
+    if (!eig_small_fast<TW>(c_->stream, N, m, static_cast<TW*>(Ap), s.vec() + 2 * c_->m, static_cast<TW*>(C1),
+                            eig_ws(N, m), fl.as<int>()))
+      eig_small<TW>(c_->stream, N, m, static_cast<TW*>(Ap), s.vec() + 2 * c_->m, static_cast<TW*>(C1),
+                    eig_ws(N, m));
     MPL_CUDA(cudaMemcpyAsync(lam, s.vec() + 2 * c_->m, sizeof(double) * m, cudaMemcpyDeviceToHost, c_->stream));
     sync("small_eig");
   }
@@ -430,7 +434,7 @@ class Engine : public EngineBase {
     MPL_CUDA(cudaStreamSynchronize(c_->stream));
   }
   void* eig_ws(int N, int m) {
-    eigws_.ensure(eig_ws_bytes(N, m, sizeof(TW)));
+    eigws_.ensure(std::max(eig_ws_bytes(N, m, sizeof(TW)), eig_fast_ws_bytes(N, m, sizeof(TW))));
     return eigws_.ptr();
   }
   void make_low_op();

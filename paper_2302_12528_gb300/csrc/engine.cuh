@@ -4,6 +4,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -144,7 +145,10 @@ struct PreFromFactor : Pre<TW> {
   }
 };
 
+enum Phase { PH_APPLY = 0, PH_RESID, PH_PRECOND, PH_PROJECT, PH_ALG2, PH_GRAM, PH_EIG, PH_HL, PH_UPDATE, PH_CHECK, PH_N };
+
 struct Progress {
+  double phase_ms[PH_N] = {0};
   double apply_ms = 0.0, apply_flops = 0.0;
   long long apply_calls = 0;
   std::vector<double> hist;
@@ -178,7 +182,7 @@ class Stage {
     part_.alloc((size_t)(ceil_div(n_, 2048) + 1) * 2 * m * sizeof(double));
     tsq_.alloc(tsqr_ws_elems(n_, m_, nullptr) * sizeof(TQ));
     tsw_.alloc(tsqr_ws_elems(n_, m_, nullptr) * sizeof(TW));
-    eigw_.alloc(eig_ws_bytes(3 * m_, m_, sizeof(TW)));
+    eigw_.alloc(std::max(eig_ws_bytes(3 * m_, m_, sizeof(TW)), eig_fast_ws_bytes(3 * m_, m_, sizeof(TW))));
     info_.alloc(16);
     size_t sbytes = (size_t)48 << 20;  // split-K partials
     scr_mem_.alloc(sbytes);
@@ -199,6 +203,11 @@ class Stage {
     op->apply(st, X, n_, Y, n_, ncols);
     atimer_.end(st);
     prog_.apply_flops += op->flops(ncols);
+  }
+  void ph_begin(cudaStream_t st, int p) { ptimer_[p].begin(st); }
+  void ph_end(cudaStream_t st, int p) { ptimer_[p].end(st); }
+  void ph_harvest() {
+    for (int p = 0; p < PH_N; ++p) ptimer_[p].harvest();
   }
 
   // small buffers
@@ -257,10 +266,16 @@ class Stage {
   void rayleigh_ritz(cudaStream_t st, const TW* S, const TW* AS, int ncol, int m, bool hl) {
     prepare();
     TW* Ap_ = Ap();
+    ph_begin(st, PH_GRAM);
     gemm<TW>(st, true, false, ncol, ncol, n_, 1, S, n_, AS, n_, 0, Ap_, ncol, true, scr_);
     herm_from_lower<TW>(st, ncol, Ap_, ncol);
-    eig_small<TW>(st, ncol, m, Ap_, vec() + 2 * m_, Ccoef(), eigw_.as<void>());
+    ph_end(st, PH_GRAM);
+    ph_begin(st, PH_EIG);
+    if (!eig_small_fast<TW>(st, ncol, m, Ap_, vec() + 2 * m_, Ccoef(), eigw_.as<void>(), info_.as<int>() + 1))
+      eig_small<TW>(st, ncol, m, Ap_, vec() + 2 * m_, Ccoef(), eigw_.as<void>());
+    ph_end(st, PH_EIG);
     if (hl) {
+      ph_begin(st, PH_HL);
       // [C1 | E1 - C1 C1(1:m, :)^*] -> Householder Q, columns m .. 2m-1: an
       // orthonormal basis, orthogonal to C1, of the part of the old X
       // coordinates outside the new Ritz vectors (span = span C(:, m+1:end) V)
@@ -269,7 +284,9 @@ class Stage {
       TW* Y2 = Y + (size_t)m * ncol;
       set_identity<TW>(st, ncol, m, Y2, ncol);
       gemm<TW>(st, false, true, ncol, m, m, -1, Ccoef(), ncol, Ccoef(), ncol, 1, Y2, ncol, false, scr_);
-      thin_q<TW>(st, ncol, 2 * m, Y, m, m, Ccoef() + (size_t)m * ncol, hb());
+      if (!thin_q_fast<TW>(st, ncol, 2 * m, Y, m, m, Ccoef() + (size_t)m * ncol, hb()))
+        thin_q<TW>(st, ncol, 2 * m, Y, m, m, Ccoef() + (size_t)m * ncol, hb());
+      ph_end(st, PH_HL);
     }
   }
 
@@ -286,6 +303,7 @@ class Stage {
     MPL_CUDA(cudaMemcpyAsync(S, X0, sizeof(TW) * n * m, cudaMemcpyDeviceToDevice, st));
     if (!mixed_qr(st, S, m, qr_low)) throw MplError{MPL_ERANK, "Algorithm 2 failed on the start block", 0};
     atimer_.reset();
+    for (int p = 0; p < PH_N; ++p) ptimer_[p].reset();
     timed_apply(st, op, S, AS_[0].as<TW>(), m);
     rayleigh_ritz(st, S, AS_[0].as<TW>(), m, m, false);
     update(st, m, m);  // X <- X C, AX <- AX C
@@ -294,7 +312,9 @@ class Stage {
     for (int it = 1; it <= maxit + 1; ++it) {
       TW* X = S_[cur_].as<TW>();
       TW* AX = AS_[cur_].as<TW>();
+      ph_begin(st, PH_RESID);
       residual<TW>(st, n_, m, AX, n, X, n, vec() + 2 * m, R_.as<TW>(), n, part_.as<double>(), vec());
+      ph_end(st, PH_RESID);
       int nc = fetch_and_test(st, k, tol, normA);
       if (nc < 0) throw MplError{MPL_ENUMERICAL, "non-finite residual norm", it};
       prog_.hist.push_back(last_max_);
@@ -302,8 +322,10 @@ class Stage {
       if (nc >= k && verify) {
         // confirm with an explicit product A X (AX is carried through the updates)
         ++prog_.explicit_checks;
+        ph_begin(st, PH_CHECK);
         timed_apply(st, op, X, V_.as<TW>(), m);
         residual<TW>(st, n_, m, V_.as<TW>(), n, X, n, vec() + 2 * m, R_.as<TW>(), n, part_.as<double>(), vec());
+        ph_end(st, PH_CHECK);
         nc = fetch_and_test(st, k, tol, normA);
         prog_.max_rel = last_max_;
         prog_.hist.back() = last_max_;
@@ -327,13 +349,22 @@ class Stage {
       }
       const int wcol = hasP ? 2 * m : m;
       TW* W = X + (size_t)wcol * n;
+      ph_begin(st, PH_PRECOND);
       pre->apply(st, R_.as<TW>(), n, vec(), W, n, m);
+      ph_end(st, PH_PRECOND);
+      ph_begin(st, PH_PROJECT);
       project(st, X, wcol, W, m);
-      if (!mixed_qr(st, W, m, qr_low)) throw MplError{MPL_ERANK, "Algorithm 2 broke down", it};
+      ph_end(st, PH_PROJECT);
+      ph_begin(st, PH_ALG2);
+      const bool qr_ok = mixed_qr(st, W, m, qr_low);
+      ph_end(st, PH_ALG2);
+      if (!qr_ok) throw MplError{MPL_ERANK, "Algorithm 2 broke down", it};
       timed_apply(st, op, W, AX + (size_t)wcol * n, m);
       const int ncol = wcol + m;
       rayleigh_ritz(st, X, AX, ncol, m, true);
+      ph_begin(st, PH_UPDATE);
       update(st, ncol, 2 * m);
+      ph_end(st, PH_UPDATE);
       hasP = true;
       check_launch("lobpcg iteration");
     }
@@ -361,8 +392,11 @@ class Stage {
 
   void finish_timing() {
     atimer_.harvest();
+    ph_harvest();
     prog_.apply_ms = atimer_.total_ms;
     prog_.apply_calls = atimer_.calls;
+    prog_.phase_ms[PH_APPLY] = atimer_.total_ms;
+    for (int p = 1; p < PH_N; ++p) prog_.phase_ms[p] = ptimer_[p].total_ms;
   }
 
   // Read [rn2 | xn2 | theta] and apply Eq. (stop); returns n_c (leading
@@ -372,6 +406,7 @@ class Stage {
     MPL_CUDA(cudaMemcpyAsync(host_, vec(), sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, st));
     MPL_CUDA(cudaStreamSynchronize(st));
     atimer_.harvest();
+    ph_harvest();
     int nc = 0;
     bool run = true;
     double mx = 0.0;
@@ -396,6 +431,7 @@ class Stage {
   double last_max_ = 0.0;
   Progress prog_;
   EventTimer atimer_;
+  EventTimer ptimer_[PH_N];
 };
 
 }  // namespace mpl

@@ -18,22 +18,9 @@
 // (clusters: gaps below 1e-3 ||T||_1), and back-transformation through the
 // reflectors.  Only the m wanted eigenvectors are formed.
 #include "small.cuh"
+#include "small_dev.cuh"
 
 namespace mpl {
-
-template <typename R> __device__ __forceinline__ R sqrt_(R x);
-template <> __device__ __forceinline__ float sqrt_<float>(float x) { return sqrtf(x); }
-template <> __device__ __forceinline__ double sqrt_<double>(double x) { return sqrt(x); }
-
-template <typename T> __device__ __forceinline__ T div_(T a, T b) { return a / b; }
-template <> __device__ __forceinline__ zf div_<zf>(zf a, zf b) {
-  const float s = 1.0f / abs2_(b);
-  return (a * conj_(b)) * s;
-}
-template <> __device__ __forceinline__ zd div_<zd>(zd a, zd b) {
-  const double s = 1.0 / abs2_(b);
-  return (a * conj_(b)) * s;
-}
 
 // ------------------------------------------------------------------------
 // Householder QR of an N x m column-major matrix held by one CTA.
@@ -270,88 +257,8 @@ size_t eig_ws_bytes(int N, int m, size_t elem) {
   return 2 * (size_t)N * elem + 3 * (size_t)N * 8 + 5 * (size_t)N * m * 8 + (size_t)N * m * 4 + 256;
 }
 
-// Sturm count: number of eigenvalues of the real symmetric tridiagonal (d, f)
-// that are smaller than x.
-template <typename R>
-__device__ int sturm_count(int N, const R* d, const R* f, R x, R pivmin) {
-  int cnt = 0;
-  R q = d[0] - x;
-  if (fabs((double)q) < (double)pivmin) q = -pivmin;
-  if (q < R(0)) ++cnt;
-  for (int i = 1; i < N; ++i) {
-    q = d[i] - x - f[i - 1] * f[i - 1] / q;
-    if (fabs((double)q) < (double)pivmin) q = -pivmin;
-    if (q < R(0)) ++cnt;
-  }
-  return cnt;
-}
-
-// LU with partial pivoting of the tridiagonal (T - lam I): on return dl holds
-// the multipliers, dd/du/du2 the three diagonals of U, piv[i] = 1 if rows i
-// and i+1 were interchanged.  Zero pivots are replaced by ``tiny``.
-template <typename R>
-__device__ void tri_lu(int N, const R* d, const R* f, R lam, R tiny, R* dl, R* dd, R* du, R* du2,
-                       int* piv) {
-  for (int i = 0; i < N; ++i) dd[i] = d[i] - lam;
-  for (int i = 0; i + 1 < N; ++i) { dl[i] = f[i]; du[i] = f[i]; du2[i] = R(0); }
-  for (int i = 0; i + 1 < N; ++i) {
-    if (fabs((double)dd[i]) >= fabs((double)dl[i])) {
-      piv[i] = 0;
-      if (dd[i] == R(0)) dd[i] = tiny;
-      const R fac = dl[i] / dd[i];
-      dl[i] = fac;
-      dd[i + 1] -= fac * du[i];
-    } else {
-      piv[i] = 1;
-      const R fac = dd[i] / dl[i];
-      dd[i] = dl[i];
-      dl[i] = fac;
-      const R tmp = du[i];
-      du[i] = dd[i + 1];
-      dd[i + 1] = tmp - fac * dd[i + 1];
-      if (i + 2 < N) {
-        du2[i] = du[i + 1];
-        du[i + 1] = -fac * du[i + 1];
-      }
-    }
-  }
-  if (dd[N - 1] == R(0)) dd[N - 1] = tiny;
-}
-
-// Solve (T - lam I) x = b with the factors of tri_lu, in place in b.
-template <typename R>
-__device__ void tri_solve(int N, const R* dl, const R* dd, const R* du, const R* du2,
-                          const int* piv, R* b) {
-  for (int i = 0; i + 1 < N; ++i) {
-    if (piv[i] == 0) {
-      b[i + 1] -= dl[i] * b[i];
-    } else {
-      const R t = b[i];
-      b[i] = b[i + 1];
-      b[i + 1] = t - dl[i] * b[i];
-    }
-  }
-  b[N - 1] /= dd[N - 1];
-  if (N > 1) b[N - 2] = (b[N - 2] - du[N - 2] * b[N - 1]) / dd[N - 2];
-  for (int i = N - 3; i >= 0; --i) b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) / dd[i];
-}
-
-template <typename R>
-__device__ void scale_unit(int N, R* z) {
-  R mx = R(0);
-  for (int i = 0; i < N; ++i) mx = fmax(mx, (R)fabs((double)z[i]));
-  if (!(mx > R(0)) || !isfinite((double)mx)) {
-    for (int i = 0; i < N; ++i) z[i] = R(1);
-    mx = R(1);
-  }
-  R s = R(0);
-  for (int i = 0; i < N; ++i) { z[i] /= mx; s += z[i] * z[i]; }
-  s = R(1) / sqrt_(s);
-  for (int i = 0; i < N; ++i) z[i] *= s;
-}
-
 template <typename T>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(1024)
 eig_small_kernel(int N, int m, T* A, double* lam_out, T* C1, unsigned char* ws) {
   using R = real_t<T>;
   extern __shared__ unsigned char smem_raw[];
@@ -390,11 +297,17 @@ eig_small_kernel(int N, int m, T* A, double* lam_out, T* C1, unsigned char* ws) 
     const R t = R(1) / (alpha * (alpha + ax0));
     for (int i = r0 + tid; i < N; i += nt) u[i] = (i == r0) ? u0 : A[i + j * ld];
     __syncthreads();
-    // p = t B u with B = A(r0:N, r0:N)
+    // p = t B u with B = A(r0:N, r0:N): one thread per row (coalesced down
+    // each column), two independent accumulators
     for (int i = r0 + tid; i < N; i += nt) {
-      T acc = zero_<T>();
-      for (int c = r0; c < N; ++c) fma_(acc, A[i + c * ld], u[c]);
-      p[i] = acc * t;
+      T acc0 = zero_<T>(), acc1 = zero_<T>();
+      int c = r0;
+      for (; c + 1 < N; c += 2) {
+        fma_(acc0, A[i + c * ld], u[c]);
+        fma_(acc1, A[i + (c + 1) * ld], u[c + 1]);
+      }
+      if (c < N) fma_(acc0, A[i + c * ld], u[c]);
+      p[i] = (acc0 + acc1) * t;
     }
     __syncthreads();
     // K = t (u^* p) / 2 (real: B is Hermitian) ; q = p - K u
@@ -404,14 +317,19 @@ eig_small_kernel(int N, int m, T* A, double* lam_out, T* C1, unsigned char* ws) 
     const R K = up * t * R(0.5);
     for (int i = r0 + tid; i < N; i += nt) p[i] = p[i] - K * u[i];
     __syncthreads();
-    // B -= u q^* + q u^*
-    const int w = N - r0;
-    for (int e = tid; e < w * w; e += nt) {
-      const int i = r0 + e % w, c = r0 + e / w;
-      T v = A[i + c * ld];
-      v = v - u[i] * conj_(p[c]);
-      v = v - p[i] * conj_(u[c]);
-      A[i + c * ld] = v;
+    // B -= u q^* + q u^*: one warp per column, lanes down the rows
+    {
+      const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+      for (int c = r0 + wid; c < N; c += nw) {
+        const T pc = conj_(p[c]), uc = conj_(u[c]);
+        T* col = A + (long long)c * ld;
+        for (int i = r0 + lane; i < N; i += 32) {
+          T v = col[i];
+          v = v - u[i] * pc;
+          v = v - p[i] * uc;
+          col[i] = v;
+        }
+      }
     }
     __syncthreads();
     if (tid == 0) {
@@ -478,8 +396,12 @@ eig_small_kernel(int N, int m, T* A, double* lam_out, T* C1, unsigned char* ws) 
     }
   }
   __syncthreads();
-  // clusters: re-orthogonalise against earlier members, then one more solve
+  // clusters: re-orthogonalise against the earlier members (classical
+  // Gram-Schmidt applied twice: all dot products first, one warp per member,
+  // then one update), then one more inverse-iteration solve
   const R ortol = R(1e-3) * tnorm;
+  R* dots = reinterpret_cast<R*>(u);  // smem, N >= m entries
+  const int lanec = tid & 31, widc = tid >> 5, nwc = nt >> 5;
   for (int k = 1; k < m; ++k) {
     int c0 = k;
     while (c0 > 0 && lamv[c0] - lamv[c0 - 1] <= ortol) --c0;
@@ -487,14 +409,20 @@ eig_small_kernel(int N, int m, T* A, double* lam_out, T* C1, unsigned char* ws) 
     R* zk = z + (size_t)k * N;
     for (int rep = 0; rep < 2; ++rep) {
       for (int pass = 0; pass < 2; ++pass) {
-        for (int l = c0; l < k; ++l) {
+        for (int l = c0 + widc; l < k; l += nwc) {
           const R* zl = z + (size_t)l * N;
-          R s = R(0);
-          for (int i = tid; i < N; i += nt) s += zl[i] * zk[i];
-          s = block_sum(s, red);
-          for (int i = tid; i < N; i += nt) zk[i] -= s * zl[i];
-          __syncthreads();
+          R sacc = R(0);
+          for (int i = lanec; i < N; i += 32) sacc += zl[i] * zk[i];
+          sacc = warp_sum(sacc);
+          if (lanec == 0) dots[l - c0] = sacc;
         }
+        __syncthreads();
+        for (int i = tid; i < N; i += nt) {
+          R acc = zk[i];
+          for (int l = c0; l < k; ++l) acc -= dots[l - c0] * z[(size_t)l * N + i];
+          zk[i] = acc;
+        }
+        __syncthreads();
       }
       if (tid == 0) {
         if (rep == 0) {
@@ -539,14 +467,14 @@ void eig_small(cudaStream_t st, int N, int m, T* Ap, double* lam, T* C1, void* w
   const size_t sm = 2 * (size_t)N * sizeof(T);
   if (sm > 48 * 1024) cudaFuncSetAttribute(eig_small_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   count_launch();
-  eig_small_kernel<T><<<1, 512, sm, st>>>(N, m, Ap, lam, C1, static_cast<unsigned char*>(ws));
+  eig_small_kernel<T><<<1, 1024, sm, st>>>(N, m, Ap, lam, C1, static_cast<unsigned char*>(ws));
 }
 
 // ------------------------------------------------------------------------
 // Selected columns of the Q factor of a Householder QR
 // ------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) thin_q_kernel(int N, int q, T* Y, int c0, int nq, T* Q, T* hb) {
+__global__ void __launch_bounds__(1024) thin_q_kernel(int N, int q, T* Y, int c0, int nq, T* Q, T* hb) {
   __shared__ real_t<T> red[32];
   T* uhead = hb;
   real_t<T>* tau = reinterpret_cast<real_t<T>*>(hb + q);
@@ -582,7 +510,7 @@ __global__ void __launch_bounds__(256) thin_q_kernel(int N, int q, T* Y, int c0,
 template <typename T>
 void thin_q(cudaStream_t st, int N, int q, T* Y, int c0, int nq, T* Q, T* ws) {
   count_launch();
-  thin_q_kernel<T><<<1, 256, 0, st>>>(N, q, Y, c0, nq, Q, ws);
+  thin_q_kernel<T><<<1, 1024, 0, st>>>(N, q, Y, c0, nq, Q, ws);
 }
 
 // ------------------------------------------------------------------------

@@ -42,4 +42,16 @@ void eig_small(cudaStream_t st, int N, int m, T* Ap, double* lam, T* C1, void* w
 template <typename T>
 void thin_q(cudaStream_t st, int N, int q, T* Y, int c0, int nq, T* Q, T* ws);
 
+// Cluster versions (eig_cluster.cu): the same results computed on a
+// thread-block cluster of 16 (or 8) SMs.  Return false, with nothing
+// launched, when the cluster configuration cannot run (caller falls back to
+// the single-CTA kernels above).  ``ws`` holds eig_fast_ws_bytes(N, m, elem)
+// bytes; fail_dev (one int) reports whether the Cholesky-QR step fell back to
+// Gram-Schmidt.  thin_q_fast uses ``ws`` for 2q elements like thin_q.
+size_t eig_fast_ws_bytes(int N, int m, size_t elem);
+template <typename T>
+bool eig_small_fast(cudaStream_t st, int N, int m, T* Ap, double* lam, T* C1, void* ws, int* fail_dev);
+template <typename T>
+bool thin_q_fast(cudaStream_t st, int N, int q, T* Y, int c0, int nq, T* Q, T* ws);
+
 }  // namespace mpl
