@@ -172,12 +172,17 @@ trsm_step_kernel(int n, int nblk, int k, const T* __restrict__ L, long long ldl,
       }
     }
     __syncthreads();
+    T upd[CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) upd[q] = zero_<T>();
 #pragma unroll 4
     for (int kk = 0; kk < NB; ++kk) {
       const T a = Ls[kk * LDS + r];
 #pragma unroll
-      for (int q = 0; q < CPT; ++q) acc[q] = acc[q] - a * Ys[kk * CT + cg * CPT + q];
+      for (int q = 0; q < CPT; ++q) fma_(upd[q], a, Ys[kk * CT + cg * CPT + q]);
     }
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) acc[q] = acc[q] - upd[q];
     __syncthreads();
   }
   const bool diag = only_diag || (BACK ? (i == k - 1) : (i == k + 1));

@@ -13,11 +13,15 @@
 //     deterministic); each CTA applies the rank-2 update to its own columns.
 // Two cluster barriers per step order the publication and the reads.  The
 // tridiagonal eigenproblem is then solved for the m wanted pairs by
-// Sturm-sequence bisection and inverse iteration (one thread per pair),
+// Sturm-sequence multisection and inverse iteration (one warp per pair),
 // followed by two Cholesky-QR passes over the m vectors (they are orthogonal
 // up to u ||T|| / gap; the passes restore orthogonality inside clusters), and
 // the vectors are back-transformed by one warp each over many CTAs.
 #include <cooperative_groups.h>
+
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "small.cuh"
 #include "small_dev.cuh"
@@ -143,34 +147,35 @@ tridiag_cluster_kernel(int N, const T* __restrict__ Ag, T* __restrict__ U, T* __
 }
 
 // ------------------------------------------------------------------------
-// Eigenpairs of the tridiagonal: bisection, inverse iteration, Cholesky-QR
+// Eigenpairs of the tridiagonal
 // ------------------------------------------------------------------------
+// Real symmetric tridiagonal (d, f) from the Hermitian one (d, e) by the
+// diagonal unitary similarity delta (delta_0 = 1, delta_{i+1} = delta_i e_i/|e_i|).
 template <typename T>
-__global__ void __launch_bounds__(1024)
-tri_eigvec_kernel(int N, int m, const real_t<T>* __restrict__ dd_in, const T* __restrict__ e_in,
-                  T* delta, real_t<T>* z, real_t<T>* lu, int* piv, real_t<T>* G, double* lam_out,
-                  int* fail) {
+__global__ void tri_real_kernel(int N, const T* __restrict__ e_in, T* delta, real_t<T>* f) {
   using R = real_t<T>;
-  extern __shared__ __align__(16) unsigned char smem[];
-  R* d = reinterpret_cast<R*>(smem);
-  R* f = d + N;
-  R* lamv = f + N;
-  __shared__ int bad;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < N; i += nt) d[i] = dd_in[i];
-  if (tid == 0) {
-    bad = 0;
-    delta[0] = from_real<T>(R(1));
-    for (int i = 0; i + 1 < N; ++i) {
-      const T e = e_in[i];
-      const R ae = sqrt_(abs2_(e));
-      f[i] = ae;
-      const T ph = ae > R(0) ? e * (R(1) / ae) : from_real<T>(R(1));
-      delta[i + 1] = delta[i] * ph;
-    }
-    f[N - 1] = R(0);
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  delta[0] = from_real<T>(R(1));
+  for (int i = 0; i + 1 < N; ++i) {
+    const T e = e_in[i];
+    const R ae = sqrt_(abs2_(e));
+    f[i] = ae;
+    const T ph = ae > R(0) ? e * (R(1) / ae) : from_real<T>(R(1));
+    delta[i + 1] = delta[i] * ph;
   }
-  __syncthreads();
+  f[N - 1] = R(0);
+}
+
+// One warp per wanted eigenvalue: multisection (the 32 lanes evaluate the
+// Sturm count at 32 interior points, shrinking the bracket 33-fold per round)
+// followed by inverse iteration on lane 0.
+template <typename R>
+__global__ void __launch_bounds__(128)
+tri_multisect_kernel(int N, int m, const R* __restrict__ d, const R* __restrict__ f, R* lamv, R* z, R* lu,
+                     int* piv) {
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (k >= m) return;
   R glo = d[0], ghi = d[0], tnorm = R(0);
   for (int i = 0; i < N; ++i) {
     const R r = (i > 0 ? f[i - 1] : R(0)) + f[i];
@@ -181,33 +186,52 @@ tri_eigvec_kernel(int N, int m, const real_t<T>* __restrict__ dd_in, const T* __
   const R eps = (sizeof(R) == 8) ? R(1.1102230246251565e-16) : R(5.9604645e-08);
   const R pivmin = (sizeof(R) == 8 ? R(1e-290) : R(1e-35)) + tnorm * eps * eps;
   const R spread = fmax(ghi - glo, tnorm * eps);
-  glo -= spread * eps * R(4) + pivmin;
-  ghi += spread * eps * R(4) + pivmin;
-  for (int k = tid; k < m; k += nt) {
-    R lo = glo, hi = ghi;
-    for (int it = 0; it < 256; ++it) {
-      const R mid = R(0.5) * (lo + hi);
-      if (mid <= lo || mid >= hi) break;
-      if (hi - lo <= R(2) * eps * fmax((R)fabs((double)lo), (R)fabs((double)hi)) + pivmin) break;
-      if (sturm_count(N, d, f, mid, pivmin) > k) hi = mid;
-      else lo = mid;
+  R lo = glo - (spread * eps * R(4) + pivmin);
+  R hi = ghi + (spread * eps * R(4) + pivmin);
+  for (int round = 0; round < 64; ++round) {
+    if (hi - lo <= R(2) * eps * fmax((R)fabs((double)lo), (R)fabs((double)hi)) + pivmin) break;
+    const R x = lo + (hi - lo) * (R)(lane + 1) / R(33);
+    const bool above = (x > lo && x < hi) && sturm_count(N, d, f, x, pivmin) > k;
+    const unsigned mask = __ballot_sync(0xffffffffu, above);
+    // counts are monotone in x: the first lane with count > k bounds from above
+    R nlo = lo, nhi = hi;
+    if (mask) {
+      const int l = __ffs(mask) - 1;
+      nhi = lo + (hi - lo) * (R)(l + 1) / R(33);
+      if (l > 0) nlo = lo + (hi - lo) * (R)l / R(33);
+    } else {
+      nlo = lo + (hi - lo) * R(32) / R(33);
     }
-    lamv[k] = R(0.5) * (lo + hi);
+    if (!(nhi < hi || nlo > lo)) break;  // no progress (rounding): converged
+    lo = nlo;
+    hi = nhi;
   }
-  __syncthreads();
-  const R tiny = eps * tnorm + pivmin;
-  for (int k = tid; k < m; k += nt) {
+  const R lam = R(0.5) * (lo + hi);
+  if (lane == 0) {
+    lamv[k] = lam;
+    const R tiny = eps * tnorm + pivmin;
     R* zk = z + (size_t)k * N;
     R* dl = lu + (size_t)k * 4 * N;
-    tri_lu(N, d, f, lamv[k], tiny, dl, dl + N, dl + 2 * N, dl + 3 * N, piv + (size_t)k * N);
+    int* pv = piv + (size_t)k * N;
+    tri_lu(N, d, f, lam, tiny, dl, dl + N, dl + 2 * N, dl + 3 * N, pv);
     for (int i = 0; i < N; ++i) zk[i] = R(1) + R(0.25) * (R)(((i + 1) * 7919 + (k + 1) * 104729) % 101) / R(101);
     for (int it = 0; it < 3; ++it) {
-      tri_solve(N, dl, dl + N, dl + 2 * N, dl + 3 * N, piv + (size_t)k * N, zk);
+      tri_solve(N, dl, dl + N, dl + 2 * N, dl + 3 * N, pv, zk);
       scale_unit(N, zk);
     }
   }
+}
+
+// Two Cholesky-QR passes over the m vectors (Z <- Z L^-T, Z^T Z = L L^T);
+// Gram-Schmidt inside eigenvalue clusters if the Cholesky breaks down.
+template <typename R>
+__global__ void __launch_bounds__(1024)
+cholqr_vectors_kernel(int N, int m, const R* __restrict__ d, const R* __restrict__ f, const R* lamv, R* z,
+                      R* lu, int* piv, R* G, double* lam_out, int* fail) {
+  __shared__ int bad;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) bad = 0;
   __syncthreads();
-  // two Cholesky-QR passes: Z <- Z L^-T with Z^T Z = L L^T
   for (int pass = 0; pass < 2 && m > 1; ++pass) {
     for (int e = tid; e < m * m; e += nt) {
       const int a = e % m, b = e / m;
@@ -219,7 +243,7 @@ tri_eigvec_kernel(int N, int m, const real_t<T>* __restrict__ dd_in, const T* __
       G[a + (size_t)b * m] = s;
     }
     __syncthreads();
-    for (int jj = 0; jj < m; ++jj) {  // Cholesky of the m x m Gram matrix (lower, in place)
+    for (int jj = 0; jj < m; ++jj) {
       if (tid == 0) {
         R s = G[jj + (size_t)jj * m];
         for (int l = 0; l < jj; ++l) s -= G[jj + (size_t)l * m] * G[jj + (size_t)l * m];
@@ -237,7 +261,7 @@ tri_eigvec_kernel(int N, int m, const real_t<T>* __restrict__ dd_in, const T* __
       __syncthreads();
     }
     if (bad) break;
-    for (int i = tid; i < N; i += nt) {  // row i: y L^T = z  (forward over columns)
+    for (int i = tid; i < N; i += nt) {
       for (int b = 0; b < m; ++b) {
         R v = z[(size_t)b * N + i];
         for (int a = 0; a < b; ++a) v -= z[(size_t)a * N + i] * G[b + (size_t)a * m];
@@ -247,9 +271,8 @@ tri_eigvec_kernel(int N, int m, const real_t<T>* __restrict__ dd_in, const T* __
     __syncthreads();
   }
   if (bad) {
-    // Cholesky-QR failed (nearly parallel vectors of a repeated eigenvalue):
-    // re-orthogonalise inside clusters (gaps below 1e-3 ||T||_1) by
-    // Gram-Schmidt, twice, then one more inverse-iteration solve
+    R tnorm = R(0);
+    for (int i = 0; i < N; ++i) tnorm = fmax(tnorm, (R)fabs((double)d[i]) + (i > 0 ? f[i - 1] : R(0)) + f[i]);
     const R ortol = R(1e-3) * tnorm;
     R* dots = G;
     const int lanec = tid & 31, widc = tid >> 5, nwc = nt >> 5;
@@ -429,8 +452,26 @@ qform_kernel(int N, int q, const T* __restrict__ Y, const T* __restrict__ uhead,
 // ------------------------------------------------------------------------
 // host
 // ------------------------------------------------------------------------
+// Cluster size the device can co-schedule for ``kernel`` (16, else 8, else
+// none), cached per (device, kernel, shared-memory need).
 template <typename K>
 static int pick_cluster(K kernel, size_t smem_of_cl(int), int* out_cl, size_t* out_sm) {
+  static std::mutex mu;
+  static std::map<std::pair<std::pair<int, const void*>, size_t>, std::pair<int, size_t>> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_pair(std::make_pair(dev, reinterpret_cast<const void*>(kernel)), smem_of_cl(16));
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      *out_cl = it->second.first;
+      *out_sm = it->second.second;
+      return it->second.first > 0;
+    }
+  }
+  int found_cl = 0;
+  size_t found_sm = 0;
   int cand[2] = {16, 8};
   for (int ci = 0; ci < 2; ++ci) {
     const int CL = cand[ci];
@@ -461,12 +502,16 @@ static int pick_cluster(K kernel, size_t smem_of_cl(int), int* out_cl, size_t* o
       continue;
     }
     if (nclusters >= 1) {
-      *out_cl = CL;
-      *out_sm = sm;
-      return 1;
+      found_cl = CL;
+      found_sm = sm;
+      break;
     }
   }
-  return 0;
+  std::lock_guard<std::mutex> lock(mu);
+  cache[key] = std::make_pair(found_cl, found_sm);
+  *out_cl = found_cl;
+  *out_sm = found_sm;
+  return found_cl > 0;
 }
 
 template <typename T>
@@ -479,8 +524,8 @@ template <typename T> int ClusterSizes<T>::N_ = 0;
 template <typename T> int ClusterSizes<T>::q_ = 0;
 
 size_t eig_fast_ws_bytes(int N, int m, size_t elem) {
-  return (size_t)N * N * elem + 5 * (size_t)N * elem + 3 * (size_t)N * 8 + 5 * (size_t)N * m * 8 +
-         (size_t)N * m * 4 + (size_t)m * m * 8 + 1024;
+  return (size_t)N * N * elem + 5 * (size_t)N * elem + 4 * (size_t)N * 8 + 5 * (size_t)N * m * 8 +
+         (size_t)N * m * 4 + (size_t)m * m * 8 + (size_t)m * 8 + 1024;
 }
 
 template <typename T>
@@ -520,15 +565,20 @@ bool eig_small_fast(cudaStream_t st, int N, int m, T* Ap, double* lam, T* C1, vo
   R* z = d + N;
   R* lu = z + (size_t)N * m;
   R* G = lu + 4 * (size_t)N * m;
-  int* piv = reinterpret_cast<int*>(G + (size_t)m * m);
+  int* piv = reinterpret_cast<int*>(G + (size_t)m * m + N + m);
   count_launch();
   if (launch_cluster<T>(tridiag_cluster_kernel<T>, CL, sm, st, N, Ap, U, uh, tau, d, e) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  const size_t sm2 = (2 * (size_t)N + (size_t)m) * sizeof(R) + 64;
+  R* f = G + (size_t)m * m;                 // N reals after the Gram block
+  R* lamv = f + N;                          // m reals
   count_launch();
-  tri_eigvec_kernel<T><<<1, 1024, sm2, st>>>(N, m, d, e, delta, z, lu, piv, G, lam, fail_dev);
+  tri_real_kernel<T><<<1, 32, 0, st>>>(N, e, delta, f);
+  count_launch();
+  tri_multisect_kernel<R><<<ceil_div(m, 4), 128, 0, st>>>(N, m, d, f, lamv, z, lu, piv);
+  count_launch();
+  cholqr_vectors_kernel<R><<<1, 1024, 0, st>>>(N, m, d, f, lamv, z, lu, piv, G, lam, fail_dev);
   count_launch();
   backtransform_kernel<T><<<ceil_div(m, 4), 128, 0, st>>>(N, m, z, delta, U, uh, tau, C1);
   return true;
