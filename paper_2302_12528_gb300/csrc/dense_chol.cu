@@ -1,17 +1,18 @@
 // Dense lower-precision Cholesky factor and the multi-right-hand-side
-// triangular sweeps that apply T = L^-* L^-1 (Section 5.1: "solving two
-// triangular systems in single precision").
+// triangular sweeps that apply T = L^-* L^-1 (Section 5.1: the preconditioner
+// is applied as a forward and a backward triangular solve in the lower
+// precision).
 //
 // Factor: blocked right-looking.  Per NB-column step k one CTA factors the
 // diagonal block in shared memory and also writes its inverse Dinv_k; the
 // panel L_ik = A_ik Dinv_k^* and the lower-triangular trailing update
 // A_ij -= L_ik L_jk^* are GEMMs.  Dinv is kept for the sweeps.
 //
-// Sweeps: one launch per block row.  Forward step k subtracts L_ik Y_k from
-// every block row i > k (all m right-hand sides at once, staged in shared
-// memory) and the CTA that owns row block k+1 finishes Y_{k+1} = Dinv_{k+1}
-// B_{k+1} in the same launch.  The backward sweep does the same with
-// (L_ki)^* and Dinv^*.
+// Sweeps: one launch per sweep block row (NBS rows, NBS dividing NB).
+// Forward step k subtracts L_ik Y_k from every block row i > k (CT
+// right-hand sides per CTA, staged in shared memory) and the CTAs that own
+// block row k+1 finish Y_{k+1} = Dinv_{k+1} B_{k+1} in the same launch.  The
+// backward sweep does the same with (L_ki)^* and Dinv^*.
 #include "dense_chol.cuh"
 
 namespace mpl {
@@ -129,123 +130,170 @@ void dense_cholesky(cudaStream_t st, DenseFactor<T>& F, T* tmp, int* info, Scrat
 // ------------------------------------------------------------------------
 // triangular sweeps
 // ------------------------------------------------------------------------
-constexpr int SWEEP_CT = 32;  // right-hand sides per CTA
+// Sweep geometry.  A step of the sweep is one launch whose latency is that of
+// a single CTA (the one that also finishes the next diagonal block), so the
+// sweep block NBS is smaller than the factor block: the diagonal NBS x NBS
+// sub-blocks of the stored Dinv_k are the inverses of the diagonal
+// sub-blocks of the triangular L_kk.  FP32 types use NBS = 64, FP64 types
+// 32 (their FMA rate is 1/64 of FP32, so the per-CTA critical path is kept
+// short); every CTA handles CT = 32 right-hand sides with a 16 x 16 thread
+// grid, each thread owning an (NBS/16) x 2 register tile.
+template <typename T> struct Sweep { static constexpr int NBS = 32, CT = 32; };
+template <> struct Sweep<float> { static constexpr int NBS = 64, CT = 32; };
+template <> struct Sweep<zf> { static constexpr int NBS = 64, CT = 32; };
 
-template <typename T, int NB, bool BACK>
+template <typename T, int NBS, int CT, bool BACK>
 __global__ void __launch_bounds__(256)
-trsm_step_kernel(int n, int nblk, int k, const T* __restrict__ L, long long ldl,
-                 const T* __restrict__ Dinv, T* B, long long ldb, int m, int only_diag) {
-  constexpr int CT = SWEEP_CT;
-  constexpr int LDS = NB + 1;
-  constexpr int CG = 256 / NB;
-  constexpr int CPT = CT / CG;
+trsm_step_kernel(int n, int nsb, int k, const T* __restrict__ L, long long ldl, const T* __restrict__ Dinv,
+                 int dnb, T* B, long long ldb, int m, int only_diag) {
+  constexpr int LDS = NBS + 1;
+  constexpr int TM = NBS / 16, TN = CT / 16;
   extern __shared__ unsigned char sm[];
   T* Ls = reinterpret_cast<T*>(sm);  // Ls[kk * LDS + r]
-  T* Ys = Ls + NB * LDS;             // Ys[kk * CT + c]
+  T* Ys = Ls + NBS * LDS;            // Ys[kk * CT + c]
   const int tid = threadIdx.x;
   int i;
-  if (only_diag) i = BACK ? nblk - 1 : 0;
+  if (only_diag) i = BACK ? nsb - 1 : 0;
   else i = BACK ? (k - 1 - (int)blockIdx.x) : (k + 1 + (int)blockIdx.x);
   const int ct0 = blockIdx.y * CT;
   const int cw = min(CT, m - ct0);
-  const int r0 = i * NB, rb = min(NB, n - r0);
-  const int r = tid % NB, cg = tid / NB;
+  const int r0 = i * NBS, rb = min(NBS, n - r0);
+  const int tr = tid & 15, tc = tid >> 4;
 
-  T acc[CPT];
-#pragma unroll
-  for (int q = 0; q < CPT; ++q) {
-    const int c = cg * CPT + q;
-    acc[q] = (r < rb && c < cw) ? B[(r0 + r) + (long long)(ct0 + c) * ldb] : zero_<T>();
-  }
+  // Programmatic dependent launch: the next step may be scheduled now; the
+  // factor tile L_ik is final before the sweep starts, so it is staged
+  // before waiting for the previous step's B to be complete and visible.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int rk0 = k * NBS, kb = min(NBS, n - rk0);
   if (!only_diag) {
-    const int rk0 = k * NB, kb = min(NB, n - rk0);
-    for (int e = tid; e < NB * CT; e += 256) {
-      const int kk = e % NB, c = e / NB;
-      Ys[kk * CT + c] = (kk < kb && c < cw) ? B[(rk0 + kk) + (long long)(ct0 + c) * ldb] : zero_<T>();
-    }
-    for (int e = tid; e < NB * NB; e += 256) {
-      const int a = e % NB, b = e / NB;
+    for (int e = tid; e < NBS * NBS; e += 256) {
+      const int a = e % NBS, b = e / NBS;
       if (!BACK) {  // L_ik(r = a, kk = b)
         Ls[b * LDS + a] = (a < rb && b < kb) ? L[(r0 + a) + (long long)(rk0 + b) * ldl] : zero_<T>();
       } else {      // (L_ki)^*(r = b, kk = a) = conj(L_ki(a, b))
         Ls[a * LDS + b] = (a < kb && b < rb) ? conj_(L[(rk0 + a) + (long long)(r0 + b) * ldl]) : zero_<T>();
       }
     }
-    __syncthreads();
-    T upd[CPT];
+  }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+
+  T acc[TM][TN];
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) upd[q] = zero_<T>();
-#pragma unroll 4
-    for (int kk = 0; kk < NB; ++kk) {
-      const T a = Ls[kk * LDS + r];
+  for (int a = 0; a < TM; ++a)
 #pragma unroll
-      for (int q = 0; q < CPT; ++q) fma_(upd[q], a, Ys[kk * CT + cg * CPT + q]);
+    for (int b = 0; b < TN; ++b) {
+      const int r = tr + 16 * a, c = tc + 16 * b;
+      acc[a][b] = (r < rb && c < cw) ? B[(r0 + r) + (long long)(ct0 + c) * ldb] : zero_<T>();
     }
+  if (!only_diag) {
+    for (int e = tid; e < NBS * CT; e += 256) {
+      const int kk = e % NBS, c = e / NBS;
+      Ys[kk * CT + c] = (kk < kb && c < cw) ? B[(rk0 + kk) + (long long)(ct0 + c) * ldb] : zero_<T>();
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < NBS; ++kk) {
+      T av[TM], bv[TN];
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) acc[q] = acc[q] - upd[q];
+      for (int a = 0; a < TM; ++a) av[a] = -Ls[kk * LDS + tr + 16 * a];
+#pragma unroll
+      for (int b = 0; b < TN; ++b) bv[b] = Ys[kk * CT + tc + 16 * b];
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TN; ++b) fma_(acc[a][b], av[a], bv[b]);
+    }
     __syncthreads();
   }
   const bool diag = only_diag || (BACK ? (i == k - 1) : (i == k + 1));
   if (diag) {
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) Ys[r * CT + cg * CPT + q] = acc[q];
-    const T* Di = Dinv + (size_t)i * NB * NB;
-    for (int e = tid; e < NB * NB; e += 256) {
-      const int a = e % NB, b = e / NB;
-      if (!BACK) Ls[b * LDS + a] = Di[a + b * NB];           // Dinv(r = a, kk = b)
-      else Ls[a * LDS + b] = conj_(Di[a + b * NB]);          // Dinv^*(r = b, kk = a)
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TN; ++b) Ys[(tr + 16 * a) * CT + tc + 16 * b] = acc[a][b];
+    // diagonal sub-block of Dinv for sweep block i (ld dnb)
+    const int fb = r0 / dnb, off = r0 % dnb;
+    const T* Di = Dinv + (size_t)fb * dnb * dnb + off + (size_t)off * dnb;
+    for (int e = tid; e < NBS * NBS; e += 256) {
+      const int a = e % NBS, b = e / NBS;
+      const T v = (a < rb && b < rb) ? Di[a + (size_t)b * dnb] : zero_<T>();
+      if (!BACK) Ls[b * LDS + a] = v;           // Dinv(r = a, kk = b)
+      else Ls[a * LDS + b] = conj_(v);          // Dinv^*(r = b, kk = a)
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) acc[q] = zero_<T>();
-#pragma unroll 4
-    for (int kk = 0; kk < NB; ++kk) {
-      const T a = Ls[kk * LDS + r];
+    for (int a = 0; a < TM; ++a)
 #pragma unroll
-      for (int q = 0; q < CPT; ++q) fma_(acc[q], a, Ys[kk * CT + cg * CPT + q]);
+      for (int b = 0; b < TN; ++b) acc[a][b] = zero_<T>();
+#pragma unroll 4
+    for (int kk = 0; kk < NBS; ++kk) {
+      T av[TM], bv[TN];
+#pragma unroll
+      for (int a = 0; a < TM; ++a) av[a] = Ls[kk * LDS + tr + 16 * a];
+#pragma unroll
+      for (int b = 0; b < TN; ++b) bv[b] = Ys[kk * CT + tc + 16 * b];
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TN; ++b) fma_(acc[a][b], av[a], bv[b]);
     }
   }
 #pragma unroll
-  for (int q = 0; q < CPT; ++q) {
-    const int c = cg * CPT + q;
-    if (r < rb && c < cw) B[(r0 + r) + (long long)(ct0 + c) * ldb] = acc[q];
-  }
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TN; ++b) {
+      const int r = tr + 16 * a, c = tc + 16 * b;
+      if (r < rb && c < cw) B[(r0 + r) + (long long)(ct0 + c) * ldb] = acc[a][b];
+    }
 }
 
 template <typename T>
 static size_t sweep_smem() {
-  constexpr int NB = CholBlock<T>::NB;
-  return ((size_t)NB * (NB + 1) + (size_t)NB * SWEEP_CT) * sizeof(T);
+  constexpr int NBS = Sweep<T>::NBS, CT = Sweep<T>::CT;
+  return ((size_t)NBS * (NBS + 1) + (size_t)NBS * CT) * sizeof(T);
+}
+
+template <typename T, bool BACK>
+static void dense_sweep(cudaStream_t st, const DenseFactor<T>& F, T* B, long long ldb, int m) {
+  constexpr int NB = CholBlock<T>::NB, NBS = Sweep<T>::NBS, CT = Sweep<T>::CT;
+  static_assert(NB % NBS == 0, "sweep block must divide the factor block");
+  const int n = F.n, nsb = ceil_div(n, NBS);
+  const size_t sm = sweep_smem<T>();
+  auto kern = trsm_step_kernel<T, NBS, CT, BACK>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const int cty = ceil_div(m, CT);
+  count_launch();
+  kern<<<dim3(1, cty), 256, sm, st>>>(n, nsb, BACK ? nsb : -1, F.L, F.ldl, F.Dinv, NB, B, ldb, m, 1);
+  // FP32 sweeps: the remaining steps are programmatic dependent launches of
+  // one another (a step is latency-bound).  FP64 steps are bound by the FP64
+  // pipe; early-scheduled CTAs would share SMs with running ones, so they are
+  // ordinary stream-ordered launches (griddepcontrol is then a no-op).
+  constexpr bool kPDL = sizeof(real_t<T>) == 4;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = kPDL ? 1 : 0;
+  for (int s = 1; s < nsb; ++s) {
+    const int k = BACK ? nsb - s : s - 1;  // forward: rows > k; backward: rows < k
+    cfg.gridDim = dim3(BACK ? k : nsb - 1 - k, cty);
+    count_launch();
+    cudaLaunchKernelEx(&cfg, kern, n, nsb, k, (const T*)F.L, (long long)F.ldl, (const T*)F.Dinv, NB, B, ldb, m, 0);
+  }
 }
 
 template <typename T>
 void dense_trsm_fwd(cudaStream_t st, const DenseFactor<T>& F, T* B, long long ldb, int m) {
-  constexpr int NB = CholBlock<T>::NB;
-  const int nblk = F.nblk, n = F.n;
-  const size_t sm = sweep_smem<T>();
-  cudaFuncSetAttribute(trsm_step_kernel<T, NB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  const int cty = ceil_div(m, SWEEP_CT);
-  count_launch();
-  trsm_step_kernel<T, NB, false><<<dim3(1, cty), 256, sm, st>>>(n, nblk, -1, F.L, F.ldl, F.Dinv, B, ldb, m, 1);
-  for (int k = 0; k + 1 < nblk; ++k) {
-    count_launch();
-    trsm_step_kernel<T, NB, false><<<dim3(nblk - 1 - k, cty), 256, sm, st>>>(n, nblk, k, F.L, F.ldl, F.Dinv, B, ldb, m, 0);
-  }
+  dense_sweep<T, false>(st, F, B, ldb, m);
 }
 
 template <typename T>
 void dense_trsm_bwd(cudaStream_t st, const DenseFactor<T>& F, T* B, long long ldb, int m) {
-  constexpr int NB = CholBlock<T>::NB;
-  const int nblk = F.nblk, n = F.n;
-  const size_t sm = sweep_smem<T>();
-  cudaFuncSetAttribute(trsm_step_kernel<T, NB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  const int cty = ceil_div(m, SWEEP_CT);
-  count_launch();
-  trsm_step_kernel<T, NB, true><<<dim3(1, cty), 256, sm, st>>>(n, nblk, nblk, F.L, F.ldl, F.Dinv, B, ldb, m, 1);
-  for (int k = nblk - 1; k >= 1; --k) {
-    count_launch();
-    trsm_step_kernel<T, NB, true><<<dim3(k, cty), 256, sm, st>>>(n, nblk, k, F.L, F.ldl, F.Dinv, B, ldb, m, 0);
-  }
+  dense_sweep<T, true>(st, F, B, ldb, m);
 }
 
 template <typename T>

@@ -616,9 +616,38 @@ bool thin_q_fast(cudaStream_t st, int N, int q, T* Y, int c0, int nq, T* Q, T* h
   return true;
 }
 
+template <typename T>
+bool qr_cluster_inplace(cudaStream_t st, int N, int q, T* Y, T* hb) {
+  using R = real_t<T>;
+  ClusterSizes<T>::N_ = N;
+  ClusterSizes<T>::q_ = q;
+  int CL = 0;
+  size_t sm = 0;
+  if (!pick_cluster(qr_cluster_kernel<T>, &ClusterSizes<T>::qr, &CL, &sm)) return false;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL);
+  cfg.blockDim = dim3(CLUSTER_THREADS);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  count_launch();
+  if (cudaLaunchKernelEx(&cfg, qr_cluster_kernel<T>, N, q, Y, hb, reinterpret_cast<R*>(hb + q)) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
 #define MPL_INST_FAST(T)                                                                          \
   template bool eig_small_fast<T>(cudaStream_t, int, int, T*, double*, T*, void*, int*);          \
-  template bool thin_q_fast<T>(cudaStream_t, int, int, T*, int, int, T*, T*);
+  template bool thin_q_fast<T>(cudaStream_t, int, int, T*, int, int, T*, T*);                     \
+  template bool qr_cluster_inplace<T>(cudaStream_t, int, int, T*, T*);
 MPL_INST_FAST(float)
 MPL_INST_FAST(double)
 MPL_INST_FAST(zf)

@@ -17,6 +17,8 @@
 // their eigenvectors with modified Gram-Schmidt inside eigenvalue clusters
 // (clusters: gaps below 1e-3 ||T||_1), and back-transformation through the
 // reflectors.  Only the m wanted eigenvectors are formed.
+#include <algorithm>
+
 #include "small.cuh"
 #include "small_dev.cuh"
 
@@ -134,6 +136,30 @@ tsqr_merge_kernel(int cnt, int m, const TQ* __restrict__ Rin, TQ* Rout, TQ* slot
   }
 }
 
+// Stack cnt R factors (m x m each, consecutive) into a (cnt m) x m matrix.
+template <typename TQ>
+__global__ void stack_r_kernel(int cnt, int m, const TQ* __restrict__ Rin, TQ* Y) {
+  const long long rows = (long long)cnt * m;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < rows * m;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e % rows;
+    const int c = (int)(e / rows);
+    const long long q = i / m, ii = i % m;
+    Y[e] = Rin[q * m * m + ii + (long long)c * m];
+  }
+}
+
+// Upper triangle of the leading m x m block of Y (ld ldy) into R (m x m).
+template <typename TQ>
+__global__ void extract_r_kernel(int m, const TQ* __restrict__ Y, long long ldy, TQ* R) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
+    const int i = e % m, c = e / m;
+    R[e] = (i <= c) ? Y[i + (long long)c * ldy] : zero_<TQ>();
+  }
+}
+
+constexpr int TSQR_CLUSTER_MAX = 16;  // R factors stacked for the cluster QR
+
 template <typename T, typename TQ>
 void tsqr_r(cudaStream_t st, int n, int m, const T* W, long long ldw, TQ* R, TQ* ws) {
   int b = 0;
@@ -149,7 +175,31 @@ void tsqr_r(cudaStream_t st, int n, int m, const T* W, long long ldw, TQ* R, TQ*
   int cnt = nleaf;
   TQ* src = Ra;
   TQ* dst = Rb;
-  while (cnt > 1) {
+  while (cnt > TSQR_CLUSTER_MAX) {
+    const int groups = ceil_div(cnt, TSQR_G);
+    count_launch();
+    tsqr_merge_kernel<TQ><<<groups, 256, 0, st>>>(cnt, m, src, dst, slots, slot, hbuf);
+    cnt = groups;
+    TQ* t = src;
+    src = dst;
+    dst = t;
+  }
+  if (cnt == 1) {
+    cudaMemcpyAsync(R, src, sizeof(TQ) * m * m, cudaMemcpyDeviceToDevice, st);
+    return;
+  }
+  // the last <= 16 factors: one Householder QR of the stacked matrix on a
+  // thread-block cluster (the slots area holds cnt m x m >= the stack)
+  TQ* Y = slots;
+  const long long tot = (long long)cnt * m * m;
+  count_launch();
+  stack_r_kernel<TQ><<<(int)std::min<long long>((tot + 255) / 256, 4 * NUM_SMS), 256, 0, st>>>(cnt, m, src, Y);
+  if (qr_cluster_inplace<TQ>(st, cnt * m, m, Y, hbuf)) {
+    count_launch();
+    extract_r_kernel<TQ><<<ceil_div((long long)m * m, 256), 256, 0, st>>>(m, Y, (long long)cnt * m, R);
+    return;
+  }
+  while (cnt > 1) {  // no cluster: single-CTA merges
     const int groups = ceil_div(cnt, TSQR_G);
     TQ* out = (groups == 1) ? R : dst;
     count_launch();
@@ -158,9 +208,7 @@ void tsqr_r(cudaStream_t st, int n, int m, const T* W, long long ldw, TQ* R, TQ*
     TQ* t = src;
     src = dst;
     dst = t;
-    if (groups == 1) return;
   }
-  cudaMemcpyAsync(R, Ra, sizeof(TQ) * m * m, cudaMemcpyDeviceToDevice, st);
 }
 
 // ------------------------------------------------------------------------
