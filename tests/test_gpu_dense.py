@@ -43,7 +43,13 @@ def test_apply_A_parity(cplx, n, ncols):
     h.apply_A(torch_dev(Xt), Y, ncols)
     ref = A @ Xt.T
     got = to_np(Y).T
-    bound = 2 * n * U_H * np.linalg.norm(np.abs(A) @ np.abs(Xt.T))
+    if cplx:
+        # complex FP64 products use three real products (Gauss form); its error
+        # bound (Higham 1992) carries (|re|+|im|) magnitudes in place of |.|
+        mag = (np.abs(A.real) + np.abs(A.imag)) @ (np.abs(Xt.T.real) + np.abs(Xt.T.imag))
+        bound = 2 * (n + 4) * U_H * np.linalg.norm(mag)
+    else:
+        bound = 2 * n * U_H * np.linalg.norm(np.abs(A) @ np.abs(Xt.T))
     assert np.linalg.norm(got - ref) <= bound
     # lower-precision copy of A (stage 1)
     Xl = Xt.astype(np.complex64 if cplx else np.float32)
