@@ -11,6 +11,10 @@ complex Gaussian).  Prints one JSON line.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload NAME] [--policy mp] [--no-fp64] [--no-e2e]
                   [--no-cpu-baseline]
+  profiling helpers (their lines are marked as not bench values):
+                  [--profile-iters I] [--n N] [--kernel-probe apply|precond|eig]
+  With MPL_PROFILE_RANGE=a:b set, the library brackets working-precision
+  iterations a..b with cudaProfilerStart/Stop (for ncu --profile-from-start off).
 
 --impl reference times the CPU oracle (oracle/, NumPy/SciPy on the host
 cores) on a bounded sample of the same workload: the lower-precision factor
@@ -54,6 +58,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling runs only: cap the iterations (result may be unconverged)")
+    ap.add_argument("--n", type=int, default=0,
+                    help="profiling runs only: override the order n of a dense workload")
+    ap.add_argument("--kernel-probe", default="", choices=["", "apply", "precond", "eig"],
+                    help="profiling runs only: time one step entry point (A X, T R, or the "
+                         "3m x 3m eigensolver) K times after W warm-ups instead of full solves")
     return ap.parse_args()
 
 
@@ -211,6 +220,11 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     w = W.WORKLOADS[args.workload]
+    if args.n:
+        if w.kind == "csr":
+            raise SystemExit("--n applies to dense workloads only")
+        import dataclasses
+        w = dataclasses.replace(w, name=f"{w.name}_at_n{args.n}", n=args.n)
     import torch
     dist = None
     if world > 1:
@@ -243,8 +257,10 @@ def main():
     torch.cuda.synchronize()
 
     h = make_handle(M, w, d, args.policy, stream)
-    unconv = args.profile_iters > 0
-    if unconv:
+    if args.kernel_probe:
+        return kernel_probe(args, w, h, X0, stream, torch)
+    unconv = args.profile_iters > 0 or bool(args.n)
+    if args.profile_iters > 0:
         args.maxit = args.profile_iters
     # warm-up steps (untimed)
     for _ in range(args.warmup):
@@ -301,16 +317,26 @@ def main():
     if apply_calls:
         per_launch_s = apply_ms / 1000.0 / apply_calls
         achieved = apply_flops / apply_calls / per_launch_s / 1e9
-        out["roofline"] = {"kernel": "gemm_kernel (working-precision A X, FP64 DFMA)", "bound": "alu",
+        cplx = w.kind == "dense_complex"
+        kname = ("gemm3m_kernel (working-precision complex A X: three real FP64 products per complex "
+                 "product, DFMA)" if cplx else
+                 "gemm_kernel (working-precision A X, FP64 DFMA)" if w.kind != "csr" else
+                 "spmm_csr (working-precision A X, FP64)")
+        out["roofline"] = {"kernel": kname, "bound": "alu",
                            "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                           "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                           "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic_per_launch(w),
                            "flops_per_launch": apply_flops / apply_calls, "launches": apply_calls,
                            "avg_launch_ms": per_launch_s * 1e3,
-                           "peak_note": "nominal FP64 of the recipe table (DFMA microbenchmark: 1190)"}
+                           "peak_note": "nominal FP64 of the recipe table, 152 SMs x 2 DFMA/clk x 2 flop x "
+                                        "2.07 GHz (DFMA microbenchmark: 1190); achieved counts the FP64 flops "
+                                        "the pipe executes"}
+        if cplx:
+            out["roofline"]["complex_equivalent_gflops"] = achieved * 8.0 / 6.0
     if ck:
         out["clocks"] = ck
     if unconv:
-        out["profile_run"] = f"iterations capped at {args.profile_iters}; not a bench value"
+        out["profile_run"] = (f"iterations capped at {args.profile_iters}" if args.profile_iters else
+                              f"order overridden to n={w.n}") + "; not a bench value"
     if rank == 0 and not args.no_fp64 and args.policy != "dchol" and not unconv:
         h2 = make_handle(M, w, d, "dchol", stream)
         h2.factor()
@@ -340,6 +366,72 @@ def main():
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+# DRAM bytes per launch of the A X kernel from one ncu capture of the current
+# kernel version (dram__bytes_read.sum, dram__bytes_write.sum) on a smaller
+# order n0 of the same workload, scaled to the workload's n: reads by
+# (n/n0)^2 (A is streamed once per launch), writes by n/n0 (the n x m block
+# and its split-K partials).  Summary and command: profiles/gemm3m_*.txt.
+# None when no capture of the current kernel exists.
+TRAFFIC_CAPTURES = {"dense_complex": (8192, 1.100558e9, 0.048918e9)}  # kind -> (n0, read, write)
+
+
+def traffic_per_launch(w):
+    cap = TRAFFIC_CAPTURES.get(w.kind)
+    if not cap:
+        return None
+    n0, rd, wr = cap
+    return rd * (w.n / n0) ** 2 + wr * (w.n / n0)
+
+
+def kernel_probe(args, w, h, X0, stream, torch):
+    """Profiling helper: time one step entry point with CUDA events on the
+    launching stream (the A X product, the preconditioner T R, or the
+    3m x 3m eigensolver), W warm-ups then K timed calls."""
+    dev = X0.device
+    m = w.m
+    if args.kernel_probe == "apply":
+        Y = torch.empty_like(X0)
+        call = lambda: h.apply_A(X0, Y, m)
+        c = 2.0 if w.kind != "dense_complex" else 6.0
+        flops = c * w.n * w.n * m if w.kind != "csr" else None
+    elif args.kernel_probe == "precond":
+        h.factor()
+        Wt = torch.empty_like(X0)
+        call = lambda: h.precond(X0, Wt, m)
+        flops = None
+    else:
+        N = 3 * m
+        cplx = X0.dtype == torch.complex128
+        rng = np.random.default_rng(7)
+        G = rng.standard_normal((N, N)) + (1j * rng.standard_normal((N, N)) if cplx else 0)
+        Q = np.linalg.qr(G)[0]
+        Ap = (Q * np.logspace(0, 8, N)[None, :]) @ Q.conj().T
+        Ap = torch.from_numpy(np.ascontiguousarray((0.5 * (Ap + Ap.conj().T)).T)).to(dev)
+        C1 = torch.empty((m, N), dtype=X0.dtype, device=dev)
+        call = lambda: h.small_eig(Ap, N, m, C1)
+        flops = None
+    for _ in range(max(args.warmup, 1)):
+        call()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    h.close()
+    out = {"kernel_probe": args.kernel_probe, "workload": w.name, "n": w.n, "m": m,
+           "ms_min": min(ts), "ms_median": float(np.median(ts)), "calls": len(ts),
+           "note": "profiling helper; not a bench value"}
+    if flops:
+        out["gflops"] = flops / (min(ts) / 1e3) / 1e9
+    print(json.dumps(out))
     return 0
 
 

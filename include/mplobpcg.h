@@ -74,14 +74,23 @@ typedef struct {
   double apply_ms;        /* working-precision products A X of the last solve (stage 2):
                              summed device time, CUDA events around each launch      */
   int64_t apply_calls;    /* number of those products                                 */
-  double apply_flops;     /* their algorithmic flops (dense: 2 n^2 per column, x4
-                             complex; CSR: 2 nnz per column)                          */
+  double apply_flops;     /* flops the FP64 pipe executes for them (dense real: 2 n^2
+                             per column; dense complex: 6 n^2 per column, three real
+                             products per complex product; CSR: 2 nnz per column)  */
   int64_t kernel_launches;/* kernels launched by the last mpl_factor + mpl_solve      */
   double phase_ms[10];    /* device time of the working-precision loop by phase (CUDA
                              events): 0 A X/A W products, 1 residual + test, 2
                              preconditioner, 3 projections, 4 Algorithm 2, 5 Gram
                              S^*AS, 6 small eigenproblem, 7 HL coefficients, 8 basis
                              update, 9 explicit check                                */
+  int64_t cluster_fallbacks; /* thread-block-cluster kernels (small eigensolver, HL QR,
+                             top of the TSQR tree) that fell back to their single-CTA
+                             forms during the last solve call (or small-eigensolver /
+                             Rayleigh-Ritz step call)                                 */
+  int32_t cluster_fail_code; /* first reason since the library loaded: 1000 x stage +
+                             cudaError_t (stage 1 shared memory over 227 KB, 3 cluster
+                             size attribute, 4 occupancy query, 5 no cluster fits, 6
+                             launch); 0 = none                                        */
 } mpl_stats;
 
 /*
@@ -130,6 +139,22 @@ mpl_status mpl_factor(mpl_handle h);
 mpl_status mpl_solve(mpl_handle h, const void* X0, int x0_is_device, int maxit, double* lambda,
                      void* X, int x_is_device, double* resid_hist, int hist_cap, int* hist_len,
                      int* iters);
+
+/*
+ * Algorithm 1 (block PINVIT, Section 3) on the same kernels: per step the
+ * block X~ is orthonormalised (Householder step in FP64), A X is formed, a
+ * Rayleigh-Ritz rotation of span(X) makes Theta diagonal, R = A X - X Theta
+ * is tested with Eq. (stop), and X~ = X - T R with T = L^-* L^-1 from the
+ * handle's factor (the FP64 factor for MPL_D_DCHOL, the lower-precision one
+ * otherwise); every other operation is in FP64.  mpl_factor must have run.
+ * Arguments as for mpl_solve, except rho_hist (host, hist_cap doubles, may be
+ * NULL): the Rayleigh quotient of the first column per step (Theorem 1's
+ * quantity), and iters (may be NULL): one int, the number of steps.
+ * Returns MPL_ENOT_CONVERGED (with the last iterate) if maxit is reached.
+ */
+mpl_status mpl_solve_pinvit(mpl_handle h, const void* X0, int x0_is_device, int maxit, double* lambda,
+                            void* X, int x_is_device, double* rho_hist, int hist_cap, int* hist_len,
+                            int* iters);
 
 mpl_status mpl_get_stats(mpl_handle h, mpl_stats* s);
 const char* mpl_last_error(mpl_handle h);

@@ -42,7 +42,7 @@ class Stats(C.Structure):
                 ("factor_shift", _d), ("norm_est", _d), ("qr_fallbacks", _i), ("explicit_checks", _i),
                 ("nnz_L", _i64), ("nsuper", _i64), ("max_rel_resid", _d), ("apply_ms", _d),
                 ("apply_calls", _i64), ("apply_flops", _d), ("kernel_launches", _i64),
-                ("phase_ms", _d * 10)]
+                ("phase_ms", _d * 10), ("cluster_fallbacks", _i64), ("cluster_fail_code", C.c_int32)]
     PHASES = ("apply", "residual", "precond", "project", "alg2", "gram", "eig", "hl", "update", "check")
 
     def as_dict(self):
@@ -63,6 +63,10 @@ _create_csr = _sig("mpl_create_csr", _i, [C.POINTER(_h), _i64, _i64, _p, _p, _p,
                                           _i, _p])
 _factor = _sig("mpl_factor", _i, [_h])
 _solve = _sig("mpl_solve", _i, [_h, _p, _i, _i, _p, _p, _i, _p, _i, _p, _p])
+_pinvit = _sig("mpl_solve_pinvit", _i, [_h, _p, _i, _i, _p, _p, _i, _p, _i, _p, _p])
+_adjoint = _sig("mpl_adjoint", _i, [_h, _p, _p, _p, _i, _d, _p, _p])
+_fv_assemble = _sig("mpl_fv_assemble", _i, [_i, _p, _p, _p, _p, _p, _p])
+_fv_assemble_adjoint = _sig("mpl_fv_assemble_adjoint", _i, [_i, _p, _p, _p, _p, _p, _p])
 _stats = _sig("mpl_get_stats", _i, [_h, C.POINTER(Stats)])
 _last_error = _sig("mpl_last_error", C.c_char_p, [_h])
 _last_info = _sig("mpl_last_info", _i64, [_h])
@@ -147,6 +151,31 @@ class Handle:
                     C.byref(hl), its)
         self._check(st, (0, 4) if allow_not_converged else (0,))
         return lam, X_out, hist[: hl.value].tolist(), (its[0], its[1]), st
+
+    def solve_pinvit(self, X0, maxit=2000, X_out=None, hist_cap=4096, allow_not_converged=False):
+        """Algorithm 1 (block PINVIT) with the handle's factor.  X0: (m, n).
+        Returns (lambda (k,), X_out, rho history list, steps, status)."""
+        lam = np.zeros(self.k)
+        rho = np.zeros(max(hist_cap, 1))
+        hl = C.c_int(0)
+        its = C.c_int(0)
+        st = _pinvit(self._h, _ptr(X0), _is_dev(X0), maxit, lam.ctypes.data, _ptr(X_out),
+                     _is_dev(X_out) if X_out is not None else 0, rho.ctypes.data, hist_cap,
+                     C.byref(hl), C.byref(its))
+        self._check(st, (0, 4) if allow_not_converged else (0,))
+        return lam, X_out, rho[: hl.value].tolist(), its.value, st
+
+    def adjoint(self, grad, gbar_lambda=None, gbar_X=None, maxit=500, tol=1e-10):
+        """mpl_adjoint: dL/dA of the last solve into ``grad`` (device; CSR: nnz
+        values in the caller's order, dense: n x n column-major).  gbar_lambda:
+        (k,) host; gbar_X: (k, n) device tensor (column-major n x k).
+        Returns (CG iterations, final relative residual)."""
+        gl = None if gbar_lambda is None else np.ascontiguousarray(gbar_lambda, dtype=np.float64)
+        its = C.c_int(0)
+        rr = C.c_double(0.0)
+        self._check(_adjoint(self._h, None if gl is None else gl.ctypes.data, _ptr(gbar_X), _ptr(grad),
+                             maxit, tol, C.byref(its), C.byref(rr)))
+        return its.value, rr.value
 
     def stats(self):
         s = Stats()
@@ -304,3 +333,85 @@ def residual_noalloc(dtype, n, m, AX, X, theta, R, norms2, stream=None):
                            _stream_ptr(stream))
     if st != 0:
         raise MplError(st, "mpl_residual_noalloc failed", 0)
+
+
+def fv_assemble(dims, c, rowptr, colind, vals, stream=None):
+    """mpl_fv_assemble: finite-volume diffusion values for coefficient c on
+    the grid's CSR pattern (device tensors; vals is written)."""
+    d = np.ascontiguousarray(dims, dtype=np.int32)
+    st = _fv_assemble(len(d), d.ctypes.data, _ptr(c), _ptr(rowptr), _ptr(colind), _ptr(vals), _stream_ptr(stream))
+    if st != 0:
+        raise MplError(st, "mpl_fv_assemble failed", 0)
+
+
+def fv_assemble_adjoint(dims, rowptr, colind, grad_vals, grad_c, stream=None):
+    """mpl_fv_assemble_adjoint: grad_c = (d vals / d c)^T grad_vals."""
+    d = np.ascontiguousarray(dims, dtype=np.int32)
+    st = _fv_assemble_adjoint(len(d), d.ctypes.data, _ptr(rowptr), _ptr(colind), _ptr(grad_vals), _ptr(grad_c),
+                              _stream_ptr(stream))
+    if st != 0:
+        raise MplError(st, "mpl_fv_assemble_adjoint failed", 0)
+
+
+# ---- torch.autograd wrappers (argument marshalling around the calls above) ----
+def _autograd():
+    import torch
+
+    class FVValues(torch.autograd.Function):
+        """c (device, n) -> CSR values of the finite-volume operator."""
+
+        @staticmethod
+        def forward(ctx, c, dims, rowptr, colind):
+            vals = torch.empty(colind.shape[0], dtype=torch.float64, device=c.device)
+            fv_assemble(dims, c.contiguous(), rowptr, colind, vals, torch.cuda.current_stream(c.device))
+            ctx.dims, ctx.rowptr, ctx.colind = dims, rowptr, colind
+            return vals
+
+        @staticmethod
+        def backward(ctx, gvals):
+            gc = torch.empty(ctx.rowptr.shape[0] - 1, dtype=torch.float64, device=gvals.device)
+            fv_assemble_adjoint(ctx.dims, ctx.rowptr, ctx.colind, gvals.contiguous(), gc,
+                                torch.cuda.current_stream(gvals.device))
+            return gc, None, None, None
+
+    class EigshCSR(torch.autograd.Function):
+        """CSR values (device) -> (lambda (k,), X (n, k)) by Algorithm 3; the
+        backward pass is mpl_adjoint."""
+
+        @staticmethod
+        def forward(ctx, vals, rowptr, colind, k, m, tol, policy, grid_dims, X0, Omega, maxit, adj_tol):
+            h = create_csr(rowptr, colind, vals.detach().contiguous(), k, m, tol, policy, Omega=Omega,
+                           grid_dims=grid_dims, stream=torch.cuda.current_stream(vals.device))
+            h.factor()
+            n = rowptr.shape[0] - 1
+            Xo = torch.empty((k, n), dtype=torch.float64, device=vals.device)
+            lam, _, _, _, _ = h.solve(X0, maxit=maxit, X_out=Xo)
+            ctx.h, ctx.nnz, ctx.adj_tol = h, colind.shape[0], adj_tol
+            return torch.from_numpy(lam).to(vals.device), Xo.t().contiguous()
+
+        @staticmethod
+        def backward(ctx, glam, gX):
+            h = ctx.h
+            gl = None if glam is None else glam.detach().double().cpu().numpy()
+            gXt = None if gX is None else gX.detach().double().t().contiguous()
+            grad = torch.empty(ctx.nnz, dtype=torch.float64, device=glam.device if glam is not None else gX.device)
+            h.adjoint(grad, gl, gXt, tol=ctx.adj_tol)
+            h.close()
+            ctx.h = None
+            return (grad,) + (None,) * 11
+
+    return FVValues, EigshCSR
+
+
+def fv_values(c, dims, rowptr, colind):
+    """Differentiable c -> finite-volume CSR values (GPU kernels both ways)."""
+    return _autograd()[0].apply(c, dims, rowptr, colind)
+
+
+def eigsh_csr(vals, rowptr, colind, k, m, X0, Omega, tol=1e-12, policy="mp", grid_dims=None, maxit=1000,
+              adj_tol=1e-10):
+    """Differentiable k smallest eigenpairs of the CSR matrix with values
+    ``vals`` (device tensor): returns (lambda (k,), X (n, k)); gradients
+    flow back to vals through mpl_adjoint."""
+    return _autograd()[1].apply(vals, rowptr, colind, k, m, tol, policy, grid_dims, X0, Omega, maxit, adj_tol)
+

@@ -3,7 +3,9 @@
 #include <chrono>
 #include <cstdio>
 
+#include "adjoint.cuh"
 #include "engine.cuh"
+#include "mplobpcg_adjoint.h"
 #include "mplobpcg_steps.h"
 #include "sparse.cuh"
 
@@ -23,7 +25,12 @@ struct DenseOp : Op<T> {
   void apply(cudaStream_t st, const T* X, long long ldx, T* Y, long long ldy, int ncols) override {
     gemm<T>(st, false, false, n, ncols, n, 1, A, lda, X, ldx, 0, Y, ldy, false, scr);
   }
-  double flops(int ncols) const override { return (tr<T>::cx ? 8.0 : 2.0) * (double)n * n * ncols; }
+  // flops the pipe executes: 2 n^2 per column (real), 8 n^2 complex FP32,
+  // 6 n^2 complex FP64 (three real products per complex product)
+  double flops(int ncols) const override {
+    const double c = !tr<T>::cx ? 2.0 : (sizeof(real_t<T>) == 8 ? 6.0 : 8.0);
+    return c * (double)n * n * ncols;
+  }
 };
 
 template <typename T>
@@ -51,6 +58,10 @@ struct EngineBase {
   virtual void factor() = 0;
   virtual mpl_status solve(const void* X0, int x0_dev, int maxit, double* lambda, void* X, int x_dev,
                            double* hist, int hist_cap, int* hist_len, int* iters) = 0;
+  virtual mpl_status solve_pinvit(const void* X0, int x0_dev, int maxit, double* lambda, void* X, int x_dev,
+                                  double* rho_hist, int hist_cap, int* hist_len, int* iters) = 0;
+  virtual void adjoint(const double* gl, const void* gX, double* grad, int maxit, double tol, int* iters,
+                       double* rel_resid) = 0;
   virtual void step_apply_A(const void* X, void* Y, int ncols, int lower) = 0;
   virtual void step_residual(const void* AX, const void* X, const double* theta, int m, void* R,
                              double* norms2) = 0;
@@ -121,7 +132,8 @@ class Engine : public EngineBase {
     Aw_.alloc(sizeof(TW) * n * n);
     MPL_CUDA(cudaMemcpy2DAsync(Aw_.ptr(), sizeof(TW) * n, A, sizeof(TW) * lda, sizeof(TW) * n, n,
                                is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-    scr_mem_.alloc((size_t)48 << 20);
+    // split-K partials of A X: up to 4 slices of an n x m block
+    scr_mem_.alloc(std::max<size_t>((size_t)48 << 20, (size_t)4 * n * c_->m * sizeof(TW)));
     scr_.ptr = scr_mem_.ptr();
     scr_.bytes = scr_mem_.bytes();
     dense_op_.A = Aw_.as<TW>();
@@ -256,17 +268,8 @@ class Engine : public EngineBase {
     const long long n = c_->n;
     const int m = c_->m, k = c_->k;
     const long long l0 = launch_counter().load();
-    X0_.ensure(sizeof(TW) * n * m);
-    TW* x0 = X0_.as<TW>();
-    if (c_->sparse && !c_->perm.empty()) {
-      tmpx_.ensure(sizeof(TW) * n * m);
-      MPL_CUDA(cudaMemcpyAsync(tmpx_.ptr(), X0, sizeof(TW) * n * m,
-                               x0_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-      permute_rows<TW>(st, (int)n, m, perm_dev_.as<long long>(), false, tmpx_.as<TW>(), n, x0, n);
-    } else {
-      MPL_CUDA(cudaMemcpyAsync(x0, X0, sizeof(TW) * n * m,
-                               x0_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-    }
+    const long long cf0 = cluster_fallback_counter().load();
+    TW* x0 = upload_x0(X0, x0_dev);
     std::vector<double> h;
     Progress p1;
     const TW* start = x0;
@@ -315,22 +318,264 @@ class Engine : public EngineBase {
     c_->stats.apply_flops = p2.apply_flops;
     for (int q = 0; q < PH_N; ++q) c_->stats.phase_ms[q] = p2.phase_ms[q];
     c_->stats.kernel_launches = launches_factor_ + (launch_counter().load() - l0);
+    c_->stats.cluster_fallbacks = cluster_fallback_counter().load() - cf0;
+    c_->stats.cluster_fail_code = cluster_fail_code().load();
+    last_X_ = Xfin;
+    last_theta_.assign(th, th + m);
     if (lambda) for (int j = 0; j < k; ++j) lambda[j] = th[j];
+    download_x(Xfin, X, x_dev);
+    if (hist) for (int i = 0; i < (int)h.size() && i < hist_cap; ++i) hist[i] = h[i];
+    if (hist_len) *hist_len = (int)h.size();
+    if (iters) { iters[0] = p1.iters; iters[1] = p2.iters; }
+    check_launch("solve");
+    return p2.converged ? MPL_OK : MPL_ENOT_CONVERGED;
+  }
+
+  // X0 (caller's ordering, host or device) into the permuted working copy.
+  TW* upload_x0(const void* X0, int x0_dev) {
+    cudaStream_t st = c_->stream;
+    const long long n = c_->n;
+    const int m = c_->m;
+    X0_.ensure(sizeof(TW) * n * m);
+    TW* x0 = X0_.as<TW>();
+    if (c_->sparse && !c_->perm.empty()) {
+      tmpx_.ensure(sizeof(TW) * n * m);
+      MPL_CUDA(cudaMemcpyAsync(tmpx_.ptr(), X0, sizeof(TW) * n * m,
+                               x0_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+      permute_rows<TW>(st, (int)n, m, perm_dev_.as<long long>(), false, tmpx_.as<TW>(), n, x0, n);
+    } else {
+      MPL_CUDA(cudaMemcpyAsync(x0, X0, sizeof(TW) * n * m,
+                               x0_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    }
+    return x0;
+  }
+
+  // First k columns of Xfin, un-permuted, into the caller's X; synchronises.
+  void download_x(const TW* Xfin, void* X, int x_dev) {
+    cudaStream_t st = c_->stream;
+    const long long n = c_->n;
+    const int k = c_->k;
     if (X) {
-      TW* src = Xfin;
+      const TW* src = Xfin;
       if (c_->sparse && !c_->perm.empty()) {
-        tmpx_.ensure(sizeof(TW) * n * m);
+        tmpx_.ensure(sizeof(TW) * n * c_->m);
         permute_rows<TW>(st, (int)n, k, perm_dev_.as<long long>(), true, Xfin, n, tmpx_.as<TW>(), n);
         src = tmpx_.as<TW>();
       }
       MPL_CUDA(cudaMemcpyAsync(X, src, sizeof(TW) * n * k, x_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     }
     MPL_CUDA(cudaStreamSynchronize(st));
-    if (hist) for (int i = 0; i < (int)h.size() && i < hist_cap; ++i) hist[i] = h[i];
-    if (hist_len) *hist_len = (int)h.size();
-    if (iters) { iters[0] = p1.iters; iters[1] = p2.iters; }
-    check_launch("solve");
-    return p2.converged ? MPL_OK : MPL_ENOT_CONVERGED;
+  }
+
+  // Algorithm 1 with the handle's factor: the FP64 factor for D-dchol, the
+  // lower-precision factor otherwise; every other operation in FP64.
+  mpl_status solve_pinvit(const void* X0, int x0_dev, int maxit, double* lambda, void* X, int x_dev,
+                          double* rho_hist, int hist_cap, int* hist_len, int* iters) override {
+    if (!c_->factored) throw MplError{MPL_ESTATE, "mpl_solve_pinvit before mpl_factor", 0};
+    cudaStream_t st = c_->stream;
+    const long long l0 = launch_counter().load();
+    const long long cf0 = cluster_fallback_counter().load();
+    TW* x0 = upload_x0(X0, x0_dev);
+    auto& stg = stage_w<TW>();
+    Timer t2(st);
+    Progress p;
+    if (c_->policy == MPL_D_DCHOL) {
+      PreFromFactor<TW, TW> pre;
+      pre.F = factor_work();
+      pre.n = (int)c_->n;
+      p = stg.run_pinvit(st, opw_, &pre, x0, c_->k, c_->tol, c_->norm_est, maxit);
+    } else {
+      PreFromFactor<TW, TL> pre;
+      pre.F = factor_low();
+      pre.n = (int)c_->n;
+      p = stg.run_pinvit(st, opw_, &pre, x0, c_->k, c_->tol, c_->norm_est, maxit);
+    }
+    c_->stats.t_stage1_ms = 0.0;
+    c_->stats.t_stage2_ms = t2.stop();
+    c_->stats.iters_stage1 = 0;
+    c_->stats.iters_stage2 = p.iters;
+    c_->stats.qr_fallbacks = p.qr_fallbacks;
+    c_->stats.explicit_checks = 0;
+    c_->stats.max_rel_resid = p.max_rel;
+    c_->stats.apply_ms = p.apply_ms;
+    c_->stats.apply_calls = p.apply_calls;
+    c_->stats.apply_flops = p.apply_flops;
+    for (int q = 0; q < PH_N; ++q) c_->stats.phase_ms[q] = p.phase_ms[q];
+    c_->stats.kernel_launches = launches_factor_ + (launch_counter().load() - l0);
+    c_->stats.cluster_fallbacks = cluster_fallback_counter().load() - cf0;
+    c_->stats.cluster_fail_code = cluster_fail_code().load();
+    const double* th = stg.theta_host();
+    last_X_ = stg.X();
+    last_theta_.assign(th, th + c_->m);
+    if (lambda) for (int j = 0; j < c_->k; ++j) lambda[j] = th[j];
+    download_x(stg.X(), X, x_dev);
+    if (rho_hist) for (int i = 0; i < (int)p.rho.size() && i < hist_cap; ++i) rho_hist[i] = p.rho[i];
+    if (hist_len) *hist_len = (int)p.rho.size();
+    if (iters) *iters = p.iters;
+    check_launch("solve_pinvit");
+    return p.converged ? MPL_OK : MPL_ENOT_CONVERGED;
+  }
+
+  // Adjoint of the last solve (real symmetric A): grad = dL/dA on the stored
+  // pattern for dL/dlambda_j = gl[j] and dL/dx_j = gX(:, j).  The eigenvector
+  // part needs mu_j = (A - lambda_j I)^+ gX(:, j): its component inside
+  // span(X_k) is exact, (x_i^T g_j)/(lambda_i - lambda_j); on the complement
+  // P = I - X_k X_k^T (where A - lambda_j I is positive definite, lambda_j <
+  // lambda_{k+1}) block CG on P (A - lambda_j I) P z_j = P g_j, preconditioned
+  // by P T P with the handle's factor T.
+  void adjoint(const double* gl, const void* gX, double* grad, int maxit, double tol, int* iters,
+               double* rel_resid) override {
+    if constexpr (!std::is_same<TW, double>::value) {
+      throw MplError{MPL_EINVAL, "the adjoint is defined for real symmetric matrices (MPL_R64)", 0};
+    } else {
+      if (!last_X_) throw MplError{MPL_ESTATE, "mpl_adjoint before a solve", 0};
+      cudaStream_t st = c_->stream;
+      const long long n = c_->n;
+      const int k = c_->k;
+      const size_t blk = sizeof(double) * n * k;
+      adj_.ensure(blk * 8 + sizeof(double) * ((size_t)ceil_div(n, 4096) * k + 8 * (size_t)k * k + 16 * k));
+      double* G = adj_.as<double>();
+      double* Z = G + n * k;
+      double* Rr = Z + n * k;
+      double* Y = Rr + n * k;
+      double* Pp = Y + n * k;
+      double* Q = Pp + n * k;
+      double* MU = Q + n * k;
+      double* T1 = MU + n * k;
+      double* part = T1 + n * k;
+      double* Csm = part + (size_t)ceil_div(n, 4096) * k;
+      double* Wsm = Csm + (size_t)k * k;
+      double* dv = Wsm + (size_t)k * k;          // per-column scalars: 8 k
+      double* d_gl = dv + 8 * k;
+      double* d_th = d_gl + k;
+      double* d_coef = d_th + k;
+      const double* Xk = last_X_;
+      std::vector<double> h(8 * (size_t)k * k + 8 * k);
+      int its = 0;
+      double worst = 0.0;
+      MPL_CUDA(cudaMemsetAsync(MU, 0, blk, st));
+      if (gX) {
+        if (c_->sparse && !c_->perm.empty())
+          permute_rows<double>(st, (int)n, k, perm_dev_.as<long long>(), false, static_cast<const double*>(gX), n, G, n);
+        else
+          MPL_CUDA(cudaMemcpyAsync(G, gX, blk, cudaMemcpyDeviceToDevice, st));
+        auto project = [&](double* V) {  // V <- V - X_k (X_k^T V)
+          gemm<double>(st, true, false, k, k, (int)n, 1, Xk, n, V, n, 0, Csm, k, false, scr_);
+          gemm<double>(st, false, false, (int)n, k, k, -1, Xk, n, Csm, k, 1, V, n, false, scr_);
+        };
+        // in-span part: MU = X_k W, W(i, j) = (x_i^T g_j) / (lambda_i - lambda_j), i != j
+        gemm<double>(st, true, false, k, k, (int)n, 1, Xk, n, G, n, 0, Csm, k, false, scr_);
+        MPL_CUDA(cudaMemcpyAsync(h.data(), Csm, sizeof(double) * k * k, cudaMemcpyDeviceToHost, st));
+        MPL_CUDA(cudaStreamSynchronize(st));
+        for (int j = 0; j < k; ++j)
+          for (int i = 0; i < k; ++i) {
+            const double d = last_theta_[i] - last_theta_[j];
+            h[(size_t)k * k + i + (size_t)j * k] = (i == j || d == 0.0) ? 0.0 : h[i + (size_t)j * k] / d;
+          }
+        MPL_CUDA(cudaMemcpyAsync(Wsm, h.data() + (size_t)k * k, sizeof(double) * k * k, cudaMemcpyHostToDevice, st));
+        gemm<double>(st, false, false, (int)n, k, k, 1, Xk, n, Wsm, k, 0, MU, n, false, scr_);
+        // complement: r = P g, z = 0
+        MPL_CUDA(cudaMemcpyAsync(Rr, G, blk, cudaMemcpyDeviceToDevice, st));
+        project(Rr);
+        MPL_CUDA(cudaMemsetAsync(Z, 0, blk, st));
+        MPL_CUDA(cudaMemcpyAsync(d_th, last_theta_.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
+        PreFromFactor<double, float> pre_l;
+        PreFromFactor<double, double> pre_w;
+        Pre<double>* pre = nullptr;
+        if (c_->policy == MPL_D_DCHOL) {
+          pre_w.F = factor_work();
+          pre_w.n = (int)n;
+          pre = &pre_w;
+        } else {
+          pre_l.F = factor_low();
+          pre_l.n = (int)n;
+          pre = &pre_l;
+        }
+        auto precond = [&](const double* R, double* Yo) {  // Yo = P T R
+          pre->apply(st, R, n, nullptr, Yo, n, k);
+          project(Yo);
+        };
+        auto dots = [&](const double* A, const double* B, double* hostv) {
+          col_dots(st, (int)n, k, A, B, part, dv);
+          MPL_CUDA(cudaMemcpyAsync(hostv, dv, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+          MPL_CUDA(cudaStreamSynchronize(st));
+        };
+        double* bn = h.data() + 2 * (size_t)k * k;
+        double* rho = bn + k;
+        double* tmp = rho + k;
+        double* coef = tmp + k;
+        dots(Rr, Rr, bn);
+        precond(Rr, Y);
+        MPL_CUDA(cudaMemcpyAsync(Pp, Y, blk, cudaMemcpyDeviceToDevice, st));
+        dots(Rr, Y, rho);
+        bool done = true;
+        for (int j = 0; j < k; ++j) done = done && bn[j] == 0.0;
+        while (!done && its < maxit) {
+          ++its;
+          opw_->apply(st, Pp, n, Q, n, k);                 // Q = P (A - lambda_j) Pp
+          col_axpy(st, (int)n, k, -1.0, d_th, Pp, Q);
+          project(Q);
+          dots(Pp, Q, tmp);
+          for (int j = 0; j < k; ++j) coef[j] = (tmp[j] != 0.0) ? rho[j] / tmp[j] : 0.0;
+          MPL_CUDA(cudaMemcpyAsync(d_coef, coef, sizeof(double) * k, cudaMemcpyHostToDevice, st));
+          col_axpy(st, (int)n, k, 1.0, d_coef, Pp, Z);
+          col_axpy(st, (int)n, k, -1.0, d_coef, Q, Rr);
+          dots(Rr, Rr, tmp);
+          done = true;
+          worst = 0.0;
+          for (int j = 0; j < k; ++j) {
+            const double rel = bn[j] > 0.0 ? std::sqrt(tmp[j] / bn[j]) : 0.0;
+            worst = std::max(worst, rel);
+            done = done && rel <= tol;
+          }
+          if (done) break;
+          precond(Rr, Y);
+          dots(Rr, Y, tmp);
+          for (int j = 0; j < k; ++j) {
+            coef[j] = (rho[j] != 0.0) ? tmp[j] / rho[j] : 0.0;
+            rho[j] = tmp[j];
+          }
+          MPL_CUDA(cudaMemcpyAsync(d_coef, coef, sizeof(double) * k, cudaMemcpyHostToDevice, st));
+          col_xpby(st, (int)n, k, d_coef, Y, Pp);
+        }
+        std::vector<double> ones(k, 1.0);
+        MPL_CUDA(cudaMemcpyAsync(d_coef, ones.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
+        col_axpy(st, (int)n, k, 1.0, d_coef, Z, MU);   // mu = in-span part + z
+        MPL_CUDA(cudaStreamSynchronize(st));
+        if (!done) {
+          if (iters) *iters = its;
+          if (rel_resid) *rel_resid = worst;
+          throw MplError{MPL_ENOT_CONVERGED, "adjoint CG did not reach tol", its};
+        }
+      }
+      std::vector<double> glh(k, 0.0);
+      if (gl) glh.assign(gl, gl + k);
+      MPL_CUDA(cudaMemcpyAsync(d_gl, glh.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
+      if (c_->sparse) {
+        // X_k and MU back to the caller's ordering, sampled on the caller's pattern
+        const double* Xo = Xk;
+        const double* Mo = MU;
+        if (!c_->perm.empty()) {
+          permute_rows<double>(st, (int)n, k, perm_dev_.as<long long>(), true, Xk, n, T1, n);
+          permute_rows<double>(st, (int)n, k, perm_dev_.as<long long>(), true, MU, n, Q, n);
+          Xo = T1;
+          Mo = Q;
+        }
+        csr_outer_sample(st, (int)n, k, orig_rp_.as<long long>(), orig_ci_.as<int>(), d_gl, Xo, Mo, grad);
+      } else {
+        // dense: grad = (X_k diag(gl) - MU) X_k^T  (n x n, ld n)
+        MPL_CUDA(cudaMemsetAsync(T1, 0, blk, st));
+        col_axpy(st, (int)n, k, 1.0, d_gl, Xk, T1);
+        std::vector<double> ones(k, 1.0);
+        MPL_CUDA(cudaMemcpyAsync(d_coef, ones.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
+        col_axpy(st, (int)n, k, -1.0, d_coef, MU, T1);
+        gemm<double>(st, false, true, (int)n, (int)n, k, 1, T1, n, Xk, n, 0, grad, n, false, scr_);
+      }
+      MPL_CUDA(cudaStreamSynchronize(st));
+      check_launch("adjoint");
+      if (iters) *iters = its;
+      if (rel_resid) *rel_resid = worst;
+    }
   }
 
   // ---- steps ----
@@ -401,6 +646,7 @@ class Engine : public EngineBase {
   void step_small_eig(void* Ap, int N, int m, double* lam, void* C1) override {
     auto& s = step_stage();
     s.prepare();
+    const long long cf0 = cluster_fallback_counter().load();
     DevMem fl(16);
     if (!eig_small_fast<TW>(c_->stream, N, m, static_cast<TW*>(Ap), s.vec() + 2 * c_->m, static_cast<TW*>(C1),
                             eig_ws(N, m), fl.as<int>()))
@@ -408,14 +654,19 @@ class Engine : public EngineBase {
                     eig_ws(N, m));
     MPL_CUDA(cudaMemcpyAsync(lam, s.vec() + 2 * c_->m, sizeof(double) * m, cudaMemcpyDeviceToHost, c_->stream));
     sync("small_eig");
+    c_->stats.cluster_fallbacks = cluster_fallback_counter().load() - cf0;
+    c_->stats.cluster_fail_code = cluster_fail_code().load();
   }
   void step_rr(const void* S, const void* AS, int ncol, int m, double* lam, void* Ccoef) override {
     auto& s = step_stage();
     s.prepare();
+    const long long cf0 = cluster_fallback_counter().load();
     s.rayleigh_ritz(c_->stream, static_cast<const TW*>(S), static_cast<const TW*>(AS), ncol, m, true);
     MPL_CUDA(cudaMemcpyAsync(lam, s.vec() + 2 * c_->m, sizeof(double) * m, cudaMemcpyDeviceToHost, c_->stream));
     MPL_CUDA(cudaMemcpyAsync(Ccoef, s.Ccoef(), sizeof(TW) * ncol * 2 * m, cudaMemcpyDeviceToDevice, c_->stream));
     sync("rayleigh_ritz");
+    c_->stats.cluster_fallbacks = cluster_fallback_counter().load() - cf0;
+    c_->stats.cluster_fail_code = cluster_fail_code().load();
   }
   void get_factor_dense(void* L) override {
     if (c_->sparse || !c_->factored) throw MplError{MPL_ESTATE, "no dense factor", 0};
@@ -441,7 +692,9 @@ class Engine : public EngineBase {
 
   mpl_ctx* c_;
   DevMem Aw_, Al_, Lbuf_, Dbuf_, tmp_, info_, scr_mem_, X0_, x0l_, tmpx_, eigws_, perm_dev_;
-  DevMem rp_, ci_, vw_, vl_;
+  DevMem rp_, ci_, vw_, vl_, orig_rp_, orig_ci_, adj_;
+  const TW* last_X_ = nullptr;       // Ritz block of the last solve (internal ordering)
+  std::vector<double> last_theta_;   // its Ritz values
   long long csr_nnz_ = 0;
   long long launches_factor_ = 0;
   Scratch scr_;
@@ -514,6 +767,8 @@ struct HostSymEngine : EngineBase {
   [[noreturn]] static void no() { throw MplError{MPL_ESTATE, "host-only symbolic handle", 0}; }
   void factor() override { no(); }
   mpl_status solve(const void*, int, int, double*, void*, int, double*, int, int*, int*) override { no(); }
+  mpl_status solve_pinvit(const void*, int, int, double*, void*, int, double*, int, int*, int*) override { no(); }
+  void adjoint(const double*, const void*, double*, int, double, int*, double*) override { no(); }
   void step_apply_A(const void*, void*, int, int) override { no(); }
   void step_residual(const void*, const void*, const double*, int, void*, double*) override { no(); }
   void step_precond(const void*, void*, int, int) override { no(); }
@@ -639,6 +894,48 @@ extern "C" mpl_status mpl_solve(mpl_handle h, const void* X0, int x0_is_device, 
   });
   if (s == MPL_ENOT_CONVERGED) h->err = "maximum number of iterations reached";
   return s;
+}
+
+extern "C" mpl_status mpl_solve_pinvit(mpl_handle h, const void* X0, int x0_is_device, int maxit,
+                                       double* lambda, void* X, int x_is_device, double* rho_hist, int hist_cap,
+                                       int* hist_len, int* iters) {
+  if (!h || !X0 || maxit < 0 || (rho_hist && hist_cap < 0)) return MPL_EINVAL;
+  mpl_status s = guarded(h, [&]() {
+    return h->eng->solve_pinvit(X0, x0_is_device, maxit, lambda, X, x_is_device, rho_hist, hist_cap, hist_len,
+                                iters);
+  });
+  if (s == MPL_ENOT_CONVERGED) h->err = "maximum number of iterations reached";
+  return s;
+}
+
+extern "C" mpl_status mpl_adjoint(mpl_handle h, const double* gbar_lambda, const void* gbar_X, double* grad,
+                                  int maxit, double tol, int* iters, double* rel_resid) {
+  if (!h || !grad || maxit < 0 || !(tol > 0.0)) return MPL_EINVAL;
+  return guarded(h, [&]() {
+    h->eng->adjoint(gbar_lambda, gbar_X, grad, maxit, tol, iters, rel_resid);
+    return MPL_OK;
+  });
+}
+
+extern "C" mpl_status mpl_fv_assemble(int ndims, const int* dims, const double* c, const int64_t* rowptr,
+                                      const int32_t* colind, double* vals, void* stream) {
+  if ((ndims != 2 && ndims != 3) || !dims || !c || !rowptr || !colind || !vals) return MPL_EINVAL;
+  for (int a = 0; a < ndims; ++a)
+    if (dims[a] < 2) return MPL_EINVAL;
+  mpl::fv_assemble(static_cast<cudaStream_t>(stream), ndims, dims, c, reinterpret_cast<const long long*>(rowptr),
+                   colind, vals);
+  return cudaGetLastError() == cudaSuccess ? MPL_OK : MPL_ECUDA;
+}
+
+extern "C" mpl_status mpl_fv_assemble_adjoint(int ndims, const int* dims, const int64_t* rowptr,
+                                              const int32_t* colind, const double* grad_vals, double* grad_c,
+                                              void* stream) {
+  if ((ndims != 2 && ndims != 3) || !dims || !rowptr || !colind || !grad_vals || !grad_c) return MPL_EINVAL;
+  for (int a = 0; a < ndims; ++a)
+    if (dims[a] < 2) return MPL_EINVAL;
+  mpl::fv_assemble_adjoint(static_cast<cudaStream_t>(stream), ndims, dims,
+                           reinterpret_cast<const long long*>(rowptr), colind, grad_vals, grad_c);
+  return cudaGetLastError() == cudaSuccess ? MPL_OK : MPL_ECUDA;
 }
 
 extern "C" mpl_status mpl_get_stats(mpl_handle h, mpl_stats* s) {

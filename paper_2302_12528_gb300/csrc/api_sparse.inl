@@ -38,6 +38,11 @@ void Engine<TW>::create_csr(const long long* rowptr, const int* colind, const do
     perm_dev_.alloc(sizeof(long long) * n);
     MPL_CUDA(cudaMemcpyAsync(perm_dev_.ptr(), sym_->perm.data(), sizeof(long long) * n, cudaMemcpyHostToDevice, st));
     csr_nnz_ = nnz;
+    // the caller's pattern, for gradients returned in the caller's order
+    orig_rp_.alloc(sizeof(long long) * (n + 1));
+    orig_ci_.alloc(sizeof(int) * nnz);
+    MPL_CUDA(cudaMemcpyAsync(orig_rp_.ptr(), hrp.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, st));
+    MPL_CUDA(cudaMemcpyAsync(orig_ci_.ptr(), hci.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, st));
     rp_.alloc(sizeof(long long) * (n + 1));
     ci_.alloc(sizeof(int) * nnz);
     vw_.alloc(sizeof(double) * nnz);

@@ -26,7 +26,7 @@ template <typename T, bool OPA, bool OPB>
 __global__ void __launch_bounds__(256)
 gemm_kernel(int M, int N, int K, real_t<T> alpha, const T* __restrict__ A, long long lda,
             const T* __restrict__ B, long long ldb, real_t<T> beta, T* __restrict__ C,
-            long long ldc, int lower_only, int kchunk, T* __restrict__ ws) {
+            long long ldc, int lower_only, int kchunk, int swap_xy, T* __restrict__ ws) {
   using Cfg = GemmCfg<T>;
   constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK, TM = Cfg::TM, TN = Cfg::TN;
   constexpr int SX = BM / TM, SY = BN / TN;  // thread grid, SX * SY == 256
@@ -34,7 +34,9 @@ gemm_kernel(int M, int N, int K, real_t<T> alpha, const T* __restrict__ A, long 
   __shared__ T As[BK][BM];
   __shared__ T Bs[BK][BN];
 
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  // swap_xy: column tiles vary fastest, so the CTAs that share a row panel of
+  // op(A) run together and read it from L2
+  const int m0 = (swap_xy ? blockIdx.y : blockIdx.x) * BM, n0 = (swap_xy ? blockIdx.x : blockIdx.y) * BN;
   if (lower_only && n0 > m0 + BM - 1) return;  // tile strictly above the diagonal
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
@@ -121,14 +123,16 @@ template <bool OPA, bool OPB>
 __global__ void __launch_bounds__(256)
 gemm3m_kernel(int M, int N, int K, double alpha, const zd* __restrict__ A, long long lda,
               const zd* __restrict__ B, long long ldb, double beta, zd* __restrict__ C,
-              long long ldc, int lower_only, int kchunk, zd* __restrict__ ws) {
+              long long ldc, int lower_only, int kchunk, int swap_xy, zd* __restrict__ ws) {
   constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2;
   constexpr int SX = BM / TM, SY = BN / TN;
   static_assert(SX * SY == 256, "256 threads");
   __shared__ double Ar[BK][BM], Ai[BK][BM], Asum[BK][BM];
   __shared__ double Br[BK][BN], Bi[BK][BN], Bsum[BK][BN];
 
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  // swap_xy: column tiles vary fastest, so the CTAs that share a row panel of
+  // op(A) run together and read it from L2
+  const int m0 = (swap_xy ? blockIdx.y : blockIdx.x) * BM, n0 = (swap_xy ? blockIdx.x : blockIdx.y) * BN;
   if (lower_only && n0 > m0 + BM - 1) return;
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
@@ -242,10 +246,14 @@ void gemm(cudaStream_t st, bool opA, bool opB, int M, int N, int K, real_t<T> al
   int tiles = gx * gy;
   if (lower_only) tiles = (tiles + gx) / 2;
   int splits = 1;
-  const int target = 2 * NUM_SMS;
+  // FP64: one CTA saturates an SM's FP64 pipe, so the end-of-grid imbalance
+  // is about one CTA's work; at least 24 CTAs per SM keep it to a few
+  // percent.  FP32: fill the SMs twice.
+  constexpr bool fp64 = sizeof(real_t<T>) == 8;
+  const int target = (fp64 ? 24 : 2) * NUM_SMS;
   if (K > 0 && tiles < target) {
     splits = ceil_div(target, tiles);
-    const int max_by_k = ceil_div(K, 4 * Cfg::BK);  // at least 4 k-steps per slice
+    const int max_by_k = ceil_div(K, (fp64 ? 16 : 4) * Cfg::BK);  // k-steps per slice
     if (splits > max_by_k) splits = max_by_k;
     const size_t per = (size_t)M * N * sizeof(T);
     const int max_by_ws = per ? (int)(scr.bytes / per) : 0;
@@ -261,16 +269,17 @@ void gemm(cudaStream_t st, bool opA, bool opB, int M, int N, int K, real_t<T> al
     splits = 1;
     kchunk = 0;
   }
-  dim3 grid(gx, gy, splits);
+  const int swap = gx <= 65535 ? 1 : 0;
+  dim3 grid(swap ? gy : gx, swap ? gx : gy, splits);
   T* ws = splits > 1 ? static_cast<T*>(scr.ptr) : nullptr;
 #define MPL_GEMM_LAUNCH(OA, OB)                                                                        \
   do {                                                                                                 \
     if constexpr (std::is_same<T, zd>::value)                                                          \
       gemm3m_kernel<OA, OB><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,        \
-                                                  lower_only, kchunk, ws);                             \
+                                                  lower_only, kchunk, swap, ws);                             \
     else                                                                                               \
       gemm_kernel<T, OA, OB><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,      \
-                                                   lower_only, kchunk, ws);                            \
+                                                   lower_only, kchunk, swap, ws);                            \
   } while (0)
   count_launch();
   if (!opA && !opB) MPL_GEMM_LAUNCH(false, false);
@@ -533,6 +542,23 @@ void conj_inplace(cudaStream_t st, int n, int m, T* X, long long ldx) {
 }
 
 template <typename T>
+__global__ void sub_from_kernel(int n, int m, T* __restrict__ X, long long ldx, const T* __restrict__ W,
+                                long long ldw) {
+  const int j = blockIdx.y;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    X[i + (long long)j * ldx] = X[i + (long long)j * ldx] - W[i + (long long)j * ldw];
+}
+
+template <typename T>
+void sub_from(cudaStream_t st, int n, int m, T* X, long long ldx, const T* W, long long ldw) {
+  if (n <= 0 || m <= 0) return;
+  int bx = ceil_div(n, 256);
+  if (bx > 64) bx = 64;
+  count_launch();
+  sub_from_kernel<T><<<dim3(bx, m), 256, 0, st>>>(n, m, X, ldx, W, ldw);
+}
+
+template <typename T>
 __global__ void permute_rows_kernel(int n, int m, const long long* __restrict__ idx, int scatter,
                                     const T* __restrict__ X, long long ldx, T* __restrict__ Y,
                                     long long ldy) {
@@ -570,6 +596,7 @@ void permute_rows(cudaStream_t st, int n, int m, const long long* idx, bool scat
   template void herm_from_lower<T>(cudaStream_t, int, T*, long long);                        \
   template void set_identity<T>(cudaStream_t, int, int, T*, long long);                      \
   template void conj_inplace<T>(cudaStream_t, int, int, T*, long long);                      \
+  template void sub_from<T>(cudaStream_t, int, int, T*, long long, const T*, long long);     \
   template void permute_rows<T>(cudaStream_t, int, int, const long long*, bool, const T*,    \
                                 long long, T*, long long);
 MPL_INST_T(float)

@@ -72,6 +72,10 @@ void set_identity(cudaStream_t st, int N, int m, T* Y, long long ldy);
 template <typename T>
 void conj_inplace(cudaStream_t st, int n, int m, T* X, long long ldx);
 
+// X <- X - W (n x m).
+template <typename T>
+void sub_from(cudaStream_t st, int n, int m, T* X, long long ldx, const T* W, long long ldw);
+
 // Row permutations of an n x m block: gather Y(i, :) = X(idx[i], :) or
 // scatter Y(idx[i], :) = X(i, :).
 template <typename T>

@@ -130,6 +130,22 @@ inline std::atomic<long long>& launch_counter() {
 }
 inline void count_launch(long long k = 1) { launch_counter().fetch_add(k, std::memory_order_relaxed); }
 
+// Fallbacks of the thread-block-cluster kernels to their single-CTA forms:
+// a process-wide count and the first reason (1000 x stage + cudaError_t).
+inline std::atomic<long long>& cluster_fallback_counter() {
+  static std::atomic<long long> c{0};
+  return c;
+}
+inline std::atomic<int>& cluster_fail_code() {
+  static std::atomic<int> c{0};
+  return c;
+}
+inline void note_cluster_fallback(int code) {
+  cluster_fallback_counter().fetch_add(1, std::memory_order_relaxed);
+  int zero = 0;
+  cluster_fail_code().compare_exchange_strong(zero, code);
+}
+
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 }  // namespace mpl

@@ -20,6 +20,7 @@
 #include <cooperative_groups.h>
 
 #include <map>
+#include <set>
 #include <mutex>
 #include <utility>
 
@@ -458,32 +459,61 @@ template <typename K>
 static int pick_cluster(K kernel, size_t smem_of_cl(int), int* out_cl, size_t* out_sm) {
   static std::mutex mu;
   static std::map<std::pair<std::pair<int, const void*>, size_t>, std::pair<int, size_t>> cache;
+  static std::map<std::pair<std::pair<int, const void*>, size_t>, int> why;
+  static std::set<std::pair<int, const void*>> opened;
   int dev = 0;
   cudaGetDevice(&dev);
   const auto key = std::make_pair(std::make_pair(dev, reinterpret_cast<const void*>(kernel)), smem_of_cl(16));
   {
+    // The dynamic shared-memory limit is a property of the kernel, shared by
+    // all of its launch configurations (one kernel serves several matrix
+    // sizes), so it is raised once to the per-CTA maximum.
     std::lock_guard<std::mutex> lock(mu);
+    if (!opened.count(key.first)) {
+      // opt-in limit per block minus the kernel's static shared memory
+      int optin = 0;
+      cudaFuncAttributes fa{};
+      if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+          cudaFuncGetAttributes(&fa, kernel) == cudaSuccess && optin > (int)fa.sharedSizeBytes) {
+        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes) != cudaSuccess)
+          cudaGetLastError();
+      } else {
+        cudaGetLastError();
+      }
+      opened.insert(key.first);
+    }
     auto it = cache.find(key);
     if (it != cache.end()) {
       *out_cl = it->second.first;
       *out_sm = it->second.second;
+      if (it->second.first <= 0) note_cluster_fallback(why[key]);
       return it->second.first > 0;
     }
   }
   int found_cl = 0;
   size_t found_sm = 0;
+  int reason = 0;
   int cand[2] = {16, 8};
   for (int ci = 0; ci < 2; ++ci) {
     const int CL = cand[ci];
     const size_t sm = smem_of_cl(CL);
-    if (sm > 227 * 1024) continue;
-    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
-      cudaGetLastError();
+    int limit = 48 * 1024;
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess) limit = fa.maxDynamicSharedSizeBytes;
+    else cudaGetLastError();
+    if (sm > (size_t)limit) {
+      reason = 1000;
       continue;
     }
-    if (CL > 8 && cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
-      cudaGetLastError();
-      continue;
+    cudaError_t e = cudaSuccess;
+    if (CL > 8) {
+      e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) {
+        reason = 3000 + (int)e;
+        cudaGetLastError();
+        continue;
+      }
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CL);
@@ -497,7 +527,9 @@ static int pick_cluster(K kernel, size_t smem_of_cl(int), int* out_cl, size_t* o
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg) != cudaSuccess) {
+    e = cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg);
+    if (e != cudaSuccess) {
+      reason = 4000 + (int)e;
       cudaGetLastError();
       continue;
     }
@@ -506,9 +538,12 @@ static int pick_cluster(K kernel, size_t smem_of_cl(int), int* out_cl, size_t* o
       found_sm = sm;
       break;
     }
+    reason = 5000;
   }
+  if (found_cl <= 0) note_cluster_fallback(reason);
   std::lock_guard<std::mutex> lock(mu);
   cache[key] = std::make_pair(found_cl, found_sm);
+  why[key] = reason;
   *out_cl = found_cl;
   *out_sm = found_sm;
   return found_cl > 0;
@@ -567,7 +602,9 @@ bool eig_small_fast(cudaStream_t st, int N, int m, T* Ap, double* lam, T* C1, vo
   R* G = lu + 4 * (size_t)N * m;
   int* piv = reinterpret_cast<int*>(G + (size_t)m * m + N + m);
   count_launch();
-  if (launch_cluster<T>(tridiag_cluster_kernel<T>, CL, sm, st, N, Ap, U, uh, tau, d, e) != cudaSuccess) {
+  const cudaError_t le = launch_cluster<T>(tridiag_cluster_kernel<T>, CL, sm, st, N, Ap, U, uh, tau, d, e);
+  if (le != cudaSuccess) {
+    note_cluster_fallback(6000 + (int)le);
     cudaGetLastError();
     return false;
   }
@@ -607,7 +644,9 @@ bool thin_q_fast(cudaStream_t st, int N, int q, T* Y, int c0, int nq, T* Q, T* h
   cfg.attrs = at;
   cfg.numAttrs = 1;
   count_launch();
-  if (cudaLaunchKernelEx(&cfg, qr_cluster_kernel<T>, N, q, Y, uh, tau) != cudaSuccess) {
+  const cudaError_t le = cudaLaunchKernelEx(&cfg, qr_cluster_kernel<T>, N, q, Y, uh, tau);
+  if (le != cudaSuccess) {
+    note_cluster_fallback(6000 + (int)le);
     cudaGetLastError();
     return false;
   }
@@ -637,7 +676,9 @@ bool qr_cluster_inplace(cudaStream_t st, int N, int q, T* Y, T* hb) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   count_launch();
-  if (cudaLaunchKernelEx(&cfg, qr_cluster_kernel<T>, N, q, Y, hb, reinterpret_cast<R*>(hb + q)) != cudaSuccess) {
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, qr_cluster_kernel<T>, N, q, Y, hb, reinterpret_cast<R*>(hb + q));
+  if (e != cudaSuccess) {
+    note_cluster_fallback(6000 + (int)e);
     cudaGetLastError();
     return false;
   }

@@ -2,6 +2,10 @@
 // stage loop of Algorithm 3, templated on the stage's working type TW and the
 // type TQ of Algorithm 2's Householder step.
 #pragma once
+#include <cuda_profiler_api.h>
+
+#include <cstdio>
+#include <cstdlib>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -147,11 +151,32 @@ struct PreFromFactor : Pre<TW> {
 
 enum Phase { PH_APPLY = 0, PH_RESID, PH_PRECOND, PH_PROJECT, PH_ALG2, PH_GRAM, PH_EIG, PH_HL, PH_UPDATE, PH_CHECK, PH_N };
 
+// Opt-in profiling window: with MPL_PROFILE_RANGE="a:b" in the environment,
+// iterations a..b of the working-precision loop are bracketed by
+// cudaProfilerStart / cudaProfilerStop, so that a profiler started with
+// profiling disabled records exactly those iterations.  Unset: no effect.
+struct ProfileWindow {
+  int first = 0, last = -1;
+  bool on = false;
+  ProfileWindow() {
+    const char* e = std::getenv("MPL_PROFILE_RANGE");
+    if (e && std::sscanf(e, "%d:%d", &first, &last) != 2) { first = 0; last = -1; }
+  }
+  void begin(int it) {
+    if (it == first && first <= last && !on) { cudaProfilerStart(); on = true; }
+  }
+  void end(int it) {
+    if (on && it == last) { cudaProfilerStop(); on = false; }
+  }
+  ~ProfileWindow() { if (on) cudaProfilerStop(); }
+};
+
 struct Progress {
   double phase_ms[PH_N] = {0};
   double apply_ms = 0.0, apply_flops = 0.0;
   long long apply_calls = 0;
   std::vector<double> hist;
+  std::vector<double> rho;  // PINVIT: Rayleigh quotient of the first column per step
   int iters = 0;
   bool converged = false;
   int qr_fallbacks = 0;
@@ -309,9 +334,11 @@ class Stage {
     update(st, m, m);  // X <- X C, AX <- AX C
     bool hasP = false;
     double window[6] = {0, 0, 0, 0, 0, 0};
+    ProfileWindow pw;
     for (int it = 1; it <= maxit + 1; ++it) {
       TW* X = S_[cur_].as<TW>();
       TW* AX = AS_[cur_].as<TW>();
+      if (!stage1) pw.begin(it);
       ph_begin(st, PH_RESID);
       residual<TW>(st, n_, m, AX, n, X, n, vec() + 2 * m, R_.as<TW>(), n, part_.as<double>(), vec());
       ph_end(st, PH_RESID);
@@ -367,8 +394,65 @@ class Stage {
       ph_end(st, PH_UPDATE);
       hasP = true;
       check_launch("lobpcg iteration");
+      if (!stage1) pw.end(it);
     }
     prog_.iters = maxit;
+    finish_timing();
+    return prog_;
+  }
+
+  // Algorithm 1 (block PINVIT with the lower-precision preconditioner T), all
+  // other operations in TW.  Per step: X <- orthonormal basis of span(X~)
+  // (Algorithm 2 with the Householder step in TW), A X, a Rayleigh-Ritz
+  // rotation of span(X) so that Theta is diagonal and Eq. (stop) applies per
+  // column, R = A X - X Theta, the test, W = T R (unscaled: the step needs
+  // the correction itself) and X~ = X - W.  Returns with the Ritz block in
+  // X() and theta in theta_host().
+  Progress run_pinvit(cudaStream_t st, Op<TW>* op, Pre<TW>* pre, const TW* X0, int k, double tol,
+                      double normA, int maxit) {
+    prepare();
+    prog_ = Progress();
+    const int m = m_;
+    const long long n = n_;
+    cur_ = 0;
+    MPL_CUDA(cudaMemcpyAsync(S_[0].as<TW>(), X0, sizeof(TW) * n * m, cudaMemcpyDeviceToDevice, st));
+    atimer_.reset();
+    for (int p = 0; p < PH_N; ++p) ptimer_[p].reset();
+    for (int it = 1; it <= maxit; ++it) {
+      TW* Xt = S_[cur_].as<TW>();
+      ph_begin(st, PH_ALG2);
+      const bool qr_ok = mixed_qr(st, Xt, m, false);
+      ph_end(st, PH_ALG2);
+      if (!qr_ok) throw MplError{MPL_ERANK, "orthonormalisation of the PINVIT block failed", it};
+      timed_apply(st, op, Xt, AS_[cur_].as<TW>(), m);
+      rayleigh_ritz(st, Xt, AS_[cur_].as<TW>(), m, m, false);
+      ph_begin(st, PH_UPDATE);
+      update(st, m, m);  // X <- X Z, AX <- AX Z
+      ph_end(st, PH_UPDATE);
+      TW* X = S_[cur_].as<TW>();
+      TW* AX = AS_[cur_].as<TW>();
+      ph_begin(st, PH_RESID);
+      residual<TW>(st, n_, m, AX, n, X, n, vec() + 2 * m, R_.as<TW>(), n, part_.as<double>(), vec());
+      ph_end(st, PH_RESID);
+      const int nc = fetch_and_test(st, k, tol, normA);
+      if (nc < 0) throw MplError{MPL_ENUMERICAL, "non-finite residual norm", it};
+      prog_.hist.push_back(last_max_);
+      prog_.rho.push_back(host_[2 * m]);
+      prog_.max_rel = last_max_;
+      prog_.iters = it;
+      if (nc >= k) {
+        prog_.converged = true;
+        finish_timing();
+        return prog_;
+      }
+      ph_begin(st, PH_PRECOND);
+      pre->apply(st, R_.as<TW>(), n, nullptr, V_.as<TW>(), n, m);
+      ph_end(st, PH_PRECOND);
+      ph_begin(st, PH_UPDATE);
+      sub_from<TW>(st, n_, m, X, n, V_.as<TW>(), n);  // X~ = X - W (in place)
+      ph_end(st, PH_UPDATE);
+      check_launch("pinvit iteration");
+    }
     finish_timing();
     return prog_;
   }

@@ -183,6 +183,8 @@ def test_small_eig_parity(cplx, N, m, spec):
     Apt = torch_dev(np.ascontiguousarray(Ap.T))
     C1 = torch.empty((m, N), dtype=Apt.dtype, device="cuda:0")
     lam = h.small_eig(Apt, N, m, C1)
+    st = h.stats()
+    assert st["cluster_fallbacks"] == 0, st["cluster_fail_code"]   # the cluster eigensolver ran
     ref = np.linalg.eigvalsh(Ap)[:m]
     nA = np.abs(ev).max()
     assert np.abs(lam - ref).max() <= 20 * N * U_H * nA
@@ -246,6 +248,7 @@ def test_solve_dense_real_n1000(policy):
         assert subspace_sin(X[:, j:j + 1], ref.X[:, j:j + 1]) <= 1e-8 / (gap / evall[-1])
     assert np.isclose(st["norm_est"], ref.normA, rtol=1e-12)
     assert hist[-1] <= w.tol
+    assert st["cluster_fallbacks"] == 0, st["cluster_fail_code"]   # cluster kernels ran
 
 
 @pytest.mark.parametrize("policy,n,kappa", [("mp", 600, 1e8), ("dchol", 600, 1e8), ("schol", 517, 1e6)])
@@ -258,7 +261,9 @@ def test_solve_dense_complex(policy, n, kappa):
     h.factor()
     Xo = torch.empty((k, n), dtype=torch.complex128, device="cuda:0")
     lam, _, hist, its, _ = h.solve(torch_dev(X0), maxit=2000, X_out=Xo)
+    st = h.stats()
     h.close()
+    assert st["cluster_fallbacks"] == 0, st["cluster_fail_code"]   # cluster kernels ran
     X = to_np(Xo).T
     evall = np.linalg.eigvalsh(A)
     rn = np.linalg.norm(A @ X - X * lam[None, :], axis=0)

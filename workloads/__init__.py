@@ -29,7 +29,7 @@ import numpy as np
 
 __all__ = [
     "dense_spd", "dense_hpd", "diffusion_csr", "laplacian_csr", "start_block",
-    "sketch", "Workload", "WORKLOADS", "make_workload",
+    "sketch", "Workload", "WORKLOADS", "make_workload", "batch_orders", "batch_spd",
 ]
 
 
@@ -219,6 +219,49 @@ def sketch(n: int, m_omega: int, seed: int, complex_: bool = False) -> np.ndarra
     (m_omega, n) row-major array, i.e. the column-major storage of Omega^T."""
     rng = _rng(seed + 0x5EED)
     return _gaussian(rng, (m_omega, n), complex_)
+
+
+def batch_orders(count: int, seed: int, nmin: int = 64, nmax: int = 1024) -> np.ndarray:
+    """Orders of a batch of problems: round(exp(U(ln nmin, ln nmax)))."""
+    rng = _rng(seed)
+    u = rng.uniform(math.log(nmin), math.log(nmax), count)
+    return np.clip(np.rint(np.exp(u)).astype(np.int64), nmin, nmax)
+
+
+def batch_spd(count: int, seed: int, kappa: float = 1e6, nmin: int = 64, nmax: int = 1024, m: int = 8,
+              device: str | None = None):
+    """A batch of independent dense real SPD problems, problem i of order n_i
+    (``batch_orders``) with A_i = Q_i diag(logspace(0, log10 kappa, n_i)) Q_i^T
+    (``dense_spd`` with seed + 1 + i), packed column-major one after another.
+
+    Returns dict: 'n' (count,), 'a_off' (count,) offsets of A_i in doubles,
+    'A' (sum n_i^2,) packed, 'x_off' (count,) offsets of n_i-row blocks,
+    'X0' (sum n_i * m,) packed start blocks (n_i x m each, column-major),
+    'Omega' (sum n_i * 8,) packed sketches (n_i x 8 each), 'lam' list of the
+    constructed spectra.  With ``device`` A is built on that device (torch)."""
+    n = batch_orders(count, seed, nmin, nmax)
+    a_off = np.concatenate([[0], np.cumsum(n.astype(np.int64) ** 2)[:-1]])
+    x_off = np.concatenate([[0], np.cumsum(n.astype(np.int64))[:-1]])
+    lam = []
+    if device is None:
+        A = np.empty(int((n.astype(np.int64) ** 2).sum()))
+    else:
+        import torch
+        A = torch.empty(int((n.astype(np.int64) ** 2).sum()), dtype=torch.float64, device=device)
+    X0 = np.empty(int(n.sum()) * m)
+    Om = np.empty(int(n.sum()) * 8)
+    for i, ni in enumerate(n):
+        ai, li = dense_spd(int(ni), seed + 1 + i, kappa, device=device)
+        o = int(a_off[i])
+        if device is None:
+            A[o:o + ni * ni] = ai.T.reshape(-1)        # column-major
+        else:
+            A[o:o + ni * ni] = ai.t().contiguous().reshape(-1)
+        lam.append(li)
+        xo = int(x_off[i])
+        X0[xo * m:(xo + ni) * m] = start_block(int(ni), m, seed + 100003 + i).reshape(-1)
+        Om[xo * 8:(xo + ni) * 8] = sketch(int(ni), 8, seed + 200003 + i).reshape(-1)
+    return {"n": n, "a_off": a_off, "x_off": x_off, "A": A, "X0": X0, "Omega": Om, "lam": lam, "m": m}
 
 
 @dataclass(frozen=True)
