@@ -234,12 +234,16 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
+        if w.kind == "batch":
+            return run_reference_batch(args, w)
         return run_reference(args, w)
 
     import paper_2302_12528_gb300 as M
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
+    if w.kind == "batch":
+        return run_batch(args, w, M, dev, stream, torch, rank, dist)
     d = {}
     seed = w.seed + 1000 * rank
     if w.kind == "csr":
@@ -431,6 +435,183 @@ def kernel_probe(args, w, h, X0, stream, torch):
            "note": "profiling helper; not a bench value"}
     if flops:
         out["gflops"] = flops / (min(ts) / 1e3) / 1e9
+    print(json.dumps(out))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# batched workload
+# ---------------------------------------------------------------------------
+def batch_oracle_sample(w, b, stride=128):
+    """Oracle solves of every ``stride``-th problem in order of size, scaled
+    by ``stride`` (a stratified sample of the batch's size distribution)."""
+    from oracle import lobpcg as OL
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] or [os.cpu_count()])
+    except Exception:
+        cores = os.cpu_count()
+    order = np.argsort(-b["n"], kind="stable")
+    pick = order[stride // 2::stride]
+    t0 = time.perf_counter()
+    for i in pick:
+        n = int(b["n"][i])
+        o = int(b["a_off"][i])
+        A = b["A"][o:o + n * n].reshape(n, n).T
+        xo = int(b["x_off"][i])
+        X0 = b["X0"][xo * w.m:(xo + n) * w.m].reshape(w.m, n).T
+        Om = b["Omega"][xo * 8:(xo + n) * 8].reshape(8, n)
+        OL.solve(OL.DenseOperator(A), A, X0, Om, w.k, tol=w.tol, policy="mp")
+    t = time.perf_counter() - t0
+    return {"value": t * len(b["n"]) / len(pick), "cores": int(cores), "t_sample": t, "problems": len(pick)}
+
+
+def run_batch(args, w, M, dev, stream, torch, rank, dist):
+    """One step = one solve of every problem of the batch (mpl_batch_solve:
+    the graph-captured persistent launch), inputs resident in HBM."""
+    b = W.batch_spd(w.n, w.seed + 1000 * rank, w.kappa, m=w.m)
+    nprob = len(b["n"])
+    A = torch.from_numpy(b["A"]).to(dev)
+    Om = torch.from_numpy(b["Omega"]).to(dev)
+    X0 = torch.from_numpy(b["X0"]).to(dev)
+    tot = int(b["n"].sum())
+
+    def outs():
+        return (torch.zeros(nprob * w.k, dtype=torch.float64, device=dev),
+                torch.zeros(tot * w.k, dtype=torch.float64, device=dev),
+                torch.zeros(2 * nprob, dtype=torch.int32, device=dev),
+                torch.zeros(nprob, dtype=torch.int32, device=dev))
+
+    def make(policy):
+        return M.Batch(b["n"], b["a_off"], b["x_off"], A, Om, w.k, w.m, tol=w.tol, policy=policy,
+                       maxit=args.maxit, stream=stream)
+
+    lam, X, its, st = outs()
+    bt = make(args.policy)
+    cfg = bt.tune(X0, lam, X, its, st)
+    for _ in range(args.warmup):
+        bt.solve(X0, lam, X, its, st)
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        bt.solve(X0, lam, X, its, st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    world = dist.get_world_size() if dist is not None else 1
+    itn = its.cpu().numpy().reshape(nprob, 2)
+    stn = st.cpu().numpy()
+    n = b["n"].astype(np.float64)
+    # FP64 flops of the products with A per problem: norm estimate (8 columns),
+    # stage-2 start (m), one A W per stage-2 iteration (m), the explicit check (m)
+    flops64 = float(np.sum(2.0 * n * n * (8 + w.m * (itn[:, 1] + 2))))
+    achieved = flops64 / (ms / 1e3) / 1e9
+    out = {
+        "metric": "time-to-k-eigenpairs at resid<=1e-12 (mixed-precision LOBPCG, Algorithm 3), whole batch",
+        "value": ms / 1000.0, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+f32", "data": "synthetic (seeded; see DESIGN.md input recipe)",
+        "config": {"workload": w.name, "problems": nprob, "n_min": int(b["n"].min()), "n_max": int(b["n"].max()),
+                   "sum_n2": int((b["n"].astype(np.int64) ** 2).sum()), "k": w.k, "m": w.m, "tol": w.tol,
+                   "policy": {"mp": "MPLOBPCG-schol", "schol": "DLOBPCG-schol", "dchol": "DLOBPCG-dchol"}[args.policy],
+                   "kappa": w.kappa, "replicas": world,
+                   "l2": "inputs larger than L2 (A: %.2f GB)" % (float((b["n"].astype(np.int64) ** 2).sum()) * 8 / 1e9),
+                   "launch": cfg},
+        "iterations": {"stage1_mean": float(itn[:, 0].mean()), "stage2_mean": float(itn[:, 1].mean()),
+                       "stage2_max": int(itn[:, 1].max())},
+        "status": {"converged": int((stn == 0).sum()), "other": int((stn != 0).sum())},
+        "gpu_launches": 1,
+        "roofline": {"kernel": "batch_kernel<float> (persistent: one block per problem; products with A in FP64 DFMA)",
+                     "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                     "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                     "flops_per_launch": flops64, "launches": args.steps, "avg_launch_ms": ms,
+                     "peak_note": "nominal FP64; achieved counts only the FP64 products with A (the "
+                                  "Gram, projection and update flops and all FP32 work are extra)"},
+    }
+    if ck:
+        out["clocks"] = ck
+    bt.close()
+    if rank == 0 and not args.no_fp64 and args.policy != "dchol":
+        lam2, X2, its2, st2 = outs()
+        b2 = make("dchol")
+        b2.tune(X0, lam2, X2, its2, st2)
+        b2.solve(X0, lam2, X2, its2, st2)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        b2.solve(X0, lam2, X2, its2, st2)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        t64 = f0.elapsed_time(f1) / 1000.0
+        b2.close()
+        out["fp64_comparator"] = {"policy": "DLOBPCG-dchol", "value": t64, "unit": "s",
+                                  "stage2_mean": float(its2.cpu().numpy().reshape(nprob, 2)[:, 1].mean()),
+                                  "speedup_mixed_vs_fp64": t64 / out["value"]}
+    if rank == 0 and not args.no_e2e:
+        Ah = torch.from_numpy(b["A"]).pin_memory()
+        Omh = torch.from_numpy(b["Omega"]).pin_memory()
+        X0h = torch.from_numpy(b["X0"]).pin_memory()
+        lamh = torch.empty(nprob * w.k, dtype=torch.float64).pin_memory()
+        Xh = torch.empty(tot * w.k, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Ad, Omd, X0d = Ah.to(dev, non_blocking=True), Omh.to(dev, non_blocking=True), X0h.to(dev, non_blocking=True)
+        l3, x3, i3, s3 = outs()
+        b3 = M.Batch(b["n"], b["a_off"], b["x_off"], Ad, Omd, w.k, w.m, tol=w.tol, policy=args.policy,
+                     maxit=args.maxit, stream=stream)
+        b3.solve(X0d, l3, x3, i3, s3)
+        lamh.copy_(l3)
+        Xh.copy_(x3)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        b3.close()
+        out["e2e"] = {"value": te, "unit": "s", "h2d_bytes_per_step": int(Ah.numel() * 8 + Omh.numel() * 8 + X0h.numel() * 8),
+                      "d2h_bytes_per_step": int(lamh.numel() * 8 + Xh.numel() * 8),
+                      "note": "untuned launch shape (no autotuning inside the timed region)"}
+    if rank == 0 and not args.no_cpu_baseline:
+        cb = batch_oracle_sample(w, b)
+        out["cpu_baseline"] = {"value": cb["value"], "unit": "s", "cores": cb["cores"], "kind": "oracle",
+                               "sample": f"oracle solves of {cb['problems']} of the {nprob} problems (every 128th "
+                                         f"by size; {cb['t_sample']:.1f} s), scaled by {nprob}/{cb['problems']}"}
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_reference_batch(args, w):
+    """Oracle arm of the batched workload: each step a stratified sample of
+    the batch (every 128th problem by size) scaled to the whole batch."""
+    b = W.batch_spd(w.n, w.seed, w.kappa, m=w.m)
+    vals = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        cb = batch_oracle_sample(w, b)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    v = float(np.mean(vals))
+    out = {"impl": "reference", "metric": "time-to-k-eigenpairs at resid<=1e-12 (mixed-precision LOBPCG, "
+                                          "Algorithm 3), whole batch",
+           "value": v, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": v * 1000.0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64+f32", "data": "synthetic (seeded)",
+           "config": {"workload": w.name, "problems": w.n, "k": w.k, "m": w.m, "tol": w.tol},
+           "cpu_baseline": {"value": v, "unit": "s", "cores": cb["cores"], "kind": "oracle",
+                            "sample": f"{cb['problems']} problems per step, scaled"},
+           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
 

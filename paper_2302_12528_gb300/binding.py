@@ -67,6 +67,11 @@ _pinvit = _sig("mpl_solve_pinvit", _i, [_h, _p, _i, _i, _p, _p, _i, _p, _i, _p, 
 _adjoint = _sig("mpl_adjoint", _i, [_h, _p, _p, _p, _i, _d, _p, _p])
 _fv_assemble = _sig("mpl_fv_assemble", _i, [_i, _p, _p, _p, _p, _p, _p])
 _fv_assemble_adjoint = _sig("mpl_fv_assemble_adjoint", _i, [_i, _p, _p, _p, _p, _p, _p])
+_batch_create = _sig("mpl_batch_create", _i, [C.POINTER(_h), _i, _p, _p, _p, _p, _p, _i, _i, _d, _i, _i, _p])
+_batch_tune = _sig("mpl_batch_tune", _i, [_h, _p, _p, _p, _p, _p, _i])
+_batch_solve = _sig("mpl_batch_solve", _i, [_h, _p, _p, _p, _p, _p])
+_batch_config = _sig("mpl_batch_get_config", _i, [_h, _p, _p, _p, _p])
+_batch_destroy = _sig("mpl_batch_destroy", None, [_h])
 _stats = _sig("mpl_get_stats", _i, [_h, C.POINTER(Stats)])
 _last_error = _sig("mpl_last_error", C.c_char_p, [_h])
 _last_info = _sig("mpl_last_info", _i64, [_h])
@@ -415,3 +420,49 @@ def eigsh_csr(vals, rowptr, colind, k, m, X0, Omega, tol=1e-12, policy="mp", gri
     flow back to vals through mpl_adjoint."""
     return _autograd()[1].apply(vals, rowptr, colind, k, m, tol, policy, grid_dims, X0, Omega, maxit, adj_tol)
 
+
+class Batch:
+    """mpl_batch_*: many small dense real SPD problems in one persistent
+    launch.  n, a_off, x_off: host int64 arrays; A, Omega: device float64
+    tensors (packed, see include/mplobpcg_batch.h), kept alive by the object."""
+
+    def __init__(self, n, a_off, x_off, A, Omega, k, m, tol=1e-12, policy="mp", maxit=1000, stream=None):
+        self.n = np.ascontiguousarray(n, dtype=np.int64)
+        self.a_off = np.ascontiguousarray(a_off, dtype=np.int64)
+        self.x_off = np.ascontiguousarray(x_off, dtype=np.int64)
+        self._keep = (A, Omega)
+        self.k, self.m = k, m
+        self._h = _h()
+        st = _batch_create(C.byref(self._h), len(self.n), self.n.ctypes.data, self.a_off.ctypes.data,
+                           self.x_off.ctypes.data, _ptr(A), _ptr(Omega), k, m, tol, POLICIES.get(policy, policy),
+                           maxit, _stream_ptr(stream))
+        if st != 0:
+            self._h = None
+            raise MplError(st, "mpl_batch_create failed", 0)
+
+    def tune(self, X0, lam, X, iters, status, sample=0):
+        st = _batch_tune(self._h, _ptr(X0), _ptr(lam), _ptr(X), _ptr(iters), _ptr(status), sample)
+        if st != 0:
+            raise MplError(st, "mpl_batch_tune failed", 0)
+        return self.config()
+
+    def solve(self, X0, lam, X, iters, status):
+        st = _batch_solve(self._h, _ptr(X0), _ptr(lam), _ptr(X), _ptr(iters), _ptr(status))
+        if st != 0:
+            raise MplError(st, "mpl_batch_solve failed", 0)
+
+    def config(self):
+        t, per, blk, ms = C.c_int(0), C.c_int(0), C.c_int(0), C.c_double(0)
+        _batch_config(self._h, C.byref(t), C.byref(per), C.byref(blk), C.byref(ms))
+        return {"threads": t.value, "blocks_per_sm": per.value, "blocks": blk.value, "tuned_ms": ms.value}
+
+    def close(self):
+        if self._h:
+            _batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

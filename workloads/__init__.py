@@ -292,6 +292,9 @@ WORKLOADS = {
     # 2D variable-coefficient diffusion, 512^2, k = 16, m = 24
     "diffusion2d_512": Workload("diffusion2d_512", "csr", 512 ** 2, 16, 24, dims=(512, 512),
                                 sigma=0.5, ell=8.0),
+    # batch of 2048 dense real SPD problems, n_i log-uniform in [64, 1024],
+    # lambda in [1, 1e6], k = 4, m = 8 (``n`` is the number of problems)
+    "batch2048": Workload("batch2048", "batch", 2048, 4, 8, kappa=1e6),
 }
 
 
