@@ -63,6 +63,20 @@ mpl_status mpl_batch_solve(mpl_batch_handle bh, const double* X0, double* lambda
 mpl_status mpl_batch_get_config(mpl_batch_handle bh, int* threads, int* blocks_per_sm, int* blocks,
                                 double* tuned_ms);
 
+/*
+ * Profiling: with MPL_BATCH_PHASES=1 in the environment at mpl_batch_create,
+ * every block's thread 0 sums clock64() cycles per phase of the last solve:
+ * 0 norm estimate, 1 factor (all shift attempts), 2 stage 1 (whole), and per
+ * stage-2 iteration work: 3 start (Algorithm 2 + first Rayleigh-Ritz),
+ * 4 residual + test, 5 preconditioner, 6 projections, 7 Algorithm 2,
+ * 8 A W, 9 Gram, 10 small eigenproblem, 11 HL coefficients, 12 basis
+ * update, 13 explicit check; entry 14 counts Jacobi sweeps (not cycles);
+ * 15 and 16 split the preconditioner's forward and backward sweeps out of 5.
+ * cycles: host, count entries (17 used).  MPL_ESTATE when profiling was
+ * not enabled.
+ */
+mpl_status mpl_batch_get_phase_cycles(mpl_batch_handle bh, unsigned long long* cycles, int count);
+
 void mpl_batch_destroy(mpl_batch_handle bh);
 
 #ifdef __cplusplus

@@ -72,6 +72,7 @@ _batch_tune = _sig("mpl_batch_tune", _i, [_h, _p, _p, _p, _p, _p, _i])
 _batch_solve = _sig("mpl_batch_solve", _i, [_h, _p, _p, _p, _p, _p])
 _batch_config = _sig("mpl_batch_get_config", _i, [_h, _p, _p, _p, _p])
 _batch_destroy = _sig("mpl_batch_destroy", None, [_h])
+_batch_phases = _sig("mpl_batch_get_phase_cycles", _i, [_h, _p, _i])
 _stats = _sig("mpl_get_stats", _i, [_h, C.POINTER(Stats)])
 _last_error = _sig("mpl_last_error", C.c_char_p, [_h])
 _last_info = _sig("mpl_last_info", _i64, [_h])
@@ -455,6 +456,17 @@ class Batch:
         t, per, blk, ms = C.c_int(0), C.c_int(0), C.c_int(0), C.c_double(0)
         _batch_config(self._h, C.byref(t), C.byref(per), C.byref(blk), C.byref(ms))
         return {"threads": t.value, "blocks_per_sm": per.value, "blocks": blk.value, "tuned_ms": ms.value}
+
+    PHASES = ("norm", "factor", "stage1", "start", "residual", "precond", "project", "alg2", "apply",
+              "gram", "eig", "hl", "update", "check", "jacobi_sweeps", "pre_fwd", "pre_bwd")
+
+    def phase_cycles(self):
+        """Per-phase clock64 sums of the last solve (MPL_BATCH_PHASES=1 at creation)."""
+        out = np.zeros(32, dtype=np.uint64)
+        st = _batch_phases(self._h, out.ctypes.data, 32)
+        if st != 0:
+            raise MplError(st, "mpl_batch_get_phase_cycles failed", 0)
+        return {name: int(out[i]) for i, name in enumerate(self.PHASES)}
 
     def close(self):
         if self._h:

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -26,7 +27,7 @@ namespace bt {
 struct SmemLayout {
   size_t xs, tile, G, V, C, Y, Rl, Ri, Gm, Lt, theta, d, cs, rn2, xn2, hb, red, order, total;
 };
-__host__ __device__ inline SmemLayout smem_layout(int nmax, int m, int nw) {
+__host__ __device__ inline SmemLayout smem_layout(int nmax, int m, int nw, int fsize) {
   SmemLayout L{};
   const int NC = 3 * m;
   size_t o = 0;
@@ -36,12 +37,14 @@ __host__ __device__ inline SmemLayout smem_layout(int nmax, int m, int nw) {
     return at;
   };
   // union: apply staging (8 nmax doubles), Cholesky workspace, sweep staging
-  const size_t uni = std::max<size_t>(std::max<size_t>((size_t)8 * nmax * 8, (size_t)(TB * (TB + 1) + 2 * 64 * (TB + 1)) * 8),
-                                      (size_t)TB * MB_MAX * 8);
+  // union: apply staging (8 nmax doubles), Cholesky workspace, the sweeps'
+  // staging plus the n x m right-hand sides (the factor type may be FP64)
+  const size_t uni = std::max<size_t>(std::max<size_t>((size_t)8 * nmax * 8, (size_t)(TB * (TB + 1) + 2 * 64 * (TB + 1)) * fsize),
+                                      (size_t)(2 * TB * MB_MAX + TB * (TB + 1) + (size_t)nmax * m) * fsize);
   L.xs = take(uni);
-  L.tile = take((size_t)GT * 2 * NC * 8);
-  L.G = take((size_t)NC * NC * 8);
-  L.V = take((size_t)NC * NC * 8);
+  L.tile = take((size_t)(GT + 1) * 2 * NC * 8);
+  L.G = take((size_t)(NC + 1) * NC * 8);
+  L.V = take((size_t)(NC + 1) * NC * 8);
   L.C = take((size_t)NC * 2 * m * 8);
   L.Y = take((size_t)NC * 2 * m * 8);
   L.Rl = take((size_t)m * m * 8);
@@ -50,7 +53,7 @@ __host__ __device__ inline SmemLayout smem_layout(int nmax, int m, int nw) {
   L.Lt = take((size_t)m * m * 8);
   L.theta = take((size_t)NC * 8);
   L.d = take((size_t)NC * 8);
-  L.cs = take((size_t)(2 * NC_MAX + 2) * 8);
+  L.cs = take((size_t)(2 * NC_MAX + 4) * 8);
   L.rn2 = take((size_t)m * 8);
   L.xn2 = take((size_t)m * 8);
   L.hb = take((size_t)4 * m * 8);
@@ -106,6 +109,7 @@ struct Args {
   int* iters;                // nprob x 2
   int* status;               // nprob
   int* counter;
+  unsigned long long* phase;  // nullable: per-phase clock64 sums (see PH_*)
   unsigned char* ws;
   long long ws_stride;
   int nprob, nmax, k, m, maxit, policy;
@@ -120,6 +124,26 @@ struct Smem {
 };
 
 template <typename T> __device__ __forceinline__ T* as(double* p) { return reinterpret_cast<T*>(p); }
+
+// Phases timed with clock64 by thread 0 when Args::phase is set (stage 2
+// phases are per working-precision iteration work; stage 1 is one total).
+enum { PH_NORM = 0, PH_FACTOR, PH_STAGE1, PH_START, PH_RESID, PH_PRECOND, PH_PROJECT, PH_QR, PH_APPLY, PH_GRAM,
+       PH_EIG, PH_HL, PH_UPDATE, PH_CHECK, PH_SWEEPS, PH_PRE_FWD, PH_PRE_BWD, PH_COUNT };
+
+struct Ticker {
+  unsigned long long* acc;  // shared, PH_COUNT entries, or nullptr
+  long long last;
+  __device__ void start() {
+    if (acc && threadIdx.x == 0) last = clock64();
+  }
+  __device__ void tick(int ph) {
+    if (acc && threadIdx.x == 0) {
+      const long long t = clock64();
+      acc[ph] += (unsigned long long)(t - last);
+      last = t;
+    }
+  }
+};
 
 // ---- one LOBPCG stage (Algorithm 3 loop) in working type TW -------------
 template <typename TW>
@@ -146,17 +170,24 @@ __device__ bool mixed_qr(int n, int m, TW* W, TW* Vb, TQ* Wq, Smem& s, int* flag
       const double w = (double)Wq[i + (long long)j * n];
       v[0] += w * w;
     }
-    double* s2p = s.cs;  // scratch
+    double* s2p = s.cs;  // scratch: s2p[0] = ||.||^2, then [t, u0, beta] from thread 0
     block_sums(v, 1, s2p, part);
-    const double s2 = s2p[0];
-    const double x0 = (double)Wq[j + (long long)j * n];
-    double t = 0.0, u0 = 0.0, beta = x0;
-    if (s2 != 0.0) {
-      const double alpha = sqrt(s2 + x0 * x0);
-      beta = x0 >= 0.0 ? -alpha : alpha;
-      u0 = x0 - beta;
-      t = 1.0 / (alpha * (alpha + fabs(x0)));
+    if (threadIdx.x == 0) {
+      const double s2 = s2p[0];
+      const double x0 = (double)Wq[j + (long long)j * n];
+      double t = 0.0, u0 = 0.0, beta = x0;
+      if (s2 != 0.0) {
+        const double alpha = sqrt(s2 + x0 * x0);
+        beta = x0 >= 0.0 ? -alpha : alpha;
+        u0 = x0 - beta;
+        t = 1.0 / (alpha * (alpha + fabs(x0)));
+      }
+      s.cs[40] = t;
+      s.cs[41] = u0;
+      s.cs[42] = beta;
     }
+    __syncthreads();
+    const double t = s.cs[40], u0 = s.cs[41], beta = s.cs[42];
     // dots with the later columns
     double dv[MB_MAX];
     for (int c = 0; c < MB_MAX; ++c) dv[c] = 0.0;
@@ -168,12 +199,11 @@ __device__ bool mixed_qr(int n, int m, TW* W, TW* Vb, TQ* Wq, Smem& s, int* flag
     const int nc = m - j - 1;
     if (nc > 0) block_sums(dv + j + 1, nc, dots, part);
     for (int c = j + 1; c < m; ++c) {
-      // full dot includes the head u0 * Wq(j, c)
-      const double dot = dots[c - j - 1] + u0 * (double)Wq[j + (long long)c * n];
-      const double g = t * dot;
+      // full dot includes the head u0 * Wq(j, c); the update runs in TQ
+      const TQ g = (TQ)(t * (dots[c - j - 1] + u0 * (double)Wq[j + (long long)c * n]));
       for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x)
-        Wq[i + (long long)c * n] = (TQ)((double)Wq[i + (long long)c * n] - g * (double)Wq[i + (long long)j * n]);
-      if (threadIdx.x == 0) Rl[j + c * m] = (TQ)((double)Wq[j + (long long)c * n] - g * u0);
+        Wq[i + (long long)c * n] -= g * Wq[i + (long long)j * n];
+      if (threadIdx.x == 0) Rl[j + c * m] = Wq[j + (long long)c * n] - g * (TQ)u0;
     }
     if (threadIdx.x == 0) Rl[j + j * m] = (TQ)beta;
     __syncthreads();
@@ -207,26 +237,31 @@ __device__ bool mixed_qr(int n, int m, TW* W, TW* Vb, TQ* Wq, Smem& s, int* flag
 // Rayleigh-Ritz on span(S(:, 0:ncol)): G = S^T AS, Jacobi, theta = the m
 // smallest, C(:, 0:m) = their vectors, C(:, m:2m) = HL coefficients (hl).
 template <typename TW>
-__device__ void rayleigh_ritz(int n, int m, int ncol, const TW* S, const TW* AS, bool hl, Smem& s, int* flag) {
+__device__ void rayleigh_ritz(int n, int m, int ncol, const TW* S, const TW* AS, bool hl, Smem& s, int* flag,
+                              Ticker* tk = nullptr) {
   TW* G = as<TW>(s.G);
   TW* V = as<TW>(s.V);
   TW* C = as<TW>(s.C);
   TW* d = as<TW>(s.d);
-  gemm_tn<TW>(n, ncol, ncol, S, AS, G, as<TW>(s.tile));
+  gemm_tn<TW>(n, ncol, ncol, S, AS, V, as<TW>(s.tile));
+  // symmetrised copy into G with the odd leading dimension ncol + 1
+  const int ld = ncol + 1;
   for (int e = threadIdx.x; e < ncol * ncol; e += blockDim.x) {
     const int i = e % ncol, j = e / ncol;
-    if (i < j) {
-      const TW a = TW(0.5) * (G[i + j * ncol] + G[j + i * ncol]);
-      G[i + j * ncol] = a;
-      G[j + i * ncol] = a;
-    }
+    G[i + j * ld] = TW(0.5) * (V[i + j * ncol] + V[j + i * ncol]);
   }
   __syncthreads();
-  jacobi_eig<TW>(ncol, G, V, d, as<TW>(s.cs), s.order, flag);
-  for (int e = threadIdx.x; e < ncol * m; e += blockDim.x) C[e] = V[e];  // first m columns, ld ncol
+  if (tk) tk->tick(PH_GRAM);
+  const int sweeps = jacobi_eig<TW>(ncol, ld, G, V, d, as<TW>(s.cs), s.order);
+  for (int e = threadIdx.x; e < ncol * m; e += blockDim.x) C[e] = V[(e % ncol) + (e / ncol) * ld];  // ld ncol
   for (int j = threadIdx.x; j < m; j += blockDim.x) s.theta[j] = (double)d[j];
   __syncthreads();
+  if (tk) {
+    tk->tick(PH_EIG);
+    if (tk->acc && threadIdx.x == 0) tk->acc[PH_SWEEPS] += (unsigned long long)sweeps;
+  }
   if (hl) hl_coefficients<TW>(ncol, m, C, as<TW>(s.Y), C + (size_t)ncol * m, as<TW>(s.hb));
+  if (tk) tk->tick(PH_HL);
 }
 
 // Eq. (stop) on the first m columns: leading count n_c, and the largest
@@ -260,22 +295,34 @@ __device__ __forceinline__ int stop_test(int m, int k, double tol, double normA,
 // L^-T L^-1 in TF, back to TW into W (ld n).
 template <typename TW, typename TF>
 __device__ void precondition(int n, int m, const TW* R, const double* rn2, TW* W, TF* B, const TF* F,
-                             const TF* Dinv, Smem& s) {
-  for (int e = threadIdx.x; e < n * m; e += blockDim.x) {
-    const int j = e / n;
-    const double sc = rn2[j] > 0.0 ? 1.0 / sqrt(rn2[j]) : 1.0;
-    B[e] = (TF)((double)R[e] * sc);
-  }
+                             const TF* Dinv, Smem& s, Ticker* tk) {
+  // one scale per column (FP64 square roots and divisions are costly on
+  // this pipe: never per element); the scaling only fixes the direction
+  __shared__ float scale[MB_MAX];
+  for (int j = threadIdx.x; j < m; j += blockDim.x) scale[j] = rn2[j] > 0.0 ? (float)(1.0 / sqrt(rn2[j])) : 1.0f;
   __syncthreads();
-  chol_solve<TF>(n, m, F, Dinv, B, as<TF>(s.xs));
-  for (int e = threadIdx.x; e < n * m; e += blockDim.x) W[(e % n) + (long long)(e / n) * n] = (TW)B[e];
+  TF* ys = as<TF>(s.xs);
+  TF* Bs = ys + 2 * TB * MB_MAX + TB * (TB + 1);  // n x m right-hand sides in shared memory
+  for (int e = threadIdx.x; e < n * m; e += blockDim.x) Bs[e] = (TF)((float)R[e] * scale[e / n]);
   __syncthreads();
+  if (tk) tk->tick(PH_PRECOND);
+  chol_solve<TF>(n, m, F, Dinv, Bs, ys, [&](int pass) {
+    if (tk) tk->tick(pass == 0 ? PH_PRE_FWD : PH_PRE_BWD);
+  });
+  for (int e = threadIdx.x; e < n * m; e += blockDim.x) W[e] = (TW)Bs[e];
+  __syncthreads();
+  (void)B;
 }
 
 template <typename TW, typename TQ, typename TF>
 __device__ int run_stage(int n, int m, int k, const double* A, const TF* F, const TF* Dinv, TF* B, StageBufs<TW> bf,
                          TQ* Wq, const TW* X0, double tol, double normA, int maxit, bool stage1, bool qr_low,
-                         Smem& s, int* iters, int* cur_out, double* maxrel, int* sh) {
+                         Smem& s, int* iters, int* cur_out, double* maxrel, int* sh, Ticker* tk) {
+  Ticker* tp = stage1 ? nullptr : tk;  // stage 1 is timed as a whole by the caller
+  auto tick = [&](int ph) {
+    if (tp) tp->tick(ph);
+  };
+  if (tp) tp->start();
   int* flag = sh;
   int* ncs = sh + 1;
   int cur = 0;
@@ -293,6 +340,7 @@ __device__ int run_stage(int n, int m, int k, const double* A, const TF* F, cons
   gemm_nn<TW>(n, m, m, TW(1), bf.S[0], as<TW>(s.C), TW(0), bf.S[1]);
   gemm_nn<TW>(n, m, m, TW(1), bf.AS[0], as<TW>(s.C), TW(0), bf.AS[1]);
   cur = 1;
+  tick(PH_START);
   bool hasP = false;
   double window[6] = {0, 0, 0, 0, 0, 0};
   for (int it = 1; it <= maxit + 1; ++it) {
@@ -300,6 +348,7 @@ __device__ int run_stage(int n, int m, int k, const double* A, const TF* F, cons
     TW* AX = bf.AS[cur];
     residual<TW>(n, m, AX, X, s.theta, bf.R, s.rn2, s.xn2, s.red);
     int nc = stop_test(m, k, tol, normA, s, maxrel, ncs);
+    tick(PH_RESID);
     if (nc < 0) { *iters = it - 1; *cur_out = cur; return MPL_ENUMERICAL; }
     if (nc >= k && !stage1) {
       // explicit A X for the acceptance test (A X is carried through updates)
@@ -310,6 +359,7 @@ __device__ int run_stage(int n, int m, int k, const double* A, const TF* F, cons
         for (int e = threadIdx.x; e < n * m; e += blockDim.x) AX[e] = bf.V[e];
         __syncthreads();
       }
+      tick(PH_CHECK);
     }
     if (nc >= k) { *iters = it - 1; *cur_out = cur; return MPL_OK; }
     if (it > maxit) break;
@@ -320,18 +370,23 @@ __device__ int run_stage(int n, int m, int k, const double* A, const TF* F, cons
     }
     const int wcol = hasP ? 2 * m : m;
     TW* W = X + (size_t)wcol * n;
-    precondition<TW, TF>(n, m, bf.R, s.rn2, W, B, F, Dinv, s);
+    precondition<TW, TF>(n, m, bf.R, s.rn2, W, B, F, Dinv, s, tp);
+    tick(PH_PRECOND);
     TW* Gp = as<TW>(s.Y);  // wcol x m projection coefficients
     for (int pass = 0; pass < 2; ++pass) {
       gemm_tn<TW>(n, wcol, m, X, W, Gp, as<TW>(s.tile));
       gemm_nn<TW>(n, wcol, m, TW(-1), X, Gp, TW(1), W);
     }
+    tick(PH_PROJECT);
     if (!qr(W)) { *iters = it; *cur_out = cur; return MPL_ERANK; }
+    tick(PH_QR);
     apply_A<TW>(n, A, W, AX + (size_t)wcol * n, m, as<TW>(s.xs));
+    tick(PH_APPLY);
     const int ncol = wcol + m;
-    rayleigh_ritz<TW>(n, m, ncol, X, AX, true, s, flag);
+    rayleigh_ritz<TW>(n, m, ncol, X, AX, true, s, flag, tp);
     gemm_nn<TW>(n, ncol, 2 * m, TW(1), X, as<TW>(s.C), TW(0), bf.S[1 - cur]);
     gemm_nn<TW>(n, ncol, 2 * m, TW(1), AX, as<TW>(s.C), TW(0), bf.AS[1 - cur]);
+    tick(PH_UPDATE);
     cur = 1 - cur;
     hasP = true;
   }
@@ -341,8 +396,9 @@ __device__ int run_stage(int n, int m, int k, const double* A, const TF* F, cons
 }
 
 template <typename TF>
-__device__ void solve_problem(const Args& a, int p, unsigned char* ws, Smem& s, int* sh) {
+__device__ void solve_problem(const Args& a, int p, unsigned char* ws, Smem& s, int* sh, Ticker* tk) {
   const int n = (int)a.nvec[p], m = a.m, k = a.k;
+  tk->start();
   const double* A = a.A + a.a_off[p];
   const long long xo = a.x_off[p];
   const WsLayout L = ws_layout(a.nmax, m, (int)sizeof(TF));
@@ -362,6 +418,7 @@ __device__ void solve_problem(const Args& a, int p, unsigned char* ws, Smem& s, 
   for (int c = 0; c < 8; ++c) no += s.cs[c];
   __syncthreads();
   const double normA = sqrt(ny) / sqrt(no);
+  tk->tick(PH_NORM);
   // factor with the shift policy
   const double ul = sizeof(TF) == 4 ? ldexp(1.0, -24) : ldexp(1.0, -53);
   double sigma = 0.0;
@@ -375,6 +432,7 @@ __device__ void solve_problem(const Args& a, int p, unsigned char* ws, Smem& s, 
     info = cholesky<TF>(n, F, Dinv, as<TF>(s.xs), sh + 2);
     if (info) sigma = ldexp(1.0, j) * ul * normA;
   }
+  tk->tick(PH_FACTOR);
   int st = MPL_OK, it1 = 0, it2 = 0, cur = 0;
   double maxrel = 0.0;
   const double* X0 = a.X0 + xo * m;
@@ -396,7 +454,8 @@ __device__ void solve_problem(const Args& a, int p, unsigned char* ws, Smem& s, 
       __syncthreads();
       if constexpr (sizeof(TF) == 4) {
         const int s1 = run_stage<float, float, float>(n, m, k, A, F, Dinv, B, b1, x0f, x0l, 5e-6, normA, a.maxit,
-                                                      true, true, s, &it1, &cur, &maxrel, sh);
+                                                      true, true, s, &it1, &cur, &maxrel, sh, tk);
+        tk->tick(PH_STAGE1);
         if (s1 == MPL_OK || s1 == MPL_ENOT_CONVERGED) {
           // stage-2 start: double(X) of stage 1, staged in S1 (run_stage copies
           // its start into S0 before touching S1)
@@ -409,11 +468,11 @@ __device__ void solve_problem(const Args& a, int p, unsigned char* ws, Smem& s, 
       }
       // Algorithm 2 step 1 in the lower precision, FP64 fallback
       st = run_stage<double, float, TF>(n, m, k, A, F, Dinv, B, b2, reinterpret_cast<float*>(ws + L.Wq), start,
-                                        a.tol, normA, a.maxit, false, true, s, &it2, &cur, &maxrel, sh);
+                                        a.tol, normA, a.maxit, false, true, s, &it2, &cur, &maxrel, sh, tk);
     } else {
       // D policies: Algorithm 2 with step 1 in working precision
       st = run_stage<double, double, TF>(n, m, k, A, F, Dinv, B, b2, reinterpret_cast<double*>(ws + L.Wq), start,
-                                         a.tol, normA, a.maxit, false, false, s, &it2, &cur, &maxrel, sh);
+                                         a.tol, normA, a.maxit, false, false, s, &it2, &cur, &maxrel, sh, tk);
     }
   }
   // outputs
@@ -431,12 +490,12 @@ __device__ void solve_problem(const Args& a, int p, unsigned char* ws, Smem& s, 
 }
 
 template <typename TF>
-__global__ void batch_kernel(const Args* __restrict__ ap) {
+__global__ void __launch_bounds__(256, 2) batch_kernel(const Args* __restrict__ ap) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int sh[8];
   __shared__ int next;
   const Args a = *ap;
-  const SmemLayout SL = smem_layout(a.nmax, a.m, blockDim.x >> 5);
+  const SmemLayout SL = smem_layout(a.nmax, a.m, blockDim.x >> 5, (int)sizeof(TF));
   Smem s;
   s.xs = reinterpret_cast<double*>(smraw + SL.xs);
   s.tile = reinterpret_cast<double*>(smraw + SL.tile);
@@ -457,14 +516,19 @@ __global__ void batch_kernel(const Args* __restrict__ ap) {
   s.red = reinterpret_cast<double*>(smraw + SL.red);
   s.order = reinterpret_cast<int*>(smraw + SL.order);
   unsigned char* ws = a.ws + (size_t)blockIdx.x * a.ws_stride;
+  __shared__ unsigned long long pacc[PH_COUNT];
+  Ticker tk{a.phase ? pacc : nullptr, 0};
+  if (threadIdx.x < PH_COUNT) pacc[threadIdx.x] = 0ull;
+  __syncthreads();
   for (;;) {
     if (threadIdx.x == 0) next = atomicAdd(a.counter, 1);
     __syncthreads();
     const int q = next;
     __syncthreads();
     if (q >= a.nprob) break;
-    solve_problem<TF>(a, a.order[q], ws, s, sh);
+    solve_problem<TF>(a, a.order[q], ws, s, sh, &tk);
   }
+  if (a.phase && threadIdx.x < PH_COUNT) atomicAdd(a.phase + threadIdx.x, pacc[threadIdx.x]);
 }
 
 }  // namespace bt
@@ -487,6 +551,7 @@ struct mpl_batch {
   bt::Args* d_args = nullptr;
   bt::Args h_args{};
   int* d_counter = nullptr;
+  unsigned long long* d_phase = nullptr;  // MPL_BATCH_PHASES=1: per-phase clock64 sums
   unsigned char* d_ws = nullptr;
   int threads = 256, blocks = 0, per_sm = 1;
   double tuned_ms = 0.0;
@@ -505,6 +570,10 @@ cudaError_t launch_batch(mpl_batch* b, int threads, int blocks, size_t smem, cud
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
+  if (b->d_phase) {
+    e = cudaMemsetAsync(b->d_phase, 0, sizeof(unsigned long long) * bt::PH_COUNT, st);
+    if (e != cudaSuccess) return e;
+  }
   count_launch();
   kern<<<blocks, threads, smem, st>>>(b->d_args);
   return cudaGetLastError();
@@ -579,14 +648,14 @@ extern "C" mpl_status mpl_batch_create(mpl_batch_handle* out, int nprob, const i
   int max_blocks = 0;
   const int cand_threads[3] = {128, 256, 512};  // 512 is skipped where registers do not allow it
   for (int t : cand_threads) {
-    const size_t sm = bt::smem_layout(b->nmax, m, t / 32).total;
+    const size_t sm = bt::smem_layout(b->nmax, m, t / 32, fsize).total;
     if (sm > 227 * 1024) continue;
     if (policy == MPL_D_DCHOL)
       cudaFuncSetAttribute(bt::batch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     else
       cudaFuncSetAttribute(bt::batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaGetLastError();
-    const int per = std::min(max_blocks_per_sm(b.get(), t, sm), 2);
+    const int per = std::min(max_blocks_per_sm(b.get(), t, sm), 4);
     if (t * 12 < 3 * m * 3 * m) continue;  // Gram outputs per thread
     max_blocks = std::max(max_blocks, per * NUM_SMS);
   }
@@ -599,7 +668,13 @@ extern "C" mpl_status mpl_batch_create(mpl_batch_handle* out, int nprob, const i
     mpl_batch_destroy(b.release());
     return MPL_ENOMEM;
   }
+  const char* ph = std::getenv("MPL_BATCH_PHASES");
+  if (ph && ph[0] == '1' && !alloc((void**)&b->d_phase, sizeof(unsigned long long) * bt::PH_COUNT)) {
+    mpl_batch_destroy(b.release());
+    return MPL_ENOMEM;
+  }
   bt::Args& a = b->h_args;
+  a.phase = b->d_phase;
   a.order = b->d_order;
   a.nvec = b->d_n;
   a.a_off = b->d_aoff;
@@ -650,14 +725,14 @@ extern "C" mpl_status mpl_batch_tune(mpl_batch_handle b, const double* X0, doubl
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   for (int t : cand_threads) {
-    const size_t sm = bt::smem_layout(b->nmax, b->m, t / 32).total;
+    const size_t sm = bt::smem_layout(b->nmax, b->m, t / 32, b->policy == MPL_D_DCHOL ? 8 : 4).total;
     if (sm > 227 * 1024 || t * 12 < 9 * b->m * b->m) continue;
     if (b->policy == MPL_D_DCHOL)
       cudaFuncSetAttribute(bt::batch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     else
       cudaFuncSetAttribute(bt::batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaGetLastError();
-    const int maxper = std::min(max_blocks_per_sm(b, t, sm), 2);
+    const int maxper = std::min(max_blocks_per_sm(b, t, sm), 4);
     for (int per = 1; per <= maxper; ++per) {
       const int blocks = std::min(per * NUM_SMS, b->nprob);
       const size_t ws_stride = (size_t)b->h_args.ws_stride;
@@ -702,7 +777,7 @@ extern "C" mpl_status mpl_batch_solve(mpl_batch_handle b, const double* X0, doub
   cudaStream_t st = b->stream;
   if (b->blocks == 0) {  // untuned: 256 threads, one block per SM
     b->threads = 256;
-    b->smem = bt::smem_layout(b->nmax, b->m, 8).total;
+    b->smem = bt::smem_layout(b->nmax, b->m, 8, b->policy == MPL_D_DCHOL ? 8 : 4).total;
     b->per_sm = 1;
     b->blocks = std::min(NUM_SMS, b->nprob);
   }
@@ -751,8 +826,21 @@ extern "C" mpl_status mpl_batch_get_config(mpl_batch_handle b, int* threads, int
   return MPL_OK;
 }
 
+extern "C" mpl_status mpl_batch_get_phase_cycles(mpl_batch_handle b, unsigned long long* cycles, int count) {
+  if (!b || !cycles || count <= 0) return MPL_EINVAL;
+  for (int i = 0; i < count; ++i) cycles[i] = 0ull;
+  if (!b->d_phase) return MPL_ESTATE;
+  const int c = std::min(count, (int)bt::PH_COUNT);
+  if (cudaMemcpy(cycles, b->d_phase, sizeof(unsigned long long) * c, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return MPL_ECUDA;
+  }
+  return MPL_OK;
+}
+
 extern "C" void mpl_batch_destroy(mpl_batch_handle b) {
   if (!b) return;
+  cudaFree(b->d_phase);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   cudaFree(b->d_order);

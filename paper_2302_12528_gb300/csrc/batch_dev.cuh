@@ -53,7 +53,19 @@ __device__ void apply_A(int n, const double* __restrict__ A, const TC* X, TC* Y,
 #pragma unroll
       for (int c = 0; c < 8; ++c) acc[c] = TC(0);
       const double* Ai = A + i;
-      for (int j = 0; j < n; ++j) {
+      int j = 0;
+      for (; j + 4 <= n; j += 4) {
+        TC a4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a4[u] = (TC)Ai[(long long)(j + u) * n];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const TC* xj = xs + (j + u) * 8;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) acc[c] = fmad(a4[u], xj[c], acc[c]);
+        }
+      }
+      for (; j < n; ++j) {
         const TC a = (TC)Ai[(long long)j * n];
         const TC* xj = xs + j * 8;
 #pragma unroll
@@ -65,25 +77,27 @@ __device__ void apply_A(int n, const double* __restrict__ A, const TC* X, TC* Y,
   __syncthreads();
 }
 
-// G (p x q, ld p, shared) = A(:, 0:p)^T B(:, 0:q); tile: shared, GT (p + q)
-// values.  Requires p q <= MAXO * blockDim.x.
+// G (p x q, ld p, shared) = A(:, 0:p)^T B(:, 0:q); tile: shared, (GT + 1)
+// (p + q) values (odd leading dimension: lanes that read different columns
+// of a tile hit different banks).  Requires p q <= MAXO * blockDim.x.
 template <typename TC>
 __device__ void gemm_tn(int n, int p, int q, const TC* A, const TC* B, TC* G, TC* tile) {
+  constexpr int LT = GT + 1;
   TC acc[MAXO];
 #pragma unroll
   for (int o = 0; o < MAXO; ++o) acc[o] = TC(0);
-  TC* As = tile;           // As[r + GT * i]
-  TC* Bs = tile + GT * p;  // Bs[r + GT * j]
+  TC* As = tile;           // As[r + LT * i]
+  TC* Bs = tile + LT * p;  // Bs[r + LT * j]
   for (int r0 = 0; r0 < n; r0 += GT) {
     const int rw = min(GT, n - r0);
     __syncthreads();
     for (int e = threadIdx.x; e < GT * p; e += blockDim.x) {
       const int r = e % GT, i = e / GT;
-      As[e] = r < rw ? A[r0 + r + (long long)i * n] : TC(0);
+      As[r + LT * i] = r < rw ? A[r0 + r + (long long)i * n] : TC(0);
     }
     for (int e = threadIdx.x; e < GT * q; e += blockDim.x) {
       const int r = e % GT, j = e / GT;
-      Bs[e] = r < rw ? B[r0 + r + (long long)j * n] : TC(0);
+      Bs[r + LT * j] = r < rw ? B[r0 + r + (long long)j * n] : TC(0);
     }
     __syncthreads();
 #pragma unroll
@@ -91,8 +105,8 @@ __device__ void gemm_tn(int n, int p, int q, const TC* A, const TC* B, TC* G, TC
       const int idx = threadIdx.x + o * blockDim.x;
       if (idx < p * q) {
         const int i = idx % p, j = idx / p;
-        const TC* a = As + GT * i;
-        const TC* b = Bs + GT * j;
+        const TC* a = As + LT * i;
+        const TC* b = Bs + LT * j;
         TC s = acc[o];
         for (int r = 0; r < GT; ++r) s = fmad(a[r], b[r], s);
         acc[o] = s;
@@ -323,82 +337,79 @@ __device__ int cholesky(int n, TF* F, TF* Dinv, TF* sm, int* flag) {
   return 0;
 }
 
-// B <- L^-T L^-1 B in place (B: n x q of TF, ld n); F, Dinv from cholesky.
-// ys: shared, TB * q values.
-template <typename TF>
-__device__ void chol_solve(int n, int q, const TF* F, const TF* Dinv, TF* B, TF* ys) {
+// B <- L^-T L^-1 B in place, B (n x q of TF, ld n) in shared memory for the
+// whole solve; F, Dinv from cholesky (global).  ys: shared, 2 TB MB_MAX +
+// TB (TB + 1) values of TF.  mark(pass) is called by every thread after each
+// pass (profiling hook).
+template <typename TF, typename Mark>
+__device__ void chol_solve(int n, int q, const TF* F, const TF* Dinv, TF* B, TF* ys, Mark mark) {
+  constexpr int LD = TB + 1;      // odd leading dimension of the staged Dinv block
   const int nb = (n + TB - 1) / TB;
-  // forward: L Y = B
-  for (int kb = 0; kb < nb; ++kb) {
-    const int k0 = kb * TB, kw = min(TB, n - k0);
-    const TF* Di = Dinv + (size_t)kb * TB * TB;
-    __syncthreads();
-    for (int e = threadIdx.x; e < TB * q; e += blockDim.x) {
-      const int r = e % TB, c = e / TB;
-      ys[e] = r < kw ? B[k0 + r + (long long)c * n] : TF(0);
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < kw * q; e += blockDim.x) {
-      const int r = e % kw, c = e / kw;
-      TF s = TF(0);
-      for (int l = 0; l <= r; ++l) s = fmad(Di[r + l * TB], ys[l + c * TB], s);
-      B[k0 + r + (long long)c * n] = s;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < TB * q; e += blockDim.x) {
-      const int r = e % TB, c = e / TB;
-      ys[e] = r < kw ? B[k0 + r + (long long)c * n] : TF(0);
-    }
-    __syncthreads();
-    for (int i = k0 + kw + threadIdx.x; i < n; i += blockDim.x) {
-      TF acc[MB_MAX];
+  TF* zk = ys + TB * MB_MAX;      // solved block (TB x q)
+  TF* Dk = ys + 2 * TB * MB_MAX;  // Dinv block (TB x TB, ld LD)
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool back = pass == 1;
+    for (int s = 0; s < nb; ++s) {
+      const int kb = back ? nb - 1 - s : s;
+      const int k0 = kb * TB, kw = min(TB, n - k0);
+      const TF* Di = Dinv + (size_t)kb * TB * TB;
+      // stage Dinv_k: all loads of a thread issued before its stores
+      {
+        constexpr int PER = (TB * TB + 127) / 128;
+        TF v[PER];
 #pragma unroll
-      for (int c = 0; c < MB_MAX; ++c) acc[c] = TF(0);
-      for (int l = 0; l < kw; ++l) {
-        const TF a = F[i + (long long)(k0 + l) * n];
+        for (int u = 0; u < PER; ++u) {
+          const int e = threadIdx.x + u * blockDim.x;
+          v[u] = e < TB * TB ? Di[e] : TF(0);
+        }
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+          const int e = threadIdx.x + u * blockDim.x;
+          if (e < TB * TB) Dk[(e % TB) + (e / TB) * LD] = v[u];
+        }
+        for (int e = threadIdx.x + PER * blockDim.x; e < TB * TB; e += blockDim.x)
+          Dk[(e % TB) + (e / TB) * LD] = Di[e];
+      }
+      __syncthreads();
+      // diagonal block: forward Dinv y, backward Dinv^T y (Dinv lower, zero above)
+      for (int e = threadIdx.x; e < TB * q; e += blockDim.x) {
+        const int r = e % TB, c = e / TB;
+        TF acc = TF(0);
+#pragma unroll
+        for (int l = 0; l < TB; ++l) {
+          const TF y = l < kw ? B[k0 + l + c * n] : TF(0);
+          acc = fmad(back ? Dk[l + r * LD] : Dk[r + l * LD], y, acc);
+        }
+        zk[e] = acc;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < kw * q; e += blockDim.x) {
+        const int r = e % kw, c = e / kw;
+        B[k0 + r + c * n] = zk[r + c * TB];
+      }
+      // update the remaining rows: forward rows below the block with L(:, block),
+      // backward rows above it with U(:, block) = L(block, :)^T
+      const int i0 = back ? 0 : k0 + kw, i1 = back ? k0 : n;
+      for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        TF a[TB];
+#pragma unroll
+        for (int l = 0; l < TB; ++l) a[l] = l < kw ? F[i + (long long)(k0 + l) * n] : TF(0);
+        TF acc[MB_MAX];
+#pragma unroll
+        for (int c = 0; c < MB_MAX; ++c) acc[c] = TF(0);
+#pragma unroll
+        for (int l = 0; l < TB; ++l)
+#pragma unroll
+          for (int c = 0; c < MB_MAX; ++c)
+            if (c < q) acc[c] = fmad(a[l], zk[l + c * TB], acc[c]);
 #pragma unroll
         for (int c = 0; c < MB_MAX; ++c)
-          if (c < q) acc[c] = fmad(a, ys[l + c * TB], acc[c]);
+          if (c < q) B[i + c * n] -= acc[c];
       }
-      for (int c = 0; c < q; ++c) B[i + (long long)c * n] -= acc[c];
+      __syncthreads();
     }
+    mark(pass);
   }
-  // backward: L^T Z = Y, with U = L^T in the strict upper triangle
-  for (int kb = nb - 1; kb >= 0; --kb) {
-    const int k0 = kb * TB, kw = min(TB, n - k0);
-    const TF* Di = Dinv + (size_t)kb * TB * TB;
-    __syncthreads();
-    for (int e = threadIdx.x; e < TB * q; e += blockDim.x) {
-      const int r = e % TB, c = e / TB;
-      ys[e] = r < kw ? B[k0 + r + (long long)c * n] : TF(0);
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < kw * q; e += blockDim.x) {
-      const int r = e % kw, c = e / kw;
-      TF s = TF(0);
-      for (int l = r; l < kw; ++l) s = fmad(Di[l + r * TB], ys[l + c * TB], s);  // Dinv^T
-      B[k0 + r + (long long)c * n] = s;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < TB * q; e += blockDim.x) {
-      const int r = e % TB, c = e / TB;
-      ys[e] = r < kw ? B[k0 + r + (long long)c * n] : TF(0);
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < k0; j += blockDim.x) {
-      TF acc[MB_MAX];
-#pragma unroll
-      for (int c = 0; c < MB_MAX; ++c) acc[c] = TF(0);
-      for (int l = 0; l < kw; ++l) {
-        const TF u = F[j + (long long)(k0 + l) * n];  // U(j, k0 + l) = L(k0 + l, j)
-#pragma unroll
-        for (int c = 0; c < MB_MAX; ++c)
-          if (c < q) acc[c] = fmad(u, ys[l + c * TB], acc[c]);
-      }
-      for (int c = 0; c < q; ++c) B[j + (long long)c * n] -= acc[c];
-    }
-  }
-  __syncthreads();
 }
 
 }  // namespace bt

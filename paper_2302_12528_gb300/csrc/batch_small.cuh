@@ -8,104 +8,110 @@
 namespace mpl {
 namespace bt {
 
-// Eigen-decomposition of the symmetric N x N matrix G (shared, ld N) by the
-// cyclic Jacobi method with the round-robin ordering (N/2 disjoint rotations
-// per round, N-1 rounds per sweep; Golub & Van Loan, Matrix Computations,
-// Sect. 8.5): on exit d[0..N) ascending, V (shared, N x N, ld N) the
-// corresponding orthonormal eigenvectors.  G is destroyed.  cs: shared,
-// 2 * NC_MAX + 2 values; order: shared, NC_MAX + 1 ints.
+// Eigen-decomposition of the symmetric N x N matrix G by the cyclic Jacobi
+// method with the round-robin ordering (N/2 disjoint rotations per round,
+// N-1 rounds per sweep; Golub & Van Loan, Matrix Computations, Sect. 8.5).
+// A rotation is skipped when |g_pq| <= eps sqrt(|g_pp g_qq|) (threshold
+// Jacobi) and the iteration stops after a sweep without a rotation.  The
+// rotation angles of a round are computed by warp 0 (one lane per pair:
+// FP64 square roots and divisions are costly, so they are not repeated);
+// the row and column updates are spread over the whole block.  G and V are
+// N x N in shared memory with leading dimension ld (odd, against bank
+// conflicts).  On exit d[0..N) ascending, V the corresponding orthonormal
+// eigenvectors; G is destroyed.  cs: shared, 2 * NC_MAX + 2 values; order:
+// shared, NC_MAX + 1 ints.  Returns the number of sweeps.
 template <typename T>
-__device__ void jacobi_eig(int N, T* G, T* V, T* d, T* cs, int* order, int* flag) {
+__device__ int jacobi_eig(int N, int ld, T* G, T* V, T* d, T* cs, int* order) {
+  __shared__ int rotated;
   const int Np = N + (N & 1);  // even number of players (the last is a dummy if N is odd)
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) V[e] = (e % N == e / N) ? T(1) : T(0);
-  __syncthreads();
-  const T eps = sizeof(T) == 8 ? T(1e-16) : T(6e-8);
-  for (int sweep = 0; sweep < 30; ++sweep) {
-    // convergence: off(G)^2 <= eps^2 ||G||_F^2
-    if (threadIdx.x == 0) {
-      T off = T(0), tot = T(0);
-      for (int j = 0; j < N; ++j)
-        for (int i = 0; i < N; ++i) {
-          const T g = G[i + j * N] * G[i + j * N];
-          tot += g;
-          if (i != j) off += g;
-        }
-      *flag = (off <= eps * eps * tot) ? 1 : 0;
-    }
+  const int half = Np / 2;
+  const T eps = sizeof(T) == 8 ? T(2.3e-16) : T(1.2e-7);
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) V[(e % N) + (e / N) * ld] = (e % N == e / N) ? T(1) : T(0);
+  // player at position i in round r: 0 stays, the others rotate
+  auto player = [&](int i, int r) { return i == 0 ? 0 : 1 + (i - 1 + r) % (Np - 1); };
+  int sweep = 0;
+  for (; sweep < 40; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
-    if (*flag) break;
     for (int r = 0; r < Np - 1; ++r) {
-      // pairs of round r: position 0 fixed, the others rotate
-      for (int i = threadIdx.x; i < Np; i += blockDim.x) order[i] = (i == 0) ? 0 : 1 + (i - 1 + r) % (Np - 1);
-      __syncthreads();
-      for (int pi = threadIdx.x; pi < Np / 2; pi += blockDim.x) {
-        int p = order[pi], q = order[Np - 1 - pi];
+      if (threadIdx.x < half) {
+        const int pi = threadIdx.x;
+        int p = player(pi, r), q = player(Np - 1 - pi, r);
         if (p > q) { const int t = p; p = q; q = t; }
         T c = T(1), s = T(0);
         if (q < N) {
-          const T apq = G[p + q * N];
-          if (apq != T(0)) {
-            const T app = G[p + p * N], aqq = G[q + q * N];
-            const T tau = (aqq - app) / (T(2) * apq);
-            const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt_(T(1) + tau * tau));
+          const T apq = G[p + q * ld];
+          const T app = G[p + p * ld], aqq = G[q + q * ld];
+          if (apq != T(0) && fabs(apq) > eps * sqrt_(fabs(app * aqq))) {
+            // t = tan(theta) = sign(tau) / (|tau| + sqrt(1 + tau^2)), tau = (aqq - app) / (2 apq),
+            // written as 2 apq sign / (|aqq - app| + sqrt((aqq - app)^2 + 4 apq^2))
+            const T dlt = aqq - app;
+            const T sg = (dlt >= T(0)) ? T(1) : T(-1);
+            const T t = sg * T(2) * apq / (fabs(dlt) + sqrt_(dlt * dlt + T(4) * apq * apq));
             c = T(1) / sqrt_(T(1) + t * t);
             s = t * c;
+            rotated = 1;
           }
         }
+        order[2 * pi] = p;
+        order[2 * pi + 1] = q;
         cs[2 * pi] = c;
         cs[2 * pi + 1] = s;
       }
       __syncthreads();
       // rows: G <- J^T G
-      for (int e = threadIdx.x; e < (Np / 2) * N; e += blockDim.x) {
+      for (int e = threadIdx.x; e < half * N; e += blockDim.x) {
         const int pi = e / N, j = e % N;
-        int p = order[pi], q = order[Np - 1 - pi];
-        if (p > q) { const int t = p; p = q; q = t; }
-        if (q >= N) continue;
-        const T c = cs[2 * pi], s = cs[2 * pi + 1];
-        const T gp = G[p + j * N], gq = G[q + j * N];
-        G[p + j * N] = c * gp - s * gq;
-        G[q + j * N] = s * gp + c * gq;
+        const T s = cs[2 * pi + 1];
+        if (s == T(0)) continue;
+        const int p = order[2 * pi], q = order[2 * pi + 1];
+        const T c = cs[2 * pi];
+        const T gp = G[p + j * ld], gq = G[q + j * ld];
+        G[p + j * ld] = c * gp - s * gq;
+        G[q + j * ld] = s * gp + c * gq;
       }
       __syncthreads();
       // columns: G <- G J, V <- V J
-      for (int e = threadIdx.x; e < (Np / 2) * N; e += blockDim.x) {
-        const int pi = e / N, i = e % N;
-        int p = order[pi], q = order[Np - 1 - pi];
-        if (p > q) { const int t = p; p = q; q = t; }
-        if (q >= N) continue;
-        const T c = cs[2 * pi], s = cs[2 * pi + 1];
-        const T gp = G[i + p * N], gq = G[i + q * N];
-        G[i + p * N] = c * gp - s * gq;
-        G[i + q * N] = s * gp + c * gq;
-        const T vp = V[i + p * N], vq = V[i + q * N];
-        V[i + p * N] = c * vp - s * vq;
-        V[i + q * N] = s * vp + c * vq;
+      for (int e = threadIdx.x; e < 2 * half * N; e += blockDim.x) {
+        const int w = e / (half * N), f = e % (half * N);
+        const int pi = f / N, i = f % N;
+        const T s = cs[2 * pi + 1];
+        if (s == T(0)) continue;
+        const int p = order[2 * pi], q = order[2 * pi + 1];
+        const T c = cs[2 * pi];
+        T* M = w == 0 ? G : V;
+        const T mp = M[i + p * ld], mq = M[i + q * ld];
+        M[i + p * ld] = c * mp - s * mq;
+        M[i + q * ld] = s * mp + c * mq;
       }
       __syncthreads();
     }
+    const int any = rotated;  // read by every thread before thread 0 resets it
+    __syncthreads();
+    if (!any) break;
   }
   // sort ascending (rank by value, ties by index) into d and the columns of G
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    const T v = G[j + j * N];
+    const T v = G[j + j * ld];
     int rank = 0;
     for (int i = 0; i < N; ++i) {
-      const T w = G[i + i * N];
+      const T w = G[i + i * ld];
       rank += (w < v || (w == v && i < j)) ? 1 : 0;
     }
     order[j] = rank;
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < N; j += blockDim.x) d[order[j]] = G[j + j * N];
+  for (int j = threadIdx.x; j < N; j += blockDim.x) d[order[j]] = G[j + j * ld];
   __syncthreads();
   // permute V's columns through G as scratch
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
     const int i = e % N, j = e / N;
-    G[i + order[j] * N] = V[e];
+    G[i + order[j] * ld] = V[i + j * ld];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) V[e] = G[e];
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) V[(e % N) + (e / N) * ld] = G[(e % N) + (e / N) * ld];
   __syncthreads();
+  return sweep + 1;
 }
 
 // HL coefficients (Section 2): Q (N x m, ld N) = the trailing m columns of
@@ -129,37 +135,47 @@ __device__ void hl_coefficients(int N, int m, const T* C1, T* Y, T* Q, T* hb) {
   __syncthreads();
   T* tau = hb;
   T* uh = hb + q;
+  __shared__ T tub[3];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = 0; j < q && j < N; ++j) {
-    __shared__ T s2sh, x0sh;
-    if (threadIdx.x == 0) {
+    // ||Y(j+1:, j)||^2 by warp 0, scalars by its lane 0
+    if (wid == 0) {
       T s2 = T(0);
-      for (int i = j + 1; i < N; ++i) s2 += Y[i + j * N] * Y[i + j * N];
-      s2sh = s2;
-      x0sh = Y[j + j * N];
+      for (int i = j + 1 + lane; i < N; i += 32) s2 += Y[i + j * N] * Y[i + j * N];
+      s2 = warp_sum(s2);
+      if (lane == 0) {
+        const T x0 = Y[j + j * N];
+        T t = T(0), u0 = T(0), beta = x0;
+        if (s2 != T(0)) {
+          const T alpha = sqrt_(s2 + x0 * x0);
+          beta = (x0 >= T(0)) ? -alpha : alpha;
+          u0 = x0 - beta;
+          t = T(1) / (alpha * (alpha + fabs(x0)));
+        }
+        tub[0] = t;
+        tub[1] = u0;
+        tub[2] = beta;
+      }
     }
     __syncthreads();
-    const T s2 = s2sh, x0 = x0sh;
-    T t = T(0), u0 = T(0), beta = x0;
-    if (s2 != T(0)) {
-      const T alpha = sqrt_(s2 + x0 * x0);
-      beta = (x0 >= T(0)) ? -alpha : alpha;
-      u0 = x0 - beta;
-      t = T(1) / (alpha * (alpha + fabs(x0)));
-    }
-    // apply H_j = I - t u u^T to the later columns (u = [u0; Y(j+1:, j)])
-    for (int c = j + 1 + threadIdx.x; c < q; c += blockDim.x) {
-      if (t == T(0)) break;
-      T dot = u0 * Y[j + c * N];
-      for (int i = j + 1; i < N; ++i) dot += Y[i + j * N] * Y[i + c * N];
-      const T g = t * dot;
-      Y[j + c * N] -= g * u0;
-      for (int i = j + 1; i < N; ++i) Y[i + c * N] -= g * Y[i + j * N];
-    }
+    const T t = tub[0], u0 = tub[1];
+    // apply H_j = I - t u u^T to the later columns (u = [u0; Y(j+1:, j)]): one warp per column
+    if (t != T(0))
+      for (int c = j + 1 + wid; c < q; c += nw) {
+        T dot = T(0);
+        for (int i = j + 1 + lane; i < N; i += 32) dot += Y[i + j * N] * Y[i + c * N];
+        dot = warp_sum(dot) + u0 * Y[j + c * N];
+        const T g = t * dot;
+        __syncwarp();
+        if (lane == 0) Y[j + c * N] -= g * u0;
+        for (int i = j + 1 + lane; i < N; i += 32) Y[i + c * N] -= g * Y[i + j * N];
+        __syncwarp();
+      }
     __syncthreads();
     if (threadIdx.x == 0) {
       tau[j] = t;
       uh[j] = u0;
-      Y[j + j * N] = beta;
+      Y[j + j * N] = tub[2];
     }
     __syncthreads();
   }
