@@ -111,8 +111,71 @@ def lower_cholesky(A, normA_est, dtype=None, max_tries=8):
     raise np.linalg.LinAlgError("lower-precision Cholesky broke down for every shift")
 
 
+# ---- 16-bit factor stage (the lower precision taken below single) --------
+U16 = {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8}
+
+
+def round_fmt(x, fmt):
+    """Round to the 16-bit format ``fmt`` ("fp16" IEEE half, "bf16" bfloat16:
+    round to nearest, ties to even, on the top 16 bits of the float32
+    pattern), real and imaginary parts separately; returned as
+    float32 / complex64."""
+    x = np.asarray(x)
+
+    def r(v):
+        v = np.asarray(v, dtype=np.float32)
+        if fmt == "fp16":
+            return v.astype(np.float16).astype(np.float32)
+        b = v.view(np.uint32).astype(np.uint64)
+        b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+        return b.astype(np.uint32).view(np.float32)
+
+    if np.iscomplexobj(x):
+        return (r(x.real) + 1j * r(x.imag)).astype(np.complex64)
+    return r(x)
+
+
+class ScaledLowerFactor(LowerFactor):
+    """L with D (A + sigma D^-2) D ~ L L^*, D = diag(A)^-1/2; T = D L^-* L^-1 D."""
+
+    def __init__(self, L, sigma, tries, dtype, d, fmt):
+        super().__init__(L, sigma, tries, dtype)
+        self.d = d
+        self.fmt = fmt
+
+
+def lower_cholesky_fmt(A, fmt, max_tries=8):
+    """16-bit preconditioner factor: D = diag(A)^-1/2 makes the scaled matrix
+    D A D unit-diagonal (entries within the format's range); it is rounded to
+    the format, factored with FP32 arithmetic, and the factor rounded to the
+    format.  Breakdown: retry with D A D + sigma I, sigma = 2^j u_fmt (the
+    scaled matrix's mean eigenvalue trace(D A D)/n = 1 sets the scale)."""
+    A = np.asarray(A)
+    low = LOWER[A.dtype]
+    d = (1.0 / np.sqrt(np.real(np.diag(A)))).astype(np.float32)
+    S = d.astype(np.float64)[:, None] * A * d.astype(np.float64)[None, :]
+    u = U16[fmt]
+    sigma = 0.0
+    for j in range(max_tries + 1):
+        M = round_fmt(S + sigma * np.eye(A.shape[0]), fmt).astype(low)
+        try:
+            L = sla.cholesky(M, lower=True, check_finite=True)
+            if not np.all(np.isfinite(L)):
+                raise np.linalg.LinAlgError("non-finite factor")
+            return ScaledLowerFactor(round_fmt(L, fmt).astype(low), sigma, j, low, d, fmt)
+        except (np.linalg.LinAlgError, sla.LinAlgError, ValueError):
+            sigma = (2.0 ** j) * u
+    raise np.linalg.LinAlgError("16-bit Cholesky broke down for every shift")
+
+
 def apply_T(F: LowerFactor, Rl):
     """W_l = L^-* (L^-1 R_l), both triangular solves in the factor's precision."""
     Rl = np.asarray(Rl).astype(F.dtype)
+    d = getattr(F, "d", None)
+    if d is not None:   # scaled factor: T = D L^-* L^-1 D
+        Rl = (d[:, None] * Rl).astype(F.dtype)
     Y = sla.solve_triangular(F.L, Rl, lower=True, check_finite=False)
-    return sla.solve_triangular(F.L, Y, lower=True, trans="C", check_finite=False)
+    W = sla.solve_triangular(F.L, Y, lower=True, trans="C", check_finite=False)
+    if d is not None:
+        W = (d[:, None] * W).astype(F.dtype)
+    return W

@@ -173,6 +173,8 @@ def solve(op, factor_matrix, X0, Omega, k, tol=1e-12, policy="mp", maxit=2000,
         F = lower_factor
     elif policy == "dchol":
         F = D.lower_cholesky(factor_matrix, normA, dtype=work)
+    elif policy in ("hchol", "bchol"):   # Algorithm 3 with a 16-bit factor (fp16 / bf16)
+        F = D.lower_cholesky_fmt(factor_matrix, "fp16" if policy == "hchol" else "bf16")
     else:
         F = D.lower_cholesky(factor_matrix, normA, dtype=low)
 
@@ -183,7 +185,7 @@ def solve(op, factor_matrix, X0, Omega, k, tol=1e-12, policy="mp", maxit=2000,
     hist = []
     fb = 0
     X = X0
-    if policy == "mp":
+    if policy in ("mp", "hchol", "bchol"):
         def T_low(R):
             return D.apply_T(F, R.astype(low))
         X1, _, it1, h1, _, f1 = lobpcg_loop(op.low, T_low, D.lower(X0), k, STAGE1_TOL,

@@ -169,3 +169,56 @@ def test_sign_mutation_breaks_convergence(monkeypatch):
     res_bad = L.solve(L.DenseOperator(A), A, X0, Om, k=4, tol=1e-12, policy="schol", maxit=60)
     ev = np.linalg.eigvalsh(A)[:4]
     assert (not res_bad.converged) or np.max(np.abs(res_bad.theta - ev) / ev) > 1e-6
+
+
+# ---- 16-bit factor stage ------------------------------------------------
+def test_round_fmt_bf16_ties_and_fp16():
+    """bf16 keeps 8 significant bits, ties to even; fp16 is numpy's half."""
+    one = np.float32(1.0)
+    h = np.float32(2.0 ** -8)
+    assert D.round_fmt(np.float32(one + h), "bf16") == 1.0              # halfway, even -> 1
+    assert D.round_fmt(np.float32(one + 3 * h), "bf16") == 1.0 + 4 * h  # 1.5 ulp (ulp = 2^-7): tie, even -> 1 + 2^-6
+    assert D.round_fmt(np.float32(one + h * 1.5), "bf16") == 1.0 + 2 * h
+    assert D.round_fmt(np.float32(-2.0 - 2.0 ** -7), "bf16") == -2.0     # halfway at exponent 1
+    x = np.random.default_rng(3).standard_normal(100).astype(np.float32)
+    assert np.array_equal(D.round_fmt(x, "fp16"), x.astype(np.float16).astype(np.float32))
+    r = D.round_fmt(x, "bf16")
+    assert np.all(np.abs(r - x) <= D.U16["bf16"] * np.abs(x) * (1 + 1e-6))   # unit roundoff 2^-8
+
+
+@pytest.mark.parametrize("fmt", ["fp16", "bf16"])
+def test_fmt_factor_backward_error(fmt):
+    """||L L^* - D A D|| <= c n u_fmt ||D A D||: the factor is that of the
+    scaled matrix, to the format's precision (no shift needed at kappa 1e2)."""
+    A, _ = W.dense_hpd(120, seed=5, kappa=1e2)
+    F = D.lower_cholesky_fmt(A, fmt)
+    assert F.sigma == 0.0
+    S = F.d.astype(np.float64)[:, None] * A * F.d.astype(np.float64)[None, :]
+    L = F.L.astype(np.complex128)
+    err = np.linalg.norm(L @ L.conj().T - S) / np.linalg.norm(S)
+    assert err <= 4 * 120 * D.U16[fmt]
+    assert np.allclose(np.real(np.diag(S)), 1.0)
+
+
+def test_fmt_preconditioner_quality_lemma2():
+    """Lemma 2 with u = u_fp16: gamma = ||I - A^1/2 T A^1/2|| < 1 for a mildly
+    conditioned A, with T from the 16-bit scaled factor."""
+    A, _ = W.dense_spd(60, seed=6, kappa=10.0)
+    F = D.lower_cholesky_fmt(A, "fp16")
+    Linv = np.linalg.inv(F.L.astype(np.float64))
+    T = (F.d[:, None] * (Linv.T @ Linv)) * F.d[None, :]
+    from oracle import bounds as B
+    g = B.precond_gap(A, T)
+    assert g < 0.5
+
+
+@pytest.mark.parametrize("policy", ["hchol", "bchol"])
+def test_fmt_policy_solve_matches_eigh(policy):
+    n, k, m = 150, 4, 8
+    A, _ = W.dense_spd(n, seed=7, kappa=1e3)
+    X0 = W.start_block(n, m, seed=8).T
+    Om = W.sketch(n, 8, seed=9)
+    res = L.solve(L.DenseOperator(A), A, X0, Om, k, tol=1e-12, policy=policy)
+    ev = np.linalg.eigvalsh(A)[:k]
+    assert res.converged
+    assert np.allclose(res.theta, ev, rtol=1e-10)
