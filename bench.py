@@ -60,6 +60,9 @@ def parse():
                     help="profiling runs only: cap the iterations (result may be unconverged)")
     ap.add_argument("--n", type=int, default=0,
                     help="profiling runs only: override the order n of a dense workload")
+    ap.add_argument("--precision-study", action="store_true",
+                    help="dense workloads: FP32 / fp16 / bf16 factor stage vs all-FP64 at order --n "
+                         "(default 4096): iterations, time and eigenvalue error per precision")
     ap.add_argument("--kernel-probe", default="", choices=["", "apply", "precond", "eig"],
                     help="profiling runs only: time one step entry point (A X, T R, or the "
                          "3m x 3m eigensolver) K times after W warm-ups instead of full solves")
@@ -220,6 +223,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     w = W.WORKLOADS[args.workload]
+    if args.precision_study and not args.n:
+        args.n = 4096
     if args.n:
         if w.kind == "csr":
             raise SystemExit("--n applies to dense workloads only")
@@ -260,6 +265,8 @@ def main():
     X0 = torch.from_numpy(X0h).to(dev)
     torch.cuda.synchronize()
 
+    if args.precision_study:
+        return precision_study(args, w, M, d, X0, stream, torch)
     h = make_handle(M, w, d, args.policy, stream)
     if args.kernel_probe:
         return kernel_probe(args, w, h, X0, stream, torch)
@@ -388,6 +395,45 @@ def traffic_per_launch(w):
         return None
     n0, rd, wr = cap
     return rd * (w.n / n0) ** 2 + wr * (w.n / n0)
+
+
+def precision_study(args, w, M, d, X0, stream, torch):
+    """The factor-precision stage of the dense workload: the same problem
+    solved with the FP32 factor (Algorithm 3 as in the paper), a diagonally
+    scaled fp16 / bf16 factor, and all-FP64 (the reference eigenvalues)."""
+    rows = {}
+    ref = None
+    for pol in ("dchol", "mp", "hchol", "bchol"):
+        h = make_handle(M, w, d, pol, stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        status = "ok"
+        try:
+            h.factor()
+            lam, _, hist, its, st = h.solve(X0, maxit=args.maxit, allow_not_converged=True)
+            if st != 0:
+                status = "not converged"
+        except M.MplError as e:
+            lam, hist, its, status = None, [], (0, 0), str(e).split(":")[0]
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        stt = h.stats()
+        h.close()
+        row = {"status": status, "time_s": t, "factor_ms": stt["t_factor_ms"], "factor_shift": stt["factor_shift"],
+               "factor_tries": stt["factor_tries"], "iterations": list(its),
+               "final_rel_resid": hist[-1] if hist else None}
+        if lam is not None:
+            if pol == "dchol":
+                ref = lam
+            if ref is not None:
+                row["max_rel_eig_err_vs_fp64"] = float(np.max(np.abs(lam - ref) / np.abs(ref)))
+        rows[{"dchol": "fp64", "mp": "fp32", "hchol": "fp16", "bchol": "bf16"}[pol]] = row
+    out = {"precision_study": w.name, "n": w.n, "k": w.k, "m": w.m, "kappa": w.kappa, "tol": w.tol,
+           "maxit": args.maxit, "results": rows,
+           "note": "factor precision of Algorithm 3's preconditioner; fp16/bf16: D = diag(A)^-1/2, D A D stored "
+                   "in the format with FP32 arithmetic; not a bench value"}
+    print(json.dumps(out))
+    return 0
 
 
 def kernel_probe(args, w, h, X0, stream, torch):

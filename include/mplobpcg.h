@@ -49,8 +49,12 @@ typedef enum {
 typedef enum {
   MPL_D_DCHOL = 0,   /* DLOBPCG-dchol: everything in FP64, FP64 Cholesky               */
   MPL_D_SCHOL = 1,   /* DLOBPCG-schol: FP64 except the FP32 preconditioner              */
-  MPL_MP_SCHOL = 2   /* MPLOBPCG-schol: Algorithm 3 (FP32 stage 1, FP32 preconditioner,
+  MPL_MP_SCHOL = 2,  /* MPLOBPCG-schol: Algorithm 3 (FP32 stage 1, FP32 preconditioner,
                         Algorithm 2 orthogonalisation)                                    */
+  MPL_MP_HCHOL = 3,  /* Algorithm 3 with a 16-bit factor (dense only): D = diag(A)^-1/2,
+                        D A D stored in IEEE fp16 through the factorisation (FP32
+                        arithmetic), T = D L^-* L^-1 D; breakdown shifts 2^j u_fp16     */
+  MPL_MP_BCHOL = 4   /* the same with bfloat16 storage                                  */
 } mpl_policy;
 
 typedef enum { MPL_R64 = 0, MPL_C128 = 1 } mpl_dtype;

@@ -18,8 +18,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libmplobpcg.so")
 
 MPL_R64, MPL_C128 = 0, 1
-MPL_D_DCHOL, MPL_D_SCHOL, MPL_MP_SCHOL = 0, 1, 2
-POLICIES = {"dchol": MPL_D_DCHOL, "schol": MPL_D_SCHOL, "mp": MPL_MP_SCHOL}
+MPL_D_DCHOL, MPL_D_SCHOL, MPL_MP_SCHOL, MPL_MP_HCHOL, MPL_MP_BCHOL = 0, 1, 2, 3, 4
+POLICIES = {"dchol": MPL_D_DCHOL, "schol": MPL_D_SCHOL, "mp": MPL_MP_SCHOL, "hchol": MPL_MP_HCHOL,
+            "bchol": MPL_MP_BCHOL}
 STATUS = {0: "MPL_OK", 1: "MPL_EINVAL", 2: "MPL_ENOT_HPD", 3: "MPL_ERANK", 4: "MPL_ENOT_CONVERGED",
           5: "MPL_ENUMERICAL", 6: "MPL_ENOMEM", 7: "MPL_ECUDA", 8: "MPL_ESTATE"}
 

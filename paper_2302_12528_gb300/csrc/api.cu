@@ -49,8 +49,21 @@ struct CsrOp : Op<T> {
 template <typename TF>
 struct DenseFactorSolve : FactorSolve<TF> {
   DenseFactor<TF> F;
-  void solve(cudaStream_t st, TF* B, long long ldb, int m) override { dense_precond<TF>(st, F, B, ldb, m); }
+  const float* rowscale = nullptr;  // D of a scaled factor: T = D L^-* L^-1 D
+  void solve(cudaStream_t st, TF* B, long long ldb, int m) override {
+    if (rowscale) scale_rows<TF>(st, F.n, m, B, ldb, rowscale);
+    dense_precond<TF>(st, F, B, ldb, m);
+    if (rowscale) scale_rows<TF>(st, F.n, m, B, ldb, rowscale);
+  }
 };
+
+// Policies of the Algorithm 3 family (FP32 stage 1, lower-precision
+// preconditioner, Algorithm 2 with the FP32 Householder step).
+inline bool mp_like(int policy) {
+  return policy == MPL_MP_SCHOL || policy == MPL_MP_HCHOL || policy == MPL_MP_BCHOL;
+}
+// 16-bit storage format of the factor: 0 none, 1 fp16, 2 bf16.
+inline int fmt16_of(int policy) { return policy == MPL_MP_HCHOL ? 1 : policy == MPL_MP_BCHOL ? 2 : 0; }
 
 // ---- engine ------------------------------------------------------------
 struct EngineBase {
@@ -141,7 +154,7 @@ class Engine : public EngineBase {
     dense_op_.n = (int)n;
     dense_op_.scr = scr_;
     opw_ = &dense_op_;
-    if (c_->policy == MPL_MP_SCHOL) {
+    if (mp_like(c_->policy)) {
       Al_.alloc(sizeof(TL) * n * n);
       cast<TL, TW>(st, (int)n, (int)n, Aw_.as<TW>(), n, Al_.as<TL>(), n);
       dense_op_l_.A = Al_.as<TL>();
@@ -216,12 +229,21 @@ class Engine : public EngineBase {
       F.ldl = n;
       F.n = (int)n;
     }
-    const double u = (sizeof(real_t<TF>) == 4) ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
+    // 16-bit factor: scaled by D = diag(A)^-1/2, stored in the format; its
+    // shifts are 2^j u_fmt (the scaled matrix's mean eigenvalue is 1)
+    const int fmt = (sizeof(real_t<TF>) == 4) ? fmt16_of(c_->policy) : 0;
+    const double u = fmt == 1 ? std::ldexp(1.0, -11) : fmt == 2 ? std::ldexp(1.0, -8)
+                     : (sizeof(real_t<TF>) == 4) ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
+    const double scale = fmt ? 1.0 : c_->norm_est;
+    if (fmt) dscale_.ensure(sizeof(float) * n);
+    FS.rowscale = fmt ? dscale_.as<float>() : nullptr;
     double sigma = 0.0;
     for (int j = 0; j <= 8; ++j) {
-      cast<TF, TW>(st, (int)n, (int)n, Aw_.as<TW>(), n, F.L, n);
+      if (fmt) scaled_lower_copy<TF, TW>(st, (int)n, Aw_.as<TW>(), n, dscale_.as<float>(), F.L, n);
+      else cast<TF, TW>(st, (int)n, (int)n, Aw_.as<TW>(), n, F.L, n);
       if (sigma != 0.0) add_diag<TF>(st, (int)n, F.L, n, sigma);
-      dense_cholesky<TF>(st, F, tmp_.as<TF>(), info_.as<int>(), scr_);
+      round_block<TF>(st, (int)n, (int)n, F.L, n, fmt, true);
+      dense_cholesky<TF>(st, F, tmp_.as<TF>(), info_.as<int>(), scr_, -1, 0, true, fmt);
       int info = 0;
       MPL_CUDA(cudaMemcpyAsync(&info, info_.ptr(), sizeof(int), cudaMemcpyDeviceToHost, st));
       MPL_CUDA(cudaStreamSynchronize(st));
@@ -233,7 +255,7 @@ class Engine : public EngineBase {
         return;
       }
       c_->info = info;
-      sigma = std::ldexp(1.0, j) * u * c_->norm_est;
+      sigma = std::ldexp(1.0, j) * u * scale;
     }
     throw MplError{MPL_ENOT_HPD, "Cholesky factorisation broke down for every shift", c_->info};
   }
@@ -273,7 +295,7 @@ class Engine : public EngineBase {
     std::vector<double> h;
     Progress p1;
     const TW* start = x0;
-    if (c_->policy == MPL_MP_SCHOL) {
+    if (mp_like(c_->policy)) {
       // Algorithm 3 line 1: lower-precision LOBPCG from single(X0)
       Timer t1(st);
       x0l_.ensure(sizeof(TL) * n * m);
@@ -692,7 +714,7 @@ class Engine : public EngineBase {
 
   mpl_ctx* c_;
   DevMem Aw_, Al_, Lbuf_, Dbuf_, tmp_, info_, scr_mem_, X0_, x0l_, tmpx_, eigws_, perm_dev_;
-  DevMem rp_, ci_, vw_, vl_, orig_rp_, orig_ci_, adj_;
+  DevMem rp_, ci_, vw_, vl_, orig_rp_, orig_ci_, adj_, dscale_;
   const TW* last_X_ = nullptr;       // Ritz block of the last solve (internal ordering)
   std::vector<double> last_theta_;   // its Ritz values
   long long csr_nnz_ = 0;
@@ -811,7 +833,7 @@ static mpl_status guarded(mpl_ctx* c, F&& f) {
 
 static bool valid_common(int k, int m, long long n, double tol, int policy) {
   return n > 0 && k >= 1 && m >= k && 3LL * m <= n && tol > 0.0 && policy >= MPL_D_DCHOL &&
-         policy <= MPL_MP_SCHOL && m <= 1024;
+         policy <= MPL_MP_BCHOL && m <= 1024;
 }
 
 extern "C" mpl_status mpl_create_dense(mpl_handle* h, int dtype, int64_t n, const void* A, int64_t lda,
@@ -856,6 +878,7 @@ extern "C" mpl_status mpl_create_csr(mpl_handle* h, int64_t n, int64_t nnz, cons
   if (!h) return MPL_EINVAL;
   *h = nullptr;
   if (!rowptr || !colind || !vals || !Omega || m_omega < 1 || nnz < n || !valid_common(k, m, n, tol, policy) ||
+      policy > MPL_MP_SCHOL ||  // the 16-bit factor is dense only
       n > (1LL << 31) - 1 || (grid_dims && ndims != 2 && ndims != 3))
     return MPL_EINVAL;
   mpl_ctx* c = new (std::nothrow) mpl_ctx();

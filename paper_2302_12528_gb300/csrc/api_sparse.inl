@@ -55,7 +55,7 @@ void Engine<TW>::create_csr(const long long* rowptr, const int* colind, const do
     csr_op_.n = (int)n;
     csr_op_.nnz = nnz;
     opw_ = &csr_op_;
-    if (c_->policy == MPL_MP_SCHOL) make_low_op();
+    if (mp_like(c_->policy)) make_low_op();
     // the sketch indexes the permuted ordering
     norm_estimate(Om, mo, om_dev);
     check_launch("create_csr");

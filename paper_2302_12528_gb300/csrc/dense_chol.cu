@@ -13,6 +13,11 @@
 // right-hand sides per CTA, staged in shared memory) and the CTAs that own
 // block row k+1 finish Y_{k+1} = Dinv_{k+1} B_{k+1} in the same launch.  The
 // backward sweep does the same with (L_ki)^* and Dinv^*.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
 #include "dense_chol.cuh"
 
 namespace mpl {
@@ -89,9 +94,41 @@ __global__ void copy_block_kernel(int rows, int cols, const T* __restrict__ S, l
   }
 }
 
+// ---- 16-bit storage format of the factor ---------------------------------
+// Rounding to fp16 / bf16 at the points where a factorisation that stores
+// its matrix in the format would store (scaled input, diagonal block, panel,
+// trailing update); arithmetic stays FP32.
+__device__ __forceinline__ float round16(float v, int fmt) {
+  return fmt == 1 ? __half2float(__float2half_rn(v)) : __bfloat162float(__float2bfloat16_rn(v));
+}
+__device__ __forceinline__ float round16v(float v, int fmt) { return round16(v, fmt); }
+__device__ __forceinline__ zf round16v(zf v, int fmt) { return {round16(v.x, fmt), round16(v.y, fmt)}; }
+__device__ __forceinline__ double round16v(double v, int) { return v; }
+__device__ __forceinline__ zd round16v(zd v, int) { return v; }
+
+template <typename T>
+__global__ void round_block_kernel(int rows, int cols, T* A, long long lda, int fmt, int lower_only) {
+  const long long tot = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % rows), j = (int)(e / rows);
+    if (lower_only && i < j) continue;
+    T* a = A + i + (long long)j * lda;
+    *a = round16v(*a, fmt);
+  }
+}
+
+template <typename T>
+void round_block(cudaStream_t st, int rows, int cols, T* A, long long lda, int fmt, bool lower_only) {
+  if (fmt == 0 || rows <= 0 || cols <= 0) return;
+  const long long tot = (long long)rows * cols;
+  count_launch();
+  round_block_kernel<T><<<(int)std::min<long long>((tot + 255) / 256, 8 * NUM_SMS), 256, 0, st>>>(
+      rows, cols, A, lda, fmt, lower_only ? 1 : 0);
+}
+
 template <typename T>
 void dense_cholesky(cudaStream_t st, DenseFactor<T>& F, T* tmp, int* info, Scratch scr, int nfact,
-                    long long col_offset, bool reset_info) {
+                    long long col_offset, bool reset_info, int fmt16) {
   constexpr int NB = CholBlock<T>::NB;
   const int n = F.n;
   if (nfact < 0 || nfact > n) nfact = n;
@@ -109,6 +146,7 @@ void dense_cholesky(cudaStream_t st, DenseFactor<T>& F, T* tmp, int* info, Scrat
     T* Db = F.Dinv + (size_t)b * NB * NB;
     count_launch();
     potrf_diag_kernel<T, NB><<<1, 256, sm, st>>>(kb, Akk, lda, Db, (int)(col_offset + k), info);
+    round_block<T>(st, kb, kb, Akk, lda, fmt16, true);
     const int rest = n - k - kb;
     if (rest <= 0) continue;
     T* Aik = F.L + (k + kb) + (long long)k * lda;
@@ -120,11 +158,58 @@ void dense_cholesky(cudaStream_t st, DenseFactor<T>& F, T* tmp, int* info, Scrat
     if (blocks > 8 * NUM_SMS) blocks = 8 * NUM_SMS;
     count_launch();
     copy_block_kernel<T><<<blocks, 256, 0, st>>>(rest, kb, tmp, rest, Aik, lda);
+    round_block<T>(st, rest, kb, Aik, lda, fmt16, false);
     // trailing update, lower triangle only
     T* Att = F.L + (k + kb) + (long long)(k + kb) * lda;
     gemm<T>(st, false, true, rest, rest, kb, real_t<T>(-1), Aik, lda, Aik, lda, real_t<T>(1), Att,
             lda, true, scr);
+    round_block<T>(st, rest, rest, Att, lda, fmt16, true);
   }
+}
+
+// d_i = 1 / sqrt(re A_ii) (FP64 arithmetic, stored FP32).
+template <typename TW>
+__global__ void diag_rsqrt_kernel(int n, const TW* __restrict__ A, long long lda, float* __restrict__ d) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    d[i] = (float)(1.0 / sqrt((double)re_(A[i + (long long)i * lda])));
+}
+
+// L = T(D A D) (lower triangle and diagonal; the upper is cleared by the factorisation).
+template <typename T, typename TW>
+__global__ void cast_scaled_kernel(int n, const TW* __restrict__ A, long long lda, const float* __restrict__ d,
+                                   T* __restrict__ L, long long ldl) {
+  const long long tot = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    if (i < j) continue;
+    const double s = (double)d[i] * (double)d[j];
+    L[i + (long long)j * ldl] = cvt<T, TW>(s * A[i + (long long)j * lda]);
+  }
+}
+
+template <typename T, typename TW>
+void scaled_lower_copy(cudaStream_t st, int n, const TW* A, long long lda, float* d, T* L, long long ldl) {
+  count_launch();
+  diag_rsqrt_kernel<TW><<<ceil_div(n, 256), 256, 0, st>>>(n, A, lda, d);
+  const long long tot = (long long)n * n;
+  count_launch();
+  cast_scaled_kernel<T, TW><<<(int)std::min<long long>((tot + 255) / 256, 16 * NUM_SMS), 256, 0, st>>>(n, A, lda, d,
+                                                                                                      L, ldl);
+}
+
+// B(i, :) *= d_i for B n x m (ld ldb).
+template <typename T>
+__global__ void scale_rows_kernel(int n, int m, T* B, long long ldb, const float* __restrict__ d) {
+  const int j = blockIdx.y;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    B[i + (long long)j * ldb] = (real_t<T>)d[i] * B[i + (long long)j * ldb];
+}
+
+template <typename T>
+void scale_rows(cudaStream_t st, int n, int m, T* B, long long ldb, const float* d) {
+  if (n <= 0 || m <= 0) return;
+  count_launch();
+  scale_rows_kernel<T><<<dim3(std::min(ceil_div(n, 256), 64), m), 256, 0, st>>>(n, m, B, ldb, d);
 }
 
 // ------------------------------------------------------------------------
@@ -304,7 +389,9 @@ void dense_precond(cudaStream_t st, const DenseFactor<T>& F, T* B, long long ldb
 
 #define MPL_INST_CHOL(T)                                                                      \
   template void dense_cholesky<T>(cudaStream_t, DenseFactor<T>&, T*, int*, Scratch, int,     \
-                                  long long, bool);                                          \
+                                  long long, bool, int);                                     \
+  template void scale_rows<T>(cudaStream_t, int, int, T*, long long, const float*);         \
+  template void round_block<T>(cudaStream_t, int, int, T*, long long, int, bool);           \
   template void dense_precond<T>(cudaStream_t, const DenseFactor<T>&, T*, long long, int);   \
   template void dense_trsm_fwd<T>(cudaStream_t, const DenseFactor<T>&, T*, long long, int);  \
   template void dense_trsm_bwd<T>(cudaStream_t, const DenseFactor<T>&, T*, long long, int);
@@ -313,5 +400,7 @@ MPL_INST_CHOL(double)
 MPL_INST_CHOL(zf)
 MPL_INST_CHOL(zd)
 #undef MPL_INST_CHOL
+template void scaled_lower_copy<float, double>(cudaStream_t, int, const double*, long long, float*, float*, long long);
+template void scaled_lower_copy<zf, zd>(cudaStream_t, int, const zd*, long long, float*, zf*, long long);
 
 }  // namespace mpl

@@ -25,9 +25,25 @@ struct DenseFactor {
 // the 1-based column of the first pivot that is not positive (reset to 0
 // first when ``reset_info``).  Sets F.nb and
 // F.nblk for the factored columns.  Asynchronous on ``st``.
+// fmt16 (0 none, 1 fp16, 2 bf16): the matrix is stored in that 16-bit
+// format -- the diagonal block, the panel and the trailing update are
+// rounded to it after each step (arithmetic in T; FP32 types only).
 template <typename T>
 void dense_cholesky(cudaStream_t st, DenseFactor<T>& F, T* tmp, int* info, Scratch scr,
-                    int nfact = -1, long long col_offset = 0, bool reset_info = true);
+                    int nfact = -1, long long col_offset = 0, bool reset_info = true, int fmt16 = 0);
+
+// Round a rows x cols block (ld lda; lower triangle only if lower_only) to
+// the 16-bit format fmt (1 fp16, 2 bf16; 0: no-op).
+template <typename T>
+void round_block(cudaStream_t st, int rows, int cols, T* A, long long lda, int fmt, bool lower_only);
+
+// d = diag(A)^-1/2 (FP32) and L = T(D A D) in the lower triangle.
+template <typename T, typename TW>
+void scaled_lower_copy(cudaStream_t st, int n, const TW* A, long long lda, float* d, T* L, long long ldl);
+
+// B(i, :) *= d_i.
+template <typename T>
+void scale_rows(cudaStream_t st, int n, int m, T* B, long long ldb, const float* d);
 
 // B <- L^-* L^-1 B for B n x m (ld ldb), in place, two blocked sweeps.
 template <typename T>
