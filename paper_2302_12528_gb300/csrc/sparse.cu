@@ -34,6 +34,7 @@ struct SparseFactorSolve<T>::Impl {
   std::vector<long long> start, rowptr, fptr, cptr;
   std::vector<int> ncols, nrows;
   std::vector<std::vector<int>> small_lv, big_lv;
+  int ncmax_small = 1;  // largest ncols among the small fronts
   std::vector<long long> small_off;  // offsets into d_small per level
   struct Round { long long off; int cnt; int maxchunks; };
   std::vector<std::vector<Round>> rounds;
@@ -209,6 +210,158 @@ bwd_small_kernel(const int* __restrict__ list, const T* __restrict__ F, const lo
 }
 
 // gather G(q, c) = B(rows[q], c) for the below-rows of a (large) block
+// Front solves with the front's top nc x m block held in shared memory
+// (small fronts: nc < 256).  Forward: extend-add of the children, then
+// L11 y = b by 32-column panels -- the diagonal block by one warp per
+// right-hand side (lanes = rows, registers and shuffles), the rows below it
+// in one parallel pass -- and finally C_b -= L21 y with one thread per row
+// and 16 right-hand sides per pass (each L21 element loaded once per pass).
+constexpr int FPW = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+fwd_front_kernel(const int* __restrict__ list, const T* __restrict__ F, const long long* __restrict__ fptr,
+                 const int* __restrict__ ncols, const int* __restrict__ nrows, const long long* __restrict__ start,
+                 const long long* __restrict__ rowptr, const int* __restrict__ relpos, const int* __restrict__ chptr,
+                 const int* __restrict__ chlist, const long long* __restrict__ cptr, T* contrib, T* B, long long ldb,
+                 int m, int ncmax) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* Y = reinterpret_cast<T*>(smraw);  // nc x m, ld nc
+  T* Lp = Y + (size_t)ncmax * m;       // panel rows j0.., ld LDP
+  const int LDP = ncmax + 1;
+  const int b = list[blockIdx.x];
+  const int nc = ncols[b], nr = nrows[b], nbl = nr - nc;
+  const long long f = start[b];
+  const T* A = F + fptr[b];
+  T* Cb = contrib + cptr[b] * m;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  for (long long e = tid; e < (long long)nbl * m; e += nt) Cb[e] = T(0);
+  __syncthreads();
+  for (int q = chptr[b]; q < chptr[b + 1]; ++q) {
+    const int ch = chlist[q];
+    const int ncc = ncols[ch], nbc = nrows[ch] - ncc;
+    const T* Cc = contrib + cptr[ch] * m;
+    const int* rp = relpos + rowptr[ch] + ncc;
+    for (long long e = tid; e < (long long)nbc * m; e += nt) {
+      const int i = (int)(e % nbc), c = (int)(e / nbc);
+      const int pos = rp[i];
+      const T v = Cc[i + (long long)c * nbc];
+      if (pos < nc) B[(f + pos) + (long long)c * ldb] += v;
+      else Cb[(pos - nc) + (long long)c * nbl] += v;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nc * m; e += nt) Y[e] = B[(f + e % nc) + (long long)(e / nc) * ldb];
+  __syncthreads();
+  for (int j0 = 0; j0 < nc; j0 += FPW) {
+    const int pw = min(FPW, nc - j0), rws = nc - j0;
+    for (int e = tid; e < rws * pw; e += nt) {
+      const int r = e % rws, jj = e / rws;
+      Lp[r + jj * LDP] = A[(j0 + r) + (long long)(j0 + jj) * nr];
+    }
+    __syncthreads();
+    for (int c = wid; c < m; c += nw) {
+      T y = lane < pw ? Y[j0 + lane + c * nc] : T(0);
+      for (int jj = 0; jj < pw; ++jj) {
+        if (lane == jj) y = y / Lp[jj + jj * LDP];
+        const T yj = __shfl_sync(0xffffffffu, y, jj);
+        if (lane > jj && lane < pw) y -= Lp[lane + jj * LDP] * yj;
+      }
+      if (lane < pw) Y[j0 + lane + c * nc] = y;
+    }
+    __syncthreads();
+    const int below = rws - pw;
+    for (int e = tid; e < below * m; e += nt) {
+      const int r = pw + e % below, c = e / below;
+      T acc = Y[j0 + r + c * nc];
+#pragma unroll 8
+      for (int jj = 0; jj < pw; ++jj) acc -= Lp[r + jj * LDP] * Y[j0 + jj + c * nc];
+      Y[j0 + r + c * nc] = acc;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nc * m; e += nt) B[(f + e % nc) + (long long)(e / nc) * ldb] = Y[e];
+  for (int c0 = 0; c0 < m; c0 += 16) {
+    const int qc = min(16, m - c0);
+    for (int i = tid; i < nbl; i += nt) {
+      T acc[16];
+#pragma unroll
+      for (int cc = 0; cc < 16; ++cc) acc[cc] = T(0);
+      const T* a = A + nc + i;
+      for (int j = 0; j < nc; ++j) {
+        const T lij = a[(long long)j * nr];
+        const T* yj = Y + j + (long long)c0 * nc;
+#pragma unroll
+        for (int cc = 0; cc < 16; ++cc)
+          if (cc < qc) acc[cc] += lij * yj[(long long)cc * nc];
+      }
+      for (int cc = 0; cc < qc; ++cc) Cb[i + (long long)(c0 + cc) * nbl] -= acc[cc];
+    }
+  }
+}
+
+// Backward: t = y - L21^T x_below into shared memory, then L11^T x = t by
+// 32-row panels from the bottom (the panel's rows of L staged in shared
+// memory with coalesced row loads), the diagonal block by one warp per
+// right-hand side, the rows above the panel in one parallel pass.
+template <typename T>
+__global__ void __launch_bounds__(256)
+bwd_front_kernel(const int* __restrict__ list, const T* __restrict__ F, const long long* __restrict__ fptr,
+                 const int* __restrict__ ncols, const int* __restrict__ nrows, const long long* __restrict__ start,
+                 const long long* __restrict__ rowptr, const int* __restrict__ rows, T* B, long long ldb, int m,
+                 int ncmax) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* Y = reinterpret_cast<T*>(smraw);  // nc x m, ld nc
+  T* Lp = Y + (size_t)ncmax * m;       // rows j0..j0+pw of L, Lp[jj + i * (FPW + 1)]
+  constexpr int L1 = FPW + 1;
+  const int b = list[blockIdx.x];
+  const int nc = ncols[b], nr = nrows[b];
+  const long long f = start[b];
+  const T* A = F + fptr[b];
+  const int* rw = rows + rowptr[b];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  for (int e = tid; e < nc * m; e += nt) {
+    const int i = e % nc, c = e / nc;
+    T acc = B[(f + i) + (long long)c * ldb];
+    const T* li = A + (long long)i * nr;
+    for (int q = nc; q < nr; ++q) acc -= li[q] * B[rw[q] + (long long)c * ldb];
+    Y[e] = acc;
+  }
+  __syncthreads();
+  for (int p = (nc - 1) / FPW; p >= 0; --p) {
+    const int j0 = p * FPW, pw = min(FPW, nc - j0), cols = j0 + pw;
+    for (int e = tid; e < pw * cols; e += nt) {
+      const int jj = e % pw, i = e / pw;
+      Lp[jj + i * L1] = A[(j0 + jj) + (long long)i * nr];
+    }
+    __syncthreads();
+    for (int c = wid; c < m; c += nw) {
+      T y = lane < pw ? Y[j0 + lane + c * nc] : T(0);
+      for (int kk = pw - 1; kk >= 0; --kk) {
+        if (lane == kk) y = y / Lp[kk + (j0 + kk) * L1];
+        const T xk = __shfl_sync(0xffffffffu, y, kk);
+        if (lane < kk) y -= Lp[kk + (j0 + lane) * L1] * xk;  // L^T(lane, kk) = L(kk, lane)
+      }
+      if (lane < pw) Y[j0 + lane + c * nc] = y;
+    }
+    __syncthreads();
+    for (int e = tid; e < j0 * m; e += nt) {
+      const int i = e % j0, c = e / j0;
+      T acc = Y[i + c * nc];
+#pragma unroll 8
+      for (int jj = 0; jj < pw; ++jj) acc -= Lp[jj + i * L1] * Y[j0 + jj + c * nc];
+      Y[i + c * nc] = acc;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nc * m; e += nt) B[(f + e % nc) + (long long)(e / nc) * ldb] = Y[e];
+}
+
+template <typename T>
+static size_t front_smem(int ncmax, int m) {
+  return ((size_t)ncmax * m + (size_t)(FPW + 1) * (ncmax + 1)) * sizeof(T);
+}
+
 template <typename T>
 __global__ void gather_rows_kernel(int nbl, int m, const int* __restrict__ rw, const T* __restrict__ B,
                                    long long ldb, T* G) {
@@ -322,6 +475,7 @@ SparseFactorSolve<T>::SparseFactorSolve(const SparseSymbolic& S, cudaStream_t st
       dinv_total += (long long)ceil_div(I.ncols[b], NB) * NB * NB;
     } else {
       I.small_lv[S.bk_level[b]].push_back((int)b);
+      I.ncmax_small = std::max(I.ncmax_small, I.ncols[b]);
     }
   }
   std::vector<int> small_all;
@@ -448,10 +602,24 @@ void SparseFactorSolve<T>::solve(cudaStream_t st, T* B, long long ldb, int m) {
     I.mcap = m;
   }
   T* C = I.contrib.template as<T>();
+  // the shared-memory front kernels when the largest small front fits
+  const size_t fsm = front_smem<T>(I.ncmax_small, m);
+  const bool use_front = fsm <= 200 * 1024;
+  if (use_front) {
+    cudaFuncSetAttribute(fwd_front_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+    cudaFuncSetAttribute(bwd_front_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+  }
   // forward
   for (int l = 0; l <= I.maxlevel; ++l) {
     const long long ns = I.small_off[l + 1] - I.small_off[l];
-    if (ns > 0) {
+    if (ns > 0 && use_front) {
+      count_launch();
+      fwd_front_kernel<T><<<(int)ns, 256, fsm, st>>>(
+          I.d_small.template as<int>() + I.small_off[l], I.F.template as<T>(), I.d_fptr.template as<long long>(),
+          I.d_ncols.template as<int>(), I.d_nrows.template as<int>(), I.d_start.template as<long long>(),
+          I.d_rowptr.template as<long long>(), I.d_relpos.template as<int>(), I.d_chptr.template as<int>(),
+          I.d_chlist.template as<int>(), I.d_cptr.template as<long long>(), C, B, ldb, m, I.ncmax_small);
+    } else if (ns > 0) {
       count_launch();
       fwd_small_kernel<T><<<(int)ns, 256, 0, st>>>(
           I.d_small.template as<int>() + I.small_off[l], -1, I.F.template as<T>(), I.d_fptr.template as<long long>(), I.d_ncols.template as<int>(),
@@ -503,7 +671,13 @@ void SparseFactorSolve<T>::solve(cudaStream_t st, T* B, long long ldb, int m) {
       dense_trsm_bwd<T>(st, D, top, ldb, m);
     }
     const long long ns = I.small_off[l + 1] - I.small_off[l];
-    if (ns > 0) {
+    if (ns > 0 && use_front) {
+      count_launch();
+      bwd_front_kernel<T><<<(int)ns, 256, fsm, st>>>(
+          I.d_small.template as<int>() + I.small_off[l], I.F.template as<T>(), I.d_fptr.template as<long long>(),
+          I.d_ncols.template as<int>(), I.d_nrows.template as<int>(), I.d_start.template as<long long>(),
+          I.d_rowptr.template as<long long>(), I.d_rows.template as<int>(), B, ldb, m, I.ncmax_small);
+    } else if (ns > 0) {
       count_launch();
       bwd_small_kernel<T><<<(int)ns, 256, 0, st>>>(
           I.d_small.template as<int>() + I.small_off[l], I.F.template as<T>(), I.d_fptr.template as<long long>(), I.d_ncols.template as<int>(),
