@@ -45,6 +45,24 @@ struct SparseFactorSolve<T>::Impl {
       d_chptr, d_chlist, d_small, d_pairs, d_cptr, dinv, tmp, info, contrib, gbuf, scr_mem;
   Scratch scr;
   int mcap = 0;
+  int maxnbl = 1;
+  // The dense (big) fronts of one level are independent in both sweeps: they
+  // run concurrently on these streams, forked from and joined back into the
+  // caller's stream with events; each stream has its own split-K scratch
+  // and gather buffer.
+  static constexpr int NAUX = 8;
+  static constexpr size_t AUX_SCR = (size_t)16 << 20;
+  cudaStream_t aux[NAUX] = {};
+  cudaEvent_t fork = nullptr, join[NAUX] = {};
+  DevMem aux_scr, aux_gbuf;
+  bool aux_ready = false;
+  ~Impl() {
+    for (int i = 0; i < NAUX; ++i) {
+      if (aux[i]) cudaStreamDestroy(aux[i]);
+      if (join[i]) cudaEventDestroy(join[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
+  }
 };
 
 // ---- kernels -------------------------------------------------------------
@@ -217,6 +235,7 @@ bwd_small_kernel(const int* __restrict__ list, const T* __restrict__ F, const lo
 // in one parallel pass -- and finally C_b -= L21 y with one thread per row
 // and 16 right-hand sides per pass (each L21 element loaded once per pass).
 constexpr int FPW = 32;
+constexpr int BW_ACC = 48;  // outputs per thread of the backward L21^T pass
 
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -320,12 +339,54 @@ bwd_front_kernel(const int* __restrict__ list, const T* __restrict__ F, const lo
   const T* A = F + fptr[b];
   const int* rw = rows + rowptr[b];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-  for (int e = tid; e < nc * m; e += nt) {
-    const int i = e % nc, c = e / nc;
-    T acc = B[(f + i) + (long long)c * ldb];
-    const T* li = A + (long long)i * nr;
-    for (int q = nc; q < nr; ++q) acc -= li[q] * B[rw[q] + (long long)c * ldb];
-    Y[e] = acc;
+  // t = y - L21^T x_below, by 32-row chunks of L21 and of the gathered
+  // x_below staged in shared memory (each thread owns <= BW_ACC outputs)
+  const int tot = nc * m;
+  if (tot <= BW_ACC * nt) {
+    T* Ls = Lp;                          // 32 rows of L21: Ls[qq + i * L1]
+    T* Xs = Lp + (size_t)L1 * ncmax;     // 32 rows of x_below: Xs[qq + c * FPW]
+    T acc[BW_ACC];
+#pragma unroll
+    for (int k = 0; k < BW_ACC; ++k) acc[k] = T(0);
+    for (int q0 = nc; q0 < nr; q0 += FPW) {
+      const int qw = min(FPW, nr - q0);
+      for (int e = tid; e < FPW * m; e += nt) {
+        const int qq = e % FPW, c = e / FPW;
+        Xs[e] = qq < qw ? B[rw[q0 + qq] + (long long)c * ldb] : T(0);
+      }
+      for (int e = tid; e < FPW * nc; e += nt) {
+        const int qq = e % FPW, i = e / FPW;
+        Ls[qq + i * L1] = qq < qw ? A[(q0 + qq) + (long long)i * nr] : T(0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < BW_ACC; ++k) {
+        const int e = tid + k * nt;
+        if (e < tot) {
+          const int i = e % nc, c = e / nc;
+          const T* li = Ls + i * L1;
+          const T* xc = Xs + c * FPW;
+          T s = acc[k];
+#pragma unroll 8
+          for (int qq = 0; qq < FPW; ++qq) s += li[qq] * xc[qq];
+          acc[k] = s;
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < BW_ACC; ++k) {
+      const int e = tid + k * nt;
+      if (e < tot) Y[e] = B[(f + e % nc) + (long long)(e / nc) * ldb] - acc[k];
+    }
+  } else {
+    for (int e = tid; e < tot; e += nt) {
+      const int i = e % nc, c = e / nc;
+      T a = B[(f + i) + (long long)c * ldb];
+      const T* li = A + (long long)i * nr;
+      for (int q = nc; q < nr; ++q) a -= li[q] * B[rw[q] + (long long)c * ldb];
+      Y[e] = a;
+    }
   }
   __syncthreads();
   for (int p = (nc - 1) / FPW; p >= 0; --p) {
@@ -359,7 +420,24 @@ bwd_front_kernel(const int* __restrict__ list, const T* __restrict__ F, const lo
 
 template <typename T>
 static size_t front_smem(int ncmax, int m) {
-  return ((size_t)ncmax * m + (size_t)(FPW + 1) * (ncmax + 1)) * sizeof(T);
+  return ((size_t)ncmax * m + (size_t)(FPW + 1) * (ncmax + 1) + (size_t)FPW * m) * sizeof(T);
+}
+
+// Extend-add of one child into its (dense) parent: the child's contribution
+// rows go to the parent's own rows of B or to its contribution block.
+// Positions within one child are distinct, so a grid over the child's
+// entries is race-free; children are added by successive launches.
+template <typename T>
+__global__ void gather_child_kernel(int nbc, int m, const T* __restrict__ Cc, const int* __restrict__ rp, int nc,
+                                    int nbl, long long f, T* B, long long ldb, T* Cb) {
+  const long long tot = (long long)nbc * m;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % nbc), c = (int)(e / nbc);
+    const int pos = rp[i];
+    const T v = Cc[i + (long long)c * nbc];
+    if (pos < nc) B[(f + pos) + (long long)c * ldb] += v;
+    else Cb[(pos - nc) + (long long)c * nbl] += v;
+  }
 }
 
 template <typename T>
@@ -598,9 +676,36 @@ void SparseFactorSolve<T>::solve(cudaStream_t st, T* B, long long ldb, int m) {
     I.contrib.alloc(sizeof(T) * (size_t)std::max<long long>(I.cptr[I.nb], 1) * m);
     int maxnbl = 1;
     for (long long b = 0; b < I.nb; ++b) maxnbl = std::max(maxnbl, I.nrows[b] - I.ncols[b]);
+    I.maxnbl = maxnbl;
     I.gbuf.alloc(sizeof(T) * (size_t)maxnbl * m);
+    I.aux_gbuf.alloc(sizeof(T) * (size_t)maxnbl * m * Impl::NAUX);
     I.mcap = m;
   }
+  if (!I.aux_ready) {
+    for (int i = 0; i < Impl::NAUX; ++i) {
+      MPL_CUDA(cudaStreamCreateWithFlags(&I.aux[i], cudaStreamNonBlocking));
+      MPL_CUDA(cudaEventCreateWithFlags(&I.join[i], cudaEventDisableTiming));
+    }
+    MPL_CUDA(cudaEventCreateWithFlags(&I.fork, cudaEventDisableTiming));
+    I.aux_scr.alloc(Impl::AUX_SCR * Impl::NAUX);
+    I.aux_ready = true;
+  }
+  auto fork_aux = [&](cudaStream_t main) {
+    MPL_CUDA(cudaEventRecord(I.fork, main));
+    for (int i = 0; i < Impl::NAUX; ++i) MPL_CUDA(cudaStreamWaitEvent(I.aux[i], I.fork, 0));
+  };
+  auto join_aux = [&](cudaStream_t main, int used) {
+    for (int i = 0; i < Impl::NAUX && i < used; ++i) {
+      MPL_CUDA(cudaEventRecord(I.join[i], I.aux[i]));
+      MPL_CUDA(cudaStreamWaitEvent(main, I.join[i], 0));
+    }
+  };
+  auto aux_scratch = [&](int i) {
+    Scratch sc;
+    sc.ptr = static_cast<unsigned char*>(I.aux_scr.ptr()) + (size_t)i * Impl::AUX_SCR;
+    sc.bytes = Impl::AUX_SCR;
+    return sc;
+  };
   T* C = I.contrib.template as<T>();
   // the shared-memory front kernels when the largest small front fits
   const size_t fsm = front_smem<T>(I.ncmax_small, m);
@@ -626,13 +731,27 @@ void SparseFactorSolve<T>::solve(cudaStream_t st, T* B, long long ldb, int m) {
           I.d_nrows.template as<int>(), I.d_start.template as<long long>(), I.d_rowptr.template as<long long>(), I.d_relpos.template as<int>(),
           I.d_chptr.template as<int>(), I.d_chlist.template as<int>(), I.d_cptr.template as<long long>(), C, B, ldb, m, 0);
     }
-    for (int b : I.big_lv[l]) {
-      // gather children into B / C_b (single CTA over a one-element list)
-      count_launch();
-      fwd_small_kernel<T><<<1, 256, 0, st>>>(
-          nullptr, b, I.F.template as<T>(), I.d_fptr.template as<long long>(), I.d_ncols.template as<int>(),
-          I.d_nrows.template as<int>(), I.d_start.template as<long long>(), I.d_rowptr.template as<long long>(), I.d_relpos.template as<int>(),
-          I.d_chptr.template as<int>(), I.d_chlist.template as<int>(), I.d_cptr.template as<long long>(), C, B, ldb, m, 1);
+    const auto& bl = I.big_lv[l];
+    const bool par = bl.size() > 1;
+    if (par) fork_aux(st);
+    for (size_t idx = 0; idx < bl.size(); ++idx) {
+      const int b = bl[idx];
+      cudaStream_t s = par ? I.aux[idx % Impl::NAUX] : st;
+      Scratch sc = par ? aux_scratch((int)(idx % Impl::NAUX)) : I.scr;
+      // gather children into B / C_b: zero C_b, then one grid-wide launch per child
+      {
+        const int nblb = I.nrows[b] - I.ncols[b];
+        if (nblb > 0) MPL_CUDA(cudaMemsetAsync(C + I.cptr[b] * m, 0, sizeof(T) * (size_t)nblb * m, s));
+        for (int ch : I.children[b]) {
+          const int ncc = I.ncols[ch], nbc = I.nrows[ch] - ncc;
+          if (nbc <= 0) continue;
+          const int gb = (int)std::min<long long>(((long long)nbc * m + 255) / 256, 8 * NUM_SMS);
+          count_launch();
+          gather_child_kernel<T><<<gb, 256, 0, s>>>(nbc, m, C + I.cptr[ch] * m,
+                                                    I.d_relpos.template as<int>() + I.rowptr[ch] + ncc, I.ncols[b],
+                                                    nblb, I.start[b], B, ldb, C + I.cptr[b] * m);
+        }
+      }
       DenseFactor<T> D;
       D.L = I.F.template as<T>() + I.fptr[b];
       D.ldl = I.nrows[b];
@@ -641,16 +760,25 @@ void SparseFactorSolve<T>::solve(cudaStream_t st, T* B, long long ldb, int m) {
       D.nblk = ceil_div(I.ncols[b], D.nb);
       D.Dinv = I.dinv.template as<T>() + I.big_dinv[b];
       T* top = B + I.start[b];
-      dense_trsm_fwd<T>(st, D, top, ldb, m);
+      dense_trsm_fwd<T>(s, D, top, ldb, m);
       const int nbl = I.nrows[b] - I.ncols[b];
       if (nbl > 0)
-        gemm<T>(st, false, false, nbl, m, I.ncols[b], T(-1), D.L + I.ncols[b], D.ldl, top, ldb, T(1),
-                C + I.cptr[b] * m, nbl, false, I.scr);
+        gemm<T>(s, false, false, nbl, m, I.ncols[b], T(-1), D.L + I.ncols[b], D.ldl, top, ldb, T(1),
+                C + I.cptr[b] * m, nbl, false, sc);
     }
+    if (par) join_aux(st, (int)bl.size());
   }
   // backward
   for (int l = I.maxlevel; l >= 0; --l) {
-    for (int b : I.big_lv[l]) {
+    const auto& bl = I.big_lv[l];
+    const bool par = bl.size() > 1;
+    if (par) fork_aux(st);
+    for (size_t idx = 0; idx < bl.size(); ++idx) {
+      const int b = bl[idx];
+      const int si = (int)(idx % Impl::NAUX);
+      cudaStream_t s = par ? I.aux[si] : st;
+      Scratch sc = par ? aux_scratch(si) : I.scr;
+      T* gb_buf = par ? I.aux_gbuf.template as<T>() + (size_t)si * I.maxnbl * m : I.gbuf.template as<T>();
       DenseFactor<T> D;
       D.L = I.F.template as<T>() + I.fptr[b];
       D.ldl = I.nrows[b];
@@ -663,13 +791,14 @@ void SparseFactorSolve<T>::solve(cudaStream_t st, T* B, long long ldb, int m) {
       if (nbl > 0) {
         int gb = (int)std::min<long long>(((long long)nbl * m + 255) / 256, 8 * NUM_SMS);
         count_launch();
-        gather_rows_kernel<T><<<gb, 256, 0, st>>>(nbl, m, I.d_rows.template as<int>() + I.rowptr[b] + I.ncols[b], B, ldb,
-                                                  I.gbuf.template as<T>());
-        gemm<T>(st, true, false, I.ncols[b], m, nbl, T(-1), D.L + I.ncols[b], D.ldl, I.gbuf.template as<T>(), nbl, T(1),
-                top, ldb, false, I.scr);
+        gather_rows_kernel<T><<<gb, 256, 0, s>>>(nbl, m, I.d_rows.template as<int>() + I.rowptr[b] + I.ncols[b], B, ldb,
+                                                 gb_buf);
+        gemm<T>(s, true, false, I.ncols[b], m, nbl, T(-1), D.L + I.ncols[b], D.ldl, gb_buf, nbl, T(1), top, ldb,
+                false, sc);
       }
-      dense_trsm_bwd<T>(st, D, top, ldb, m);
+      dense_trsm_bwd<T>(s, D, top, ldb, m);
     }
+    if (par) join_aux(st, (int)bl.size());
     const long long ns = I.small_off[l + 1] - I.small_off[l];
     if (ns > 0 && use_front) {
       count_launch();
