@@ -35,6 +35,7 @@ struct SparseFactorSolve<T>::Impl {
   std::vector<int> ncols, nrows;
   std::vector<std::vector<int>> small_lv, big_lv;
   int ncmax_small = 1;  // largest ncols among the small fronts
+  std::vector<int> small_nrmax;  // largest nrows among a level's small fronts
   std::vector<long long> small_off;  // offsets into d_small per level
   struct Round { long long off; int cnt; int maxchunks; };
   std::vector<std::vector<Round>> rounds;
@@ -54,8 +55,35 @@ struct SparseFactorSolve<T>::Impl {
   static constexpr size_t AUX_SCR = (size_t)16 << 20;
   cudaStream_t aux[NAUX] = {};
   cudaEvent_t fork = nullptr, join[NAUX] = {};
-  DevMem aux_scr, aux_gbuf;
+  DevMem aux_scr, aux_gbuf, aux_tmp;
   bool aux_ready = false;
+  size_t tmp_elems = 0;  // per-stream factor panel buffer (elements)
+  void ensure_aux() {
+    if (aux_ready) return;
+    for (int i = 0; i < NAUX; ++i) {
+      MPL_CUDA(cudaStreamCreateWithFlags(&aux[i], cudaStreamNonBlocking));
+      MPL_CUDA(cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming));
+    }
+    MPL_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    aux_scr.alloc(AUX_SCR * NAUX);
+    aux_ready = true;
+  }
+  void fork_aux(cudaStream_t main) {
+    MPL_CUDA(cudaEventRecord(fork, main));
+    for (int i = 0; i < NAUX; ++i) MPL_CUDA(cudaStreamWaitEvent(aux[i], fork, 0));
+  }
+  void join_aux(cudaStream_t main, int used) {
+    for (int i = 0; i < NAUX && i < used; ++i) {
+      MPL_CUDA(cudaEventRecord(join[i], aux[i]));
+      MPL_CUDA(cudaStreamWaitEvent(main, join[i], 0));
+    }
+  }
+  Scratch aux_scratch(int i) {
+    Scratch sc;
+    sc.ptr = static_cast<unsigned char*>(aux_scr.ptr()) + (size_t)i * AUX_SCR;
+    sc.bytes = AUX_SCR;
+    return sc;
+  }
   ~Impl() {
     for (int i = 0; i < NAUX; ++i) {
       if (aux[i]) cudaStreamDestroy(aux[i]);
@@ -107,6 +135,81 @@ extend_add_kernel(const int2* __restrict__ pairs, T* F, const long long* __restr
 
 // Partial Cholesky of a small front: the first nc columns, Schur update of
 // the rest (one CTA per front).
+// Small-front factorisation by column panels of PW held in shared memory:
+// the panel (rows j0.., PW columns) is factored there column by column, then
+// written back, and the trailing lower triangle receives one rank-PW update
+// per panel (a warp per column, lanes down the rows) -- one global
+// read-modify-write per element and panel instead of per column.
+template <typename T, int PW>
+__global__ void __launch_bounds__(256)
+factor_front_kernel(const int* __restrict__ list, T* F, const long long* __restrict__ fptr,
+                    const int* __restrict__ ncols, const int* __restrict__ nrows,
+                    const long long* __restrict__ start, int* info, int nrmax) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* P = reinterpret_cast<T*>(smraw);  // P[r + jj * LDP], r relative to j0
+  const int LDP = nrmax + 1;
+  const int b = list[blockIdx.x];
+  const int nc = ncols[b], nr = nrows[b];
+  T* A = F + fptr[b];
+  __shared__ T piv;
+  __shared__ int bad;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  if (tid == 0) bad = 0;
+  for (int j0 = 0; j0 < nc; j0 += PW) {
+    const int pw = min(PW, nc - j0), rws = nr - j0;
+    for (int e = tid; e < rws * pw; e += nt) {
+      const int r = e % rws, jj = e / rws;
+      P[r + jj * LDP] = A[(j0 + r) + (long long)(j0 + jj) * nr];
+    }
+    __syncthreads();
+    for (int jj = 0; jj < pw; ++jj) {
+      if (tid == 0) {
+        T d = P[jj + jj * LDP];
+        if (!(d > T(0)) || !isfinite((double)d)) {
+          if (bad == 0) bad = j0 + jj + 1;
+          d = T(1);
+        }
+        d = (sizeof(T) == 8) ? (T)sqrt((double)d) : (T)sqrtf((float)d);
+        P[jj + jj * LDP] = d;
+        piv = T(1) / d;
+      }
+      __syncthreads();
+      const T rs = piv;
+      for (int r = jj + 1 + tid; r < rws; r += nt) P[r + jj * LDP] *= rs;
+      __syncthreads();
+      const int h = rws - jj - 1, w = pw - jj - 1;
+      for (int e = tid; e < h * w; e += nt) {
+        const int r = jj + 1 + e % h, c = jj + 1 + e / h;
+        if (r >= c) P[r + c * LDP] -= P[r + jj * LDP] * P[c + jj * LDP];
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < rws * pw; e += nt) {
+      const int r = e % rws, jj = e / rws;
+      if (r >= jj) A[(j0 + r) + (long long)(j0 + jj) * nr] = P[r + jj * LDP];
+    }
+    for (int col = j0 + pw + wid; col < nr; col += nw) {
+      T fj[PW];
+#pragma unroll
+      for (int jj = 0; jj < PW; ++jj) fj[jj] = jj < pw ? P[(col - j0) + jj * LDP] : T(0);
+      T* ac = A + (long long)col * nr;
+      for (int row = col + lane; row < nr; row += 32) {
+        T acc = ac[row];
+        const T* pr = P + (row - j0);
+#pragma unroll
+        for (int jj = 0; jj < PW; ++jj)
+          if (jj < pw) acc -= pr[jj * LDP] * fj[jj];  // columns past pw are not loaded
+        ac[row] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && bad != 0) atomicCAS(info, 0, (int)(start[b] + bad));
+}
+
+template <typename T> struct FrontPanel { static constexpr int PW = 32; };
+template <> struct FrontPanel<double> { static constexpr int PW = 16; };
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 factor_small_kernel(const int* __restrict__ list, T* F, const long long* __restrict__ fptr,
@@ -542,6 +645,7 @@ SparseFactorSolve<T>::SparseFactorSolve(const SparseSymbolic& S, cudaStream_t st
   const int L = I.maxlevel + 1;
   I.small_lv.assign(L, {});
   I.big_lv.assign(L, {});
+  I.small_nrmax.assign(L, 1);
   I.big_dinv.assign(nb, -1);
   long long dinv_total = 0;
   constexpr int NB = CholBlock<T>::NB;
@@ -554,6 +658,7 @@ SparseFactorSolve<T>::SparseFactorSolve(const SparseSymbolic& S, cudaStream_t st
     } else {
       I.small_lv[S.bk_level[b]].push_back((int)b);
       I.ncmax_small = std::max(I.ncmax_small, I.ncols[b]);
+      I.small_nrmax[S.bk_level[b]] = std::max(I.small_nrmax[S.bk_level[b]], I.nrows[b]);
     }
   }
   std::vector<int> small_all;
@@ -612,6 +717,7 @@ SparseFactorSolve<T>::SparseFactorSolve(const SparseSymbolic& S, cudaStream_t st
   int maxnr = 1;
   for (long long b = 0; b < nb; ++b) maxnr = std::max(maxnr, I.nrows[b]);
   I.tmp.alloc(sizeof(T) * (size_t)maxnr * NB);
+  I.tmp_elems = (size_t)maxnr * NB;
   I.info.alloc(16);
   I.scr_mem.alloc((size_t)32 << 20);
   I.scr.ptr = I.scr_mem.ptr();
@@ -646,21 +752,47 @@ int SparseFactorSolve<T>::factorize(cudaStream_t st, double sigma) {
           I.d_relpos.template as<int>(), I.d_ncols.template as<int>(), I.d_nrows.template as<int>());
     }
     const long long ns = I.small_off[l + 1] - I.small_off[l];
-    if (ns > 0) {
+    constexpr int PW = FrontPanel<T>::PW;
+    const size_t psm = (size_t)(I.small_nrmax[l] + 1) * PW * sizeof(T);
+    if (ns > 0 && psm <= 200 * 1024) {
+      auto kern = factor_front_kernel<T, PW>;
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+      count_launch();
+      kern<<<(int)ns, 256, psm, st>>>(I.d_small.template as<int>() + I.small_off[l], I.F.template as<T>(),
+                                      I.d_fptr.template as<long long>(), I.d_ncols.template as<int>(),
+                                      I.d_nrows.template as<int>(), I.d_start.template as<long long>(),
+                                      I.info.template as<int>(), I.small_nrmax[l]);
+    } else if (ns > 0) {
       count_launch();
       factor_small_kernel<T><<<(int)ns, 256, 0, st>>>(I.d_small.template as<int>() + I.small_off[l], I.F.template as<T>(),
                                                        I.d_fptr.template as<long long>(), I.d_ncols.template as<int>(),
                                                        I.d_nrows.template as<int>(), I.d_start.template as<long long>(),
                                                        I.info.template as<int>());
     }
-    for (int b : I.big_lv[l]) {
+    // dense fronts of the level: independent, concurrent on the auxiliary
+    // streams (own panel buffer and split-K scratch each; the pivot status
+    // word is updated with atomics)
+    const auto& bl = I.big_lv[l];
+    const bool par = bl.size() > 1;
+    if (par) {
+      I.ensure_aux();
+      if (I.aux_tmp.bytes() < sizeof(T) * I.tmp_elems * Impl::NAUX) I.aux_tmp.alloc(sizeof(T) * I.tmp_elems * Impl::NAUX);
+      I.fork_aux(st);
+    }
+    for (size_t idx = 0; idx < bl.size(); ++idx) {
+      const int b = bl[idx];
+      const int si = (int)(idx % Impl::NAUX);
+      cudaStream_t s = par ? I.aux[si] : st;
       DenseFactor<T> D;
       D.L = I.F.template as<T>() + I.fptr[b];
       D.ldl = I.nrows[b];
       D.n = I.nrows[b];
       D.Dinv = I.dinv.template as<T>() + I.big_dinv[b];
-      dense_cholesky<T>(st, D, I.tmp.template as<T>(), I.info.template as<int>(), I.scr, I.ncols[b], I.start[b], false);
+      T* tmp = par ? I.aux_tmp.template as<T>() + (size_t)si * I.tmp_elems : I.tmp.template as<T>();
+      dense_cholesky<T>(s, D, tmp, I.info.template as<int>(), par ? I.aux_scratch(si) : I.scr, I.ncols[b],
+                        I.start[b], false);
     }
+    if (par) I.join_aux(st, (int)bl.size());
   }
   check_launch("sparse factorize");
   int info = 0;
@@ -681,31 +813,10 @@ void SparseFactorSolve<T>::solve(cudaStream_t st, T* B, long long ldb, int m) {
     I.aux_gbuf.alloc(sizeof(T) * (size_t)maxnbl * m * Impl::NAUX);
     I.mcap = m;
   }
-  if (!I.aux_ready) {
-    for (int i = 0; i < Impl::NAUX; ++i) {
-      MPL_CUDA(cudaStreamCreateWithFlags(&I.aux[i], cudaStreamNonBlocking));
-      MPL_CUDA(cudaEventCreateWithFlags(&I.join[i], cudaEventDisableTiming));
-    }
-    MPL_CUDA(cudaEventCreateWithFlags(&I.fork, cudaEventDisableTiming));
-    I.aux_scr.alloc(Impl::AUX_SCR * Impl::NAUX);
-    I.aux_ready = true;
-  }
-  auto fork_aux = [&](cudaStream_t main) {
-    MPL_CUDA(cudaEventRecord(I.fork, main));
-    for (int i = 0; i < Impl::NAUX; ++i) MPL_CUDA(cudaStreamWaitEvent(I.aux[i], I.fork, 0));
-  };
-  auto join_aux = [&](cudaStream_t main, int used) {
-    for (int i = 0; i < Impl::NAUX && i < used; ++i) {
-      MPL_CUDA(cudaEventRecord(I.join[i], I.aux[i]));
-      MPL_CUDA(cudaStreamWaitEvent(main, I.join[i], 0));
-    }
-  };
-  auto aux_scratch = [&](int i) {
-    Scratch sc;
-    sc.ptr = static_cast<unsigned char*>(I.aux_scr.ptr()) + (size_t)i * Impl::AUX_SCR;
-    sc.bytes = Impl::AUX_SCR;
-    return sc;
-  };
+  I.ensure_aux();
+  auto fork_aux = [&](cudaStream_t main) { I.fork_aux(main); };
+  auto join_aux = [&](cudaStream_t main, int used) { I.join_aux(main, used); };
+  auto aux_scratch = [&](int i) { return I.aux_scratch(i); };
   T* C = I.contrib.template as<T>();
   // the shared-memory front kernels when the largest small front fits
   const size_t fsm = front_smem<T>(I.ncmax_small, m);
