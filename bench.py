@@ -69,6 +69,17 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x, dist, device):
+    """The largest value of x over the ranks of the process group (the job's
+    time is its slowest rank's); x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------------------
 # inputs (seeded, synthetic)
 # ---------------------------------------------------------------------------
@@ -237,11 +248,12 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
 
     if args.impl == "reference":
-        if rank != 0:
-            return 0
-        if w.kind == "batch":
-            return run_reference_batch(args, w)
-        return run_reference(args, w)
+        rc = 0
+        if rank == 0:   # the oracle arm runs once; the other ranks exit without work
+            rc = run_reference_batch(args, w) if w.kind == "batch" else run_reference(args, w)
+        if dist is not None:
+            dist.destroy_process_group()
+        return rc
 
     import paper_2302_12528_gb300 as M
     dev = torch.device(f"cuda:{local}")
@@ -301,10 +313,8 @@ def main():
     torch.cuda.synchronize()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms, dist, dev)
     if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     stats = h.stats()
     h.close()
@@ -551,10 +561,7 @@ def run_batch(args, w, M, dev, stream, torch, rank, dist):
     torch.cuda.synchronize()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     world = dist.get_world_size() if dist is not None else 1
     itn = its.cpu().numpy().reshape(nprob, 2)
     stn = st.cpu().numpy()
