@@ -253,7 +253,7 @@ void gemm(cudaStream_t st, bool opA, bool opB, int M, int N, int K, real_t<T> al
   const int target = (fp64 ? 24 : 2) * NUM_SMS;
   if (K > 0 && tiles < target) {
     splits = ceil_div(target, tiles);
-    const int max_by_k = ceil_div(K, (fp64 ? 16 : 4) * Cfg::BK);  // k-steps per slice
+    const int max_by_k = ceil_div(K, 4 * Cfg::BK);  // at least 4 k-steps per slice
     if (splits > max_by_k) splits = max_by_k;
     const size_t per = (size_t)M * N * sizeof(T);
     const int max_by_ws = per ? (int)(scr.bytes / per) : 0;
