@@ -323,7 +323,7 @@ def main():
         "metric": "time-to-k-eigenpairs at resid<=1e-12 (mixed-precision LOBPCG, Algorithm 3)",
         "value": ms / 1000.0, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64+f32", "data": "synthetic (seeded; see DESIGN.md input recipe)",
+        "dtype": "f64+f32", "data": "synthetic (seeded generators of workloads/; random-init inputs)",
         "config": {"workload": w.name, "n": w.n, "k": w.k, "m": w.m, "tol": w.tol,
                    "policy": {"mp": "MPLOBPCG-schol", "schol": "DLOBPCG-schol", "dchol": "DLOBPCG-dchol"}[args.policy],
                    "kind": w.kind, "kappa": w.kappa if w.kind != "csr" else None,
@@ -574,7 +574,7 @@ def run_batch(args, w, M, dev, stream, torch, rank, dist):
         "metric": "time-to-k-eigenpairs at resid<=1e-12 (mixed-precision LOBPCG, Algorithm 3), whole batch",
         "value": ms / 1000.0, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64+f32", "data": "synthetic (seeded; see DESIGN.md input recipe)",
+        "dtype": "f64+f32", "data": "synthetic (seeded generators of workloads/; random-init inputs)",
         "config": {"workload": w.name, "problems": nprob, "n_min": int(b["n"].min()), "n_max": int(b["n"].max()),
                    "sum_n2": int((b["n"].astype(np.int64) ** 2).sum()), "k": w.k, "m": w.m, "tol": w.tol,
                    "policy": {"mp": "MPLOBPCG-schol", "schol": "DLOBPCG-schol", "dchol": "DLOBPCG-dchol"}[args.policy],

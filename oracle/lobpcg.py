@@ -10,7 +10,7 @@ Policies (Section 5.1, "The following variants ... are tested"):
                            working precision with lower-precision
                            preconditioner and Algorithm 2 orthogonalisation.
 
-Readings of points the paper leaves open (each is listed in the design doc):
+Readings of points the paper leaves open:
   * n_c counts the leading columns (ascending Ritz values) that pass Eq. (stop).
   * The residual columns are scaled to unit norm before single(.); only
     span(W) matters because W is re-orthonormalised.
