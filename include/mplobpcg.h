@@ -63,7 +63,7 @@ typedef struct {
   double t_create_ms;     /* upload, permutation, lower copy, norm estimate             */
   double t_symbolic_ms;   /* sparse: ordering + symbolic analysis on the host           */
   double t_factor_ms;     /* numeric lower-precision (or FP64) factorisation           */
-  double t_stage1_ms;     /* Algorithm 3 line 1 (lower-precision LOBPCG)               */
+  double t_stage1_ms;     /* Algorithm 3 first stage (lower-precision LOBPCG)           */
   double t_stage2_ms;     /* working-precision loop                                     */
   int iters_stage1;
   int iters_stage2;

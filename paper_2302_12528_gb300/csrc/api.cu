@@ -296,7 +296,7 @@ class Engine : public EngineBase {
     Progress p1;
     const TW* start = x0;
     if (mp_like(c_->policy)) {
-      // Algorithm 3 line 1: lower-precision LOBPCG from single(X0)
+      // Algorithm 3, first stage: lower-precision LOBPCG from single(X0)
       Timer t1(st);
       x0l_.ensure(sizeof(TL) * n * m);
       cast<TL, TW>(st, (int)n, m, x0, n, x0l_.as<TL>(), n);

@@ -184,7 +184,7 @@ struct Progress {
   double max_rel = 0.0;
 };
 
-// One LOBPCG loop (Algorithm 3 lines 3-18) in working type TW with the QR of
+// One LOBPCG loop (the iteration of Algorithm 3) in working type TW with the QR of
 // Algorithm 2 step 1 in TQ.
 template <typename TW, typename TQ>
 class Stage {
