@@ -45,7 +45,7 @@ typedef enum {
   MPL_ESTATE = 8           /* call out of order (e.g. solve before factor)              */
 } mpl_status;
 
-/* Precision policies of Section 5.1 ("The following variants ... are tested"). */
+/* Precision policies: the variants compared in Section 5.1. */
 typedef enum {
   MPL_D_DCHOL = 0,   /* DLOBPCG-dchol: everything in FP64, FP64 Cholesky               */
   MPL_D_SCHOL = 1,   /* DLOBPCG-schol: FP64 except the FP32 preconditioner              */

@@ -1,7 +1,7 @@
 """Algorithm 3 (mixed-precision LOBPCG) and Algorithm 1 (mixed-precision
 PINVIT), test infrastructure only.
 
-Policies (Section 5.1, "The following variants ... are tested"):
+Policies (the variants compared in Section 5.1):
   "dchol"  DLOBPCG-dchol   everything in working precision (FP64), factor too.
   "schol"  DLOBPCG-schol   working precision except the preconditioner
                            (lower-precision Cholesky + triangular solves).

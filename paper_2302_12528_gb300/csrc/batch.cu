@@ -466,7 +466,7 @@ __device__ void solve_problem(const Args& a, int p, unsigned char* ws, Smem& s, 
           start = X2;
         }
       }
-      // Algorithm 2 step 1 in the lower precision, FP64 fallback
+      // Algorithm 2's Householder QR step in the lower precision, FP64 fallback
       st = run_stage<double, float, TF>(n, m, k, A, F, Dinv, B, b2, reinterpret_cast<float*>(ws + L.Wq), start,
                                         a.tol, normA, a.maxit, false, true, s, &it2, &cur, &maxrel, sh, tk);
     } else {

@@ -185,7 +185,7 @@ struct Progress {
 };
 
 // One LOBPCG loop (the iteration of Algorithm 3) in working type TW with the QR of
-// Algorithm 2 step 1 in TQ.
+// Algorithm 2's Householder QR step in TQ.
 template <typename TW, typename TQ>
 class Stage {
  public:

@@ -3,11 +3,11 @@
 //
 //  * tsqr_r         Householder QR of single(W) (n x m) by a tree of per-CTA
 //                   Householder factorisations (leaves of 128+ rows, merges of
-//                   4 stacked R factors); only R is formed (Algorithm 2 step 1).
-//  * trinv_upper_ct (R^*)^-1 for the triangular solves of Algorithm 2 step 2.
-//  * chol_inv       V^* V = L L^* and L^-1 (Algorithm 2 steps 3-4).
-//  * eig_small      the m smallest eigenpairs of A_p = S^* A S (Algorithm 3,
-//                   "Solve eigenvalue problem of A_p").
+//                   4 stacked R factors); only R is formed (Algorithm 2's Householder QR step).
+//  * trinv_upper_ct (R^*)^-1 for the triangular solves of the triangular solve of Algorithm 2.
+//  * chol_inv       V^* V = L L^* and L^-1 (the Cholesky and back-substitution steps of Algorithm 2).
+//  * eig_small      the m smallest eigenpairs of A_p = S^* A S (the small
+//                   eigenproblem of Algorithm 3).
 //  * thin_q         orth(C(1:m, m+1:end)^*) of the Hetmaniuk-Lehoucq step.
 //
 // The eigensolver follows the textbook route (Golub & Van Loan, Ch. 8):

@@ -1,5 +1,5 @@
 // Small dense kernels of the LOBPCG step (m x m and 3m x 3m problems) and the
-// tall-skinny Householder QR (TSQR) of Algorithm 2, step 1.
+// tall-skinny Householder QR (TSQR) of Algorithm 2's Householder QR step.
 #pragma once
 #include "common.cuh"
 

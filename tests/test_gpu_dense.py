@@ -3,7 +3,7 @@ C ABI, against the CPU oracle on the same seeded inputs.
 
 Tolerances follow the arithmetic: FP64 contractions of length n agree with
 the oracle to gamma_n |A||X| (normwise); single-precision steps (factor,
-triangular sweeps, Algorithm 2 step 1) agree to multiples of n u_l times the
+triangular sweeps, Algorithm 2's Householder QR step) agree to multiples of n u_l times the
 conditioning that their forward errors carry."""
 import numpy as np
 import pytest
