@@ -12,7 +12,7 @@ complex Gaussian).  Prints one JSON line.
                   [--workload NAME] [--policy mp] [--no-fp64] [--no-e2e]
                   [--no-cpu-baseline]
   profiling helpers (their lines are marked as not bench values):
-                  [--profile-iters I] [--n N] [--kernel-probe apply|precond|eig]
+                  [--profile-iters I] [--n N] [--kernel-probe apply|precond|eig|factor]
   With MPL_PROFILE_RANGE=a:b set, the library brackets working-precision
   iterations a..b with cudaProfilerStart/Stop (for ncu --profile-from-start off).
 
@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dense_complex_n16384", choices=sorted(W.WORKLOADS))
-    ap.add_argument("--policy", default="mp", choices=["mp", "schol", "dchol"])
+    ap.add_argument("--policy", default="mp", choices=["mp", "schol", "dchol", "hchol", "bchol"])
     ap.add_argument("--maxit", type=int, default=1000)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--precision-study", action="store_true",
                     help="dense workloads: FP32 / fp16 / bf16 factor stage vs all-FP64 at order --n "
                          "(default 4096): iterations, time and eigenvalue error per precision")
-    ap.add_argument("--kernel-probe", default="", choices=["", "apply", "precond", "eig"],
+    ap.add_argument("--kernel-probe", default="", choices=["", "apply", "precond", "eig", "factor"],
                     help="profiling runs only: time one step entry point (A X, T R, or the "
                          "3m x 3m eigensolver) K times after W warm-ups instead of full solves")
     return ap.parse_args()
@@ -457,6 +457,9 @@ def kernel_probe(args, w, h, X0, stream, torch):
         call = lambda: h.apply_A(X0, Y, m)
         c = 2.0 if w.kind != "dense_complex" else 6.0
         flops = c * w.n * w.n * m if w.kind != "csr" else None
+    elif args.kernel_probe == "factor":
+        call = lambda: h.factor()
+        flops = (4.0 if w.kind == "dense_complex" else 1.0) * w.n ** 3 / 3.0
     elif args.kernel_probe == "precond":
         h.factor()
         Wt = torch.empty_like(X0)
@@ -485,10 +488,17 @@ def kernel_probe(args, w, h, X0, stream, torch):
         e1.record(stream)
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
+    stt = h.stats()
     h.close()
     out = {"kernel_probe": args.kernel_probe, "workload": w.name, "n": w.n, "m": m,
            "ms_min": min(ts), "ms_median": float(np.median(ts)), "calls": len(ts),
            "note": "profiling helper; not a bench value"}
+    if args.kernel_probe == "factor":
+        # the shifted retries of the factorisation each refactor: report per try
+        tries = max(int(stt["factor_tries"]), 1)
+        out.update(policy=args.policy, factor_tries=tries, factor_shift=stt["factor_shift"],
+                   ms_per_try=min(ts) / tries, fmt16_tc=os.environ.get("MPL_FMT16_TC", "1"))
+        flops *= tries
     if flops:
         out["gflops"] = flops / (min(ts) / 1e3) / 1e9
     print(json.dumps(out))

@@ -104,6 +104,22 @@ mpl_status mpl_analyze_host(mpl_handle* h, int64_t n, int64_t nnz, const int64_t
  * n), for checking the numeric factor (a slow single-CTA sweep; checks only). */
 mpl_status mpl_step_apply_L(mpl_handle h, const float* X, float* Y, int ncols);
 
+/*
+ * Tensor-core trailing update of the 16-bit factor stage (the factorisation
+ * of Section 5.1 with its matrix stored in a 16-bit format): C -= A A^T
+ * (A A^H when is_complex) on the lower triangle of C (n x n, ld ldc), for A
+ * (n x k, ld lda; 1 <= k <= 128 real, <= 64 complex) whose values are
+ * converted to the format fmt (1 fp16, 2 bf16; exact when they already are
+ * values of it), products accumulated in FP32 by tcgen05.mma (kind::f16).
+ * Storage is column-major FP32, complex interleaved (re, im) with ld in
+ * complex elements.  round_out != 0: the updated entries are rounded to the
+ * format.  The strictly upper part of C is not touched.  Device pointers;
+ * synchronous on stream.  Errors: MPL_EINVAL (sizes, fmt), MPL_ENOMEM,
+ * MPL_ECUDA (launch error, or the wait for the MMAs' completion gave up).
+ */
+mpl_status mpl_step_lowp_syrk(int fmt, int is_complex, int64_t n, int64_t k, const void* A, int64_t lda, void* C,
+                              int64_t ldc, int round_out, void* stream);
+
 /* Residual without device allocation (the paper has no counterpart).
  *
  * For callers that cannot call cudaMalloc: code that runs while a stream is

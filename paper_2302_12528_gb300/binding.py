@@ -74,6 +74,7 @@ _batch_solve = _sig("mpl_batch_solve", _i, [_h, _p, _p, _p, _p, _p])
 _batch_config = _sig("mpl_batch_get_config", _i, [_h, _p, _p, _p, _p])
 _batch_destroy = _sig("mpl_batch_destroy", None, [_h])
 _batch_phases = _sig("mpl_batch_get_phase_cycles", _i, [_h, _p, _i])
+_lowp_syrk = _sig("mpl_step_lowp_syrk", _i, [_i, _i, _i64, _i64, _p, _i64, _p, _i64, _i, _p])
 _stats = _sig("mpl_get_stats", _i, [_h, C.POINTER(Stats)])
 _last_error = _sig("mpl_last_error", C.c_char_p, [_h])
 _last_info = _sig("mpl_last_info", _i64, [_h])
@@ -479,3 +480,15 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def lowp_syrk(fmt, A, C, round_out=False, stream=None):
+    """mpl_step_lowp_syrk: C -= A A^H (lower) on the tensor cores.  A and C
+    are column-major device tensors given as (k, n) / (n, n) row-major
+    arrays, float32 or complex64; fmt "fp16" or "bf16"."""
+    k, n = A.shape
+    cx = 1 if A.is_complex() else 0
+    st = _lowp_syrk({"fp16": 1, "bf16": 2}[fmt], cx, n, k, _ptr(A), n, _ptr(C), n, 1 if round_out else 0,
+                    _stream_ptr(stream))
+    if st != 0:
+        raise MplError(st, "mpl_step_lowp_syrk failed", 0)

@@ -1,6 +1,7 @@
 // C ABI (include/mplobpcg.h, include/mplobpcg_steps.h): handle lifetime,
 // the precision policies of Section 5.1 and the two stages of Algorithm 3.
 #include <chrono>
+#include <cstdlib>
 #include <cstdio>
 
 #include "adjoint.cuh"
@@ -64,6 +65,15 @@ inline bool mp_like(int policy) {
 }
 // 16-bit storage format of the factor: 0 none, 1 fp16, 2 bf16.
 inline int fmt16_of(int policy) { return policy == MPL_MP_HCHOL ? 1 : policy == MPL_MP_BCHOL ? 2 : 0; }
+// The real 16-bit factor's trailing update runs on the tensor cores unless
+// MPL_FMT16_TC=0 (then on the CUDA-core GEMM, for comparison).
+inline bool fmt16_tc() {
+  static const bool on = [] {
+    const char* e = std::getenv("MPL_FMT16_TC");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
 
 // ---- engine ------------------------------------------------------------
 struct EngineBase {
@@ -243,18 +253,21 @@ class Engine : public EngineBase {
       else cast<TF, TW>(st, (int)n, (int)n, Aw_.as<TW>(), n, F.L, n);
       if (sigma != 0.0) add_diag<TF>(st, (int)n, F.L, n, sigma);
       round_block<TF>(st, (int)n, (int)n, F.L, n, fmt, true);
-      dense_cholesky<TF>(st, F, tmp_.as<TF>(), info_.as<int>(), scr_, -1, 0, true, fmt);
-      int info = 0;
-      MPL_CUDA(cudaMemcpyAsync(&info, info_.ptr(), sizeof(int), cudaMemcpyDeviceToHost, st));
+      int* tc_err = (fmt && fmt16_tc()) ? info_.as<int>() + 1 : nullptr;
+      if (tc_err) MPL_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int), st));
+      dense_cholesky<TF>(st, F, tmp_.as<TF>(), info_.as<int>(), scr_, -1, 0, true, fmt, tc_err);
+      int info[2] = {0, 0};
+      MPL_CUDA(cudaMemcpyAsync(info, info_.ptr(), 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
       MPL_CUDA(cudaStreamSynchronize(st));
       check_launch("dense_cholesky");
+      if (tc_err && info[1] != 0) throw MplError{MPL_ECUDA, "tensor-core trailing update: MMA wait gave up", 0};
       c_->stats.factor_tries = j + 1;
-      if (info == 0) {
+      if (info[0] == 0) {
         c_->stats.factor_shift = sigma;
         c_->stats.nnz_L = n * (n + 1) / 2;
         return;
       }
-      c_->info = info;
+      c_->info = info[0];
       sigma = std::ldexp(1.0, j) * u * scale;
     }
     throw MplError{MPL_ENOT_HPD, "Cholesky factorisation broke down for every shift", c_->info};

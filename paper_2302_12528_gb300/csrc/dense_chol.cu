@@ -128,7 +128,7 @@ void round_block(cudaStream_t st, int rows, int cols, T* A, long long lda, int f
 
 template <typename T>
 void dense_cholesky(cudaStream_t st, DenseFactor<T>& F, T* tmp, int* info, Scratch scr, int nfact,
-                    long long col_offset, bool reset_info, int fmt16) {
+                    long long col_offset, bool reset_info, int fmt16, int* tc_err) {
   constexpr int NB = CholBlock<T>::NB;
   const int n = F.n;
   if (nfact < 0 || nfact > n) nfact = n;
@@ -161,9 +161,16 @@ void dense_cholesky(cudaStream_t st, DenseFactor<T>& F, T* tmp, int* info, Scrat
     round_block<T>(st, rest, kb, Aik, lda, fmt16, false);
     // trailing update, lower triangle only
     T* Att = F.L + (k + kb) + (long long)(k + kb) * lda;
-    gemm<T>(st, false, true, rest, rest, kb, real_t<T>(-1), Aik, lda, Aik, lda, real_t<T>(1), Att,
-            lda, true, scr);
-    round_block<T>(st, rest, rest, Att, lda, fmt16, true);
+    bool on_tc = false;
+    if constexpr (sizeof(real_t<T>) == 4)
+      if (fmt16 && tc_err)
+        on_tc = tc_syrk(st, fmt16, tr<T>::cx, rest, kb, reinterpret_cast<const float*>(Aik), lda,
+                        reinterpret_cast<float*>(Att), lda, true, tc_err);
+    if (!on_tc) {
+      gemm<T>(st, false, true, rest, rest, kb, real_t<T>(-1), Aik, lda, Aik, lda, real_t<T>(1), Att,
+              lda, true, scr);
+      round_block<T>(st, rest, rest, Att, lda, fmt16, true);
+    }
   }
 }
 
@@ -389,7 +396,7 @@ void dense_precond(cudaStream_t st, const DenseFactor<T>& F, T* B, long long ldb
 
 #define MPL_INST_CHOL(T)                                                                      \
   template void dense_cholesky<T>(cudaStream_t, DenseFactor<T>&, T*, int*, Scratch, int,     \
-                                  long long, bool, int);                                     \
+                                  long long, bool, int, int*);                               \
   template void scale_rows<T>(cudaStream_t, int, int, T*, long long, const float*);         \
   template void round_block<T>(cudaStream_t, int, int, T*, long long, int, bool);           \
   template void dense_precond<T>(cudaStream_t, const DenseFactor<T>&, T*, long long, int);   \

@@ -28,9 +28,21 @@ struct DenseFactor {
 // fmt16 (0 none, 1 fp16, 2 bf16): the matrix is stored in that 16-bit
 // format -- the diagonal block, the panel and the trailing update are
 // rounded to it after each step (arithmetic in T; FP32 types only).
+// tc_err (FP32 types with fmt16 only): when given, the trailing update runs
+// on the tensor cores (tcgen05, 16-bit operands exact, FP32 accumulation,
+// rounded to the format in its epilogue) and *tc_err becomes nonzero if an
+// MMA completion wait gave up.
 template <typename T>
 void dense_cholesky(cudaStream_t st, DenseFactor<T>& F, T* tmp, int* info, Scratch scr,
-                    int nfact = -1, long long col_offset = 0, bool reset_info = true, int fmt16 = 0);
+                    int nfact = -1, long long col_offset = 0, bool reset_info = true, int fmt16 = 0,
+                    int* tc_err = nullptr);
+
+// Tensor-core C -= A A^T (A A^H when cx, A and C then complex interleaved;
+// lower triangle; A n x k, k <= 128 real / 64 complex, values of the 16-bit
+// format fmt: 1 fp16, 2 bf16), the result rounded to the format when
+// round_out.  False when k or fmt is out of range.
+bool tc_syrk(cudaStream_t st, int fmt, bool cx, int n, int k, const float* A, long long lda, float* C,
+             long long ldc, bool round_out, int* err);
 
 // Round a rows x cols block (ld lda; lower triangle only if lower_only) to
 // the 16-bit format fmt (1 fp16, 2 bf16; 0: no-op).
