@@ -4,13 +4,14 @@
 // rounded to the format -- the contraction of the blocked Cholesky step with
 // the factor stored in the lower precision.
 //
-// One CTA (4 warps) computes one 128 x 128 lower-triangle tile with
+// One CTA (8 warps) computes one 128 x 128 lower-triangle tile with
 // tcgen05.mma (kind::f16, FP32 accumulator in tensor memory): the operand
 // tiles (128 rows x K <= 128, K-major, converted to the format on the way
 // in) are staged in shared memory in the canonical no-swizzle layout of
 // 8-row x 16-byte core matrices, one thread issues the K/16 MMAs, their
 // completion is committed to an mbarrier (waited on with an iteration
-// limit), and each warp reads its 32 accumulator lanes back with tcgen05.ld.
+// limit), and each warp reads 32 accumulator lanes x 64 columns back with
+// tcgen05.ld.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -21,7 +22,7 @@
 namespace mpl {
 
 constexpr int TC_M = 128, TC_N = 128, TC_KMAX = 128;
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;  // two warpgroups: both stage operands, each reads half the columns
 constexpr long long TC_WAIT_LIMIT = 1LL << 22;  // mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -184,13 +185,15 @@ tc_syrk_kernel(int n, int k, const float* __restrict__ A, long long lda, float* 
   if (!done && tid == 0) atomicExch(err, 1);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (done) {
-    // warp w owns accumulator lanes (rows) 32w .. 32w + 31
-    const int row = m0 + 32 * wid + lane;
-    for (int c0 = 0; c0 < TC_N; c0 += 16) {
+    // warp w may read accumulator lanes (rows) 32 (w % 4) .. + 31 only; the
+    // two warpgroups split the columns
+    const int lg = wid & 3, ch = wid >> 2;
+    const int row = m0 + 32 * lg + lane;
+    for (int c0 = ch * (TC_N / 2); c0 < (ch + 1) * (TC_N / 2); c0 += 16) {
       uint32_t v[NACC][16];
 #pragma unroll
       for (int h = 0; h < NACC; ++h) {
-        const uint32_t taddr = tmem + ((uint32_t)(32 * wid) << 16) + (uint32_t)(h * TC_N + c0);
+        const uint32_t taddr = tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(h * TC_N + c0);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
             "%14, %15}, [%16];"
