@@ -12,6 +12,26 @@ deterministic *grid-geometric nested dissection*:
            nd(left [lo, mid)) + nd(right [mid+1, hi)) + the separator plane
            {mid} listed lexicographically.
 
+For a CSR pattern without grid dimensions the reading is the level-structure
+nested dissection of George & Liu (Computer Solution of Large Sparse
+Positive Definite Systems, 1981, ch. 8) made deterministic:
+
+  gnd(S), S a connected vertex set:
+    if |S| <= LEAF: S ascending is one block;
+    r = pseudo-peripheral node of G[S] (start at min S; repeatedly move to
+        the node of least degree in G[S] on the last BFS level, ties by
+        smallest index, while the eccentricity grows);
+    levels L_0 .. L_e of the BFS from r in G[S];
+    if e < 2: S ascending is one block;
+    else the separator is L_j, j = (e + 1) // 2: the connected components of
+        G[S \\ L_j] in order of their smallest vertex are ordered by gnd,
+        then L_j ascending as one block.
+  The whole graph: its connected components in order of smallest vertex.
+
+A separator level is one block even where it is disconnected in G: the levels
+before it are connected and numbered earlier, so it is connected in the
+filled graph and its columns form one subtree of the elimination tree.
+
 ``perm[new] = old``; the permuted matrix is B[i, j] = A[perm[i], perm[j]].
 
 Everything after the ordering is a plain definition written out:
@@ -73,6 +93,95 @@ def nd_grid_order(dims, leaf=LEAF, return_blocks=False):
 
     rec([(0, d) for d in dims])
     perm = np.concatenate(out).astype(np.int64)
+    if return_blocks:
+        starts = np.cumsum([0] + [len(o) for o in out])
+        return perm, starts.astype(np.int64)
+    return perm
+
+
+def _neighbours(rowptr, colind, v):
+    return [int(u) for u in colind[rowptr[v]:rowptr[v + 1]] if u != v]
+
+
+def _bfs_levels(rowptr, colind, inset, root):
+    """BFS level sets from root inside the vertex set ``inset`` (a Python
+    set); each level ascending."""
+    levels = [[root]]
+    seen = {root}
+    while True:
+        nxt = set()
+        for v in levels[-1]:
+            for u in _neighbours(rowptr, colind, v):
+                if u in inset and u not in seen:
+                    nxt.add(u)
+        if not nxt:
+            return levels
+        seen |= nxt
+        levels.append(sorted(nxt))
+
+
+def _components(rowptr, colind, inset):
+    """Connected components of G[inset], each ascending, ordered by their
+    smallest vertex."""
+    left = set(inset)
+    comps = []
+    for s in sorted(inset):
+        if s not in left:
+            continue
+        comp = set()
+        stack = [s]
+        left.discard(s)
+        while stack:
+            v = stack.pop()
+            comp.add(v)
+            for u in _neighbours(rowptr, colind, v):
+                if u in left:
+                    left.discard(u)
+                    stack.append(u)
+        comps.append(sorted(comp))
+    return comps
+
+
+def pseudo_peripheral(rowptr, colind, inset):
+    """George-Liu pseudo-peripheral node of the connected set ``inset``."""
+    r = min(inset)
+    levels = _bfs_levels(rowptr, colind, inset, r)
+    while True:
+        deg = lambda v: sum(1 for u in _neighbours(rowptr, colind, v) if u in inset)
+        x = min(levels[-1], key=lambda v: (deg(v), v))
+        lx = _bfs_levels(rowptr, colind, inset, x)
+        if len(lx) > len(levels):
+            r, levels = x, lx
+        else:
+            return r, levels
+
+
+def nd_graph_order(rowptr, colind, leaf=LEAF, return_blocks=False):
+    """Level-structure nested dissection of a structurally symmetric CSR
+    pattern (reading above).  Returns perm (int64), perm[new] = old, and
+    with ``return_blocks`` the block starts (leaf sets and separator
+    levels, in the new order) followed by n."""
+    n = len(rowptr) - 1
+    out = []
+
+    def gnd(S):
+        if len(S) <= leaf:
+            out.append(sorted(S))
+            return
+        inset = set(S)
+        _, levels = pseudo_peripheral(rowptr, colind, inset)
+        e = len(levels) - 1
+        if e < 2:
+            out.append(sorted(S))
+            return
+        sep = levels[(e + 1) // 2]
+        for comp in _components(rowptr, colind, inset - set(sep)):
+            gnd(comp)
+        out.append(sorted(sep))
+
+    for comp in _components(rowptr, colind, set(range(n))):
+        gnd(comp)
+    perm = np.array([v for blk in out for v in blk], dtype=np.int64)
     if return_blocks:
         starts = np.cumsum([0] + [len(o) for o in out])
         return perm, starts.astype(np.int64)

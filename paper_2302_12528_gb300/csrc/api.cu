@@ -1071,7 +1071,7 @@ extern "C" mpl_status mpl_get_symbolic(mpl_handle h, int64_t* parent, int64_t* c
     cp(colcount, s->colcount);
     cp(sn_start, s->sn_start);
     cp(sn_rowptr, s->sn_rowptr);
-    cp(sn_rows, s->sn_rows);
+    if (sn_rows) std::copy(s->sn_rows.begin(), s->sn_rows.end(), sn_rows);
     cp(sn_level, s->sn_level);
     return MPL_OK;
   });

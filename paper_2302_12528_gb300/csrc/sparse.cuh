@@ -17,7 +17,7 @@ struct SparseSymbolic {
   std::vector<long long> colcount;   // |L(:, j)| including the diagonal
   std::vector<long long> sn_start;   // nsuper + 1 first columns
   std::vector<long long> sn_rowptr;  // nsuper + 1
-  std::vector<long long> sn_rows;    // per supernode: its columns, then struct below, ascending
+  std::vector<int> sn_rows;          // per supernode: its columns, then struct below, ascending
   std::vector<long long> sn_parent;  // supernodal tree
   std::vector<long long> sn_level;   // 0 = leaf, 1 + max(child levels)
   // Relaxed partition used by the numeric factor: the nested-dissection
@@ -42,7 +42,13 @@ struct SparseSymbolic {
 std::vector<long long> nd_grid_order(const int* dims, int ndims, int leaf,
                                      std::vector<long long>* blocks = nullptr);
 
-// Ordering + symbolic analysis.  ``dims`` may be null (natural order).
+// Level-structure nested dissection of a structurally symmetric CSR pattern
+// (perm[new] = old; block starts of the leaf sets and separator levels).
+std::vector<long long> nd_graph_order(long long n, const long long* rowptr, const int* colind, int leaf,
+                                      std::vector<long long>* blocks);
+
+// Ordering + symbolic analysis.  ``dims`` may be null (then the
+// level-structure nested dissection of the pattern).
 void analyze_csr(long long n, const long long* rowptr, const int* colind, const double* vals,
                  const int* dims, int ndims, SparseSymbolic& S);
 

@@ -6,6 +6,19 @@
 // its longest axis (ties: x, then y, then z) at mid = lo + (hi - lo) / 2 of the
 // half-open range, and ordered as left part, right part, separator plane.
 //
+// Without grid dimensions the ordering is George & Liu's level-structure
+// nested dissection (Computer Solution of Large Sparse Positive Definite
+// Systems, 1981, ch. 8), made deterministic: a connected set of at most LEAF
+// vertices is one block, ascending; otherwise a pseudo-peripheral root is
+// found (start at the smallest vertex, move to the least-degree vertex of
+// the last BFS level, ties by index, while the eccentricity grows), and with
+// e + 1 >= 3 BFS levels the middle level j = (e + 1) / 2 is the separator:
+// the connected components of the rest, in order of their smallest vertex,
+// are dissected first, then the separator level follows, ascending, as one
+// block (it is connected through the earlier levels in the filled graph).
+// With fewer than three levels the set is one block.  Disconnected graphs:
+// components in order of their smallest vertex.
+//
 // Symbolic analysis of B = Pi^* A Pi:
 //   * elimination tree by Liu's algorithm (path-compressed ancestor links);
 //   * column structures struct(j) = adj_>(j) U struct(children) \ {j}, merged
@@ -17,6 +30,7 @@
 #include <algorithm>
 #include <cstring>
 #include <functional>
+#include <iterator>
 #include <numeric>
 
 #include "sparse.cuh"
@@ -74,15 +88,133 @@ std::vector<long long> nd_grid_order(const int* dims, int ndims, int leaf,
   return out;
 }
 
+std::vector<long long> nd_graph_order(long long n, const long long* rowptr, const int* colind, int leaf,
+                                      std::vector<long long>* blocks) {
+  std::vector<long long> out;
+  out.reserve(n);
+  if (blocks) blocks->clear();
+  std::vector<long long> owner(n, -1);  // id of the vertex set a vertex is in
+  std::vector<long long> seen(n, -1);   // BFS stamp
+  long long set_id = 0, bfs_id = 0;
+  auto emit = [&](std::vector<long long>& v) {
+    std::sort(v.begin(), v.end());
+    if (blocks) blocks->push_back((long long)out.size());
+    out.insert(out.end(), v.begin(), v.end());
+  };
+  // BFS inside set `id` from root: vertices by level in q, level starts in
+  // ls (strictly increasing; the last entry is |q|)
+  auto bfs = [&](long long id, long long root, std::vector<long long>& q, std::vector<long long>& ls) {
+    const long long st = bfs_id++;
+    q.clear();
+    ls.assign(1, 0);
+    q.push_back(root);
+    seen[root] = st;
+    long long head = 0;
+    while (head < (long long)q.size()) {
+      const long long end = (long long)q.size();
+      for (; head < end; ++head) {
+        const long long v = q[head];
+        for (long long k = rowptr[v]; k < rowptr[v + 1]; ++k) {
+          const long long u = colind[k];
+          if (u != v && owner[u] == id && seen[u] != st) {
+            seen[u] = st;
+            q.push_back(u);
+          }
+        }
+      }
+      ls.push_back(end);
+    }
+  };
+  std::vector<long long> q, ls, q2, ls2;
+  // connected components of set `id` among `verts` (ascending), by smallest vertex
+  auto components = [&](long long id, const std::vector<long long>& verts) {
+    std::vector<std::vector<long long>> comps;
+    for (long long s0 : verts) {
+      if (owner[s0] != id) continue;
+      const long long cid = ++set_id;
+      std::vector<long long> comp{s0};
+      owner[s0] = cid;
+      for (size_t h = 0; h < comp.size(); ++h) {
+        const long long v = comp[h];
+        for (long long k = rowptr[v]; k < rowptr[v + 1]; ++k) {
+          const long long u = colind[k];
+          if (owner[u] == id) {
+            owner[u] = cid;
+            comp.push_back(u);
+          }
+        }
+      }
+      comps.push_back(std::move(comp));
+    }
+    return comps;
+  };
+  // work stack: dissect a connected set, or emit a separator level
+  struct Task { bool emit_only; std::vector<long long> v; };
+  std::vector<Task> work;
+  {
+    std::vector<long long> all(n);
+    std::iota(all.begin(), all.end(), 0LL);
+    const long long id = ++set_id;
+    for (long long v = 0; v < n; ++v) owner[v] = id;
+    auto comps = components(id, all);
+    for (auto it = comps.rbegin(); it != comps.rend(); ++it) work.push_back({false, std::move(*it)});
+  }
+  while (!work.empty()) {
+    Task t = std::move(work.back());
+    work.pop_back();
+    std::vector<long long>& S = t.v;
+    if (t.emit_only || (long long)S.size() <= leaf) {
+      emit(S);
+      continue;
+    }
+    std::sort(S.begin(), S.end());
+    const long long id = ++set_id;
+    for (long long v : S) owner[v] = id;
+    auto degree = [&](long long v) {
+      long long d = 0;
+      for (long long k = rowptr[v]; k < rowptr[v + 1]; ++k)
+        if (colind[k] != v && owner[colind[k]] == id) ++d;
+      return d;
+    };
+    // pseudo-peripheral root and its level structure (q, ls); a candidate's
+    // structure goes to (q2, ls2) and replaces it only if it is deeper
+    bfs(id, S[0], q, ls);
+    while (true) {
+      long long x = -1, dx = 0;
+      for (long long h = ls[ls.size() - 2]; h < ls.back(); ++h) {
+        const long long v = q[h], dv = degree(v);
+        if (x < 0 || dv < dx || (dv == dx && v < x)) {
+          x = v;
+          dx = dv;
+        }
+      }
+      bfs(id, x, q2, ls2);
+      if (ls2.size() <= ls.size()) break;  // eccentricity did not grow: keep the previous root
+      q.swap(q2);
+      ls.swap(ls2);
+    }
+    const long long e = (long long)ls.size() - 2;  // levels 0..e
+    if (e < 2) {
+      emit(S);
+      continue;
+    }
+    const long long j = (e + 1) / 2;
+    std::vector<long long> sep(q.begin() + ls[j], q.begin() + ls[j + 1]);
+    for (long long v : sep) owner[v] = -1;
+    auto comps = components(id, S);
+    work.push_back({true, std::move(sep)});
+    for (auto it = comps.rbegin(); it != comps.rend(); ++it) work.push_back({false, std::move(*it)});
+  }
+  if (blocks) blocks->push_back((long long)out.size());
+  return out;
+}
+
 void analyze_csr(long long n, const long long* rowptr, const int* colind, const double* vals,
                  const int* dims, int ndims, SparseSymbolic& S) {
   S.n = n;
   std::vector<long long> blocks;
   if (dims) S.perm = nd_grid_order(dims, ndims, ND_LEAF, &blocks);
-  else {
-    S.perm.resize(n);
-    std::iota(S.perm.begin(), S.perm.end(), 0LL);
-  }
+  else S.perm = nd_graph_order(n, rowptr, colind, ND_LEAF, &blocks);
   if ((long long)S.perm.size() != n) throw MplError{MPL_EINVAL, "grid dims do not match n", n};
   std::vector<long long> inv(n);
   for (long long i = 0; i < n; ++i) inv[S.perm[i]] = i;
@@ -153,18 +285,25 @@ void analyze_csr(long long n, const long long* rowptr, const int* colind, const 
       chead[p] = j;
     }
   }
-  // column structures by merging into the parent; supernodes on the fly
+  // column structures by merging into the parent; supernodes on the fly.
+  // struct(j) is stored as a suffix of a pool vector: pool[own[j]] from
+  // off[j] on.  A column with one child c whose adjacency lies in struct(c)
+  // has struct(j) = struct(c) \ {j}, i.e. the same vector one entry further
+  // (min struct(c) = parent(c) = j): chains of such columns share storage.
   S.colcount.assign(n, 0);
-  std::vector<std::vector<int>> st(n);
+  std::vector<std::vector<int>> pool(n);
+  std::vector<long long> own(n, -1), off(n, 0);
+  auto sbeg = [&](long long j) { return pool[own[j]].cbegin() + off[j]; };
+  auto send = [&](long long j) { return pool[own[j]].cend(); };
   std::vector<long long> mark(n, -1);
-  std::vector<int> buf;
+  std::vector<int> adj, buf, tmp;
   S.sn_start.clear();
   S.sn_rowptr.assign(1, 0);
   S.sn_rows.clear();
   auto close_super = [&](long long first, long long last) {
     S.sn_start.push_back(first);
-    for (long long c = first; c <= last; ++c) S.sn_rows.push_back(c);
-    for (int r : st[last]) S.sn_rows.push_back(r);
+    for (long long c = first; c <= last; ++c) S.sn_rows.push_back((int)c);
+    S.sn_rows.insert(S.sn_rows.end(), sbeg(last), send(last));
     S.sn_rowptr.push_back((long long)S.sn_rows.size());
   };
   long long cur_first = 0;
@@ -178,34 +317,59 @@ void analyze_csr(long long n, const long long* rowptr, const int* colind, const 
   S.bk_rows.clear();
   const bool grid_blocks = !blocks.empty();
   for (long long j = 0; j < n; ++j) {
-    buf.clear();
+    adj.clear();
     // adj_>(j): column j of the lower part = row j of the upper part; B is
-    // symmetric, so take row j of the full CSR with column index > j
+    // symmetric, so take row j of the full CSR with column index > j (the
+    // permuted rows are sorted)
     for (long long k = S.p_rowptr[j]; k < S.p_rowptr[j + 1]; ++k) {
       const int i = S.p_colind[k];
       if (i > j && mark[i] != j) {
         mark[i] = j;
-        buf.push_back(i);
+        adj.push_back(i);
       }
     }
-    for (long long c = chead[j]; c != -1; c = cnext[c]) {
-      for (int i : st[c])
-        if (i != j && mark[i] != j) {
-          mark[i] = j;
-          buf.push_back(i);
+    bool shared = false;
+    if (nchild[j] == 1) {
+      const long long c = chead[j];
+      shared = true;
+      for (int i : adj)
+        if (!std::binary_search(sbeg(c) + 1, send(c), i)) {
+          shared = false;
+          break;
         }
+      if (shared) {
+        own[j] = own[c];
+        off[j] = off[c] + 1;
+      }
     }
-    std::sort(buf.begin(), buf.end());
-    st[j] = buf;
+    if (!shared) {
+      // union with each child's structure minus j: sorted ranges, linear merges
+      buf.assign(adj.begin(), adj.end());
+      for (long long c = chead[j]; c != -1; c = cnext[c]) {
+        const auto b0 = (sbeg(c) != send(c) && *sbeg(c) == j) ? sbeg(c) + 1 : sbeg(c);
+        tmp.clear();
+        std::set_union(buf.begin(), buf.end(), b0, send(c), std::back_inserter(tmp));
+        buf.swap(tmp);
+      }
+      pool[j].assign(buf.begin(), buf.end());
+      own[j] = j;
+      off[j] = 0;
+    }
+    const long long len = (long long)(send(j) - sbeg(j));
     if (grid_blocks) {
-      // union of struct(j) over the block's columns, rows beyond the block
+      // rows of the block beyond its columns: the union of struct(j) over its
+      // columns; a column whose parent lies in the block adds nothing
+      // (struct(j) is within {parent(j)} U struct(parent(j)))
       while (j >= blocks[blk + 1]) ++blk;
       const long long bend = blocks[blk + 1];
       if (j == blocks[blk]) ubuf.clear();
-      for (int i : buf)
-        if (i >= bend && umark[i] != blk) {
-          umark[i] = blk;
-          ubuf.push_back(i);
+      if (S.parent[j] < 0 || S.parent[j] >= bend)
+        for (auto it = sbeg(j); it != send(j); ++it) {
+          const int i = *it;
+          if (i >= bend && umark[i] != blk) {
+            umark[i] = blk;
+            ubuf.push_back(i);
+          }
         }
       if (j == bend - 1) {
         std::sort(ubuf.begin(), ubuf.end());
@@ -215,8 +379,8 @@ void analyze_csr(long long n, const long long* rowptr, const int* colind, const 
         S.bk_rowptr.push_back((long long)S.bk_rows.size());
       }
     }
-    S.colcount[j] = (long long)buf.size() + 1;
-    if (!buf.empty() && buf[0] != S.parent[j]) throw MplError{MPL_EINVAL, "matrix pattern is not structurally symmetric", j};
+    S.colcount[j] = len + 1;
+    if (len > 0 && *sbeg(j) != S.parent[j]) throw MplError{MPL_EINVAL, "matrix pattern is not structurally symmetric", j};
     if (j > 0) {
       const bool join = S.parent[j - 1] == j && S.colcount[j - 1] == S.colcount[j] + 1 && nchild[j] == 1;
       if (!join) {
@@ -224,9 +388,10 @@ void analyze_csr(long long n, const long long* rowptr, const int* colind, const 
         cur_first = j;
       }
     }
-    // a child's structure is not needed once merged: a supernode ending at
-    // column j-1 was closed above, before its structure is released here
-    for (long long c = chead[j]; c != -1; c = cnext[c]) std::vector<int>().swap(st[c]);
+    // a child's structure is not needed once merged (a supernode ending at
+    // column j-1 was closed above); storage passed on to j stays
+    for (long long c = chead[j]; c != -1; c = cnext[c])
+      if (own[c] != own[j]) std::vector<int>().swap(pool[own[c]]);
   }
   if (n > 0) close_super(cur_first, n - 1);
   S.sn_start.push_back(n);
@@ -251,7 +416,7 @@ void analyze_csr(long long n, const long long* rowptr, const int* colind, const 
   if (!grid_blocks) {
     S.bk_start.assign(S.sn_start.begin(), S.sn_start.end() - 1);
     S.bk_rowptr = S.sn_rowptr;
-    S.bk_rows = S.sn_rows;
+    S.bk_rows.assign(S.sn_rows.begin(), S.sn_rows.end());
   }
   S.bk_start.push_back(n);
   S.nblock = (long long)S.bk_start.size() - 1;

@@ -61,26 +61,70 @@ def test_symbolic_bit_exact(dims):
     h.close()
 
 
-def test_symbolic_natural_order_is_fundamental():
+def _graph_inputs():
+    rp, ci, _ = W.laplacian_csr((7, 7))
+    yield rp, ci
+    rp, ci, _ = W.laplacian_csr((9, 7, 5))
+    yield rp, ci
+    rp, ci, _ = W.laplacian_csr((20, 13))
+    yield rp, ci
+    rp, ci, _ = W.laplacian_csr((16, 16, 16))
+    yield rp, ci
+    rp, ci, _ = W.geometric_csr(2000, 21)
+    yield rp, ci
+    rp, ci, _ = W.geometric_csr(1500, 22, dim=3)
+    yield rp, ci
+    # a disconnected pattern: two geometric graphs with interleaved labels and
+    # isolated vertices
+    rp1, ci1, _ = W.geometric_csr(300, 23, avg_degree=4.0)
+    n = 2 * 300 + 5
+    rows = [[i] for i in range(n)]
+    for i in range(300):
+        for j in ci1[rp1[i]:rp1[i + 1]]:
+            if j != i:
+                rows[2 * i].append(2 * int(j))
+                rows[2 * i + 1].append(2 * int(j) + 1)
+    rp = np.cumsum([0] + [len(r) for r in rows]).astype(np.int64)
+    yield rp, np.array([c for r in rows for c in sorted(r)], dtype=np.int32)
+
+
+@pytest.mark.parametrize("case", list(range(7)))
+def test_graph_nd_symbolic_bit_exact(case):
+    """Without grid dimensions: the level-structure nested dissection and
+    everything after it equal the oracle's bit for bit."""
     M = _lib()
-    rp, ci, v = W.laplacian_csr((6, 5, 4))
+    rp, ci = list(_graph_inputs())[case]
+    perm, starts = S.nd_graph_order(rp, ci, return_blocks=True)
+    prp, pci, _ = S.permute_csr(rp, ci, np.ones(len(ci)), perm)
+    sym = S.Symbolic(prp, pci)
+    blk = S.Blocks(prp, pci, starts)
     h = M.analyze_host(rp, ci, None)
-    sym = S.Symbolic(rp, ci)
+    assert np.array_equal(h.permutation(), perm)
     g = h.symbolic()
-    assert np.array_equal(h.permutation(), np.arange(len(rp) - 1))
     assert np.array_equal(g["parent"], sym.parent)
+    assert np.array_equal(g["colcount"], sym.colcount)
+    assert np.array_equal(g["sn_start"], sym.sn_start)
+    assert g["nnz_L"] == sym.nnz_L
+    for s in range(sym.nsuper):
+        assert np.array_equal(g["sn_rows"][g["sn_rowptr"][s]:g["sn_rowptr"][s + 1]], sym.sn_rows[s])
     b = h.blocks()
-    assert np.array_equal(b["bk_start"], sym.sn_start)   # no grid: blocks = fundamental supernodes
+    assert np.array_equal(b["bk_start"], blk.start)
+    assert np.array_equal(b["bk_parent"], blk.parent)
+    assert np.array_equal(b["bk_level"], blk.level)
+    for q in range(blk.nblock):
+        assert np.array_equal(b["bk_rows"][b["bk_rowptr"][q]:b["bk_rowptr"][q + 1]], blk.rows[q])
     h.close()
 
 
-def test_block_structure_contained_in_parent():
+@pytest.mark.parametrize("grid", [True, False])
+def test_block_structure_contained_in_parent(grid):
     """The multifrontal extend-add needs rows(child) beyond its columns to be
-    rows of its parent; the partition satisfies it on a 3D grid."""
+    rows of its parent; both partitions (grid boxes and planes; graph leaf
+    sets and separator levels) satisfy it on a 3D grid."""
     M = _lib()
     dims = (16, 12, 10)
     rp, ci, v = W.laplacian_csr(dims)
-    b = M.analyze_host(rp, ci, dims).blocks()
+    b = M.analyze_host(rp, ci, dims if grid else None).blocks()
     for q in range(b["nblock"]):
         p = b["bk_parent"][q]
         rows = b["bk_rows"][b["bk_rowptr"][q]:b["bk_rowptr"][q + 1]]

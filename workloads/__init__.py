@@ -202,6 +202,32 @@ def diffusion_csr(dims, seed: int, ell: float = 8.0, sigma: float = 1.0,
     return rowptr, cc.astype(np.int32), v.astype(np.float64), c
 
 
+def geometric_csr(n: int, seed: int, avg_degree: float = 6.0, dim: int = 2):
+    """Irregular sparse SPD matrix without grid structure: n seeded uniform
+    points in the unit square (dim 2) or cube (dim 3), an edge between two
+    points closer than r (r set for the expected average degree), values =
+    graph Laplacian + identity.  CSR, sorted rows, diagonal included."""
+    rng = _rng(seed)
+    P = rng.uniform(0.0, 1.0, (n, dim))
+    vol = math.pi if dim == 2 else 4.0 * math.pi / 3.0
+    r = (avg_degree / (n * vol)) ** (1.0 / dim)
+    rows = [[] for _ in range(n)]
+    for a in range(0, n, 512):
+        d2 = ((P[a:a + 512, None, :] - P[None, :, :]) ** 2).sum(-1)
+        ii, jj = np.nonzero(d2 < r * r)
+        for i, j in zip(ii + a, jj):
+            if i != j:
+                rows[i].append(int(j))
+    rp = np.zeros(n + 1, dtype=np.int64)
+    ci, vals = [], []
+    for i in range(n):
+        nb = sorted(rows[i] + [i])
+        ci.extend(nb)
+        vals.extend(float(len(rows[i]) + 1) if j == i else -1.0 for j in nb)
+        rp[i + 1] = len(ci)
+    return rp, np.asarray(ci, dtype=np.int32), np.asarray(vals, dtype=np.float64)
+
+
 def laplacian_csr(dims):
     """Constant-coefficient (c == 1) Dirichlet Laplacian on ``dims``."""
     return diffusion_csr(dims, seed=0, sigma=0.0)[:3]
