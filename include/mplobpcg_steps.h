@@ -105,6 +105,22 @@ mpl_status mpl_analyze_host(mpl_handle* h, int64_t n, int64_t nnz, const int64_t
 mpl_status mpl_step_apply_L(mpl_handle h, const float* X, float* Y, int ncols);
 
 /*
+ * FP64-accurate product C = A B on the bf16 tensor cores (the working-
+ * precision A X of Algorithm 3 computed by error-free splitting, Ozaki et al.
+ * 2012): the rows of A and the columns of B are cut into 7 signed 8-bit
+ * digits below their exponents; the 28 leading slice-pair products run as
+ * tcgen05.mma with the four leading shift groups accumulated exactly and
+ * folded into an int64 fixed-point sum; complex products use three real
+ * products (3M).  A: n x k, B: k x m, C: n x m, column-major FP64 device
+ * arrays (complex interleaved when is_complex, ld in complex elements);
+ * 1 <= m <= 96, k <= 2^21.  Synchronous on stream; allocates its own
+ * scratch.  Errors: MPL_EINVAL (sizes), MPL_ENOMEM, MPL_ECUDA (launch error
+ * or a completion wait gave up).
+ */
+mpl_status mpl_step_split_gemm(int is_complex, int64_t n, int64_t k, int64_t m, const void* A, int64_t lda,
+                               const void* B, int64_t ldb, void* C, int64_t ldc, void* stream);
+
+/*
  * Tensor-core trailing update of the 16-bit factor stage (the factorisation
  * of Section 5.1 with its matrix stored in a 16-bit format): C -= A A^T
  * (A A^H when is_complex) on the lower triangle of C (n x n, ld ldc), for A

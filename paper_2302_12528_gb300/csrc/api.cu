@@ -8,6 +8,7 @@
 #include "engine.cuh"
 #include "mplobpcg_adjoint.h"
 #include "mplobpcg_steps.h"
+#include "oz_gemm.cuh"
 #include "sparse.cuh"
 
 namespace mpl {
@@ -17,13 +18,81 @@ void spmm_csr(cudaStream_t st, int n, int m, const long long* rowptr, const int*
               const TV* vals, const T* X, long long ldx, T* Y, long long ldy);
 
 // ---- operators ---------------------------------------------------------
+// Working-precision A X by error-free splitting on the bf16 tensor cores
+// (oz_gemm.cu): A's row slices are made once, X's column slices per product
+// (blocks of <= 96 columns).  Opt-in with MPL_AX_SPLIT=1.
+struct SplitAX {
+  bool cx = false;
+  int n = 0, np = 1;
+  size_t qa = 0, pb = 0, tt = 0;
+  long long trows = 0;
+  DevMem e, Q, f, P, T, err;
+  void prepare(cudaStream_t st, bool complex_, int n_, const double* A, long long lda) {
+    cx = complex_;
+    n = n_;
+    np = cx ? 3 : 1;
+    qa = oz_a_elems(n, n);
+    pb = oz_b_elems(n, 96);
+    trows = oz_t_rows(n);
+    tt = (size_t)trows * 96;
+    e.alloc(sizeof(int) * np * n);
+    Q.alloc(sizeof(uint16_t) * np * qa);
+    f.alloc(sizeof(int) * np * 96);
+    P.alloc(sizeof(uint16_t) * np * pb);
+    T.alloc(sizeof(long long) * np * tt);
+    err.alloc(sizeof(int));
+    MPL_CUDA(cudaMemsetAsync(err.ptr(), 0, sizeof(int), st));
+    for (int p = 0; p < np; ++p)
+      oz_split_a(st, cx ? p + 1 : 0, n, n, A, lda, e.as<int>() + (size_t)p * n, Q.as<uint16_t>() + p * qa);
+    check_launch("split A");
+  }
+  void apply(cudaStream_t st, const double* X, long long ldx, double* Y, long long ldy, int ncols) {
+    const int elt = cx ? 2 : 1;
+    const int S = oz_shift(n);
+    for (int c0 = 0; c0 < ncols; c0 += 96) {
+      const int mc = std::min(96, ncols - c0);
+      MPL_CUDA(cudaMemsetAsync(T.ptr(), 0, sizeof(long long) * np * tt, st));
+      for (int p = 0; p < np; ++p)
+        oz_split_b(st, cx ? p + 1 : 0, n, mc, X + (size_t)elt * c0 * ldx, ldx, f.as<int>() + p * 96,
+                   P.as<uint16_t>() + p * pb);
+      for (int p = 0; p < np; ++p)
+        oz_mma(st, n, n, mc, Q.as<uint16_t>() + p * qa, P.as<uint16_t>() + p * pb, T.as<long long>() + p * tt,
+               err.as<int>());
+      double* y = Y + (size_t)elt * c0 * ldy;
+      if (cx)
+        oz_combine_3m(st, n, mc, T.as<long long>(), trows, (long long)tt, e.as<int>(), n, f.as<int>(), 96, S, y, ldy);
+      else
+        oz_combine_real(st, n, mc, T.as<long long>(), trows, e.as<int>(), f.as<int>(), S, y, ldy);
+    }
+    check_launch("split A X");
+    int h = 0;
+    MPL_CUDA(cudaMemcpyAsync(&h, err.ptr(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    MPL_CUDA(cudaStreamSynchronize(st));
+    if (h) throw MplError{MPL_ECUDA, "split A X: a completion wait gave up", 0};
+  }
+};
+
+inline bool ax_split_requested() {
+  static const bool on = [] {
+    const char* v = std::getenv("MPL_AX_SPLIT");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
+
 template <typename T>
 struct DenseOp : Op<T> {
   const T* A = nullptr;
   long long lda = 0;
   int n = 0;
   Scratch scr;
+  SplitAX* split = nullptr;  // FP64 working precision only
   void apply(cudaStream_t st, const T* X, long long ldx, T* Y, long long ldy, int ncols) override {
+    if constexpr (sizeof(real_t<T>) == 8)
+      if (split) {
+        split->apply(st, reinterpret_cast<const double*>(X), ldx, reinterpret_cast<double*>(Y), ldy, ncols);
+        return;
+      }
     gemm<T>(st, false, false, n, ncols, n, 1, A, lda, X, ldx, 0, Y, ldy, false, scr);
   }
   // flops the pipe executes: 2 n^2 per column (real), 8 n^2 complex FP32,
@@ -163,6 +232,11 @@ class Engine : public EngineBase {
     dense_op_.lda = n;
     dense_op_.n = (int)n;
     dense_op_.scr = scr_;
+    if (sizeof(real_t<TW>) == 8 && ax_split_requested() && n <= (1LL << 21)) {
+      split_ax_ = std::make_unique<SplitAX>();
+      split_ax_->prepare(st, tr<TW>::cx, (int)n, reinterpret_cast<const double*>(Aw_.ptr()), n);
+      dense_op_.split = split_ax_.get();
+    }
     opw_ = &dense_op_;
     if (mp_like(c_->policy)) {
       Al_.alloc(sizeof(TL) * n * n);
@@ -733,6 +807,7 @@ class Engine : public EngineBase {
   long long csr_nnz_ = 0;
   long long launches_factor_ = 0;
   Scratch scr_;
+  std::unique_ptr<SplitAX> split_ax_;
   DenseOp<TW> dense_op_;
   DenseOp<TL> dense_op_l_;
   CsrOp<double> csr_op_;
