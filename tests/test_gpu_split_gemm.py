@@ -3,11 +3,7 @@
 integer product bit for bit (digits, exact group sums and the int64 fold are
 all exact), and random real / complex inputs with row scales spread over
 eight orders of magnitude agree with the FP64 product within 1e-14 |A||B|
-(a dropped digit or group shows as >= 1e-12).
-
-Opt-in (MPL_TEST_SPLIT_GEMM=1) until the kernel's first GPU run."""
-import os
-
+(a dropped digit or group shows as >= 1e-12)."""
 import numpy as np
 import pytest
 
@@ -18,8 +14,6 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("no GPU", allow_module_level=True)
-if os.environ.get("MPL_TEST_SPLIT_GEMM") != "1":
-    pytest.skip("split product: opt-in until its first GPU run", allow_module_level=True)
 
 import paper_2302_12528_gb300 as M  # noqa: E402
 
