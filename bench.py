@@ -353,6 +353,8 @@ def main():
                                         "the pipe executes"}
         if cplx:
             out["roofline"]["complex_equivalent_gflops"] = achieved * 8.0 / 6.0
+        if os.environ.get("MPL_AX_SPLIT") == "1" and w.kind != "csr":
+            out["roofline"] = split_ax_roofline(w, per_launch_s, apply_calls)
     if ck:
         out["clocks"] = ck
     if unconv:
@@ -405,6 +407,41 @@ def traffic_per_launch(w):
         return None
     n0, rd, wr = cap
     return rd * (w.n / n0) ** 2 + wr * (w.n / n0)
+
+
+def split_ax_roofline(w, per_launch_s, launches):
+    """A X by error-free splitting on the bf16 tensor cores (MPL_AX_SPLIT=1):
+    per product 28 slice-pair MMAs over the padded tile grid (3 products for
+    complex A, 3M), A's row slices (7 bf16 digits) streamed from HBM once.
+    The bound is whichever of the tensor and HBM times is larger."""
+    import math
+    peaks = {}
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    bf16 = peaks.get("bf16_tflops_sustained", 1700.0) * 1e12
+    hbm = peaks.get("hbm_gbs", 6800.0) * 1e9
+    nprod = 3 if w.kind == "dense_complex" else 1
+    rows = math.ceil(w.n / 128) * 128
+    depth = math.ceil(w.n / 64) * 64
+    cols = sum(32 if c <= 32 else 64 if c <= 64 else 96 for c in
+               [min(96, w.m - c0) for c0 in range(0, w.m, 96)])
+    flops = nprod * 28 * 2.0 * rows * cols * depth
+    nblk = math.ceil(w.m / 96)
+    bytes_ = nprod * nblk * 7 * rows * depth * 2.0
+    t_tensor, t_hbm = flops / bf16, bytes_ / hbm
+    if t_tensor >= t_hbm:
+        ach, peak, unit, bound = flops / per_launch_s / 1e12, bf16 / 1e12, "TFLOP/s", "tensor"
+    else:
+        ach, peak, unit, bound = bytes_ / per_launch_s / 1e9, hbm / 1e9, "GB/s", "hbm"
+    return {"kernel": "oz_mma_kernel (FP64-accurate A X by error-free bf16 splitting, tcgen05) with its "
+                      "split and combine kernels", "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+            "frac": ach / peak, "traffic": None, "bf16_flops_per_launch": flops, "slice_bytes_per_launch": bytes_,
+            "launches": launches, "avg_launch_ms": per_launch_s * 1e3,
+            "peak_note": "measured sustained bf16 (cuBLAS) and copy bandwidth of this pool; the launch time "
+                         "covers the whole product (X's slices, the three products, the combination)"}
 
 
 def precision_study(args, w, M, d, X0, stream, torch):
