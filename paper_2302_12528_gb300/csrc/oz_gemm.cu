@@ -417,11 +417,11 @@ template <int NPAD>
 static void launch_mma(cudaStream_t st, int ntile, int nchunk, int nsplit, int cps, const uint16_t* Q,
                        const uint16_t* P, long long* T, int S, int* err) {
   const size_t sm = (size_t)OZ_S * (OZ_TILE_A * 2 + NPAD * OZ_BK * 2);
-  static bool opened = false;
-  if (!opened) {
-    cudaFuncSetAttribute(oz_mma_kernel<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    opened = true;
-  }
+  // one attribute call per instantiation (thread-safe static initialisation)
+  static const bool opened =
+      cudaFuncSetAttribute(oz_mma_kernel<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) ==
+      cudaSuccess;
+  (void)opened;
   count_launch();
   oz_mma_kernel<NPAD><<<dim3(ntile, nsplit), OZ_THREADS, sm, st>>>(ntile, nchunk, cps, Q, P, T, S, err);
 }

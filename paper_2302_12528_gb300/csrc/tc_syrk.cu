@@ -233,11 +233,11 @@ template <int FMT, bool CX>
 static void launch_tc(cudaStream_t st, int tiles, int n, int k, const float* A, long long lda, float* C,
                       long long ldc, int round_out, int* err) {
   const size_t sm = (size_t)(CX ? 3 : 2) * TC_M * TC_KMAX * 2;
-  static bool opened = false;  // one attribute call per instantiation
-  if (!opened) {
-    cudaFuncSetAttribute(tc_syrk_kernel<FMT, CX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    opened = true;
-  }
+  // one attribute call per instantiation (thread-safe static initialisation)
+  static const bool opened =
+      cudaFuncSetAttribute(tc_syrk_kernel<FMT, CX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) ==
+      cudaSuccess;
+  (void)opened;
   count_launch();
   tc_syrk_kernel<FMT, CX><<<tiles, TC_THREADS, sm, st>>>(n, k, A, lda, C, ldc, round_out, err);
 }
