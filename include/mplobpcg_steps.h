@@ -111,14 +111,16 @@ mpl_status mpl_step_apply_L(mpl_handle h, const float* X, float* Y, int ncols);
  * digits below their exponents; the 28 leading slice-pair products run as
  * tcgen05.mma with the four leading shift groups accumulated exactly and
  * folded into an int64 fixed-point sum; complex products use three real
- * products (3M).  A: n x k, B: k x m, C: n x m, column-major FP64 device
- * arrays (complex interleaved when is_complex, ld in complex elements);
+ * products (3M).  op(A): n x k (A itself, or when trans_a the transpose --
+ * conjugate transpose when complex -- of A stored k x n), B: k x m, C: n x m,
+ * column-major FP64 device arrays (complex interleaved when is_complex, ld in
+ * complex elements);
  * 1 <= m <= 96, k <= 2^21.  Synchronous on stream; allocates its own
  * scratch.  Errors: MPL_EINVAL (sizes), MPL_ENOMEM, MPL_ECUDA (launch error
  * or a completion wait gave up).
  */
-mpl_status mpl_step_split_gemm(int is_complex, int64_t n, int64_t k, int64_t m, const void* A, int64_t lda,
-                               const void* B, int64_t ldb, void* C, int64_t ldc, void* stream);
+mpl_status mpl_step_split_gemm(int is_complex, int trans_a, int64_t n, int64_t k, int64_t m, const void* A,
+                               int64_t lda, const void* B, int64_t ldb, void* C, int64_t ldc, void* stream);
 
 /*
  * Tensor-core trailing update of the 16-bit factor stage (the factorisation

@@ -74,7 +74,7 @@ _batch_solve = _sig("mpl_batch_solve", _i, [_h, _p, _p, _p, _p, _p])
 _batch_config = _sig("mpl_batch_get_config", _i, [_h, _p, _p, _p, _p])
 _batch_destroy = _sig("mpl_batch_destroy", None, [_h])
 _batch_phases = _sig("mpl_batch_get_phase_cycles", _i, [_h, _p, _i])
-_split_gemm = _sig("mpl_step_split_gemm", _i, [_i, _i64, _i64, _i64, _p, _i64, _p, _i64, _p, _i64, _p])
+_split_gemm = _sig("mpl_step_split_gemm", _i, [_i, _i, _i64, _i64, _i64, _p, _i64, _p, _i64, _p, _i64, _p])
 _lowp_syrk = _sig("mpl_step_lowp_syrk", _i, [_i, _i, _i64, _i64, _p, _i64, _p, _i64, _i, _p])
 _stats = _sig("mpl_get_stats", _i, [_h, C.POINTER(Stats)])
 _last_error = _sig("mpl_last_error", C.c_char_p, [_h])
@@ -495,13 +495,16 @@ def lowp_syrk(fmt, A, C, round_out=False, stream=None):
         raise MplError(st, "mpl_step_lowp_syrk failed", 0)
 
 
-def split_gemm(A, B, C, stream=None):
-    """mpl_step_split_gemm: C = A B, FP64-accurate, on the bf16 tensor cores.
-    Column-major device tensors given as row-major (k, n) / (m, k) / (m, n)
-    arrays, float64 or complex128."""
-    k, n = A.shape
+def split_gemm(A, B, C, trans_a=False, stream=None):
+    """mpl_step_split_gemm: C = op(A) B, FP64-accurate, on the bf16 tensor
+    cores.  Column-major device tensors given as row-major arrays: A (k, n),
+    or (n, k) holding the k x n storage whose (conjugate) transpose is used
+    when trans_a; B (m, k); C (m, n); float64 or complex128."""
     m = B.shape[0]
+    n = C.shape[1]
+    k = B.shape[1]
     cx = 1 if A.is_complex() else 0
-    st = _split_gemm(cx, n, k, m, _ptr(A), n, _ptr(B), k, _ptr(C), n, _stream_ptr(stream))
+    lda = k if trans_a else n
+    st = _split_gemm(cx, 1 if trans_a else 0, n, k, m, _ptr(A), lda, _ptr(B), k, _ptr(C), n, _stream_ptr(stream))
     if st != 0:
         raise MplError(st, "mpl_step_split_gemm failed", 0)

@@ -79,11 +79,18 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 }
 
 // value of the real operand selected by mode from real (mode 0) or
-// interleaved complex storage: 1 re, 2 im, 3 re + im (the 3M sum, in FP64)
+// interleaved complex storage: 1 re, 2 im, 3 re + im (the 3M sum, in FP64);
+// of the conjugate: 4 -im, 5 re - im
 __device__ __forceinline__ double pick(const double* A, long long idx, int mode) {
   if (mode == 0) return A[idx];
   const double re = A[2 * idx], im = A[2 * idx + 1];
-  return mode == 1 ? re : mode == 2 ? im : re + im;
+  switch (mode) {
+    case 1: return re;
+    case 2: return im;
+    case 3: return re + im;
+    case 4: return -im;
+    default: return re - im;
+  }
 }
 
 __device__ __forceinline__ int exp_of(double amax) {
@@ -158,6 +165,24 @@ __global__ void split_rows_kernel(int n, int k, const double* __restrict__ A, lo
        id += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(id % rows), kk = (int)(id / rows);
     const double x = (r < n && kk < k) ? pick(A, r + (long long)kk * lda, mode) : 0.0;
+    uint16_t d[OZ_S];
+    digits(x, r < n ? e[r] : 0, d);
+    const int t = r / OZ_BM, c = kk / OZ_BK;
+    const int off = core_off64(r % OZ_BM, kk % OZ_BK);
+#pragma unroll
+    for (int i = 0; i < OZ_S; ++i) Q[(((long long)i * ntile + t) * nchunk + c) * OZ_TILE_A + off] = d[i];
+  }
+}
+
+// The same row slices of op(A) = A^T (A^H through the conjugate modes) from
+// storage k x n (ld lda): depth runs along the stored columns (coalesced).
+__global__ void split_rows_t_kernel(int n, int k, const double* __restrict__ A, long long lda, int mode,
+                                    const int* __restrict__ e, int ntile, int nchunk, uint16_t* __restrict__ Q) {
+  const long long kpad = (long long)nchunk * OZ_BK, tot = (long long)ntile * OZ_BM * kpad;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int kk = (int)(id % kpad), r = (int)(id / kpad);
+    const double x = (r < n && kk < k) ? pick(A, kk + (long long)r * lda, mode) : 0.0;
     uint16_t d[OZ_S];
     digits(x, r < n ? e[r] : 0, d);
     const int t = r / OZ_BM, c = kk / OZ_BK;
@@ -394,8 +419,17 @@ size_t oz_b_elems(int k, int npad) {
 }
 int oz_npad(int m) { return m <= 32 ? 32 : m <= 64 ? 64 : 96; }
 
-void oz_split_a(cudaStream_t st, int mode, int n, int k, const double* A, long long lda, int* e, uint16_t* Q) {
+void oz_split_a(cudaStream_t st, int mode, int n, int k, const double* A, long long lda, int* e, uint16_t* Q,
+                bool trans) {
   const int ntile = (n + OZ_BM - 1) / OZ_BM, nchunk = (k + OZ_BK - 1) / OZ_BK;
+  if (trans) {
+    // row r of op(A) is stored column r: one block per row reduces its exponent
+    count_launch(2);
+    col_exp_kernel<<<n, 256, 0, st>>>(k, A, lda, mode, e);
+    const long long tot = (long long)ntile * OZ_BM * nchunk * OZ_BK;
+    split_rows_t_kernel<<<grid_for(tot), 256, 0, st>>>(n, k, A, lda, mode, e, ntile, nchunk, Q);
+    return;
+  }
   count_launch(3);
   fill_int_kernel<<<grid_for(n), 256, 0, st>>>(n, e, INT_MIN);
   row_exp_kernel<<<dim3((n + 255) / 256, (k + 255) / 256), 256, 0, st>>>(n, k, A, lda, mode, e);
@@ -464,10 +498,10 @@ long long oz_t_rows(int n) { return (long long)((n + OZ_BM - 1) / OZ_BM) * OZ_BM
 
 #include "mplobpcg_steps.h"
 
-extern "C" mpl_status mpl_step_split_gemm(int is_complex, int64_t n, int64_t k, int64_t m, const void* A,
-                                          int64_t lda, const void* B, int64_t ldb, void* C, int64_t ldc,
-                                          void* stream) {
-  if (n < 1 || k < 1 || m < 1 || m > 96 || !A || !B || !C || lda < n || ldb < k || ldc < n ||
+extern "C" mpl_status mpl_step_split_gemm(int is_complex, int trans_a, int64_t n, int64_t k, int64_t m,
+                                          const void* A, int64_t lda, const void* B, int64_t ldb, void* C,
+                                          int64_t ldc, void* stream) {
+  if (n < 1 || k < 1 || m < 1 || m > 96 || !A || !B || !C || lda < (trans_a ? k : n) || ldb < k || ldc < n ||
       n > (1LL << 30) || k > (1LL << 21) || mpl::oz_shift(k) < 24)
     return MPL_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -500,7 +534,9 @@ extern "C" mpl_status mpl_step_split_gemm(int is_complex, int64_t n, int64_t k, 
     cudaMemsetAsync(T, 0, sizeof(long long) * np * tt, st);
     for (int p = 0; p < np; ++p) {
       const int mode = is_complex ? p + 1 : 0;  // 3M: re, im, re + im
-      mpl::oz_split_a(st, mode, (int)n, (int)k, a, lda, e + p * n, Q + p * qa);
+      // op(A) = A^H: re, -im, re - im of the stored matrix
+      const int amode = (is_complex && trans_a) ? (p == 0 ? 1 : p == 1 ? 4 : 5) : mode;
+      mpl::oz_split_a(st, amode, (int)n, (int)k, a, lda, e + p * n, Q + p * qa, trans_a != 0);
       mpl::oz_split_b(st, mode, (int)k, (int)m, b, ldb, f + p * m, P + p * pb);
     }
     for (int p = 0; p < np; ++p)

@@ -19,8 +19,11 @@ size_t oz_a_elems(int n, int k);       // bf16 elements of the row slices of an 
 size_t oz_b_elems(int k, int npad);    // bf16 elements of the column slices of a k x m operand
 long long oz_t_rows(int n);            // rows (= leading dimension) of the int64 accumulator
 
-// mode: 0 real FP64 storage; complex interleaved storage: 1 re, 2 im, 3 re + im
-void oz_split_a(cudaStream_t st, int mode, int n, int k, const double* A, long long lda, int* e, uint16_t* Q);
+// mode: 0 real FP64 storage; complex interleaved storage: 1 re, 2 im, 3 re + im,
+// and of the conjugate 4 -im, 5 re - im.  trans: A is stored k x n and
+// op(A) = its transpose (with the conjugate modes: A^H).
+void oz_split_a(cudaStream_t st, int mode, int n, int k, const double* A, long long lda, int* e, uint16_t* Q,
+                bool trans = false);
 void oz_split_b(cudaStream_t st, int mode, int k, int m, const double* B, long long ldb, int* f, uint16_t* P);
 // T (oz_t_rows(n) x oz_npad(m) int64, zeroed) += the fixed-point product
 void oz_mma(cudaStream_t st, int n, int k, int m, const uint16_t* Q, const uint16_t* P, long long* T, int* err);

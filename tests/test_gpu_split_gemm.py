@@ -64,3 +64,26 @@ def test_split_gemm_rejects_bad_sizes():
     B = torch.zeros((97, 8), dtype=torch.float64, device="cuda:0")
     with pytest.raises(M.MplError):
         M.split_gemm(A, B, C)                 # m = 97 > 96
+
+
+@pytest.mark.skipif(__import__("os").environ.get("MPL_TEST_SPLIT_TRANS") != "1",
+                    reason="conjugate-transposed left operand: opt-in until its first GPU run")
+@pytest.mark.parametrize("cx", [False, True])
+@pytest.mark.parametrize("n,k,m", [(288, 1000, 96), (40, 700, 20)])
+def test_split_gemm_transposed_left_operand(cx, n, k, m):
+    """Gram-type products S^H (A S): op(A) = A^H from k x n storage."""
+    rng = np.random.default_rng(11 * n + k)
+    S = rng.standard_normal((k, n)) * np.logspace(-3, 3, n)[None, :]
+    B = rng.standard_normal((k, m))
+    if cx:
+        S = S + 1j * rng.standard_normal((k, n))
+        B = B + 1j * rng.standard_normal((k, m))
+    Sd = torch_dev(np.ascontiguousarray(S.T))          # column-major k x n storage
+    Bd = torch_dev(np.ascontiguousarray(B.T))
+    Cd = torch.zeros((m, n), dtype=Sd.dtype, device="cuda:0")
+    M.split_gemm(Sd, Bd, Cd, trans_a=True)
+    torch.cuda.synchronize()
+    C = Cd.cpu().numpy().T
+    ref = S.conj().T @ B
+    err = np.abs(C - ref) / (np.abs(S).T @ np.abs(B))
+    assert err.max() <= 1e-14, err.max()

@@ -152,10 +152,11 @@ def test_step_entries_validate_arguments_before_any_device_work():
     call is made, so this runs without a GPU)."""
     M = _lib()
     b = M.binding
-    # mpl_step_split_gemm(is_complex, n, k, m, A, lda, B, ldb, C, ldc, stream)
+    # mpl_step_split_gemm(is_complex, trans_a, n, k, m, A, lda, B, ldb, C, ldc, stream)
     dummy = 1 << 20  # never dereferenced: validation fails first
-    for n, k, m, lda in ((0, 8, 8, 8), (8, 8, 97, 8), (8, 8, 8, 4), (8, (1 << 21) + 1, 8, 8)):
-        assert b._split_gemm(0, n, k, m, dummy, lda, dummy, max(k, 1), dummy, max(n, 1), None) == 1
+    for tr, n, k, m, lda in ((0, 0, 8, 8, 8), (0, 8, 8, 97, 8), (0, 8, 8, 8, 4), (0, 8, (1 << 21) + 1, 8, 8),
+                             (1, 8, 16, 8, 8)):   # transposed storage needs lda >= k
+        assert b._split_gemm(0, tr, n, k, m, dummy, lda, dummy, max(k, 1), dummy, max(n, 1), None) == 1
     # mpl_step_lowp_syrk(fmt, is_complex, n, k, A, lda, C, ldc, round_out, stream)
     for fmt, cx, k in ((3, 0, 8), (1, 0, 0), (1, 0, 129), (2, 1, 65)):
         assert b._lowp_syrk(fmt, cx, 16, k, dummy, 16, dummy, 16, 0, None) == 1
