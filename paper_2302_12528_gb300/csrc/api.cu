@@ -60,9 +60,10 @@ struct SplitAX {
                err.as<int>());
       double* y = Y + (size_t)elt * c0 * ldy;
       if (cx)
-        oz_combine_3m(st, n, mc, T.as<long long>(), trows, (long long)tt, e.as<int>(), n, f.as<int>(), 96, S, y, ldy);
+        oz_combine_3m(st, n, mc, T.as<long long>(), trows, (long long)tt, e.as<int>(), n, f.as<int>(), 96, S, y, ldy,
+                      1.0, 0.0, false, 0);
       else
-        oz_combine_real(st, n, mc, T.as<long long>(), trows, e.as<int>(), f.as<int>(), S, y, ldy);
+        oz_combine_real(st, n, mc, T.as<long long>(), trows, e.as<int>(), f.as<int>(), S, y, ldy, 1.0, 0.0, false, 0);
     }
     check_launch("split A X");
     int h = 0;
@@ -1001,7 +1002,11 @@ extern "C" mpl_status mpl_solve(mpl_handle h, const void* X0, int x0_is_device, 
                                 int* iters) {
   if (!h || !X0 || maxit < 0 || (resid_hist && hist_cap < 0)) return MPL_EINVAL;
   mpl_status s = guarded(h, [&]() {
-    return h->eng->solve(X0, x0_is_device, maxit, lambda, X, x_is_device, resid_hist, hist_cap, hist_len, iters);
+    const mpl_status r =
+        h->eng->solve(X0, x0_is_device, maxit, lambda, X, x_is_device, resid_hist, hist_cap, hist_len, iters);
+    if (mpl::oz_gemm_requested() && mpl::oz_take_error(h->stream))
+      throw mpl::MplError{MPL_ECUDA, "split FP64 product: a completion wait gave up", 0};
+    return r;
   });
   if (s == MPL_ENOT_CONVERGED) h->err = "maximum number of iterations reached";
   return s;

@@ -10,6 +10,7 @@
 #include <type_traits>
 
 #include "blas.cuh"
+#include "oz_gemm.cuh"
 
 namespace mpl {
 
@@ -242,6 +243,14 @@ void gemm(cudaStream_t st, bool opA, bool opB, int M, int N, int K, real_t<T> al
           long long ldc, bool lower_only, Scratch scr) {
   using Cfg = GemmCfg<T>;
   if (M <= 0 || N <= 0) return;
+  if constexpr (sizeof(real_t<T>) == 8) {
+    // opt-in: large FP64 products on the tensor cores by error-free splitting
+    if (oz_gemm_requested() && (long long)M * N * K >= (1LL << 28) &&
+        oz_gemm_fp64(st, tr<T>::cx, opA, opB, M, N, K, (double)alpha, reinterpret_cast<const double*>(A), lda,
+                     reinterpret_cast<const double*>(B), ldb, (double)beta, reinterpret_cast<double*>(C), ldc,
+                     lower_only))
+      return;
+  }
   const int gx = ceil_div(M, Cfg::BM), gy = ceil_div(N, Cfg::BN);
   int tiles = gx * gy;
   if (lower_only) tiles = (tiles + gx) / 2;

@@ -36,6 +36,9 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <cstdlib>
+#include <map>
+#include <mutex>
 
 #include "common.cuh"
 #include "oz_gemm.cuh"
@@ -210,6 +213,24 @@ __global__ void split_cols_kernel(int k, int m, const double* __restrict__ B, lo
   }
 }
 
+// The same column slices of op(B) = B^T (B^H through the conjugate modes)
+// from storage m x k (ld ldb).
+__global__ void split_cols_t_kernel(int k, int m, const double* __restrict__ B, long long ldb, int mode,
+                                    const int* __restrict__ f, int nchunk, int npad, uint16_t* __restrict__ P) {
+  const long long tot = (long long)npad * nchunk * OZ_BK;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(id % npad), kk = (int)(id / npad);
+    const double x = (c < m && kk < k) ? pick(B, c + (long long)kk * ldb, mode) : 0.0;
+    uint16_t d[OZ_S];
+    digits(x, c < m ? f[c] : 0, d);
+    const int ch = kk / OZ_BK;
+    const int off = core_off64(c, kk % OZ_BK);
+#pragma unroll
+    for (int j = 0; j < OZ_S; ++j) P[((long long)j * nchunk + ch) * npad * OZ_BK + off] = d[j];
+  }
+}
+
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   uint32_t done = 0;
   for (long long it = 0; it < OZ_WAIT_LIMIT && !done; ++it) {
@@ -370,29 +391,39 @@ oz_mma_kernel(int ntile, int nchunk, int chunks_per_split, const uint16_t* __res
 // C(r, c) = 2^(e_r + f_c - 16 - S) T(r, c)   (real), or the 3M combination
 // of three such products (complex): Re = T1 - T2, Im = T3 - T1 - T2.
 __global__ void combine_real_kernel(int n, int m, const long long* __restrict__ T, long long ldt,
-                                    const int* __restrict__ e, const int* __restrict__ f, int S,
-                                    double* __restrict__ C, long long ldc) {
+                                    const int* __restrict__ e, const int* __restrict__ f, int S, double alpha,
+                                    double beta, int lower_only, int col0, double* __restrict__ C, long long ldc) {
   const long long tot = (long long)n * m;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot;
        id += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(id % n), c = (int)(id / n);
-    C[r + c * ldc] = ldexp((double)T[r + c * ldt], e[r] + f[c] - 16 - S);
+    if (lower_only && r < col0 + c) continue;
+    double v = alpha * ldexp((double)T[r + c * ldt], e[r] + f[c] - 16 - S);
+    if (beta != 0.0) v += beta * C[r + c * ldc];
+    C[r + c * ldc] = v;
   }
 }
 
 __global__ void combine_3m_kernel(int n, int m, const long long* __restrict__ T, long long ldt, long long tstride,
                                   const int* __restrict__ e, int estride, const int* __restrict__ f, int fstride,
-                                  int S, double* __restrict__ C, long long ldc) {
+                                  int S, double alpha, double beta, int lower_only, int col0, double* __restrict__ C,
+                                  long long ldc) {
   const long long tot = (long long)n * m;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot;
        id += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(id % n), c = (int)(id / n);
+    if (lower_only && r < col0 + c) continue;
     double p[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q)
       p[q] = ldexp((double)T[q * tstride + r + c * ldt], e[q * estride + r] + f[q * fstride + c] - 16 - S);
-    C[2 * (r + c * ldc)] = p[0] - p[1];
-    C[2 * (r + c * ldc) + 1] = p[2] - p[0] - p[1];
+    double re = alpha * (p[0] - p[1]), im = alpha * (p[2] - p[0] - p[1]);
+    if (beta != 0.0) {
+      re += beta * C[2 * (r + c * ldc)];
+      im += beta * C[2 * (r + c * ldc) + 1];
+    }
+    C[2 * (r + c * ldc)] = re;
+    C[2 * (r + c * ldc) + 1] = im;
   }
 }
 
@@ -439,8 +470,19 @@ void oz_split_a(cudaStream_t st, int mode, int n, int k, const double* A, long l
   split_rows_kernel<<<grid_for(tot), 256, 0, st>>>(n, k, A, lda, mode, e, ntile, nchunk, Q);
 }
 
-void oz_split_b(cudaStream_t st, int mode, int k, int m, const double* B, long long ldb, int* f, uint16_t* P) {
+void oz_split_b(cudaStream_t st, int mode, int k, int m, const double* B, long long ldb, int* f, uint16_t* P,
+                bool trans) {
   const int npad = oz_npad(m), nchunk = (k + OZ_BK - 1) / OZ_BK;
+  if (trans) {
+    // column c of op(B) is stored row c: row maxima by atomics
+    count_launch(4);
+    fill_int_kernel<<<grid_for(m), 256, 0, st>>>(m, f, INT_MIN);
+    row_exp_kernel<<<dim3((m + 255) / 256, (k + 255) / 256), 256, 0, st>>>(m, k, B, ldb, mode, f);
+    clamp_exp_kernel<<<grid_for(m), 256, 0, st>>>(m, f);
+    const long long tot = (long long)npad * nchunk * OZ_BK;
+    split_cols_t_kernel<<<grid_for(tot), 256, 0, st>>>(k, m, B, ldb, mode, f, nchunk, npad, P);
+    return;
+  }
   count_launch(2);
   col_exp_kernel<<<m, 256, 0, st>>>(k, B, ldb, mode, f);
   const long long tot = (long long)npad * nchunk * OZ_BK;
@@ -477,19 +519,116 @@ void oz_mma(cudaStream_t st, int n, int k, int m, const uint16_t* Q, const uint1
 }
 
 void oz_combine_real(cudaStream_t st, int n, int m, const long long* T, long long ldt, const int* e, const int* f,
-                     int S, double* C, long long ldc) {
+                     int S, double* C, long long ldc, double alpha, double beta, bool lower_only, int col0) {
   count_launch();
-  combine_real_kernel<<<grid_for((long long)n * m), 256, 0, st>>>(n, m, T, ldt, e, f, S, C, ldc);
+  combine_real_kernel<<<grid_for((long long)n * m), 256, 0, st>>>(n, m, T, ldt, e, f, S, alpha, beta,
+                                                                   lower_only ? 1 : 0, col0, C, ldc);
 }
 
 void oz_combine_3m(cudaStream_t st, int n, int m, const long long* T, long long ldt, long long tstride, const int* e,
-                   int estride, const int* f, int fstride, int S, double* C, long long ldc) {
+                   int estride, const int* f, int fstride, int S, double* C, long long ldc, double alpha, double beta,
+                   bool lower_only, int col0) {
   count_launch();
   combine_3m_kernel<<<grid_for((long long)n * m), 256, 0, st>>>(n, m, T, ldt, tstride, e, estride, f, fstride, S,
-                                                                 C, ldc);
+                                                                 alpha, beta, lower_only ? 1 : 0, col0, C, ldc);
 }
 
 long long oz_t_rows(int n) { return (long long)((n + OZ_BM - 1) / OZ_BM) * OZ_BM; }
+
+}  // namespace mpl
+
+// ---- C = alpha op(A) op(B) + beta C through the split product -------------
+namespace mpl {
+namespace {
+struct OzPool {
+  void* p[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // e, f, Q, P, T
+  size_t bytes[5] = {0, 0, 0, 0, 0};
+  int* err = nullptr;
+  bool grow(int i, size_t b) {
+    if (b <= bytes[i]) return true;
+    if (p[i]) cudaFree(p[i]);
+    p[i] = nullptr;
+    bytes[i] = 0;
+    if (cudaMalloc(&p[i], b) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    bytes[i] = b;
+    return true;
+  }
+};
+std::mutex& pool_mutex() {
+  static std::mutex m;
+  return m;
+}
+std::map<cudaStream_t, OzPool>& pools() {
+  static std::map<cudaStream_t, OzPool> p;
+  return p;
+}
+}  // namespace
+
+bool oz_gemm_requested() {
+  static const bool on = [] {
+    const char* v = std::getenv("MPL_GEMM_SPLIT");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
+
+bool oz_gemm_fp64(cudaStream_t st, bool cx, bool ta, bool tb, int M, int N, int K, double alpha, const double* A,
+                  long long lda, const double* B, long long ldb, double beta, double* C, long long ldc,
+                  bool lower_only) {
+  if (M < 1 || N < 1 || K < 1 || K > (1 << 21) || oz_shift(K) < 24 || !(beta == 0.0 || beta == 1.0)) return false;
+  std::lock_guard<std::mutex> lock(pool_mutex());
+  OzPool& P = pools()[st];
+  const int np = cx ? 3 : 1, elt = cx ? 2 : 1;
+  const size_t qa = oz_a_elems(M, K), pb = oz_b_elems(K, 96);
+  const long long trows = oz_t_rows(M);
+  const size_t tt = (size_t)trows * 96;
+  if (!P.err) {
+    if (cudaMalloc(&P.err, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      P.err = nullptr;
+      return false;
+    }
+    cudaMemsetAsync(P.err, 0, sizeof(int), st);
+  }
+  if (!P.grow(0, sizeof(int) * np * M) || !P.grow(1, sizeof(int) * np * 96) || !P.grow(2, 2 * np * qa) ||
+      !P.grow(3, 2 * np * pb) || !P.grow(4, sizeof(long long) * np * tt))
+    return false;
+  int* e = static_cast<int*>(P.p[0]);
+  int* f = static_cast<int*>(P.p[1]);
+  uint16_t* Q = static_cast<uint16_t*>(P.p[2]);
+  uint16_t* Pb = static_cast<uint16_t*>(P.p[3]);
+  long long* T = static_cast<long long*>(P.p[4]);
+  // 3M operands: re, im, re + im; of a conjugate transpose: re, -im, re - im
+  auto mode_of = [&](int p, bool t) { return !cx ? 0 : !t ? p + 1 : (p == 0 ? 1 : p == 1 ? 4 : 5); };
+  for (int p = 0; p < np; ++p) oz_split_a(st, mode_of(p, ta), M, K, A, lda, e + p * M, Q + p * qa, ta);
+  const int S = oz_shift(K);
+  for (int c0 = 0; c0 < N; c0 += 96) {
+    const int nb = std::min(96, N - c0);
+    // columns c0.. of op(B): stored columns (no transpose) or stored rows
+    const double* Bc = B + (size_t)elt * (tb ? (size_t)c0 : (size_t)c0 * ldb);
+    cudaMemsetAsync(T, 0, sizeof(long long) * np * tt, st);
+    for (int p = 0; p < np; ++p) oz_split_b(st, mode_of(p, tb), K, nb, Bc, ldb, f + p * 96, Pb + p * pb, tb);
+    for (int p = 0; p < np; ++p) oz_mma(st, M, K, nb, Q + p * qa, Pb + p * pb, T + p * tt, P.err);
+    double* Cc = C + (size_t)elt * c0 * ldc;
+    if (cx) oz_combine_3m(st, M, nb, T, trows, (long long)tt, e, M, f, 96, S, Cc, ldc, alpha, beta, lower_only, c0);
+    else oz_combine_real(st, M, nb, T, trows, e, f, S, Cc, ldc, alpha, beta, lower_only, c0);
+  }
+  return true;
+}
+
+int oz_take_error(cudaStream_t st) {
+  std::lock_guard<std::mutex> lock(pool_mutex());
+  auto it = pools().find(st);
+  if (it == pools().end() || !it->second.err) return 0;
+  int h = 0;
+  cudaMemcpyAsync(&h, it->second.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  if (h) cudaMemsetAsync(it->second.err, 0, sizeof(int), st);
+  return h;
+}
 
 }  // namespace mpl
 
@@ -544,9 +683,9 @@ extern "C" mpl_status mpl_step_split_gemm(int is_complex, int trans_a, int64_t n
     const int S = mpl::oz_shift(k);
     if (is_complex)
       mpl::oz_combine_3m(st, (int)n, (int)m, T, trows, (long long)tt, e, (int)n, f, (int)m, S,
-                         static_cast<double*>(C), ldc);
+                         static_cast<double*>(C), ldc, 1.0, 0.0, false, 0);
     else
-      mpl::oz_combine_real(st, (int)n, (int)m, T, trows, e, f, S, static_cast<double*>(C), ldc);
+      mpl::oz_combine_real(st, (int)n, (int)m, T, trows, e, f, S, static_cast<double*>(C), ldc, 1.0, 0.0, false, 0);
     if (cudaGetLastError() != cudaSuccess) s = MPL_ECUDA;
     if (s == MPL_OK && (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                         cudaStreamSynchronize(st) != cudaSuccess))

@@ -24,12 +24,29 @@ long long oz_t_rows(int n);            // rows (= leading dimension) of the int6
 // op(A) = its transpose (with the conjugate modes: A^H).
 void oz_split_a(cudaStream_t st, int mode, int n, int k, const double* A, long long lda, int* e, uint16_t* Q,
                 bool trans = false);
-void oz_split_b(cudaStream_t st, int mode, int k, int m, const double* B, long long ldb, int* f, uint16_t* P);
+// trans: B is stored m x k and op(B) = its transpose (conjugate modes: B^H)
+void oz_split_b(cudaStream_t st, int mode, int k, int m, const double* B, long long ldb, int* f, uint16_t* P,
+                bool trans = false);
 // T (oz_t_rows(n) x oz_npad(m) int64, zeroed) += the fixed-point product
 void oz_mma(cudaStream_t st, int n, int k, int m, const uint16_t* Q, const uint16_t* P, long long* T, int* err);
+// C = alpha (the product) + beta C (beta 0: C not read); lower_only skips
+// rows above the diagonal (col0: the first column's index in C)
 void oz_combine_real(cudaStream_t st, int n, int m, const long long* T, long long ldt, const int* e, const int* f,
-                     int S, double* C, long long ldc);
+                     int S, double* C, long long ldc, double alpha, double beta, bool lower_only, int col0);
 void oz_combine_3m(cudaStream_t st, int n, int m, const long long* T, long long ldt, long long tstride, const int* e,
-                   int estride, const int* f, int fstride, int S, double* C, long long ldc);
+                   int estride, const int* f, int fstride, int S, double* C, long long ldc, double alpha, double beta,
+                   bool lower_only, int col0);
+
+// C = alpha op(A) op(B) + beta C in FP64 (complex interleaved when cx; op =
+// conjugate transpose when ta / tb) through the split product, with a
+// per-stream workspace; false when the shape or beta is not supported (the
+// caller computes it otherwise).  Opt-in: oz_gemm_requested() reads
+// MPL_GEMM_SPLIT=1.  oz_take_error() returns and clears the stream's
+// completion-wait error flag (synchronising).
+bool oz_gemm_requested();
+bool oz_gemm_fp64(cudaStream_t st, bool cx, bool ta, bool tb, int M, int N, int K, double alpha, const double* A,
+                  long long lda, const double* B, long long ldb, double beta, double* C, long long ldc,
+                  bool lower_only);
+int oz_take_error(cudaStream_t st);
 
 }  // namespace mpl
