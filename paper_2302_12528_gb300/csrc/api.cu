@@ -20,7 +20,7 @@ void spmm_csr(cudaStream_t st, int n, int m, const long long* rowptr, const int*
 // ---- operators ---------------------------------------------------------
 // Working-precision A X by error-free splitting on the bf16 tensor cores
 // (oz_gemm.cu): A's row slices are made once, X's column slices per product
-// (blocks of <= 96 columns).  Opt-in with MPL_AX_SPLIT=1.
+// (blocks of <= 96 columns).  Opt-in with MPL_AX_SPLIT=1 (or MPL_GEMM_SPLIT=1).
 struct SplitAX {
   bool cx = false;
   int n = 0, np = 1;
@@ -73,10 +73,12 @@ struct SplitAX {
   }
 };
 
+// MPL_GEMM_SPLIT=1 (every large FP64 product split) implies it: A's slices
+// are made once instead of at every product.
 inline bool ax_split_requested() {
   static const bool on = [] {
     const char* v = std::getenv("MPL_AX_SPLIT");
-    return v && v[0] == '1';
+    return (v && v[0] == '1') || oz_gemm_requested();
   }();
   return on;
 }
