@@ -353,7 +353,7 @@ def main():
                                         "the pipe executes"}
         if cplx:
             out["roofline"]["complex_equivalent_gflops"] = achieved * 8.0 / 6.0
-        if os.environ.get("MPL_AX_SPLIT") == "1" and w.kind != "csr":
+        if "1" in (os.environ.get("MPL_AX_SPLIT"), os.environ.get("MPL_GEMM_SPLIT")) and w.kind != "csr":
             out["roofline"] = split_ax_roofline(w, per_launch_s, apply_calls)
     if ck:
         out["clocks"] = ck
