@@ -355,6 +355,8 @@ def main():
             out["roofline"]["complex_equivalent_gflops"] = achieved * 8.0 / 6.0
         if "1" in (os.environ.get("MPL_AX_SPLIT"), os.environ.get("MPL_GEMM_SPLIT")) and w.kind != "csr":
             out["roofline"] = split_ax_roofline(w, per_launch_s, apply_calls)
+            out["config"]["fp64_products"] = ("A X and products >= 2^28 FMAs" if os.environ.get("MPL_GEMM_SPLIT") == "1"
+                                              else "A X") + " by error-free bf16 splitting on the tensor cores"
     if ck:
         out["clocks"] = ck
     if unconv:
