@@ -1,0 +1,30 @@
+"""Host arithmetic of bench.py that needs no GPU: the roofline of the
+split-product A X (bf16 flops and slice bytes per product, the bound taken
+from the larger of the tensor and HBM times)."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+import workloads as W  # noqa: E402
+
+
+def test_split_roofline_counts_dense_complex():
+    w = W.WORKLOADS["dense_complex_n16384"]          # n = 16384, m = 96, complex: 3 products (3M)
+    r = bench.split_ax_roofline(w, 3e-3, 10)
+    n = 16384
+    assert r["bf16_flops_per_launch"] == 3 * 28 * 2.0 * n * 96 * n
+    assert r["slice_bytes_per_launch"] == 3 * 7 * n * n * 2.0
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert abs(r["achieved"] - r["bf16_flops_per_launch"] / 3e-3 / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+
+
+def test_split_roofline_pads_and_picks_hbm_for_narrow_blocks():
+    w = W.WORKLOADS["dense_real_n1000"]              # n = 1000 -> 1024 rows / depth, m = 20 -> 32 columns
+    r = bench.split_ax_roofline(w, 1e-4, 10)
+    assert r["bf16_flops_per_launch"] == 28 * 2.0 * 1024 * 32 * 1024
+    assert r["slice_bytes_per_launch"] == 7 * 1024 * 1024 * 2.0
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
