@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--workload", default="dense_complex_n16384", choices=sorted(W.WORKLOADS))
     ap.add_argument("--policy", default="mp", choices=["mp", "schol", "dchol", "hchol", "bchol"])
     ap.add_argument("--maxit", type=int, default=1000)
+    ap.add_argument("--ordering", default="grid", choices=["grid", "graph"],
+                    help="sparse workloads: grid nested dissection, or the level-structure ordering of the "
+                         "pattern (as for a CSR matrix given without grid dimensions)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -110,10 +113,11 @@ def dense_input(w, rank, device):
     return At
 
 
-def make_handle(M, w, d, policy, stream=None):
+def make_handle(M, w, d, policy, stream=None, grid=True):
     if w.kind == "csr":
+        # grid: the grid nested dissection; else the level-structure ordering of the pattern
         return M.create_csr(d["rowptr"], d["colind"], d["vals"], w.k, w.m, w.tol, policy,
-                            Omega=d["Omega_np"], grid_dims=w.dims, stream=stream)
+                            Omega=d["Omega_np"], grid_dims=w.dims if grid else None, stream=stream)
     return M.create_dense(d["A"], w.k, w.m, w.tol, policy, Omega=d["Omega"], stream=stream)
 
 
@@ -279,7 +283,7 @@ def main():
 
     if args.precision_study:
         return precision_study(args, w, M, d, X0, stream, torch)
-    h = make_handle(M, w, d, args.policy, stream)
+    h = make_handle(M, w, d, args.policy, stream, grid=args.ordering == "grid")
     if args.kernel_probe:
         return kernel_probe(args, w, h, X0, stream, torch)
     unconv = args.profile_iters > 0 or bool(args.n)
@@ -327,6 +331,7 @@ def main():
         "config": {"workload": w.name, "n": w.n, "k": w.k, "m": w.m, "tol": w.tol,
                    "policy": {"mp": "MPLOBPCG-schol", "schol": "DLOBPCG-schol", "dchol": "DLOBPCG-dchol"}[args.policy],
                    "kind": w.kind, "kappa": w.kappa if w.kind != "csr" else None,
+                   "ordering": (args.ordering if w.kind == "csr" else None),
                    "replicas": world, "l2": "inputs larger than L2 (A: %.2f GB)" % (
                        (w.n * w.n * (16 if w.kind == 'dense_complex' else 8) / 1e9) if w.kind != "csr" else 0.0)},
         "iterations": {"stage1": its[0], "stage2": its[1]},
@@ -363,7 +368,7 @@ def main():
         out["profile_run"] = (f"iterations capped at {args.profile_iters}" if args.profile_iters else
                               f"order overridden to n={w.n}") + "; not a bench value"
     if rank == 0 and not args.no_fp64 and args.policy != "dchol" and not unconv:
-        h2 = make_handle(M, w, d, "dchol", stream)
+        h2 = make_handle(M, w, d, "dchol", stream, grid=args.ordering == "grid")
         h2.factor()
         h2.solve(X0, maxit=args.maxit)        # warm-up (allocations)
         torch.cuda.synchronize()
@@ -744,7 +749,7 @@ def e2e(M, w, d, X0h, args, stream, torch):
     t0 = time.perf_counter()
     if w.kind == "csr":
         h = M.create_csr(d["rowptr"], d["colind"], d["vals"], w.k, w.m, w.tol, args.policy, Omega=Om_h.numpy(),
-                         grid_dims=w.dims, stream=stream)
+                         grid_dims=w.dims if args.ordering == "grid" else None, stream=stream)
     else:
         h = M.create_dense(A_h, w.k, w.m, w.tol, args.policy, Omega=Om_h, stream=stream)
     h.factor()

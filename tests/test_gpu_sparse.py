@@ -171,3 +171,26 @@ def test_sparse_full_size_64cubed_properties():
     # Rayleigh quotients from the explicit product agree with the returned values
     rq = np.einsum("ij,ij->j", X, A @ X)
     assert np.allclose(rq, lam, rtol=1e-12)
+
+
+@pytest.mark.skipif(__import__("os").environ.get("MPL_TEST_GRAPH_ORDER") != "1",
+                    reason="CSR without grid dimensions: opt-in until the graph partition's first GPU run")
+@pytest.mark.parametrize("dims,k,m", [((12, 10, 9), 6, 12), ((40, 30), 5, 10)])
+def test_csr_without_grid_dims_uses_graph_ordering(dims, k, m):
+    """The level-structure nested dissection (no grid dimensions) drives the
+    same multifrontal factor and solve: eigenpairs equal LAPACK's."""
+    rp, ci, v, _ = W.diffusion_csr(dims, 5, ell=3.0, sigma=1.0)
+    n = len(rp) - 1
+    Om = W.sketch(n, 8, seed=7)
+    h = M.create_csr(rp, ci, v, k, m, tol=1e-12, policy="mp", Omega=Om, grid_dims=None)
+    assert np.array_equal(h.permutation(), S.nd_graph_order(rp, ci))
+    h.factor()
+    Xo = torch.empty((k, n), dtype=torch.float64, device="cuda:0")
+    lam, _, _, its, _ = h.solve(torch_dev(W.start_block(n, m, seed=8)), maxit=2000, X_out=Xo)
+    h.close()
+    A = SP.csr_to_scipy(rp, ci, v).toarray()
+    ev = np.linalg.eigvalsh(A)
+    X = to_np(Xo).T
+    rn = np.linalg.norm(A @ X - X * lam[None, :], axis=0)
+    assert np.all(rn <= 1e-12 * (ev[-1] + np.abs(lam)) * np.linalg.norm(X, axis=0))
+    assert np.allclose(lam, ev[:k], rtol=1e-10)
