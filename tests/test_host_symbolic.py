@@ -88,12 +88,45 @@ def _graph_inputs():
     yield rp, np.array([c for r in rows for c in sorted(r)], dtype=np.int32)
 
 
-@pytest.mark.parametrize("case", list(range(7)))
+def _rows_to_csr(rows):
+    rows = [sorted(set(r)) for r in rows]
+    rp = np.cumsum([0] + [len(r) for r in rows]).astype(np.int64)
+    return rp, np.array([c for r in rows for c in r], dtype=np.int32)
+
+
+def _adversarial_inputs():
+    # star: centre 0 joined to 199 leaves (eccentricity 1 from the centre)
+    rows = [[i] for i in range(200)]
+    for i in range(1, 200):
+        rows[0].append(i)
+        rows[i].append(0)
+    yield _rows_to_csr(rows)
+    # complete graph on 70 vertices (> leaf, fewer than three BFS levels)
+    yield _rows_to_csr([list(range(70)) for _ in range(70)])
+    # path of 1000 vertices
+    yield _rows_to_csr([[j for j in (i - 1, i, i + 1) if 0 <= j < 1000] for i in range(1000)])
+    # 40 x 30 grid with 15 % of the vertices removed (irregular pieces)
+    rng = np.random.default_rng(5)
+    keep = rng.random(1200) > 0.15
+    idx = -np.ones(1200, dtype=np.int64)
+    idx[keep] = np.arange(keep.sum())
+    rows = [[int(idx[v])] for v in range(1200) if keep[v]]
+    for v in range(1200):
+        if not keep[v]:
+            continue
+        x, y = v % 40, v // 40
+        for u in ((v - 1) if x > 0 else -1, (v + 1) if x < 39 else -1, v - 40, v + 40):
+            if 0 <= u < 1200 and keep[u]:
+                rows[idx[v]].append(int(idx[u]))
+    yield _rows_to_csr(rows)
+
+
+@pytest.mark.parametrize("case", list(range(11)))
 def test_graph_nd_symbolic_bit_exact(case):
     """Without grid dimensions: the level-structure nested dissection and
     everything after it equal the oracle's bit for bit."""
     M = _lib()
-    rp, ci = list(_graph_inputs())[case]
+    rp, ci = (list(_graph_inputs()) + list(_adversarial_inputs()))[case]
     perm, starts = S.nd_graph_order(rp, ci, return_blocks=True)
     prp, pci, _ = S.permute_csr(rp, ci, np.ones(len(ci)), perm)
     sym = S.Symbolic(prp, pci)
