@@ -28,10 +28,13 @@
 //   * supernode rows = its columns followed by struct(last column);
 //   * level of a supernode = 0 for leaves, 1 + max over its children.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <functional>
 #include <iterator>
+#include <memory>
 #include <numeric>
+#include <thread>
 
 #include "sparse.cuh"
 
@@ -88,92 +91,117 @@ std::vector<long long> nd_grid_order(const int* dims, int ndims, int leaf,
   return out;
 }
 
-std::vector<long long> nd_graph_order(long long n, const long long* rowptr, const int* colind, int leaf,
-                                      std::vector<long long>* blocks) {
-  std::vector<long long> out;
-  out.reserve(n);
-  if (blocks) blocks->clear();
-  std::vector<long long> owner(n, -1);  // id of the vertex set a vertex is in
-  std::vector<long long> seen(n, -1);   // BFS stamp
-  long long set_id = 0, bfs_id = 0;
-  auto emit = [&](std::vector<long long>& v) {
-    std::sort(v.begin(), v.end());
-    if (blocks) blocks->push_back((long long)out.size());
-    out.insert(out.end(), v.begin(), v.end());
-  };
-  // BFS inside set `id` from root: vertices by level in q, level starts in
-  // ls (strictly increasing; the last entry is |q|)
-  auto bfs = [&](long long id, long long root, std::vector<long long>& q, std::vector<long long>& ls) {
-    const long long st = bfs_id++;
-    q.clear();
-    ls.assign(1, 0);
-    q.push_back(root);
-    seen[root] = st;
-    long long head = 0;
-    while (head < (long long)q.size()) {
-      const long long end = (long long)q.size();
-      for (; head < end; ++head) {
-        const long long v = q[head];
-        for (long long k = rowptr[v]; k < rowptr[v + 1]; ++k) {
-          const long long u = colind[k];
-          if (u != v && owner[u] == id && seen[u] != st) {
-            seen[u] = st;
-            q.push_back(u);
-          }
+namespace {
+
+// Shared state of one level-structure dissection.  Vertex sets dissected at
+// the same time are disjoint; a set is identified by a unique id stored in
+// owner[] for its vertices (BFS visits are stamped the same way), so a task
+// only ever compares another task's entries with its own id: relaxed atomics.
+struct Gnd {
+  long long n = 0;
+  const long long* rowptr = nullptr;
+  const int* colind = nullptr;
+  int leaf = 0;
+  long long par_min = 0;                       // components at least this big may run on their own thread
+  std::unique_ptr<std::atomic<long long>[]> owner, seen;
+  std::atomic<long long> next_id{1};
+  std::atomic<int> threads_left{0};
+  long long own(long long v) const { return owner[v].load(std::memory_order_relaxed); }
+  void set_own(long long v, long long id) { owner[v].store(id, std::memory_order_relaxed); }
+};
+
+// The ordering of some connected vertex sets, in order: perm, and the sizes
+// of its blocks.
+struct GndPart {
+  std::vector<long long> perm;
+  std::vector<long long> bsize;
+};
+
+void gnd_run(Gnd& G, std::vector<std::vector<long long>> sets, GndPart& out);
+
+// connected components of set `id` among `verts` (ascending), by smallest vertex
+std::vector<std::vector<long long>> gnd_components(Gnd& G, long long id, const std::vector<long long>& verts) {
+  std::vector<std::vector<long long>> comps;
+  for (long long s0 : verts) {
+    if (G.own(s0) != id) continue;
+    const long long cid = G.next_id.fetch_add(1);
+    std::vector<long long> comp{s0};
+    G.set_own(s0, cid);
+    for (size_t h = 0; h < comp.size(); ++h) {
+      const long long v = comp[h];
+      for (long long k = G.rowptr[v]; k < G.rowptr[v + 1]; ++k) {
+        const long long u = G.colind[k];
+        if (G.own(u) == id) {
+          G.set_own(u, cid);
+          comp.push_back(u);
         }
       }
-      ls.push_back(end);
     }
-  };
-  std::vector<long long> q, ls, q2, ls2;
-  // connected components of set `id` among `verts` (ascending), by smallest vertex
-  auto components = [&](long long id, const std::vector<long long>& verts) {
-    std::vector<std::vector<long long>> comps;
-    for (long long s0 : verts) {
-      if (owner[s0] != id) continue;
-      const long long cid = ++set_id;
-      std::vector<long long> comp{s0};
-      owner[s0] = cid;
-      for (size_t h = 0; h < comp.size(); ++h) {
-        const long long v = comp[h];
-        for (long long k = rowptr[v]; k < rowptr[v + 1]; ++k) {
-          const long long u = colind[k];
-          if (owner[u] == id) {
-            owner[u] = cid;
-            comp.push_back(u);
-          }
-        }
-      }
-      comps.push_back(std::move(comp));
-    }
-    return comps;
-  };
-  // work stack: dissect a connected set, or emit a separator level
-  struct Task { bool emit_only; std::vector<long long> v; };
-  std::vector<Task> work;
-  {
-    std::vector<long long> all(n);
-    std::iota(all.begin(), all.end(), 0LL);
-    const long long id = ++set_id;
-    for (long long v = 0; v < n; ++v) owner[v] = id;
-    auto comps = components(id, all);
-    for (auto it = comps.rbegin(); it != comps.rend(); ++it) work.push_back({false, std::move(*it)});
+    comps.push_back(std::move(comp));
   }
+  return comps;
+}
+
+// Dissects the given connected sets, in order.  A component of at least
+// par_min vertices met on the way is left as a placeholder and dissected on
+// its own thread when the thread budget allows (else here, afterwards); its
+// output is the contiguous segment the sequential order would give it, so
+// the result does not depend on the threads.
+void gnd_run(Gnd& G, std::vector<std::vector<long long>> sets, GndPart& out) {
+  struct Task {
+    bool emit_only, top;
+    std::vector<long long> v;
+  };
+  std::vector<Task> work;
+  for (auto it = sets.rbegin(); it != sets.rend(); ++it) work.push_back({false, true, std::move(*it)});
+  // blocks in order; a negative size -1 - d stands for deferred set d
+  std::vector<long long> bsize, perm;
+  std::vector<std::vector<long long>> deferred;
+  std::vector<long long> q, ls, q2, ls2;
+  auto bfs = [&](long long id, long long root, std::vector<long long>& qq, std::vector<long long>& ll) {
+    const long long st = G.next_id.fetch_add(1);
+    qq.clear();
+    ll.assign(1, 0);
+    qq.push_back(root);
+    G.seen[root].store(st, std::memory_order_relaxed);
+    long long head = 0;
+    while (head < (long long)qq.size()) {
+      const long long end = (long long)qq.size();
+      for (; head < end; ++head) {
+        const long long v = qq[head];
+        for (long long k = G.rowptr[v]; k < G.rowptr[v + 1]; ++k) {
+          const long long u = G.colind[k];
+          if (u != v && G.own(u) == id && G.seen[u].load(std::memory_order_relaxed) != st) {
+            G.seen[u].store(st, std::memory_order_relaxed);
+            qq.push_back(u);
+          }
+        }
+      }
+      ll.push_back(end);  // level starts strictly increase; the last entry is |qq|
+    }
+  };
   while (!work.empty()) {
     Task t = std::move(work.back());
     work.pop_back();
     std::vector<long long>& S = t.v;
-    if (t.emit_only || (long long)S.size() <= leaf) {
-      emit(S);
+    if (t.emit_only || (long long)S.size() <= G.leaf) {
+      std::sort(S.begin(), S.end());
+      bsize.push_back((long long)S.size());
+      perm.insert(perm.end(), S.begin(), S.end());
+      continue;
+    }
+    if (!t.top && (long long)S.size() >= G.par_min) {
+      bsize.push_back(-1 - (long long)deferred.size());
+      deferred.push_back(std::move(S));
       continue;
     }
     std::sort(S.begin(), S.end());
-    const long long id = ++set_id;
-    for (long long v : S) owner[v] = id;
+    const long long id = G.next_id.fetch_add(1);
+    for (long long v : S) G.set_own(v, id);
     auto degree = [&](long long v) {
       long long d = 0;
-      for (long long k = rowptr[v]; k < rowptr[v + 1]; ++k)
-        if (colind[k] != v && owner[colind[k]] == id) ++d;
+      for (long long k = G.rowptr[v]; k < G.rowptr[v + 1]; ++k)
+        if (G.colind[k] != v && G.own(G.colind[k]) == id) ++d;
       return d;
     };
     // pseudo-peripheral root and its level structure (q, ls); a candidate's
@@ -195,18 +223,77 @@ std::vector<long long> nd_graph_order(long long n, const long long* rowptr, cons
     }
     const long long e = (long long)ls.size() - 2;  // levels 0..e
     if (e < 2) {
-      emit(S);
+      bsize.push_back((long long)S.size());
+      perm.insert(perm.end(), S.begin(), S.end());
       continue;
     }
     const long long j = (e + 1) / 2;
     std::vector<long long> sep(q.begin() + ls[j], q.begin() + ls[j + 1]);
-    for (long long v : sep) owner[v] = -1;
-    auto comps = components(id, S);
-    work.push_back({true, std::move(sep)});
-    for (auto it = comps.rbegin(); it != comps.rend(); ++it) work.push_back({false, std::move(*it)});
+    for (long long v : sep) G.set_own(v, -1);
+    auto comps = gnd_components(G, id, S);
+    work.push_back({true, false, std::move(sep)});
+    for (auto it = comps.rbegin(); it != comps.rend(); ++it) work.push_back({false, false, std::move(*it)});
   }
-  if (blocks) blocks->push_back((long long)out.size());
-  return out;
+  // the deferred components: own threads while the budget lasts, else here
+  std::vector<GndPart> sub(deferred.size());
+  std::vector<std::thread> pool;
+  for (size_t d = 0; d < deferred.size(); ++d) {
+    if (G.threads_left.fetch_sub(1) > 0) {
+      pool.emplace_back([&G, &sub, &deferred, d]() {
+        gnd_run(G, {std::move(deferred[d])}, sub[d]);
+        G.threads_left.fetch_add(1);
+      });
+    } else {
+      G.threads_left.fetch_add(1);
+      gnd_run(G, {std::move(deferred[d])}, sub[d]);
+    }
+  }
+  for (auto& th : pool) th.join();
+  // stitch
+  size_t pos = 0;
+  for (long long bs : bsize) {
+    if (bs >= 0) {
+      out.bsize.push_back(bs);
+      out.perm.insert(out.perm.end(), perm.begin() + pos, perm.begin() + pos + bs);
+      pos += (size_t)bs;
+    } else {
+      const GndPart& g = sub[(size_t)(-1 - bs)];
+      out.bsize.insert(out.bsize.end(), g.bsize.begin(), g.bsize.end());
+      out.perm.insert(out.perm.end(), g.perm.begin(), g.perm.end());
+    }
+  }
+}
+
+}  // namespace
+
+std::vector<long long> nd_graph_order(long long n, const long long* rowptr, const int* colind, int leaf,
+                                      std::vector<long long>* blocks) {
+  Gnd G;
+  G.n = n;
+  G.rowptr = rowptr;
+  G.colind = colind;
+  G.leaf = leaf;
+  G.owner.reset(new std::atomic<long long>[n > 0 ? n : 1]);
+  G.seen.reset(new std::atomic<long long>[n > 0 ? n : 1]);
+  for (long long v = 0; v < n; ++v) {
+    G.owner[v].store(-1, std::memory_order_relaxed);
+    G.seen[v].store(-1, std::memory_order_relaxed);
+  }
+  const int hw = std::max(1u, std::thread::hardware_concurrency());
+  G.threads_left.store(hw - 1);
+  G.par_min = std::max<long long>(4096, n / (4LL * hw));
+  // the connected components of the whole graph, by smallest vertex
+  std::vector<long long> all(n);
+  std::iota(all.begin(), all.end(), 0LL);
+  const long long id = G.next_id.fetch_add(1);
+  for (long long v = 0; v < n; ++v) G.set_own(v, id);
+  GndPart out;
+  gnd_run(G, gnd_components(G, id, all), out);
+  if (blocks) {
+    blocks->assign(1, 0);
+    for (long long bs : out.bsize) blocks->push_back(blocks->back() + bs);
+  }
+  return std::move(out.perm);
 }
 
 void analyze_csr(long long n, const long long* rowptr, const int* colind, const double* vals,

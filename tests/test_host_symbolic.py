@@ -193,3 +193,16 @@ def test_step_entries_validate_arguments_before_any_device_work():
     # mpl_step_lowp_syrk(fmt, is_complex, n, k, A, lda, C, ldc, round_out, stream)
     for fmt, cx, k in ((3, 0, 8), (1, 0, 0), (1, 0, 129), (2, 1, 65)):
         assert b._lowp_syrk(fmt, cx, 16, k, dummy, 16, dummy, 16, 0, None) == 1
+
+
+@pytest.mark.parametrize("dims", [(24, 24, 24), (150, 100)])
+def test_graph_nd_order_bit_exact_large(dims):
+    """Large enough that components are dissected on their own threads: the
+    ordering and its blocks still equal the oracle's sequential ones."""
+    M = _lib()
+    rp, ci, v = W.laplacian_csr(dims)
+    perm, starts = S.nd_graph_order(rp, ci, return_blocks=True)
+    h = M.analyze_host(rp, ci, None)
+    assert np.array_equal(h.permutation(), perm)
+    assert np.array_equal(h.blocks()["bk_start"], starts)
+    h.close()
