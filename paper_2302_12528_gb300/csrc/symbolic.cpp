@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <exception>
 #include <functional>
 #include <iterator>
 #include <memory>
@@ -236,11 +237,16 @@ void gnd_run(Gnd& G, std::vector<std::vector<long long>> sets, GndPart& out) {
   }
   // the deferred components: own threads while the budget lasts, else here
   std::vector<GndPart> sub(deferred.size());
+  std::vector<std::exception_ptr> fail(deferred.size());
   std::vector<std::thread> pool;
   for (size_t d = 0; d < deferred.size(); ++d) {
     if (G.threads_left.fetch_sub(1) > 0) {
-      pool.emplace_back([&G, &sub, &deferred, d]() {
-        gnd_run(G, {std::move(deferred[d])}, sub[d]);
+      pool.emplace_back([&G, &sub, &deferred, &fail, d]() {
+        try {
+          gnd_run(G, {std::move(deferred[d])}, sub[d]);
+        } catch (...) {
+          fail[d] = std::current_exception();  // rethrown on the calling thread
+        }
         G.threads_left.fetch_add(1);
       });
     } else {
@@ -249,6 +255,8 @@ void gnd_run(Gnd& G, std::vector<std::vector<long long>> sets, GndPart& out) {
     }
   }
   for (auto& th : pool) th.join();
+  for (auto& f : fail)
+    if (f) std::rethrow_exception(f);
   // stitch
   size_t pos = 0;
   for (long long bs : bsize) {
