@@ -251,7 +251,11 @@ void gnd_run(Gnd& G, std::vector<std::vector<long long>> sets, GndPart& out) {
       });
     } else {
       G.threads_left.fetch_add(1);
-      gnd_run(G, {std::move(deferred[d])}, sub[d]);
+      try {  // no exception may pass the joins below
+        gnd_run(G, {std::move(deferred[d])}, sub[d]);
+      } catch (...) {
+        fail[d] = std::current_exception();
+      }
     }
   }
   for (auto& th : pool) th.join();
