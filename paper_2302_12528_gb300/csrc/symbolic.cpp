@@ -239,23 +239,32 @@ void gnd_run(Gnd& G, std::vector<std::vector<long long>> sets, GndPart& out) {
   std::vector<GndPart> sub(deferred.size());
   std::vector<std::exception_ptr> fail(deferred.size());
   std::vector<std::thread> pool;
+  auto inline_run = [&](size_t d) {
+    try {  // no exception may pass the joins below
+      gnd_run(G, {std::move(deferred[d])}, sub[d]);
+    } catch (...) {
+      fail[d] = std::current_exception();
+    }
+  };
   for (size_t d = 0; d < deferred.size(); ++d) {
+    bool spawned = false;
     if (G.threads_left.fetch_sub(1) > 0) {
-      pool.emplace_back([&G, &sub, &deferred, &fail, d]() {
-        try {
-          gnd_run(G, {std::move(deferred[d])}, sub[d]);
-        } catch (...) {
-          fail[d] = std::current_exception();  // rethrown on the calling thread
-        }
-        G.threads_left.fetch_add(1);
-      });
-    } else {
-      G.threads_left.fetch_add(1);
-      try {  // no exception may pass the joins below
-        gnd_run(G, {std::move(deferred[d])}, sub[d]);
-      } catch (...) {
-        fail[d] = std::current_exception();
+      try {
+        pool.emplace_back([&G, &sub, &deferred, &fail, d]() {
+          try {
+            gnd_run(G, {std::move(deferred[d])}, sub[d]);
+          } catch (...) {
+            fail[d] = std::current_exception();  // rethrown on the calling thread
+          }
+          G.threads_left.fetch_add(1);
+        });
+        spawned = true;
+      } catch (...) {  // no thread to be had: run it here
       }
+    }
+    if (!spawned) {
+      G.threads_left.fetch_add(1);
+      inline_run(d);
     }
   }
   for (auto& th : pool) th.join();
