@@ -38,6 +38,8 @@ from . import dense as D
 from .mqr import RankError, mixed_qr
 
 STAGE1_TOL = 5e-6   # Section 5.1: tolerance of the lower-precision initial guess
+STAGE1_WINDOW = 5   # stage 1 stagnates when the residual has not dropped below
+STAGE1_DROP = 0.9   # STAGE1_DROP x its value STAGE1_WINDOW iterations earlier
 
 
 @dataclass
@@ -56,10 +58,10 @@ def _herm(M):
     return 0.5 * (M + M.conj().T)
 
 
-def _orth_hl(Cblk):
+def _orth_hl(C, m):
     """Thin Householder Q of C(1:m, m+1:end)^* (the improved
-    Hetmaniuk-Lehoucq step of Algorithm 3)."""
-    Y = Cblk.conj().T
+    Hetmaniuk-Lehoucq step of Algorithm 3), ncol(S) - m rows by m."""
+    Y = C[:m, m:].conj().T
     q, _ = np.linalg.qr(Y, mode="reduced")
     return q
 
@@ -72,12 +74,14 @@ def _orthonormalize(W, low):
         return mixed_qr(W, low=W.dtype)[0], 1
 
 
-def lobpcg_loop(apply_A, apply_T, X, k, tol, maxit, normA, qr_low, stage1=False):
+def lobpcg_loop(apply_A, apply_T, X, k, tol, maxit, normA, qr_low, stage1=False, observe=None):
     """The loop of Algorithm 3 from X (n x m, any basis) with P = [].
 
     ``apply_A`` and ``apply_T`` act in the dtype of X (the stage's working
     precision); ``apply_T`` takes the scaled residual and returns the
-    preconditioned block in that dtype.  Returns the whole block
+    preconditioned block in that dtype.  ``observe(X_old, X_new, P)``, when
+    given, sees every basis update (tests check the HL step's span
+    properties with it).  Returns the whole block
     (X n x m, theta m, iters, hist, converged, fallbacks).
     """
     work = X.dtype
@@ -104,7 +108,7 @@ def lobpcg_loop(apply_A, apply_T, X, k, tol, maxit, normA, qr_low, stage1=False)
             return X, theta, it - 1, hist, True, fallbacks
         if stage1:
             best.append(hist[-1])
-            if len(best) > 5 and best[-1] > 0.9 * best[-6]:
+            if len(best) > STAGE1_WINDOW and best[-1] > STAGE1_DROP * best[-1 - STAGE1_WINDOW]:
                 return X, theta, it - 1, hist, False, fallbacks
         rn = D.col_norms(R)
         rn = np.where(rn > 0, rn, 1.0)
@@ -119,9 +123,11 @@ def lobpcg_loop(apply_A, apply_T, X, k, tol, maxit, normA, qr_low, stage1=False)
         AS = apply_A(S)
         Ap = _herm(S.conj().T @ AS)                             # A_p <- S^* A S
         dd, C = np.linalg.eigh(Ap)                              # A_p C = C D (ascending)
-        V = _orth_hl(C[:m, m:])                                 # orth(C(1:m, m+1:end)^*)
+        V = _orth_hl(C, m)                                      # orth(C(1:m, m+1:end)^*)
         X_new = S @ C[:, :m]
         P = S @ (C[:, m:] @ V)
+        if observe is not None:
+            observe(X, X_new, P)
         X = X_new
         theta = dd[:m].astype(np.float64)
     return X, theta, maxit, hist, False, fallbacks
