@@ -113,10 +113,20 @@ mpl_status mpl_create_dense(mpl_handle* h, int dtype, int64_t n, const void* A, 
 /*
  * Sparse real SPD matrix in CSR (0-based, both triangles stored, sorted
  * columns): rowptr (n+1, int64), colind (nnz, int32), vals (nnz, double).
- * grid_dims (ndims = 2 or 3 entries, x fastest) selects the grid
- * nested-dissection ordering Pi; with grid_dims == NULL the natural order is
- * kept.  The matrix is permuted once, Pi^* A Pi (Section 5.1).  Other
- * arguments as for mpl_create_dense (Omega is n x m_omega double).
+ * The fill-reducing ordering Pi (Section 5.1) is a nested dissection:
+ *   - grid_dims given (ndims = 2 or 3 entries, x fastest; row i of A is grid
+ *     point i): the geometric nested dissection of the grid (cut the longest
+ *     axis at its middle plane, ties x < y < z; boxes of <= 64 points are
+ *     listed lexicographically);
+ *   - grid_dims == NULL: the level-structure nested dissection of A's pattern
+ *     (George & Liu): a pseudo-peripheral root, the middle BFS level as the
+ *     separator, components of the rest recursively, sets of <= 64 vertices
+ *     as one block.  It runs on the host (multithreaded for large components;
+ *     about 0.4 s for n = 262144, nnz = 1.8e6 on 8 cores) and gives less fill
+ *     than the grid ordering on 3D grids.
+ * Both are deterministic.  The matrix is permuted once, Pi^* A Pi.  Other
+ * arguments as for mpl_create_dense (Omega is n x m_omega double, in the
+ * permuted ordering).
  */
 mpl_status mpl_create_csr(mpl_handle* h, int64_t n, int64_t nnz, const int64_t* rowptr,
                           const int32_t* colind, const double* vals, int is_device,
@@ -130,7 +140,12 @@ mpl_status mpl_create_csr(mpl_handle* h, int64_t n, int64_t nnz, const int64_t* 
 mpl_status mpl_factor(mpl_handle h);
 
 /*
- * Algorithm 3.  X0: n x m start block (working dtype, original ordering).
+ * Algorithm 3.  X0: n x m start block (working dtype, original ordering),
+ * host or device per x0_is_device; X0 == NULL draws the block from ``seed``
+ * instead (N(0,1) entries, complex (N + iN)/sqrt 2, by the counter-based
+ * Philox4x32-10 generator and the Box-Muller transform, in the original
+ * ordering; mpl_start_block in mplobpcg_steps.h gives the same block).  seed
+ * is ignored when X0 is given.
  * maxit: working-precision iterations (stage 1 is capped at maxit too).
  * Outputs: lambda (host, k doubles, ascending); X (n x k, working dtype,
  * original ordering, orthonormal columns) on the device or host per
@@ -140,9 +155,9 @@ mpl_status mpl_factor(mpl_handle h);
  * stage-1 and stage-2 iteration counts.
  * Returns MPL_ENOT_CONVERGED (with the last iterate) if maxit is reached.
  */
-mpl_status mpl_solve(mpl_handle h, const void* X0, int x0_is_device, int maxit, double* lambda,
-                     void* X, int x_is_device, double* resid_hist, int hist_cap, int* hist_len,
-                     int* iters);
+mpl_status mpl_solve(mpl_handle h, const void* X0, int x0_is_device, uint64_t seed, int maxit,
+                     double* lambda, void* X, int x_is_device, double* resid_hist, int hist_cap,
+                     int* hist_len, int* iters);
 
 /*
  * Algorithm 1 (block PINVIT, Section 3) on the same kernels: per step the
@@ -151,14 +166,14 @@ mpl_status mpl_solve(mpl_handle h, const void* X0, int x0_is_device, int maxit, 
  * is tested with Eq. (stop), and X~ = X - T R with T = L^-* L^-1 from the
  * handle's factor (the FP64 factor for MPL_D_DCHOL, the lower-precision one
  * otherwise); every other operation is in FP64.  mpl_factor must have run.
- * Arguments as for mpl_solve, except rho_hist (host, hist_cap doubles, may be
+ * Arguments as for mpl_solve (X0 == NULL: the seeded block), except rho_hist (host, hist_cap doubles, may be
  * NULL): the Rayleigh quotient of the first column per step (Theorem 1's
  * quantity), and iters (may be NULL): one int, the number of steps.
  * Returns MPL_ENOT_CONVERGED (with the last iterate) if maxit is reached.
  */
-mpl_status mpl_solve_pinvit(mpl_handle h, const void* X0, int x0_is_device, int maxit, double* lambda,
-                            void* X, int x_is_device, double* rho_hist, int hist_cap, int* hist_len,
-                            int* iters);
+mpl_status mpl_solve_pinvit(mpl_handle h, const void* X0, int x0_is_device, uint64_t seed, int maxit,
+                            double* lambda, void* X, int x_is_device, double* rho_hist, int hist_cap,
+                            int* hist_len, int* iters);
 
 mpl_status mpl_get_stats(mpl_handle h, mpl_stats* s);
 const char* mpl_last_error(mpl_handle h);

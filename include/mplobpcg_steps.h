@@ -138,6 +138,22 @@ mpl_status mpl_step_split_gemm(int is_complex, int trans_a, int64_t n, int64_t k
 mpl_status mpl_step_lowp_syrk(int fmt, int is_complex, int64_t n, int64_t k, const void* A, int64_t lda, void* C,
                               int64_t ldc, int round_out, void* stream);
 
+/*
+ * The start block mpl_solve draws when it is given X0 == NULL (Algorithm 3
+ * takes any full-rank start block; this fixes which one a seed means):
+ * X (n x m, column-major, device) <- N(0,1) entries (MPL_R64) or
+ * (N + iN)/sqrt 2 (MPL_C128, interleaved), from the counter-based generator
+ * Philox4x32-10 (Salmon et al., SC 2011) and the Box-Muller transform.
+ * Element e = i + n j uses pair p = e / 2 (real) or e (complex): counter
+ * (p mod 2^32, p / 2^32, 0, 0), key = seed; the four words give
+ * u1 = ((x0 >> 5) 2^26 + (x1 >> 6) + 1/2) 2^-53, u2 likewise from x2, x3, and
+ * z0 = r cos(2 pi u2), z1 = r sin(2 pi u2), r = sqrt(-2 ln u1); a real element
+ * is z0 (even e) or z1 (odd e), a complex one (z0 s, z1 s), s = 1/sqrt 2.
+ * Synchronous on stream.  Errors: MPL_EINVAL (dtype, sizes, NULL X),
+ * MPL_ECUDA.
+ */
+mpl_status mpl_start_block(int dtype, int64_t n, int m, uint64_t seed, void* X, void* stream);
+
 /* Residual without device allocation (the paper has no counterpart).
  *
  * For callers that cannot call cudaMalloc: code that runs while a stream is

@@ -63,8 +63,9 @@ _create_dense = _sig("mpl_create_dense", _i, [C.POINTER(_h), _i, _i64, _p, _i64,
 _create_csr = _sig("mpl_create_csr", _i, [C.POINTER(_h), _i64, _i64, _p, _p, _p, _i, _p, _i, _i, _i, _d, _i, _p, _i,
                                           _i, _p])
 _factor = _sig("mpl_factor", _i, [_h])
-_solve = _sig("mpl_solve", _i, [_h, _p, _i, _i, _p, _p, _i, _p, _i, _p, _p])
-_pinvit = _sig("mpl_solve_pinvit", _i, [_h, _p, _i, _i, _p, _p, _i, _p, _i, _p, _p])
+_solve = _sig("mpl_solve", _i, [_h, _p, _i, C.c_uint64, _i, _p, _p, _i, _p, _i, _p, _p])
+_pinvit = _sig("mpl_solve_pinvit", _i, [_h, _p, _i, C.c_uint64, _i, _p, _p, _i, _p, _i, _p, _p])
+_start_block = _sig("mpl_start_block", _i, [_i, _i64, _i, C.c_uint64, _p, _p])
 _adjoint = _sig("mpl_adjoint", _i, [_h, _p, _p, _p, _i, _d, _p, _p])
 _fv_assemble = _sig("mpl_fv_assemble", _i, [_i, _p, _p, _p, _p, _p, _p])
 _fv_assemble_adjoint = _sig("mpl_fv_assemble_adjoint", _i, [_i, _p, _p, _p, _p, _p, _p])
@@ -147,28 +148,32 @@ class Handle:
     def factor(self):
         self._check(_factor(self._h))
 
-    def solve(self, X0, maxit=2000, X_out=None, hist_cap=4096, allow_not_converged=False):
-        """Algorithm 3.  X0: (m, n) array/tensor (column-major n x m).
+    def solve(self, X0, maxit=2000, X_out=None, hist_cap=4096, allow_not_converged=False, seed=0):
+        """Algorithm 3.  X0: (m, n) array/tensor (column-major n x m), or None
+        for the block drawn from ``seed`` (``start_block``).
         X_out: optional (k, n) tensor/array receiving the eigenvectors.
         Returns (lambda (k,), X_out, hist list, (it1, it2), status)."""
         lam = np.zeros(self.k)
         hist = np.zeros(max(hist_cap, 1))
         hl = C.c_int(0)
         its = (C.c_int * 2)()
-        st = _solve(self._h, _ptr(X0), _is_dev(X0), maxit, lam.ctypes.data, _ptr(X_out),
+        st = _solve(self._h, _ptr(X0), _is_dev(X0) if X0 is not None else 0, seed, maxit, lam.ctypes.data,
+                    _ptr(X_out),
                     _is_dev(X_out) if X_out is not None else 0, hist.ctypes.data, hist_cap,
                     C.byref(hl), its)
         self._check(st, (0, 4) if allow_not_converged else (0,))
         return lam, X_out, hist[: hl.value].tolist(), (its[0], its[1]), st
 
-    def solve_pinvit(self, X0, maxit=2000, X_out=None, hist_cap=4096, allow_not_converged=False):
-        """Algorithm 1 (block PINVIT) with the handle's factor.  X0: (m, n).
+    def solve_pinvit(self, X0, maxit=2000, X_out=None, hist_cap=4096, allow_not_converged=False, seed=0):
+        """Algorithm 1 (block PINVIT) with the handle's factor.  X0: (m, n),
+        or None for the block drawn from ``seed``.
         Returns (lambda (k,), X_out, rho history list, steps, status)."""
         lam = np.zeros(self.k)
         rho = np.zeros(max(hist_cap, 1))
         hl = C.c_int(0)
         its = C.c_int(0)
-        st = _pinvit(self._h, _ptr(X0), _is_dev(X0), maxit, lam.ctypes.data, _ptr(X_out),
+        st = _pinvit(self._h, _ptr(X0), _is_dev(X0) if X0 is not None else 0, seed, maxit, lam.ctypes.data,
+                     _ptr(X_out),
                      _is_dev(X_out) if X_out is not None else 0, rho.ctypes.data, hist_cap,
                      C.byref(hl), C.byref(its))
         self._check(st, (0, 4) if allow_not_converged else (0,))
@@ -333,6 +338,18 @@ def analyze_host(rowptr, colind, grid_dims=None):
     if st != 0:
         _raise_create(st, "mpl_analyze_host")
     return Handle(h, MPL_R64, n, 1, 1)
+
+
+def start_block(X, seed, stream=None):
+    """mpl_start_block: fill the device tensor X ((m, n), float64 or
+    complex128; column-major n x m) with the block mpl_solve draws for
+    ``seed`` when it is given no start block."""
+    import torch
+    dt = MPL_C128 if X.dtype == torch.complex128 else MPL_R64
+    m, n = X.shape
+    st = _start_block(dt, n, m, seed, _ptr(X), _stream_ptr(stream))
+    if st != 0:
+        raise MplError(st, "mpl_start_block", 0)
 
 
 def residual_noalloc(dtype, n, m, AX, X, theta, R, norms2, stream=None):

@@ -9,6 +9,7 @@
 #include "mplobpcg_adjoint.h"
 #include "mplobpcg_steps.h"
 #include "oz_gemm.cuh"
+#include "rng.cuh"
 #include "sparse.cuh"
 
 namespace mpl {
@@ -151,9 +152,9 @@ inline bool fmt16_tc() {
 struct EngineBase {
   virtual ~EngineBase() {}
   virtual void factor() = 0;
-  virtual mpl_status solve(const void* X0, int x0_dev, int maxit, double* lambda, void* X, int x_dev,
+  virtual mpl_status solve(const void* X0, int x0_dev, unsigned long long seed, int maxit, double* lambda, void* X, int x_dev,
                            double* hist, int hist_cap, int* hist_len, int* iters) = 0;
-  virtual mpl_status solve_pinvit(const void* X0, int x0_dev, int maxit, double* lambda, void* X, int x_dev,
+  virtual mpl_status solve_pinvit(const void* X0, int x0_dev, unsigned long long seed, int maxit, double* lambda, void* X, int x_dev,
                                   double* rho_hist, int hist_cap, int* hist_len, int* iters) = 0;
   virtual void adjoint(const double* gl, const void* gX, double* grad, int maxit, double tol, int* iters,
                        double* rel_resid) = 0;
@@ -373,7 +374,7 @@ class Engine : public EngineBase {
   }
   FactorSolve<TW>* factor_work();
 
-  mpl_status solve(const void* X0, int x0_dev, int maxit, double* lambda, void* X, int x_dev,
+  mpl_status solve(const void* X0, int x0_dev, unsigned long long seed, int maxit, double* lambda, void* X, int x_dev,
                    double* hist, int hist_cap, int* hist_len, int* iters) override {
     if (!c_->factored) throw MplError{MPL_ESTATE, "mpl_solve before mpl_factor", 0};
     cudaStream_t st = c_->stream;
@@ -381,7 +382,7 @@ class Engine : public EngineBase {
     const int m = c_->m, k = c_->k;
     const long long l0 = launch_counter().load();
     const long long cf0 = cluster_fallback_counter().load();
-    TW* x0 = upload_x0(X0, x0_dev);
+    TW* x0 = upload_x0(X0, x0_dev, seed);
     std::vector<double> h;
     Progress p1;
     const TW* start = x0;
@@ -443,22 +444,29 @@ class Engine : public EngineBase {
     return p2.converged ? MPL_OK : MPL_ENOT_CONVERGED;
   }
 
-  // X0 (caller's ordering, host or device) into the permuted working copy.
-  TW* upload_x0(const void* X0, int x0_dev) {
+  // X0 (caller's ordering, host or device) into the permuted working copy;
+  // with X0 == NULL the seeded N(0,1) block of rng.cu, drawn in the caller's
+  // ordering (the same seed gives the same start whatever the permutation).
+  TW* upload_x0(const void* X0, int x0_dev, unsigned long long seed) {
     cudaStream_t st = c_->stream;
     const long long n = c_->n;
     const int m = c_->m;
     X0_.ensure(sizeof(TW) * n * m);
     TW* x0 = X0_.as<TW>();
-    if (c_->sparse && !c_->perm.empty()) {
+    const bool permuted = c_->sparse && !c_->perm.empty();
+    TW* dst = x0;
+    if (permuted) {
       tmpx_.ensure(sizeof(TW) * n * m);
-      MPL_CUDA(cudaMemcpyAsync(tmpx_.ptr(), X0, sizeof(TW) * n * m,
-                               x0_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-      permute_rows<TW>(st, (int)n, m, perm_dev_.as<long long>(), false, tmpx_.as<TW>(), n, x0, n);
-    } else {
-      MPL_CUDA(cudaMemcpyAsync(x0, X0, sizeof(TW) * n * m,
-                               x0_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+      dst = tmpx_.as<TW>();
     }
+    if (X0) {
+      MPL_CUDA(cudaMemcpyAsync(dst, X0, sizeof(TW) * n * m,
+                               x0_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    } else {
+      start_block(st, tr<TW>::cx, n, m, seed, reinterpret_cast<double*>(dst));
+      check_launch("seeded start block");
+    }
+    if (permuted) permute_rows<TW>(st, (int)n, m, perm_dev_.as<long long>(), false, tmpx_.as<TW>(), n, x0, n);
     return x0;
   }
 
@@ -481,13 +489,13 @@ class Engine : public EngineBase {
 
   // Algorithm 1 with the handle's factor: the FP64 factor for D-dchol, the
   // lower-precision factor otherwise; every other operation in FP64.
-  mpl_status solve_pinvit(const void* X0, int x0_dev, int maxit, double* lambda, void* X, int x_dev,
-                          double* rho_hist, int hist_cap, int* hist_len, int* iters) override {
+  mpl_status solve_pinvit(const void* X0, int x0_dev, unsigned long long seed, int maxit, double* lambda, void* X,
+                          int x_dev, double* rho_hist, int hist_cap, int* hist_len, int* iters) override {
     if (!c_->factored) throw MplError{MPL_ESTATE, "mpl_solve_pinvit before mpl_factor", 0};
     cudaStream_t st = c_->stream;
     const long long l0 = launch_counter().load();
     const long long cf0 = cluster_fallback_counter().load();
-    TW* x0 = upload_x0(X0, x0_dev);
+    TW* x0 = upload_x0(X0, x0_dev, seed);
     auto& stg = stage_w<TW>();
     Timer t2(st);
     Progress p;
@@ -879,8 +887,13 @@ struct HostSymEngine : EngineBase {
   std::unique_ptr<SparseSymbolic> sym;
   [[noreturn]] static void no() { throw MplError{MPL_ESTATE, "host-only symbolic handle", 0}; }
   void factor() override { no(); }
-  mpl_status solve(const void*, int, int, double*, void*, int, double*, int, int*, int*) override { no(); }
-  mpl_status solve_pinvit(const void*, int, int, double*, void*, int, double*, int, int*, int*) override { no(); }
+  mpl_status solve(const void*, int, unsigned long long, int, double*, void*, int, double*, int, int*, int*) override {
+    no();
+  }
+  mpl_status solve_pinvit(const void*, int, unsigned long long, int, double*, void*, int, double*, int, int*,
+                          int*) override {
+    no();
+  }
   void adjoint(const double*, const void*, double*, int, double, int*, double*) override { no(); }
   void step_apply_A(const void*, void*, int, int) override { no(); }
   void step_residual(const void*, const void*, const double*, int, void*, double*) override { no(); }
@@ -999,13 +1012,13 @@ extern "C" mpl_status mpl_factor(mpl_handle h) {
   return guarded(h, [&]() { h->eng->factor(); return MPL_OK; });
 }
 
-extern "C" mpl_status mpl_solve(mpl_handle h, const void* X0, int x0_is_device, int maxit, double* lambda,
-                                void* X, int x_is_device, double* resid_hist, int hist_cap, int* hist_len,
-                                int* iters) {
-  if (!h || !X0 || maxit < 0 || (resid_hist && hist_cap < 0)) return MPL_EINVAL;
+extern "C" mpl_status mpl_solve(mpl_handle h, const void* X0, int x0_is_device, uint64_t seed, int maxit,
+                                double* lambda, void* X, int x_is_device, double* resid_hist, int hist_cap,
+                                int* hist_len, int* iters) {
+  if (!h || maxit < 0 || (resid_hist && hist_cap < 0)) return MPL_EINVAL;
   mpl_status s = guarded(h, [&]() {
-    const mpl_status r =
-        h->eng->solve(X0, x0_is_device, maxit, lambda, X, x_is_device, resid_hist, hist_cap, hist_len, iters);
+    const mpl_status r = h->eng->solve(X0, x0_is_device, seed, maxit, lambda, X, x_is_device, resid_hist, hist_cap,
+                                       hist_len, iters);
     if (mpl::oz_gemm_requested() && mpl::oz_take_error(h->stream))
       throw mpl::MplError{MPL_ECUDA, "split FP64 product: a completion wait gave up", 0};
     return r;
@@ -1014,13 +1027,13 @@ extern "C" mpl_status mpl_solve(mpl_handle h, const void* X0, int x0_is_device, 
   return s;
 }
 
-extern "C" mpl_status mpl_solve_pinvit(mpl_handle h, const void* X0, int x0_is_device, int maxit,
+extern "C" mpl_status mpl_solve_pinvit(mpl_handle h, const void* X0, int x0_is_device, uint64_t seed, int maxit,
                                        double* lambda, void* X, int x_is_device, double* rho_hist, int hist_cap,
                                        int* hist_len, int* iters) {
-  if (!h || !X0 || maxit < 0 || (rho_hist && hist_cap < 0)) return MPL_EINVAL;
+  if (!h || maxit < 0 || (rho_hist && hist_cap < 0)) return MPL_EINVAL;
   mpl_status s = guarded(h, [&]() {
-    return h->eng->solve_pinvit(X0, x0_is_device, maxit, lambda, X, x_is_device, rho_hist, hist_cap, hist_len,
-                                iters);
+    return h->eng->solve_pinvit(X0, x0_is_device, seed, maxit, lambda, X, x_is_device, rho_hist, hist_cap,
+                                hist_len, iters);
   });
   if (s == MPL_ENOT_CONVERGED) h->err = "maximum number of iterations reached";
   return s;

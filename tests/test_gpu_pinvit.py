@@ -169,5 +169,5 @@ def test_pinvit_status_codes():
     h.factor()
     lam, _, rho, its, st = h.solve_pinvit(X0, maxit=2, allow_not_converged=True)
     assert st == 4 and its == 2 and len(rho) == 2    # MPL_ENOT_CONVERGED after maxit steps
-    assert M.lib.mpl_solve_pinvit(None, None, 0, 1, None, None, 0, None, 0, None, None) == 1
+    assert M.lib.mpl_solve_pinvit(None, None, 0, 0, 1, None, None, 0, None, 0, None, None) == 1
     h.close()

@@ -42,7 +42,12 @@ def test_create_csr_rejects(kw):
 
 def test_null_handles():
     assert b._factor(None) == EINVAL
-    assert b._solve(None, P, 1, 10, P, P, 1, None, 0, None, P) == EINVAL
+    assert b._solve(None, P, 1, 0, 10, P, P, 1, None, 0, None, P) == EINVAL
+    assert b._solve(None, None, 0, 7, 10, P, P, 1, None, 0, None, P) == EINVAL
+    assert b._pinvit(None, None, 0, 7, 10, P, P, 1, None, 0, None, P) == EINVAL
+    assert b._start_block(b.MPL_R64, 0, 4, 1, P, None) == EINVAL       # n < 1
+    assert b._start_block(b.MPL_R64, 10, 4, 1, None, None) == EINVAL    # NULL X
+    assert b._start_block(5, 10, 4, 1, P, None) == EINVAL               # dtype
     assert b.lib.mpl_last_info(None) == 0
     b.lib.mpl_destroy(None)   # harmless
 
