@@ -167,7 +167,8 @@ def solve(op, factor_matrix, X0, Omega, k, tol=1e-12, policy="mp", maxit=2000,
 
     ``op``            DenseOperator or CsrOperator on Pi^* A Pi.
     ``factor_matrix`` dense Pi^* A Pi used for the Cholesky preconditioner
-                      (ignored when ``lower_factor`` is given).
+                      (ignored when ``lower_factor`` is given; a factor
+                      with an ``apply(R)`` method applies T with it).
     ``X0``            n x m start block (working precision).
     ``Omega``         m_Omega x n Gaussian sketch for the norm estimate.
     """
@@ -184,8 +185,11 @@ def solve(op, factor_matrix, X0, Omega, k, tol=1e-12, policy="mp", maxit=2000,
     else:
         F = D.lower_cholesky(factor_matrix, normA, dtype=low)
 
+    # a factor object may bring its own solves (the sparse factor does)
+    solves = getattr(F, "apply", None) or (lambda R: D.apply_T(F, R))
+
     def T_work(R):
-        return D.working(D.apply_T(F, R.astype(F.dtype))) if F.dtype != work else D.apply_T(F, R)
+        return D.working(solves(R.astype(F.dtype))) if F.dtype != work else solves(R)
 
     it1 = 0
     hist = []
@@ -193,7 +197,7 @@ def solve(op, factor_matrix, X0, Omega, k, tol=1e-12, policy="mp", maxit=2000,
     X = X0
     if policy in ("mp", "hchol", "bchol"):
         def T_low(R):
-            return D.apply_T(F, R.astype(low))
+            return solves(R.astype(low))
         X1, _, it1, h1, _, f1 = lobpcg_loop(op.low, T_low, D.lower(X0), k, STAGE1_TOL,
                                             maxit1, normA, low, stage1=True)
         X = D.working(X1)

@@ -115,3 +115,27 @@ def test_batch_invalid_arguments():
     with pytest.raises(M.MplError) as e:
         M.Batch(np.array([20, 70]), b["a_off"], b["x_off"], A, Om, 4, 8)   # n < 3m
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("policy", ["mp", "dchol"])
+def test_batch_largest_orders_against_eigh(policy):
+    """The top of the batched workload's size range, n in [900, 1024]."""
+    b = W.batch_spd(6, seed=76, nmin=900, nmax=1024)
+    assert b["n"].min() >= 900 and b["n"].max() <= 1024
+    (outs, _) = _run(b, policy, tune=True)
+    lam, X, its, st = outs[0]
+    assert np.all(st == 0), st
+    for i in range(len(b["n"])):
+        A, X0, Om = _problem(b, i)
+        n = A.shape[0]
+        ev = np.linalg.eigvalsh(A)
+        xo = int(b["x_off"][i])
+        Xi = X[xo * K:(xo + n) * K].reshape(K, n).T
+        rn = np.linalg.norm(A @ Xi - Xi * lam[i][None, :], axis=0)
+        assert np.all(rn <= 1e-12 * (ev[-1] + np.abs(lam[i])) * np.linalg.norm(Xi, axis=0)), (i, rn)
+        gap = ev[K] - ev[K - 1]
+        assert np.all(np.abs(lam[i] - ev[:K]) <= np.maximum(1e-10 * ev[:K], 2 * rn ** 2 / gap) + 10 * U_H * ev[-1])
+        assert np.abs(Xi.T @ Xi - np.eye(K)).max() <= 1e-12
+        if i < 2 and policy == "mp":
+            ref = OL.solve(OL.DenseOperator(A), A, X0, Om, K, tol=1e-12, policy="mp")
+            assert np.allclose(lam[i], ref.theta, rtol=1e-10)
