@@ -162,7 +162,7 @@ class CsrOperator:
 
 
 def solve(op, factor_matrix, X0, Omega, k, tol=1e-12, policy="mp", maxit=2000,
-          maxit1=1000, lower_factor=None):
+          maxit1=1000, lower_factor=None, observe=None):
     """Compute the k smallest eigenpairs of the (already permuted) A.
 
     ``op``            DenseOperator or CsrOperator on Pi^* A Pi.
@@ -171,6 +171,7 @@ def solve(op, factor_matrix, X0, Omega, k, tol=1e-12, policy="mp", maxit=2000,
                       with an ``apply(R)`` method applies T with it).
     ``X0``            n x m start block (working precision).
     ``Omega``         m_Omega x n Gaussian sketch for the norm estimate.
+    ``observe``       passed to lobpcg_loop for both stages (timing, checks).
     """
     X0 = np.asarray(X0)
     work = X0.dtype
@@ -199,14 +200,14 @@ def solve(op, factor_matrix, X0, Omega, k, tol=1e-12, policy="mp", maxit=2000,
         def T_low(R):
             return solves(R.astype(low))
         X1, _, it1, h1, _, f1 = lobpcg_loop(op.low, T_low, D.lower(X0), k, STAGE1_TOL,
-                                            maxit1, normA, low, stage1=True)
+                                            maxit1, normA, low, stage1=True, observe=observe)
         X = D.working(X1)
         hist += h1
         fb += f1
         qr_low = low
     else:
         qr_low = work
-    Xm, th, it2, h2, conv, f2 = lobpcg_loop(op.work, T_work, X, k, tol, maxit, normA, qr_low)
+    Xm, th, it2, h2, conv, f2 = lobpcg_loop(op.work, T_work, X, k, tol, maxit, normA, qr_low, observe=observe)
     hist += h2
     fb += f2
     return Result(theta=th[:k], X=Xm[:, :k], iters=(it1, it2), hist=hist, normA=normA, converged=conv,
