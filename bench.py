@@ -17,9 +17,11 @@ complex Gaussian).  Prints one JSON line.
   iterations a..b with cudaProfilerStart/Stop (for ncu --profile-from-start off).
 
 --impl reference times the CPU oracle (oracle/, NumPy/SciPy on the host
-cores) on a bounded sample of the same workload: the lower-precision factor
-plus one working-precision iteration, extrapolated to the iteration counts
-of a full solve.  Under torchrun (N > 1) every rank solves its own replica
+cores) on the same workload: the full solve for small dense problems, else a
+bounded sample (factor and the first iterations of both stages through the
+oracle's real loop) completed with the oracle's own full-run iteration counts
+(stored by tests/golden/make_full_size.py) at the sampled per-iteration
+times.  Under torchrun (N > 1) every rank solves its own replica
 (independent problems, no collective on the data path); rank 0 prints.
 """
 from __future__ import annotations
@@ -59,6 +61,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-threads", type=int, default=0,
+                    help="BLAS threads of the oracle (CPU baseline and reference arm); 0: all cores")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling runs only: cap the iterations (result may be unconverged)")
     ap.add_argument("--n", type=int, default=0,
@@ -175,60 +179,102 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (bounded sample)
 # ---------------------------------------------------------------------------
-def oracle_sample(w, d_host, iters_total):
-    """Time the oracle's lower-precision factor and one working-precision
-    LOBPCG iteration on the host cores; extrapolate to ``iters_total``."""
+def oracle_counts(w, policy):
+    """The oracle's own iteration counts (stage 1, stage 2) of its full-size
+    run of this workload, stored by tests/golden/make_full_size.py (oracle
+    only); None when none is stored."""
+    path = os.path.join(ROOT, "tests", "golden", f"{w.name}_refs.json")
+    try:
+        with open(path) as f:
+            ref = json.load(f)
+        return tuple(int(x) for x in ref[policy]["iters"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def oracle_sample(w, d_host, policy="mp", gpu_iters=None, threads=None, caps=(2, 2)):
+    """The oracle's Algorithm 3 (oracle.lobpcg.solve as it stands) on the
+    host cores.  Dense n <= 2000: the full solve, timed.  Larger: a bounded
+    sample -- norm estimate, lower-precision factor, and the first caps[0] /
+    caps[1] iterations of the two stages through the real loop -- timed whole,
+    plus the remaining iterations of the oracle's own full-size run (stored
+    counts) at the per-iteration times measured in the sample (between
+    consecutive basis updates of a stage)."""
     from oracle import dense as OD
     from oracle import lobpcg as OL
     try:
-        from threadpoolctl import threadpool_info
-        cores = max([i.get("num_threads", 1) for i in threadpool_info()] or [os.cpu_count()])
-    except Exception:
-        cores = os.cpu_count()
-    if w.kind == "csr":
-        from oracle import sparse as OS
-        from oracle import symbolic as OSy
-        perm = OSy.nd_grid_order(w.dims)
-        prp, pci, pv = OSy.permute_csr(d_host["rowptr"], d_host["colind"], d_host["vals"], perm)
-        Ap = OS.csr_to_scipy(prp, pci, pv)
-        op = OL.CsrOperator(Ap)
+        from threadpoolctl import threadpool_limits
+    except Exception:  # pragma: no cover
+        threadpool_limits = None
+    ctx = threadpool_limits(limits=threads) if (threads and threadpool_limits) else None
+    try:
+        if ctx is not None:
+            ctx.__enter__()
+        try:
+            from threadpoolctl import threadpool_info
+            cores = max([i.get("num_threads", 1) for i in threadpool_info()] or [os.cpu_count()])
+        except Exception:
+            cores = os.cpu_count()
+        full = w.kind != "csr" and w.n <= 2000
+        X0 = d_host["X0"].T
+        Om = d_host["Omega_np"]
         t0 = time.perf_counter()
-        import scipy.sparse.linalg as spla
-        spla.splu(Ap.tocsc().astype(np.float32), permc_spec="NATURAL")  # sparse FP32 factor sample
+        if w.kind == "csr":
+            from oracle import sparse as OS
+            from oracle import symbolic as OSy
+            perm = OSy.nd_grid_order(w.dims)
+            prp, pci, pv = OSy.permute_csr(d_host["rowptr"], d_host["colind"], d_host["vals"], perm)
+            Ap = OS.csr_to_scipy(prp, pci, pv)
+            op = OL.CsrOperator(Ap)
+            X0 = X0[perm]
+            normA = OD.norm_estimate(op.work, Om)
+            F = OS.lower_cholesky_sparse(Ap, normA, dtype=np.float64 if policy == "dchol" else np.float32)
+            fm = None
+        else:
+            A = d_host["A"]
+            op = OL.DenseOperator(A)
+            normA = OD.norm_estimate(op.work, Om)
+            low = OD.LOWER[A.dtype]
+            F = OD.lower_cholesky(A, normA, dtype=A.dtype if policy == "dchol" else low)
+            fm = A
         t_factor = time.perf_counter() - t0
-        X = d_host["X0"].T
-        normA = OD.norm_estimate(op.work, d_host["Omega_np"])
-    else:
-        A = d_host["A"]
-        op = OL.DenseOperator(A)
-        normA = OD.norm_estimate(op.work, d_host["Omega_np"])
-        t0 = time.perf_counter()
-        F = OD.lower_cholesky(A, normA)
-        t_factor = time.perf_counter() - t0
-        X = d_host["X0"].T
-    # one working-precision iteration of Algorithm 3 (same operations as the loop body)
-    t0 = time.perf_counter()
-    m = X.shape[1]
-    AX = op.work(X)
-    R = AX - X * np.linspace(1, 2, m)[None, :]
-    OD.stop_test(R, X, np.linspace(1, 2, m), normA, w.tol)
-    if w.kind != "csr":
-        Wb = OD.working(OD.apply_T(F, OD.lower(R)))
-    else:
-        Wb = R.copy()
-    B = X
-    for _ in range(2):
-        Wb = Wb - B @ (B.conj().T @ Wb)
-    from oracle.mqr import mixed_qr
-    Wb, _ = mixed_qr(Wb)
-    S = np.concatenate([X, X, Wb], axis=1)
-    AS = op.work(S)
-    Ap = S.conj().T @ AS
-    np.linalg.eigh(0.5 * (Ap + Ap.conj().T))
-    t_iter = time.perf_counter() - t0
-    value = t_factor + iters_total * t_iter
-    return {"value": value, "t_factor_s": t_factor, "t_iter_s": t_iter, "cores": int(cores),
-            "iters_extrapolated": int(iters_total)}
+        marks = []   # (stage, time) at every basis update of the loop
+
+        def observe(x_old, x_new, p):
+            marks.append((1 if x_new.dtype in (np.float32, np.complex64) else 2, time.perf_counter()))
+
+        kw = {} if full else {"maxit1": caps[0], "maxit": caps[1]}
+        res = OL.solve(op, fm, X0, Om, w.k, tol=w.tol, policy=policy, lower_factor=F, observe=observe, **kw)
+        t_sample = time.perf_counter() - t0
+    finally:
+        if ctx is not None:
+            ctx.__exit__(None, None, None)
+    out = {"cores": int(cores), "t_factor_s": t_factor, "t_sample_s": t_sample, "policy": policy}
+    if full:
+        out.update(value=t_sample, iters=list(res.iters), converged=bool(res.converged),
+                   sample=f"oracle full solve ({policy}): {res.iters[0]} + {res.iters[1]} iterations, "
+                          f"factor {t_factor:.2f} s")
+        return out
+    per = {}
+    for st in (1, 2):
+        ts = [t for s_, t in marks if s_ == st]
+        if len(ts) >= 2:
+            per[st] = (ts[-1] - ts[0]) / (len(ts) - 1)
+    counts = oracle_counts(w, policy)
+    src = "the oracle's own full-size run (tests/golden)"
+    if counts is None and gpu_iters is not None:
+        counts, src = tuple(int(x) for x in gpu_iters), "the GPU solve's counts (no stored oracle run)"
+    elif counts is None:
+        counts, src = tuple(int(x) for x in res.iters), "the sampled iterations only (no stored oracle run)"
+    done = tuple(int(x) for x in res.iters)
+    rest = sum(max(0, counts[i] - done[i]) * per.get(i + 1, 0.0) for i in range(2))
+    out.update(value=t_sample + rest, iters=list(counts), sampled_iters=list(done),
+               t_iter_s={str(k): v for k, v in per.items()},
+               sample=f"oracle {policy}: norm estimate + factor ({t_factor:.1f} s) + the first "
+                      f"{done[0]} + {done[1]} iterations through the real loop ({t_sample:.1f} s in all), "
+                      f"then {counts[0]} + {counts[1]} iterations in all ({src}) at the sampled "
+                      f"per-iteration times")
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -387,11 +433,9 @@ def main():
         out["e2e"] = e2e(M, w, d, X0h, args, stream, torch)
     if rank == 0 and not args.no_cpu_baseline:
         dh = host_copy(w, d, X0h)
-        cb = oracle_sample(w, dh, its[0] + its[1])
+        cb = oracle_sample(w, dh, args.policy, gpu_iters=its, threads=args.cpu_threads or None)
         out["cpu_baseline"] = {"value": cb["value"], "unit": "s", "cores": cb["cores"], "kind": "oracle",
-                               "sample": "oracle lower-precision factor + 1 working-precision iteration "
-                                         f"(t_factor {cb['t_factor_s']:.2f} s, t_iter {cb['t_iter_s']:.2f} s), "
-                                         f"extrapolated to {cb['iters_extrapolated']} iterations"}
+                               "iterations": cb["iters"], "sample": cb["sample"]}
     if rank == 0:
         print(json.dumps(out))
     if dist is not None:
@@ -768,8 +812,9 @@ def e2e(M, w, d, X0h, args, stream, torch):
 
 
 def run_reference(args, w):
-    """CPU oracle arm: bounded sample per step (factor + one iteration),
-    extrapolated with the oracle's own iteration count on a smaller twin."""
+    """CPU oracle arm: each step one oracle_sample of the workload on the
+    host cores (the full solve for small dense problems, else the bounded
+    sample extrapolated with the oracle's own stored iteration counts)."""
     import torch
     seed = w.seed
     cplx = w.kind == "dense_complex"
@@ -786,21 +831,21 @@ def run_reference(args, w):
         d = {"A": A}
     d["Omega_np"] = W.sketch(w.n, 8, seed + 2, cplx)
     d["X0"] = W.start_block(w.n, w.m, seed + 1, cplx)
-    iters = int(os.environ.get("MPL_REF_ITERS", "55"))
     vals = []
     cb = None
     for i in range(args.warmup + args.steps):
-        cb = oracle_sample(w, d, iters)
+        cb = oracle_sample(w, d, args.policy, threads=args.cpu_threads or None)
         if i >= args.warmup:
             vals.append(cb["value"])
     v = float(np.mean(vals))
+    pol = {"mp": "MPLOBPCG-schol", "schol": "DLOBPCG-schol", "dchol": "DLOBPCG-dchol"}.get(args.policy, args.policy)
     out = {"impl": "reference", "metric": "time-to-k-eigenpairs at resid<=1e-12 (mixed-precision LOBPCG, Algorithm 3)",
            "value": v, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": v * 1000.0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64+f32", "data": "synthetic (seeded)",
-           "config": {"workload": w.name, "n": w.n, "k": w.k, "m": w.m, "tol": w.tol, "policy": "MPLOBPCG-schol"},
+           "config": {"workload": w.name, "n": w.n, "k": w.k, "m": w.m, "tol": w.tol, "policy": pol},
            "cpu_baseline": {"value": v, "unit": "s", "cores": cb["cores"], "kind": "oracle",
-                            "sample": f"oracle factor + 1 iteration per step, extrapolated to {iters} iterations"},
+                            "iterations": cb["iters"], "sample": cb["sample"]},
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
