@@ -25,22 +25,20 @@ void spmm_csr(cudaStream_t st, int n, int m, const long long* rowptr, const int*
 struct SplitAX {
   bool cx = false;
   int n = 0, np = 1;
-  size_t qa = 0, pb = 0, tt = 0;
-  long long trows = 0;
+  size_t qa = 0, pb = 0, tmax = 0;
   DevMem e, Q, f, P, T, err;
   void prepare(cudaStream_t st, bool complex_, int n_, const double* A, long long lda) {
     cx = complex_;
     n = n_;
     np = cx ? 3 : 1;
     qa = oz_a_elems(n, n);
-    pb = oz_b_elems(n, 96);
-    trows = oz_t_rows(n);
-    tt = (size_t)trows * 96;
+    pb = oz_b_elems(n, OZ_MAXM);
+    tmax = oz_t_elems(n, OZ_MAXM);
     e.alloc(sizeof(int) * np * n);
     Q.alloc(sizeof(uint16_t) * np * qa);
-    f.alloc(sizeof(int) * np * 96);
+    f.alloc(sizeof(int) * np * OZ_MAXM);
     P.alloc(sizeof(uint16_t) * np * pb);
-    T.alloc(sizeof(long long) * np * tt);
+    T.alloc(sizeof(long long) * np * tmax);
     err.alloc(sizeof(int));
     MPL_CUDA(cudaMemsetAsync(err.ptr(), 0, sizeof(int), st));
     for (int p = 0; p < np; ++p)
@@ -49,22 +47,21 @@ struct SplitAX {
   }
   void apply(cudaStream_t st, const double* X, long long ldx, double* Y, long long ldy, int ncols) {
     const int elt = cx ? 2 : 1;
-    const int S = oz_shift(n);
-    for (int c0 = 0; c0 < ncols; c0 += 96) {
-      const int mc = std::min(96, ncols - c0);
+    for (int c0 = 0; c0 < ncols; c0 += OZ_MAXM) {
+      const int mc = std::min(OZ_MAXM, ncols - c0);
+      const size_t tt = oz_t_elems(n, mc);
       MPL_CUDA(cudaMemsetAsync(T.ptr(), 0, sizeof(long long) * np * tt, st));
       for (int p = 0; p < np; ++p)
-        oz_split_b(st, cx ? p + 1 : 0, n, mc, X + (size_t)elt * c0 * ldx, ldx, f.as<int>() + p * 96,
+        oz_split_b(st, cx ? p + 1 : 0, n, mc, X + (size_t)elt * c0 * ldx, ldx, f.as<int>() + p * OZ_MAXM,
                    P.as<uint16_t>() + p * pb);
       for (int p = 0; p < np; ++p)
         oz_mma(st, n, n, mc, Q.as<uint16_t>() + p * qa, P.as<uint16_t>() + p * pb, T.as<long long>() + p * tt,
                err.as<int>());
       double* y = Y + (size_t)elt * c0 * ldy;
       if (cx)
-        oz_combine_3m(st, n, mc, T.as<long long>(), trows, (long long)tt, e.as<int>(), n, f.as<int>(), 96, S, y, ldy,
-                      1.0, 0.0, false, 0);
+        oz_combine_3m(st, n, mc, T.as<long long>(), e.as<int>(), n, f.as<int>(), OZ_MAXM, y, ldy, 1.0, 0.0, false, 0);
       else
-        oz_combine_real(st, n, mc, T.as<long long>(), trows, e.as<int>(), f.as<int>(), S, y, ldy, 1.0, 0.0, false, 0);
+        oz_combine_real(st, n, mc, T.as<long long>(), e.as<int>(), f.as<int>(), y, ldy, 1.0, 0.0, false, 0);
     }
     check_launch("split A X");
     int h = 0;

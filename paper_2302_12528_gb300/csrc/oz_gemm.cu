@@ -2,35 +2,43 @@
 // splitting (Ozaki, Ogita, Oishi & Rump, "Error-free transformations of
 // matrix multiplication by using fast routines of matrix multiplication and
 // its applications", Numer. Algorithms 59, 2012), for the working-precision
-// A X of the dense operator.
+// products of Algorithm 3 (A X and, on request, the large Gram and update
+// products).
 //
 // Splitting.  Row r of A is scaled by its exponent e_r (|A_rk| < 2^e_r) and
-// cut into OZ_S signed 8-bit digits by rounding to nearest:
-//   u = A_rk 2^(8 - e_r),  q_i = rint(u),  u <- 256 (u - q_i),
-// so A_rk = 2^(e_r - 8) sum_i q_i 2^(-8i) + O(2^(e_r - 8 - 8 OZ_S)), with
-// |q_0| <= 256 and |q_i| <= 128 after it; every q_i 2^(-8i) is exact in
-// bf16.  Columns of B likewise with exponents f_c.  All steps are exact in
-// FP64 (u - rint(u) and the scaling by 256 round nothing).
+// cut into OZ_S = 8 balanced signed 8-bit digits by rounding to nearest:
+//   u = A_rk 2^(7 - e_r),  q_i = rint(u),  u <- 256 (u - q_i),
+// so |q_i| <= 128 (exact in bf16) and A_rk = 2^(e_r - 7) sum_i q_i 2^(-8i)
+// up to 2^(e_r - 71).  Columns of B likewise with exponents f_c.  Every step
+// is exact in FP64 (u - rint(u) and the scaling by 256 round nothing).
 //
-// Products.  Slice pairs (i, j) with i + j = g share the scale 2^(-8g).
-// Groups g < OZ_G are accumulated in their own FP32 tensor-memory
-// accumulator over a window of OZ_WIN = 128 depth indices: every partial sum
-// is an integer multiple of 2^(-8g) below 2^24 of it, so FP32 adds nothing
-// to it.  The pairs with g >= OZ_G (relative weight <= 2^-32) share one FP32
-// accumulator.  After each window the accumulators are folded into an int64
-// fixed-point sum 2^S sum_g I_g 2^(-8g) (the tail rounded to the nearest
-// unit 2^-S) on the integer pipes -- GB300 executes FP64 at 1/64 of FP32 --
-// and depth splits of one tile add their int64 sums with exact, order-free
-// atomics.  C = 2^(e_r + f_c - 16 - S) T, one FP64 scaling per entry.
+// Products.  The slice pairs (i, j) with i + j = g <= 7 (36 pairs; the
+// dropped ones weigh <= 2^-64 of the leading product) are accumulated per
+// shift group g in their own FP32 tensor-memory accumulator, over windows of
+// OZ_WIN = 128 depth indices.  Every partial sum of group g is an integer of
+// magnitude <= (g + 1) 2^14 x 128 <= 2^24, so the tensor core's FP32 sums
+// are exact.  After each window the eight integers I_g are folded on the
+// integer pipes into two int64 sums, hi = sum_{g<4} I_g 2^(24-8g) and
+// lo = sum_{g>=4} I_g 2^(56-8g) (|hi| < 2^59, |lo| < 2^62 for depth <= 2^21),
+// and the depth splits of a tile add theirs with exact, order-free int64
+// atomics.  The product is then exact for the truncated digits:
+//   C = 2^(e_r + f_c - 14) (hi 2^-24 + lo 2^-56),
+// rounded once to FP64 in the combination kernel -- no rounding inside the
+// dot product at all, unlike an FP64 GEMM.
 //
-// Tiles.  One CTA (16 warps) per 128-row tile and depth split; a depth chunk
-// of 64 brings all OZ_S slices of A (7 x 16 KB) and of B (7 x NPAD x 128 B)
-// into shared memory with bulk copies (the slices are stored pre-blocked in
-// the canonical no-swizzle K-major core-matrix layout), one thread issues
-// the 28 pairs x 4 tcgen05.mma (kind::f16, bf16, M = 128, N = NPAD), the
-// completion is committed to an mbarrier; every wait has an iteration limit
-// after which the CTA records an error, waits once more (bounded) for what
-// it issued, frees its tensor memory and returns.
+// Tiles.  A CTA owns 128 rows of A, one block of NPAD <= 64 columns of B
+// (8 accumulators x NPAD <= 512 tensor-memory columns) and a range of depth.
+// Two column blocks of one row tile run as adjacent CTAs, so the second
+// read of A's slices is served by L2.  The slices are stored pre-blocked per
+// 32-deep chunk in the canonical no-swizzle K-major core-matrix layout, the
+// eight slices of a chunk contiguous, so one bulk copy brings a chunk of A
+// (64 KB) and one a chunk of B.  Warp roles: warp 0 copies (two stages in
+// flight), warp 1 issues the 36 x 2 tcgen05.mma of a stage and commits
+// their completion, warps 2-17 fold the accumulators after each window.
+// Every wait has an iteration limit; a role that gives up records an error
+// and raises the CTA's abort flag, the others leave their waits, and the CTA
+// waits (bounded) for the copies and MMAs it issued before it frees its
+// tensor memory.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -47,21 +55,21 @@ namespace mpl {
 
 namespace {
 
-constexpr int OZ_BM = 128;                       // rows of a tile
-constexpr int OZ_BK = 64;                        // depth of a chunk
-constexpr int OZ_WIN_CHUNKS = OZ_WIN / OZ_BK;    // chunks per exact window
-constexpr int OZ_THREADS = 512;  // four warpgroups: each reads a quarter of the columns back
-constexpr int OZ_TILE_A = OZ_BM * OZ_BK;         // elements of one A slice block
-constexpr long long OZ_WAIT_LIMIT = 1LL << 22;   // mbarrier polls before giving up
-static_assert(OZ_WIN % OZ_BK == 0, "window of whole chunks");
+constexpr int OZ_BM = 128;                         // rows of a tile
+constexpr int OZ_STAGES_PER_WIN = OZ_WIN / OZ_BK;  // stages per exact window
+constexpr int OZ_FOLD_WARPS = 16;
+constexpr int OZ_THREADS = 32 * (2 + OZ_FOLD_WARPS);
+constexpr int OZ_TILE_A = OZ_BM * OZ_BK;           // elements of one slice block of A
+constexpr long long OZ_WAIT_LIMIT = 1LL << 22;     // mbarrier polls before giving up
+static_assert(OZ_WIN % OZ_BK == 0, "window of whole stages");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// element offset of (r, kc) in a rows x 64 block, K-major core matrices
-// (8 rows x 8 elements = 128 bytes; 8 of them along the chunk's depth)
-__host__ __device__ __forceinline__ int core_off64(int r, int kc) {
+// element offset of (r, kc) in a rows x 32 block, K-major core matrices
+// (8 rows x 8 elements = 128 bytes; 4 of them along the chunk's depth)
+__host__ __device__ __forceinline__ int core_off32(int r, int kc) {
   return (((r >> 3) * (OZ_BK / 8) + (kc >> 3)) << 6) + ((r & 7) << 3) + (kc & 7);
 }
 
@@ -142,98 +150,97 @@ __global__ void clamp_exp_kernel(int n, int* e) {
     if (e[i] == INT_MIN) e[i] = 0;
 }
 
-__device__ __forceinline__ uint16_t bf16_bits_exact(double q, int i) {
-  // q integer, |q| <= 256: q 2^(-8i) has <= 8 significant bits
-  return __bfloat16_as_ushort(__float2bfloat16_rn((float)ldexp(q, -8 * i)));
-}
-
-// The OZ_S digits of one element u = x 2^(8 - ex) (|u| <= 256).
+// The OZ_S balanced digits of x below the exponent ex (|x| < 2^ex), as bf16
+// bit patterns of the integers q_i (|q_i| <= 128: exact in bf16).
 __device__ __forceinline__ void digits(double x, int ex, uint16_t out[OZ_S]) {
-  double u = ldexp(x, 8 - ex);
+  double u = ldexp(x, 7 - ex);
 #pragma unroll
   for (int i = 0; i < OZ_S; ++i) {
     const double q = rint(u);
-    out[i] = bf16_bits_exact(q, i);
+    out[i] = __bfloat16_as_ushort(__float2bfloat16_rn((float)q));
     u = (u - q) * 256.0;
   }
 }
 
-// Row slices of A (rows padded to ntile * 128, depth to nchunk * 64, zeros
-// outside): slice i of tile t, chunk c is the 128 x 64 block at
-// ((i * ntile + t) * nchunk + c) * 8192.
+__device__ __forceinline__ void store8(uint16_t* dst, const uint16_t v[8]) {
+  uint4 w;
+  w.x = (uint32_t)v[0] | ((uint32_t)v[1] << 16);
+  w.y = (uint32_t)v[2] | ((uint32_t)v[3] << 16);
+  w.z = (uint32_t)v[4] | ((uint32_t)v[5] << 16);
+  w.w = (uint32_t)v[6] | ((uint32_t)v[7] << 16);
+  *reinterpret_cast<uint4*>(dst) = w;
+}
+
+// Row slices of op(A) (n x k; rows padded to ntile * 128, depth to
+// nchunk * 32, zeros outside): slice i of tile t, chunk c is the 128 x 32
+// block at ((t * nchunk + c) * OZ_S + i) * 4096.  One thread per row and 8
+// consecutive depth indices (16-byte stores into one core-matrix row); trans:
+// op(A) = A^T (A^H through the conjugate modes) from storage k x n.
+template <bool TRANS>
 __global__ void split_rows_kernel(int n, int k, const double* __restrict__ A, long long lda, int mode,
                                   const int* __restrict__ e, int ntile, int nchunk, uint16_t* __restrict__ Q) {
-  const long long rows = (long long)ntile * OZ_BM, tot = rows * ((long long)nchunk * OZ_BK);
+  const long long rows = (long long)ntile * OZ_BM, k8 = (long long)nchunk * (OZ_BK / 8);
+  const long long tot = rows * k8;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot;
        id += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(id % rows), kk = (int)(id / rows);
-    const double x = (r < n && kk < k) ? pick(A, r + (long long)kk * lda, mode) : 0.0;
-    uint16_t d[OZ_S];
-    digits(x, r < n ? e[r] : 0, d);
-    const int t = r / OZ_BM, c = kk / OZ_BK;
-    const int off = core_off64(r % OZ_BM, kk % OZ_BK);
+    int r, kb;
+    if (TRANS) { kb = (int)(id % k8); r = (int)(id / k8); }
+    else { r = (int)(id % rows); kb = (int)(id / rows); }
+    const int ex = r < n ? e[r] : 0;
+    uint16_t d[OZ_S][8];
 #pragma unroll
-    for (int i = 0; i < OZ_S; ++i) Q[(((long long)i * ntile + t) * nchunk + c) * OZ_TILE_A + off] = d[i];
+    for (int q = 0; q < 8; ++q) {
+      const int kk = kb * 8 + q;
+      double x = 0.0;
+      if (r < n && kk < k) x = TRANS ? pick(A, kk + (long long)r * lda, mode) : pick(A, r + (long long)kk * lda, mode);
+      uint16_t dq[OZ_S];
+      digits(x, ex, dq);
+#pragma unroll
+      for (int i = 0; i < OZ_S; ++i) d[i][q] = dq[i];
+    }
+    const int t = r / OZ_BM, c = (kb * 8) / OZ_BK;
+    const int off = core_off32(r % OZ_BM, (kb * 8) % OZ_BK);
+#pragma unroll
+    for (int i = 0; i < OZ_S; ++i) store8(Q + (((long long)t * nchunk + c) * OZ_S + i) * OZ_TILE_A + off, d[i]);
   }
 }
 
-// The same row slices of op(A) = A^T (A^H through the conjugate modes) from
-// storage k x n (ld lda): depth runs along the stored columns (coalesced).
-__global__ void split_rows_t_kernel(int n, int k, const double* __restrict__ A, long long lda, int mode,
-                                    const int* __restrict__ e, int ntile, int nchunk, uint16_t* __restrict__ Q) {
-  const long long kpad = (long long)nchunk * OZ_BK, tot = (long long)ntile * OZ_BM * kpad;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot;
-       id += (long long)gridDim.x * blockDim.x) {
-    const int kk = (int)(id % kpad), r = (int)(id / kpad);
-    const double x = (r < n && kk < k) ? pick(A, kk + (long long)r * lda, mode) : 0.0;
-    uint16_t d[OZ_S];
-    digits(x, r < n ? e[r] : 0, d);
-    const int t = r / OZ_BM, c = kk / OZ_BK;
-    const int off = core_off64(r % OZ_BM, kk % OZ_BK);
-#pragma unroll
-    for (int i = 0; i < OZ_S; ++i) Q[(((long long)i * ntile + t) * nchunk + c) * OZ_TILE_A + off] = d[i];
-  }
-}
-
-// Column slices of B (k x m; columns padded to npad, depth to nchunk * 64):
-// slice j of chunk c is the npad x 64 block at (j * nchunk + c) * npad * 64.
+// Column slices of op(B) (k x m; columns padded to ncb * npad, depth to
+// nchunk * 32): slice j of column block b, chunk c is the npad x 32 block at
+// ((b * nchunk + c) * OZ_S + j) * npad * 32.  One thread per column and 8
+// consecutive depth indices; trans: op(B) = B^T (B^H) from storage m x k.
+template <bool TRANS>
 __global__ void split_cols_kernel(int k, int m, const double* __restrict__ B, long long ldb, int mode,
-                                  const int* __restrict__ f, int nchunk, int npad, uint16_t* __restrict__ P) {
-  const long long tot = (long long)npad * nchunk * OZ_BK;
+                                  const int* __restrict__ f, int nchunk, int npad, int ncb, uint16_t* __restrict__ P) {
+  const long long k8 = (long long)nchunk * (OZ_BK / 8), tot = (long long)ncb * npad * k8;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot;
        id += (long long)gridDim.x * blockDim.x) {
-    const int kk = (int)(id % ((long long)nchunk * OZ_BK)), c = (int)(id / ((long long)nchunk * OZ_BK));
-    const double x = (c < m && kk < k) ? pick(B, kk + (long long)c * ldb, mode) : 0.0;
-    uint16_t d[OZ_S];
-    digits(x, c < m ? f[c] : 0, d);
-    const int ch = kk / OZ_BK;
-    const int off = core_off64(c, kk % OZ_BK);
+    const int kb = (int)(id % k8), c = (int)(id / k8);
+    const int ex = c < m ? f[c] : 0;
+    uint16_t d[OZ_S][8];
 #pragma unroll
-    for (int j = 0; j < OZ_S; ++j) P[((long long)j * nchunk + ch) * npad * OZ_BK + off] = d[j];
+    for (int q = 0; q < 8; ++q) {
+      const int kk = kb * 8 + q;
+      double x = 0.0;
+      if (c < m && kk < k) x = TRANS ? pick(B, c + (long long)kk * ldb, mode) : pick(B, kk + (long long)c * ldb, mode);
+      uint16_t dq[OZ_S];
+      digits(x, ex, dq);
+#pragma unroll
+      for (int j = 0; j < OZ_S; ++j) d[j][q] = dq[j];
+    }
+    const int b = c / npad, cc = c % npad, ch = (kb * 8) / OZ_BK;
+    const int off = core_off32(cc, (kb * 8) % OZ_BK);
+#pragma unroll
+    for (int j = 0; j < OZ_S; ++j)
+      store8(P + (((long long)b * nchunk + ch) * OZ_S + j) * npad * OZ_BK + off, d[j]);
   }
 }
 
-// The same column slices of op(B) = B^T (B^H through the conjugate modes)
-// from storage m x k (ld ldb).
-__global__ void split_cols_t_kernel(int k, int m, const double* __restrict__ B, long long ldb, int mode,
-                                    const int* __restrict__ f, int nchunk, int npad, uint16_t* __restrict__ P) {
-  const long long tot = (long long)npad * nchunk * OZ_BK;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot;
-       id += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(id % npad), kk = (int)(id / npad);
-    const double x = (c < m && kk < k) ? pick(B, c + (long long)kk * ldb, mode) : 0.0;
-    uint16_t d[OZ_S];
-    digits(x, c < m ? f[c] : 0, d);
-    const int ch = kk / OZ_BK;
-    const int off = core_off64(c, kk % OZ_BK);
-#pragma unroll
-    for (int j = 0; j < OZ_S; ++j) P[((long long)j * nchunk + ch) * npad * OZ_BK + off] = d[j];
-  }
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  uint32_t done = 0;
-  for (long long it = 0; it < OZ_WAIT_LIMIT && !done; ++it) {
+// Bounded wait on an mbarrier phase; leaves early when the CTA aborts and
+// raises the abort flag when the limit runs out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  for (long long it = 0; it < OZ_WAIT_LIMIT; ++it) {
+    uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -242,172 +249,239 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "=r"(done)
         : "r"(bar), "r"(parity)
         : "memory");
+    if (done) return true;
+    if (*abort_flag) return false;
   }
-  return done != 0;
+  *abort_flag = 1;
+  return false;
 }
 
-// T (rows x NPAD int64, column-major, ld = ntile * 128) += the fixed-point
-// product of the slices of tile blockIdx.x over the chunks of split
-// blockIdx.y.
+// The same wait without the abort exit (teardown: waits for what was issued).
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+  for (long long it = 0; it < OZ_WAIT_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t"
+        "}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return;
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// T (hi at T, lo at T + tlo; column-major, ld ldt) += the exact fixed-point
+// product of row tile blockIdx.x / ncb with column block blockIdx.x % ncb
+// over the chunks of split blockIdx.y.
 template <int NPAD>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-oz_mma_kernel(int ntile, int nchunk, int chunks_per_split, const uint16_t* __restrict__ QA,
-              const uint16_t* __restrict__ PB, long long* __restrict__ T, int S, int* err) {
-  static_assert(NPAD % 32 == 0 && NPAD >= 32 && NPAD <= 96, "N of the tile");
-  constexpr int NACC = OZ_G + 1;                       // exact groups + the tail
-  constexpr int A_BYTES = OZ_TILE_A * 2, B_BYTES = NPAD * OZ_BK * 2;
-  constexpr int QCOLS = NPAD / 4;                      // columns a warp reads back
+oz_mma_kernel(int ncb, int nchunk, int chunks_per_split, const uint16_t* __restrict__ QA,
+              const uint16_t* __restrict__ PB, long long* __restrict__ T, long long ldt, long long tlo, int* err) {
+  static_assert(NPAD % 16 == 0 && NPAD >= 16 && NPAD <= 64, "N of the tile");
+  constexpr int A_BYTES = OZ_S * OZ_TILE_A * 2;          // the 8 slices of one chunk of the row tile
+  constexpr int B_BYTES = OZ_S * NPAD * OZ_BK * 2;       // the 8 slices of one chunk of the column block
+  constexpr int STAGE = A_BYTES + B_BYTES;
+  constexpr int QC = NPAD / 4;                           // columns a fold warp reads back
   extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char* sA = sm;                              // OZ_S slices of A
-  unsigned char* sB = sm + OZ_S * A_BYTES;             // OZ_S slices of B
-  __shared__ __align__(8) uint64_t bar_load, bar_mma;
+  __shared__ __align__(8) uint64_t bar_full[2], bar_empty[2], bar_accf, bar_acce;
   __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  __shared__ int issued, committed;                      // stages copied / whose MMAs were committed
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-  const int t = blockIdx.x;
+  const int tile = blockIdx.x / ncb, cb = blockIdx.x % ncb;
   const int c0 = blockIdx.y * chunks_per_split, c1 = min(nchunk, c0 + chunks_per_split);
+  const int nst = c1 - c0;
+  const int nwin = (nst + OZ_STAGES_PER_WIN - 1) / OZ_STAGES_PER_WIN;
 
-  if (wid == 0) {
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_full[b])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_empty[b])), "r"(1));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_accf)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_acce)), "r"(OZ_FOLD_WARPS));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_flag = 0;
+    issued = 0;
+    committed = 0;
+  }
+  if (wid == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                  "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_load)), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_mma)), "r"(1));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  const uint32_t bl = smem_u32(&bar_load), bm = smem_u32(&bar_mma);
+  const uint32_t sbase = smem_u32(sm);
 
-  long long acc[QCOLS];
-#pragma unroll
-  for (int q = 0; q < QCOLS; ++q) acc[q] = 0;
-  const int lg = wid & 3, ch = wid >> 2;               // accumulator lanes 32 lg.., columns ch * QCOLS..
-  uint32_t fresh = (1u << NACC) - 1;                   // bit g: accumulator g starts a new window
-  bool ok = true;
-  uint32_t phase = 0;
-
-  for (int c = c0; c < c1 && ok; ++c, phase ^= 1u) {
-    if (tid == 0) {
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bl),
-                   "r"((uint32_t)(OZ_S * (A_BYTES + B_BYTES)))
-                   : "memory");
-      for (int i = 0; i < OZ_S; ++i) {
-        const uint16_t* ga = QA + (((long long)i * ntile + t) * nchunk + c) * OZ_TILE_A;
-        const uint16_t* gb = PB + ((long long)i * nchunk + c) * NPAD * OZ_BK;
+  if (wid == 0) {
+    // ---- producer: one bulk copy of A's and one of B's slices per stage
+    if (lane == 0) {
+      for (int s = 0; s < nst; ++s) {
+        const int b = s & 1, r = s >> 1;
+        if (r > 0 && !mbar_wait(smem_u32(&bar_empty[b]), (r - 1) & 1, &abort_flag)) break;
+        const uint32_t fb = smem_u32(&bar_full[b]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"((uint32_t)STAGE)
+                     : "memory");
+        const uint16_t* ga = QA + ((long long)tile * nchunk + c0 + s) * OZ_S * OZ_TILE_A;
+        const uint16_t* gb = PB + ((long long)cb * nchunk + c0 + s) * OZ_S * NPAD * OZ_BK;
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_u32(sA + i * A_BYTES)),
-            "l"(ga), "r"((uint32_t)A_BYTES), "r"(bl)
+                sbase + b * STAGE),
+            "l"(ga), "r"((uint32_t)A_BYTES), "r"(fb)
             : "memory");
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_u32(sB + i * B_BYTES)),
-            "l"(gb), "r"((uint32_t)B_BYTES), "r"(bl)
+                sbase + b * STAGE + A_BYTES),
+            "l"(gb), "r"((uint32_t)B_BYTES), "r"(fb)
             : "memory");
+        issued = s + 1;
       }
     }
-    ok = __syncthreads_and(mbar_wait(bl, phase));
-    if (!ok) break;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (tid == 0) {
+  } else if (wid == 1) {
+    // ---- MMA issuer: 36 slice pairs x 2 depth steps per stage
+    if (lane == 0) {
       constexpr uint32_t LBO = 128, SBO = (OZ_BK / 8) * 128;
       constexpr uint32_t idesc = idesc_bf16(OZ_BM, NPAD);
-      for (int i = 0; i < OZ_S; ++i)
-        for (int j = 0; i + j < OZ_S; ++j) {
-          const int g = min(i + j, OZ_G);
+      uint32_t fresh = 0;
+      for (int s = 0; s < nst; ++s) {
+        const int b = s & 1, r = s >> 1, w = s / OZ_STAGES_PER_WIN;
+        const bool first = (s % OZ_STAGES_PER_WIN) == 0;
+        if (first && w > 0 && !mbar_wait(smem_u32(&bar_acce), (w - 1) & 1, &abort_flag)) break;
+        if (!mbar_wait(smem_u32(&bar_full[b]), r & 1, &abort_flag)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (first) fresh = 0xFFu;
+        const uint32_t sa = sbase + b * STAGE, sb = sa + A_BYTES;
+#pragma unroll 1
+        for (int g = 0; g < OZ_S; ++g) {
           const uint32_t d_tmem = tmem + (uint32_t)(g * NPAD);
+#pragma unroll 1
+          for (int i = 0; i <= g; ++i) {
+            const int j = g - i;
 #pragma unroll
-          for (int kk = 0; kk < OZ_BK / 16; ++kk) {
-            const uint64_t da = smem_desc(smem_u32(sA + i * A_BYTES) + kk * 256, LBO, SBO);
-            const uint64_t db = smem_desc(smem_u32(sB + j * B_BYTES) + kk * 256, LBO, SBO);
-            const uint32_t accum = ((fresh >> g) & 1u) ? 0u : 1u;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\t"
-                "setp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t"
-                "}" ::"r"(d_tmem),
-                "l"(da), "l"(db), "r"(idesc), "r"(accum)
-                : "memory");
-            fresh &= ~(1u << g);
+            for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+              const uint64_t da = smem_desc(sa + i * (OZ_TILE_A * 2) + kk * 256, LBO, SBO);
+              const uint64_t db = smem_desc(sb + j * (NPAD * OZ_BK * 2) + kk * 256, LBO, SBO);
+              const uint32_t accum = ((fresh >> g) & 1u) ? 0u : 1u;
+              asm volatile(
+                  "{\n\t.reg .pred p;\n\t"
+                  "setp.ne.b32 p, %4, 0;\n\t"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t"
+                  "}" ::"r"(d_tmem),
+                  "l"(da), "l"(db), "r"(idesc), "r"(accum)
+                  : "memory");
+              fresh &= ~(1u << g);
+            }
           }
         }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bm)
-                   : "memory");
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&bar_empty[b]))
+                     : "memory");
+        if ((s % OZ_STAGES_PER_WIN) == OZ_STAGES_PER_WIN - 1 || s == nst - 1)
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&bar_accf))
+                       : "memory");
+        committed = s + 1;
+      }
     }
-    ok = __syncthreads_and(mbar_wait(bm, phase));
-    if (!ok) break;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const bool flush = ((c - c0) % OZ_WIN_CHUNKS == OZ_WIN_CHUNKS - 1) || (c == c1 - 1);
-    if (flush) {
-      // fold the window into the int64 sum: group g holds I_g 2^(-8g) exactly
+  } else {
+    // ---- fold warps: accumulator lanes 32 (wid % 4) .., columns QC * ((wid - 2) / 4) ..
+    const int lg = wid & 3, ch = (wid - 2) >> 2;
+    long long hi[QC], lo[QC];
 #pragma unroll
-      for (int c8 = 0; c8 < QCOLS; c8 += 8) {
+    for (int q = 0; q < QC; ++q) hi[q] = lo[q] = 0;
+    bool ok = true;
+    for (int w = 0; w < nwin && ok; ++w) {
+      ok = mbar_wait(smem_u32(&bar_accf), w & 1, &abort_flag);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int g = 0; g < NACC; ++g) {
-          uint32_t v[8];
-          const uint32_t taddr = tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(g * NPAD + ch * QCOLS + c8);
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                         "=r"(v[7])
+      for (int c4 = 0; c4 < QC; c4 += 4) {
+#pragma unroll
+        for (int g = 0; g < OZ_S; ++g) {
+          uint32_t v[4];
+          const uint32_t taddr = tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(g * NPAD + ch * QC + c4);
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
                        : "r"(taddr));
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const float x = __uint_as_float(v[q]);
-            if (g < OZ_G)  // I_g = x 2^(8g), an integer below 2^24: exact conversions
-              acc[c8 + q] += (long long)__float2int_rn(ldexpf(x, 8 * g)) * (1LL << (S - 8 * g));
-            else           // the tail, rounded to the unit 2^-S
-              acc[c8 + q] += __float2ll_rn(ldexpf(x, S));
+          for (int q = 0; q < 4; ++q) {
+            const long long I = __float2ll_rn(__uint_as_float(v[q]));  // an integer below 2^24: exact
+            if (g < 4) hi[c4 + q] += I * (1LL << (24 - 8 * g));
+            else lo[c4 + q] += I * (1LL << (56 - 8 * g));
           }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();
-      fresh = (1u << NACC) - 1;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bar_acce));
+    }
+    if (ok) {
+      const long long row = (long long)tile * OZ_BM + 32 * lg + lane;
+#pragma unroll
+      for (int q = 0; q < QC; ++q) {
+        const long long col = (long long)cb * NPAD + ch * QC + q;
+        atomicAdd(reinterpret_cast<unsigned long long*>(T + row + col * ldt), (unsigned long long)hi[q]);
+        atomicAdd(reinterpret_cast<unsigned long long*>(T + tlo + row + col * ldt), (unsigned long long)lo[q]);
+      }
     }
   }
-  if (!ok) {
-    if (tid == 0) atomicExch(err, 1);
-    // let whatever was issued finish (bounded) before the memory is released
-    mbar_wait(bl, phase);
-    mbar_wait(bm, phase);
-  } else {
-    const long long ldt = (long long)ntile * OZ_BM;
-    const long long row = (long long)t * OZ_BM + 32 * lg + lane;
-#pragma unroll
-    for (int q = 0; q < QCOLS; ++q)
-      atomicAdd(reinterpret_cast<unsigned long long*>(T + row + (long long)(ch * QCOLS + q) * ldt),
-                (unsigned long long)acc[q]);
+  __syncthreads();
+  if (abort_flag) {
+    if (tid == 0) {
+      atomicExch(err, 1);
+      // let the copies and MMAs that were issued finish (bounded) before the
+      // shared and tensor memory are released
+      for (int s = max(0, issued - 2); s < issued; ++s) mbar_drain(smem_u32(&bar_full[s & 1]), (s >> 1) & 1);
+      for (int s = max(0, committed - 2); s < committed; ++s) mbar_drain(smem_u32(&bar_empty[s & 1]), (s >> 1) & 1);
+    }
+    __syncthreads();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (wid == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  if (wid == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
-// C(r, c) = 2^(e_r + f_c - 16 - S) T(r, c)   (real), or the 3M combination
-// of three such products (complex): Re = T1 - T2, Im = T3 - T1 - T2.
-__global__ void combine_real_kernel(int n, int m, const long long* __restrict__ T, long long ldt,
-                                    const int* __restrict__ e, const int* __restrict__ f, int S, double alpha,
-                                    double beta, int lower_only, int col0, double* __restrict__ C, long long ldc) {
+// value of one accumulator pair in units of the leading digit product:
+// hi 2^-24 + lo 2^-56, from an exact split into a 53-bit-safe part and the
+// low 32 bits of lo, times 2^ex
+__device__ __forceinline__ double fixed_value(long long hi, long long lo, int ex) {
+  const long long top = hi + (lo >> 32);            // lo = (lo >> 32) 2^32 + (lo & 0xffffffff)
+  const long long low = lo & 0xFFFFFFFFLL;
+  return ldexp((double)top, ex - 24) + ldexp((double)low, ex - 56);
+}
+
+// C(r, c) = alpha 2^(e_r + f_c - 14) (hi 2^-24 + lo 2^-56) (+ beta C)
+__global__ void combine_real_kernel(int n, int m, const long long* __restrict__ T, long long ldt, long long tlo,
+                                    const int* __restrict__ e, const int* __restrict__ f, double alpha, double beta,
+                                    int lower_only, int col0, double* __restrict__ C, long long ldc) {
   const long long tot = (long long)n * m;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot;
        id += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(id % n), c = (int)(id / n);
     if (lower_only && r < col0 + c) continue;
-    double v = alpha * ldexp((double)T[r + c * ldt], e[r] + f[c] - 16 - S);
+    const long long t = r + c * ldt;
+    double v = alpha * fixed_value(T[t], T[tlo + t], e[r] + f[c] - 14);
     if (beta != 0.0) v += beta * C[r + c * ldc];
     C[r + c * ldc] = v;
   }
 }
 
-__global__ void combine_3m_kernel(int n, int m, const long long* __restrict__ T, long long ldt, long long tstride,
-                                  const int* __restrict__ e, int estride, const int* __restrict__ f, int fstride,
-                                  int S, double alpha, double beta, int lower_only, int col0, double* __restrict__ C,
-                                  long long ldc) {
+// The 3M combination of three such products: Re = T1 - T2, Im = T3 - T1 - T2.
+__global__ void combine_3m_kernel(int n, int m, const long long* __restrict__ T, long long ldt, long long tlo,
+                                  long long tstride, const int* __restrict__ e, int estride,
+                                  const int* __restrict__ f, int fstride, double alpha, double beta, int lower_only,
+                                  int col0, double* __restrict__ C, long long ldc) {
   const long long tot = (long long)n * m;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot;
        id += (long long)gridDim.x * blockDim.x) {
@@ -415,8 +489,10 @@ __global__ void combine_3m_kernel(int n, int m, const long long* __restrict__ T,
     if (lower_only && r < col0 + c) continue;
     double p[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q)
-      p[q] = ldexp((double)T[q * tstride + r + c * ldt], e[q * estride + r] + f[q * fstride + c] - 16 - S);
+    for (int q = 0; q < 3; ++q) {
+      const long long t = q * tstride + r + c * ldt;
+      p[q] = fixed_value(T[t], T[tlo + t], e[q * estride + r] + f[q * fstride + c] - 14);
+    }
     double re = alpha * (p[0] - p[1]), im = alpha * (p[2] - p[0] - p[1]);
     if (beta != 0.0) {
       re += beta * C[2 * (r + c * ldc)];
@@ -431,109 +507,103 @@ inline int grid_for(long long tot) { return (int)std::min<long long>((tot + 255)
 
 }  // namespace
 
-// Fixed-point shift: with W windows of depth 128 the int64 sum stays below
-// W * 2^(23.01 + S) < 2^63.
-int oz_shift(long long k) {
-  const long long w = std::max<long long>(1, (k + OZ_WIN - 1) / OZ_WIN);
-  int lw = 0;
-  while ((1LL << lw) < w) ++lw;
-  return std::min(32, 39 - lw);
-}
+int oz_npad(int m) { return m <= 16 ? 16 : m <= 32 ? 32 : m <= 48 ? 48 : m <= 64 ? 64 : 48; }
+int oz_ncb(int m) { return (m + oz_npad(m) - 1) / oz_npad(m); }
+long long oz_t_rows(int n) { return (long long)((n + OZ_BM - 1) / OZ_BM) * OZ_BM; }
+size_t oz_t_elems(int n, int m) { return (size_t)2 * oz_t_rows(n) * oz_ncb(m) * oz_npad(m); }
 
 size_t oz_a_elems(int n, int k) {
   const long long ntile = (n + OZ_BM - 1) / OZ_BM, nchunk = (k + OZ_BK - 1) / OZ_BK;
   return (size_t)OZ_S * ntile * OZ_BM * nchunk * OZ_BK;
 }
-size_t oz_b_elems(int k, int npad) {
+size_t oz_b_elems(int k, int m) {
   const long long nchunk = (k + OZ_BK - 1) / OZ_BK;
-  return (size_t)OZ_S * npad * nchunk * OZ_BK;
+  return (size_t)OZ_S * oz_ncb(m) * oz_npad(m) * nchunk * OZ_BK;
 }
-int oz_npad(int m) { return m <= 32 ? 32 : m <= 64 ? 64 : 96; }
 
 void oz_split_a(cudaStream_t st, int mode, int n, int k, const double* A, long long lda, int* e, uint16_t* Q,
                 bool trans) {
   const int ntile = (n + OZ_BM - 1) / OZ_BM, nchunk = (k + OZ_BK - 1) / OZ_BK;
+  const long long tot = (long long)ntile * OZ_BM * nchunk * (OZ_BK / 8);
   if (trans) {
     // row r of op(A) is stored column r: one block per row reduces its exponent
     count_launch(2);
     col_exp_kernel<<<n, 256, 0, st>>>(k, A, lda, mode, e);
-    const long long tot = (long long)ntile * OZ_BM * nchunk * OZ_BK;
-    split_rows_t_kernel<<<grid_for(tot), 256, 0, st>>>(n, k, A, lda, mode, e, ntile, nchunk, Q);
+    split_rows_kernel<true><<<grid_for(tot), 256, 0, st>>>(n, k, A, lda, mode, e, ntile, nchunk, Q);
     return;
   }
-  count_launch(3);
+  count_launch(4);
   fill_int_kernel<<<grid_for(n), 256, 0, st>>>(n, e, INT_MIN);
   row_exp_kernel<<<dim3((n + 255) / 256, (k + 255) / 256), 256, 0, st>>>(n, k, A, lda, mode, e);
   clamp_exp_kernel<<<grid_for(n), 256, 0, st>>>(n, e);
-  const long long tot = (long long)ntile * OZ_BM * nchunk * OZ_BK;
-  count_launch();
-  split_rows_kernel<<<grid_for(tot), 256, 0, st>>>(n, k, A, lda, mode, e, ntile, nchunk, Q);
+  split_rows_kernel<false><<<grid_for(tot), 256, 0, st>>>(n, k, A, lda, mode, e, ntile, nchunk, Q);
 }
 
 void oz_split_b(cudaStream_t st, int mode, int k, int m, const double* B, long long ldb, int* f, uint16_t* P,
                 bool trans) {
-  const int npad = oz_npad(m), nchunk = (k + OZ_BK - 1) / OZ_BK;
+  const int npad = oz_npad(m), ncb = oz_ncb(m), nchunk = (k + OZ_BK - 1) / OZ_BK;
+  const long long tot = (long long)ncb * npad * nchunk * (OZ_BK / 8);
   if (trans) {
     // column c of op(B) is stored row c: row maxima by atomics
     count_launch(4);
     fill_int_kernel<<<grid_for(m), 256, 0, st>>>(m, f, INT_MIN);
     row_exp_kernel<<<dim3((m + 255) / 256, (k + 255) / 256), 256, 0, st>>>(m, k, B, ldb, mode, f);
     clamp_exp_kernel<<<grid_for(m), 256, 0, st>>>(m, f);
-    const long long tot = (long long)npad * nchunk * OZ_BK;
-    split_cols_t_kernel<<<grid_for(tot), 256, 0, st>>>(k, m, B, ldb, mode, f, nchunk, npad, P);
+    split_cols_kernel<true><<<grid_for(tot), 256, 0, st>>>(k, m, B, ldb, mode, f, nchunk, npad, ncb, P);
     return;
   }
   count_launch(2);
   col_exp_kernel<<<m, 256, 0, st>>>(k, B, ldb, mode, f);
-  const long long tot = (long long)npad * nchunk * OZ_BK;
-  split_cols_kernel<<<grid_for(tot), 256, 0, st>>>(k, m, B, ldb, mode, f, nchunk, npad, P);
+  split_cols_kernel<false><<<grid_for(tot), 256, 0, st>>>(k, m, B, ldb, mode, f, nchunk, npad, ncb, P);
 }
 
 template <int NPAD>
-static void launch_mma(cudaStream_t st, int ntile, int nchunk, int nsplit, int cps, const uint16_t* Q,
-                       const uint16_t* P, long long* T, int S, int* err) {
-  const size_t sm = (size_t)OZ_S * (OZ_TILE_A * 2 + NPAD * OZ_BK * 2);
+static void launch_mma(cudaStream_t st, int ntile, int ncb, int nchunk, int nsplit, int cps, const uint16_t* Q,
+                       const uint16_t* P, long long* T, long long ldt, long long tlo, int* err) {
+  const size_t sm = (size_t)2 * (OZ_S * OZ_TILE_A * 2 + OZ_S * NPAD * OZ_BK * 2);
   // one attribute call per instantiation (thread-safe static initialisation)
   static const bool opened =
       cudaFuncSetAttribute(oz_mma_kernel<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) ==
       cudaSuccess;
   (void)opened;
   count_launch();
-  oz_mma_kernel<NPAD><<<dim3(ntile, nsplit), OZ_THREADS, sm, st>>>(ntile, nchunk, cps, Q, P, T, S, err);
+  oz_mma_kernel<NPAD><<<dim3(ntile * ncb, nsplit), OZ_THREADS, sm, st>>>(ncb, nchunk, cps, Q, P, T, ldt, tlo, err);
 }
 
-// T (ntile * 128 x npad int64, zeroed by the caller) += fixed-point A B.
 void oz_mma(cudaStream_t st, int n, int k, int m, const uint16_t* Q, const uint16_t* P, long long* T, int* err) {
   const int ntile = (n + OZ_BM - 1) / OZ_BM, nchunk = (k + OZ_BK - 1) / OZ_BK;
-  const int npad = oz_npad(m);
+  const int npad = oz_npad(m), ncb = oz_ncb(m);
   // depth splits of whole windows: about 8 waves of one CTA per SM per launch
-  const int want = std::max(1, (8 * NUM_SMS + ntile - 1) / ntile);
-  const int nwin = (nchunk + OZ_WIN_CHUNKS - 1) / OZ_WIN_CHUNKS;
+  const int tiles = ntile * ncb;
+  const int want = std::max(1, (8 * NUM_SMS + tiles - 1) / tiles);
+  const int nwin = (nchunk + OZ_STAGES_PER_WIN - 1) / OZ_STAGES_PER_WIN;
   const int nsplit = std::min(want, nwin);
-  const int cps = ((nwin + nsplit - 1) / nsplit) * OZ_WIN_CHUNKS;
+  const int cps = ((nwin + nsplit - 1) / nsplit) * OZ_STAGES_PER_WIN;
   const int nsp = (nchunk + cps - 1) / cps;
-  const int S = oz_shift(k);
-  if (npad == 32) launch_mma<32>(st, ntile, nchunk, nsp, cps, Q, P, T, S, err);
-  else if (npad == 64) launch_mma<64>(st, ntile, nchunk, nsp, cps, Q, P, T, S, err);
-  else launch_mma<96>(st, ntile, nchunk, nsp, cps, Q, P, T, S, err);
+  const long long ldt = oz_t_rows(n), tlo = ldt * ncb * npad;
+  switch (npad) {
+    case 16: launch_mma<16>(st, ntile, ncb, nchunk, nsp, cps, Q, P, T, ldt, tlo, err); break;
+    case 32: launch_mma<32>(st, ntile, ncb, nchunk, nsp, cps, Q, P, T, ldt, tlo, err); break;
+    case 48: launch_mma<48>(st, ntile, ncb, nchunk, nsp, cps, Q, P, T, ldt, tlo, err); break;
+    default: launch_mma<64>(st, ntile, ncb, nchunk, nsp, cps, Q, P, T, ldt, tlo, err); break;
+  }
 }
 
-void oz_combine_real(cudaStream_t st, int n, int m, const long long* T, long long ldt, const int* e, const int* f,
-                     int S, double* C, long long ldc, double alpha, double beta, bool lower_only, int col0) {
+void oz_combine_real(cudaStream_t st, int n, int m, const long long* T, const int* e, const int* f, double* C,
+                     long long ldc, double alpha, double beta, bool lower_only, int col0) {
+  const long long ldt = oz_t_rows(n), tlo = (long long)oz_t_elems(n, m) / 2;
   count_launch();
-  combine_real_kernel<<<grid_for((long long)n * m), 256, 0, st>>>(n, m, T, ldt, e, f, S, alpha, beta,
+  combine_real_kernel<<<grid_for((long long)n * m), 256, 0, st>>>(n, m, T, ldt, tlo, e, f, alpha, beta,
                                                                    lower_only ? 1 : 0, col0, C, ldc);
 }
 
-void oz_combine_3m(cudaStream_t st, int n, int m, const long long* T, long long ldt, long long tstride, const int* e,
-                   int estride, const int* f, int fstride, int S, double* C, long long ldc, double alpha, double beta,
-                   bool lower_only, int col0) {
+void oz_combine_3m(cudaStream_t st, int n, int m, const long long* T, const int* e, int estride, const int* f,
+                   int fstride, double* C, long long ldc, double alpha, double beta, bool lower_only, int col0) {
+  const long long ldt = oz_t_rows(n), tt = (long long)oz_t_elems(n, m), tlo = tt / 2;
   count_launch();
-  combine_3m_kernel<<<grid_for((long long)n * m), 256, 0, st>>>(n, m, T, ldt, tstride, e, estride, f, fstride, S,
+  combine_3m_kernel<<<grid_for((long long)n * m), 256, 0, st>>>(n, m, T, ldt, tlo, tt, e, estride, f, fstride,
                                                                  alpha, beta, lower_only ? 1 : 0, col0, C, ldc);
 }
-
-long long oz_t_rows(int n) { return (long long)((n + OZ_BM - 1) / OZ_BM) * OZ_BM; }
 
 }  // namespace mpl
 
@@ -578,13 +648,11 @@ bool oz_gemm_requested() {
 bool oz_gemm_fp64(cudaStream_t st, bool cx, bool ta, bool tb, int M, int N, int K, double alpha, const double* A,
                   long long lda, const double* B, long long ldb, double beta, double* C, long long ldc,
                   bool lower_only) {
-  if (M < 1 || N < 1 || K < 1 || K > (1 << 21) || oz_shift(K) < 24 || !(beta == 0.0 || beta == 1.0)) return false;
+  if (M < 1 || N < 1 || K < 1 || K > (1 << 21) || !(beta == 0.0 || beta == 1.0)) return false;
   std::lock_guard<std::mutex> lock(pool_mutex());
   OzPool& P = pools()[st];
   const int np = cx ? 3 : 1, elt = cx ? 2 : 1;
-  const size_t qa = oz_a_elems(M, K), pb = oz_b_elems(K, 96);
-  const long long trows = oz_t_rows(M);
-  const size_t tt = (size_t)trows * 96;
+  const size_t qa = oz_a_elems(M, K), pb = oz_b_elems(K, OZ_MAXM), tmax = oz_t_elems(M, OZ_MAXM);
   if (!P.err) {
     if (cudaMalloc(&P.err, sizeof(int)) != cudaSuccess) {
       cudaGetLastError();
@@ -593,8 +661,8 @@ bool oz_gemm_fp64(cudaStream_t st, bool cx, bool ta, bool tb, int M, int N, int 
     }
     cudaMemsetAsync(P.err, 0, sizeof(int), st);
   }
-  if (!P.grow(0, sizeof(int) * np * M) || !P.grow(1, sizeof(int) * np * 96) || !P.grow(2, 2 * np * qa) ||
-      !P.grow(3, 2 * np * pb) || !P.grow(4, sizeof(long long) * np * tt))
+  if (!P.grow(0, sizeof(int) * np * M) || !P.grow(1, sizeof(int) * np * OZ_MAXM) || !P.grow(2, 2 * np * qa) ||
+      !P.grow(3, 2 * np * pb) || !P.grow(4, sizeof(long long) * np * tmax))
     return false;
   int* e = static_cast<int*>(P.p[0]);
   int* f = static_cast<int*>(P.p[1]);
@@ -604,17 +672,18 @@ bool oz_gemm_fp64(cudaStream_t st, bool cx, bool ta, bool tb, int M, int N, int 
   // 3M operands: re, im, re + im; of a conjugate transpose: re, -im, re - im
   auto mode_of = [&](int p, bool t) { return !cx ? 0 : !t ? p + 1 : (p == 0 ? 1 : p == 1 ? 4 : 5); };
   for (int p = 0; p < np; ++p) oz_split_a(st, mode_of(p, ta), M, K, A, lda, e + p * M, Q + p * qa, ta);
-  const int S = oz_shift(K);
-  for (int c0 = 0; c0 < N; c0 += 96) {
-    const int nb = std::min(96, N - c0);
+  for (int c0 = 0; c0 < N; c0 += OZ_MAXM) {
+    const int nb = std::min(OZ_MAXM, N - c0);
+    const size_t tt = oz_t_elems(M, nb);
     // columns c0.. of op(B): stored columns (no transpose) or stored rows
     const double* Bc = B + (size_t)elt * (tb ? (size_t)c0 : (size_t)c0 * ldb);
     cudaMemsetAsync(T, 0, sizeof(long long) * np * tt, st);
-    for (int p = 0; p < np; ++p) oz_split_b(st, mode_of(p, tb), K, nb, Bc, ldb, f + p * 96, Pb + p * pb, tb);
+    for (int p = 0; p < np; ++p)
+      oz_split_b(st, mode_of(p, tb), K, nb, Bc, ldb, f + p * OZ_MAXM, Pb + p * pb, tb);
     for (int p = 0; p < np; ++p) oz_mma(st, M, K, nb, Q + p * qa, Pb + p * pb, T + p * tt, P.err);
     double* Cc = C + (size_t)elt * c0 * ldc;
-    if (cx) oz_combine_3m(st, M, nb, T, trows, (long long)tt, e, M, f, 96, S, Cc, ldc, alpha, beta, lower_only, c0);
-    else oz_combine_real(st, M, nb, T, trows, e, f, S, Cc, ldc, alpha, beta, lower_only, c0);
+    if (cx) oz_combine_3m(st, M, nb, T, e, M, f, OZ_MAXM, Cc, ldc, alpha, beta, lower_only, c0);
+    else oz_combine_real(st, M, nb, T, e, f, Cc, ldc, alpha, beta, lower_only, c0);
   }
   return true;
 }
@@ -640,15 +709,13 @@ int oz_take_error(cudaStream_t st) {
 extern "C" mpl_status mpl_step_split_gemm(int is_complex, int trans_a, int64_t n, int64_t k, int64_t m,
                                           const void* A, int64_t lda, const void* B, int64_t ldb, void* C,
                                           int64_t ldc, void* stream) {
-  if (n < 1 || k < 1 || m < 1 || m > 96 || !A || !B || !C || lda < (trans_a ? k : n) || ldb < k || ldc < n ||
-      n > (1LL << 30) || k > (1LL << 21) || mpl::oz_shift(k) < 24)
+  if (n < 1 || k < 1 || m < 1 || m > mpl::OZ_MAXM || !A || !B || !C || lda < (trans_a ? k : n) || ldb < k ||
+      ldc < n || n > (1LL << 30) || k > (1LL << 21))
     return MPL_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int np = is_complex ? 3 : 1;
-  const int npad = mpl::oz_npad((int)m);
-  const long long trows = mpl::oz_t_rows((int)n);
-  const size_t qa = mpl::oz_a_elems((int)n, (int)k), pb = mpl::oz_b_elems((int)k, npad);
-  const size_t tt = (size_t)trows * npad;
+  const size_t qa = mpl::oz_a_elems((int)n, (int)k), pb = mpl::oz_b_elems((int)k, (int)m);
+  const size_t tt = mpl::oz_t_elems((int)n, (int)m);
   int *e = nullptr, *f = nullptr, *err = nullptr;
   uint16_t *Q = nullptr, *P = nullptr;
   long long* T = nullptr;
@@ -678,14 +745,12 @@ extern "C" mpl_status mpl_step_split_gemm(int is_complex, int trans_a, int64_t n
       mpl::oz_split_a(st, amode, (int)n, (int)k, a, lda, e + p * n, Q + p * qa, trans_a != 0);
       mpl::oz_split_b(st, mode, (int)k, (int)m, b, ldb, f + p * m, P + p * pb);
     }
-    for (int p = 0; p < np; ++p)
-      mpl::oz_mma(st, (int)n, (int)k, (int)m, Q + p * qa, P + p * pb, T + p * tt, err);
-    const int S = mpl::oz_shift(k);
+    for (int p = 0; p < np; ++p) mpl::oz_mma(st, (int)n, (int)k, (int)m, Q + p * qa, P + p * pb, T + p * tt, err);
     if (is_complex)
-      mpl::oz_combine_3m(st, (int)n, (int)m, T, trows, (long long)tt, e, (int)n, f, (int)m, S,
-                         static_cast<double*>(C), ldc, 1.0, 0.0, false, 0);
+      mpl::oz_combine_3m(st, (int)n, (int)m, T, e, (int)n, f, (int)m, static_cast<double*>(C), ldc, 1.0, 0.0, false,
+                         0);
     else
-      mpl::oz_combine_real(st, (int)n, (int)m, T, trows, e, f, S, static_cast<double*>(C), ldc, 1.0, 0.0, false, 0);
+      mpl::oz_combine_real(st, (int)n, (int)m, T, e, f, static_cast<double*>(C), ldc, 1.0, 0.0, false, 0);
     if (cudaGetLastError() != cudaSuccess) s = MPL_ECUDA;
     if (s == MPL_OK && (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                         cudaStreamSynchronize(st) != cudaSuccess))

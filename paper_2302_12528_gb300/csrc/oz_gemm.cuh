@@ -8,34 +8,38 @@
 
 namespace mpl {
 
-constexpr int OZ_S = 7;      // 8-bit digits per operand entry (56 bits below the row / column exponent)
-constexpr int OZ_G = 4;      // slice-pair groups i + j = g accumulated exactly
-constexpr int OZ_WIN = 128;  // depth of an exact accumulation window
+constexpr int OZ_S = 8;      // balanced 8-bit digits per operand entry (|digit| <= 128)
+constexpr int OZ_BK = 32;    // depth of one pipeline stage
+constexpr int OZ_WIN = 128;  // depth of an exact accumulation window (a multiple of OZ_BK)
+constexpr int OZ_MAXM = 96;  // columns of op(B) per oz_mma call
 
-// fixed-point shift S for depth k (S >= 24 needed: k <= 2^21)
-int oz_shift(long long k);
-int oz_npad(int m);                    // N of the tile: 32, 64 or 96 (m <= 96)
+int oz_npad(int m);                    // N of a column block: 16, 32, 48 or 64
+int oz_ncb(int m);                     // column blocks of width oz_npad(m) covering m (m <= 96)
 size_t oz_a_elems(int n, int k);       // bf16 elements of the row slices of an n x k operand
-size_t oz_b_elems(int k, int npad);    // bf16 elements of the column slices of a k x m operand
-long long oz_t_rows(int n);            // rows (= leading dimension) of the int64 accumulator
+size_t oz_b_elems(int k, int m);       // bf16 elements of the column slices of a k x m operand
+long long oz_t_rows(int n);            // rows (= leading dimension) of the int64 accumulators
+size_t oz_t_elems(int n, int m);       // int64 elements of one product's accumulators (hi and lo)
 
 // mode: 0 real FP64 storage; complex interleaved storage: 1 re, 2 im, 3 re + im,
 // and of the conjugate 4 -im, 5 re - im.  trans: A is stored k x n and
 // op(A) = its transpose (with the conjugate modes: A^H).
 void oz_split_a(cudaStream_t st, int mode, int n, int k, const double* A, long long lda, int* e, uint16_t* Q,
                 bool trans = false);
-// trans: B is stored m x k and op(B) = its transpose (conjugate modes: B^H)
+// trans: B is stored m x k and op(B) = its transpose (conjugate modes: B^H); m <= 96
 void oz_split_b(cudaStream_t st, int mode, int k, int m, const double* B, long long ldb, int* f, uint16_t* P,
                 bool trans = false);
-// T (oz_t_rows(n) x oz_npad(m) int64, zeroed) += the fixed-point product
+// T (oz_t_elems(n, m) int64, zeroed by the caller) += the exact fixed-point
+// product of the slices: hi at T, lo at T + oz_t_elems(n, m) / 2.
 void oz_mma(cudaStream_t st, int n, int k, int m, const uint16_t* Q, const uint16_t* P, long long* T, int* err);
 // C = alpha (the product) + beta C (beta 0: C not read); lower_only skips
-// rows above the diagonal (col0: the first column's index in C)
-void oz_combine_real(cudaStream_t st, int n, int m, const long long* T, long long ldt, const int* e, const int* f,
-                     int S, double* C, long long ldc, double alpha, double beta, bool lower_only, int col0);
-void oz_combine_3m(cudaStream_t st, int n, int m, const long long* T, long long ldt, long long tstride, const int* e,
-                   int estride, const int* f, int fstride, int S, double* C, long long ldc, double alpha, double beta,
-                   bool lower_only, int col0);
+// rows above the diagonal (col0: the first column's index in C).  T as
+// written by oz_mma for the same n, m.
+void oz_combine_real(cudaStream_t st, int n, int m, const long long* T, const int* e, const int* f, double* C,
+                     long long ldc, double alpha, double beta, bool lower_only, int col0);
+// complex 3M: three products (re, im, re + im operands) at T + q * oz_t_elems(n, m),
+// exponents at e + q * estride, f + q * fstride
+void oz_combine_3m(cudaStream_t st, int n, int m, const long long* T, const int* e, int estride, const int* f,
+                   int fstride, double* C, long long ldc, double alpha, double beta, bool lower_only, int col0);
 
 // C = alpha op(A) op(B) + beta C in FP64 (complex interleaved when cx; op =
 // conjugate transpose when ta / tb) through the split product, with a

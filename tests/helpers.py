@@ -31,3 +31,29 @@ def cluster_ranges(ev, rtol=1e-8):
             out.append((start, i))
             start = i
     return out
+
+
+def exact_matmul_rounded(A, B):
+    """A B (real float64 matrices) computed exactly with Python integers and
+    rounded once to float64 (float(Fraction) rounds to nearest)."""
+    from fractions import Fraction
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    n, k = A.shape
+    m = B.shape[1]
+    SH = 1100                                    # every double times 2^1100 is an integer
+
+    def scaled(x):
+        p, q = float(x).as_integer_ratio()       # q is a power of two
+        return p << (SH - (q.bit_length() - 1))
+
+    Ai = [[scaled(x) for x in row] for row in A.tolist()]
+    Bi = [[scaled(x) for x in col] for col in B.T.tolist()]
+    den = 1 << (2 * SH)
+    C = np.empty((n, m))
+    for r in range(n):
+        ar = Ai[r]
+        for c in range(m):
+            s = sum(a * b for a, b in zip(ar, Bi[c]))
+            C[r, c] = float(Fraction(s, den))
+    return C

@@ -173,8 +173,6 @@ def test_sparse_full_size_64cubed_properties():
     assert np.allclose(rq, lam, rtol=1e-12)
 
 
-@pytest.mark.skipif(__import__("os").environ.get("MPL_TEST_GRAPH_ORDER") != "1",
-                    reason="CSR without grid dimensions: opt-in until the graph partition's first GPU run")
 @pytest.mark.parametrize("dims,k,m", [((12, 10, 9), 6, 12), ((40, 30), 5, 10)])
 def test_csr_without_grid_dims_uses_graph_ordering(dims, k, m):
     """The level-structure nested dissection (no grid dimensions) drives the

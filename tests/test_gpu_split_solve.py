@@ -1,9 +1,7 @@
 """The dense solve with its FP64 products on the tensor cores by error-free
 splitting (MPL_GEMM_SPLIT=1: A X and the large Gram / projection / update
 products) reaches the same eigenpairs as LAPACK at the requested tolerance.
-The switch is read once per process, so the solve runs in a child process.
-
-Opt-in (MPL_TEST_SPLIT_SOLVE=1) until its first GPU run."""
+The switch is read once per process, so the solve runs in a child process."""
 import json
 import os
 import subprocess
@@ -19,8 +17,6 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("no GPU", allow_module_level=True)
-if os.environ.get("MPL_TEST_SPLIT_SOLVE") != "1":
-    pytest.skip("split-product solve: opt-in until its first GPU run", allow_module_level=True)
 
 import workloads as W  # noqa: E402
 
