@@ -21,7 +21,9 @@ from .dense import LOWER
 
 
 class RankError(np.linalg.LinAlgError):
-    """Cholesky of V^* V broke down: W is numerically rank deficient."""
+    """Cholesky of V^* V broke down: W is numerically rank deficient (a
+    pivot not positive within rounding: at or below m u max_i G_ii, or not
+    finite; Algorithm 2 requires rank(W) = m)."""
 
 
 def householder_r(W, dtype):
@@ -37,14 +39,22 @@ def mixed_qr(W, low=None):
     if low is None:
         low = LOWER[work]
     Rl = householder_r(W, low).astype(work)                                # step 1
-    V = sla.solve_triangular(Rl, W.T, lower=False, trans="T",
-                             check_finite=False).T                          # step 2: V Rl = W
+    try:
+        V = sla.solve_triangular(Rl, W.T, lower=False, trans="T",
+                                 check_finite=False).T                      # step 2: V Rl = W
+    except np.linalg.LinAlgError as e:                                       # an exactly zero pivot of R_l
+        raise RankError(str(e)) from e
     G = V.conj().T @ V
     G = 0.5 * (G + G.conj().T)
+    if not np.all(np.isfinite(G)):
+        raise RankError("non-finite V^* V")
     try:
         L = np.linalg.cholesky(G)                                           # step 3
     except np.linalg.LinAlgError as e:
         raise RankError(str(e)) from e
+    u = np.finfo(np.real(G[:1, :1]).dtype).eps / 2
+    if np.min(np.abs(np.diag(L)) ** 2) <= G.shape[0] * u * np.max(np.real(np.diag(G))):
+        raise RankError("pivot of V^* V below m u max diag")
     Q = sla.solve_triangular(L.conj().T, V.T, lower=False, trans="T",
                              check_finite=False).T                          # step 4: Q L^* = V
     return Q, L.conj().T @ Rl

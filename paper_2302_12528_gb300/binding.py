@@ -76,7 +76,7 @@ _batch_config = _sig("mpl_batch_get_config", _i, [_h, _p, _p, _p, _p])
 _batch_destroy = _sig("mpl_batch_destroy", None, [_h])
 _batch_phases = _sig("mpl_batch_get_phase_cycles", _i, [_h, _p, _i])
 _split_gemm = _sig("mpl_step_split_gemm", _i, [_i, _i, _i64, _i64, _i64, _p, _i64, _p, _i64, _p, _i64, _p])
-_lowp_syrk = _sig("mpl_step_lowp_syrk", _i, [_i, _i, _i64, _i64, _p, _i64, _p, _i64, _i, _p])
+_lowp_syrk = _sig("mpl_step_lowp_syrk", _i, [_i, _i, _i64, _i64, _p, _i64, _p, _i64, _i, _i64, _p])
 _stats = _sig("mpl_get_stats", _i, [_h, C.POINTER(Stats)])
 _last_error = _sig("mpl_last_error", C.c_char_p, [_h])
 _last_info = _sig("mpl_last_info", _i64, [_h])
@@ -402,29 +402,52 @@ def _autograd():
 
     class EigshCSR(torch.autograd.Function):
         """CSR values (device) -> (lambda (k,), X (n, k)) by Algorithm 3; the
-        backward pass is mpl_adjoint."""
+        backward pass is mpl_adjoint on the forward's handle.  The handle is
+        owned by the autograd context: freed after the first backward unless
+        keep_handle (then when the graph is freed), and freed with the graph
+        when no backward ever runs (Handle closes itself when collected)."""
 
         @staticmethod
-        def forward(ctx, vals, rowptr, colind, k, m, tol, policy, grid_dims, X0, Omega, maxit, adj_tol):
+        def forward(ctx, vals, rowptr, colind, k, m, tol, policy, grid_dims, X0, Omega, maxit, adj_tol,
+                    keep_handle):
             h = create_csr(rowptr, colind, vals.detach().contiguous(), k, m, tol, policy, Omega=Omega,
                            grid_dims=grid_dims, stream=torch.cuda.current_stream(vals.device))
             h.factor()
             n = rowptr.shape[0] - 1
             Xo = torch.empty((k, n), dtype=torch.float64, device=vals.device)
             lam, _, _, _, _ = h.solve(X0, maxit=maxit, X_out=Xo)
-            ctx.h, ctx.nnz, ctx.adj_tol = h, colind.shape[0], adj_tol
+            ctx.h, ctx.nnz, ctx.adj_tol, ctx.keep = h, colind.shape[0], adj_tol, bool(keep_handle)
             return torch.from_numpy(lam).to(vals.device), Xo.t().contiguous()
 
         @staticmethod
         def backward(ctx, glam, gX):
-            h = ctx.h
-            gl = None if glam is None else glam.detach().double().cpu().numpy()
-            gXt = None if gX is None else gX.detach().double().t().contiguous()
-            grad = torch.empty(ctx.nnz, dtype=torch.float64, device=glam.device if glam is not None else gX.device)
-            h.adjoint(grad, gl, gXt, tol=ctx.adj_tol)
-            h.close()
-            ctx.h = None
-            return (grad,) + (None,) * 11
+            return (_eigsh_backward(ctx, glam, gX),) + (None,) * 12
+
+    return FVValues, EigshCSR
+
+
+# CG iterations and final relative residual of the last eigsh_csr backward
+# pass (the adjoint's projected shifted solves).
+last_adjoint = {}
+
+
+def _eigsh_backward(ctx, glam, gX):
+    """The adjoint of EigshCSR on ctx.h (split out so its error paths can be
+    exercised without a GPU)."""
+    import torch
+    h = getattr(ctx, "h", None)
+    if h is None:
+        raise RuntimeError("eigsh_csr: the solve's handle was released after the first backward pass; "
+                           "pass keep_handle=True to backpropagate through the same graph again")
+    gl = None if glam is None else glam.detach().double().cpu().numpy()
+    gXt = None if gX is None else gX.detach().double().t().contiguous()
+    grad = torch.empty(ctx.nnz, dtype=torch.float64, device=glam.device if glam is not None else gX.device)
+    its, rr = h.adjoint(grad, gl, gXt, tol=ctx.adj_tol)
+    last_adjoint.update(cg_iterations=int(its), cg_rel_resid=float(rr))
+    if not ctx.keep:
+        h.close()
+        ctx.h = None
+    return grad
 
     return FVValues, EigshCSR
 
@@ -435,11 +458,14 @@ def fv_values(c, dims, rowptr, colind):
 
 
 def eigsh_csr(vals, rowptr, colind, k, m, X0, Omega, tol=1e-12, policy="mp", grid_dims=None, maxit=1000,
-              adj_tol=1e-10):
+              adj_tol=1e-10, keep_handle=False):
     """Differentiable k smallest eigenpairs of the CSR matrix with values
     ``vals`` (device tensor): returns (lambda (k,), X (n, k)); gradients
-    flow back to vals through mpl_adjoint."""
-    return _autograd()[1].apply(vals, rowptr, colind, k, m, tol, policy, grid_dims, X0, Omega, maxit, adj_tol)
+    flow back to vals through mpl_adjoint.  keep_handle: keep the solve's
+    handle (and its device memory) until the graph is freed, so that
+    backward can run more than once (retain_graph)."""
+    return _autograd()[1].apply(vals, rowptr, colind, k, m, tol, policy, grid_dims, X0, Omega, maxit, adj_tol,
+                                keep_handle)
 
 
 class Batch:
@@ -500,14 +526,15 @@ class Batch:
             pass
 
 
-def lowp_syrk(fmt, A, C, round_out=False, stream=None):
+def lowp_syrk(fmt, A, C, round_out=False, stream=None, wait_polls=0):
     """mpl_step_lowp_syrk: C -= A A^H (lower) on the tensor cores.  A and C
     are column-major device tensors given as (k, n) / (n, n) row-major
-    arrays, float32 or complex64; fmt "fp16" or "bf16"."""
+    arrays, float32 or complex64; fmt "fp16" or "bf16".  wait_polls: limit of
+    the MMA completion wait (0: the library's)."""
     k, n = A.shape
     cx = 1 if A.is_complex() else 0
     st = _lowp_syrk({"fp16": 1, "bf16": 2}[fmt], cx, n, k, _ptr(A), n, _ptr(C), n, 1 if round_out else 0,
-                    _stream_ptr(stream))
+                    int(wait_polls), _stream_ptr(stream))
     if st != 0:
         raise MplError(st, "mpl_step_lowp_syrk failed", 0)
 
