@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--precision-study", action="store_true",
                     help="dense workloads: FP32 / fp16 / bf16 factor stage vs all-FP64 at order --n "
                          "(default 4096): iterations, time and eigenvalue error per precision")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="sparse workloads: one step = forward (finite-volume assembly + Algorithm 3) and backward "
+                         "(the adjoint to the coefficient field) through the autograd wrappers")
     ap.add_argument("--kernel-probe", default="", choices=["", "apply", "precond", "eig", "factor"],
                     help="profiling runs only: time one step entry point (A X, T R, or the "
                          "3m x 3m eigensolver) K times after W warm-ups instead of full solves")
@@ -311,6 +314,10 @@ def main():
     stream = torch.cuda.current_stream(dev)
     if w.kind == "batch":
         return run_batch(args, w, M, dev, stream, torch, rank, dist)
+    if args.adjoint:
+        if w.kind != "csr":
+            raise SystemExit("--adjoint applies to the sparse diffusion workloads")
+        return run_adjoint(args, w, M, dev, stream, torch, rank, dist)
     d = {}
     seed = w.seed + 1000 * rank
     if w.kind == "csr":
@@ -404,10 +411,11 @@ def main():
                                         "the pipe executes"}
         if cplx:
             out["roofline"]["complex_equivalent_gflops"] = achieved * 8.0 / 6.0
-        if "1" in (os.environ.get("MPL_AX_SPLIT"), os.environ.get("MPL_GEMM_SPLIT")) and w.kind != "csr":
+        if split_ax_active(w):
             out["roofline"] = split_ax_roofline(w, per_launch_s, apply_calls)
-            out["config"]["fp64_products"] = ("A X and products >= 2^28 FMAs" if os.environ.get("MPL_GEMM_SPLIT") == "1"
-                                              else "A X") + " by error-free bf16 splitting on the tensor cores"
+            out["config"]["fp64_products"] = ("A X and products >= 2^28 FMAs" if os.environ.get("MPL_GEMM_SPLIT") != "0"
+                                              else "A X") + " by error-free bf16 splitting on the tensor cores " \
+                                                            "(exact for 64-bit digits, one rounding)"
     if ck:
         out["clocks"] = ck
     if unconv:
@@ -460,11 +468,30 @@ def traffic_per_launch(w):
     return rd * (w.n / n0) ** 2 + wr * (w.n / n0)
 
 
+def split_ax_active(w):
+    """Whether the library runs the dense working-precision A X as the split
+    product (its rule: on from n = 2048, MPL_AX_SPLIT=0 off, =1 always)."""
+    if w.kind == "csr":
+        return False
+    v = os.environ.get("MPL_AX_SPLIT")
+    if v == "0":
+        return False
+    return v == "1" or os.environ.get("MPL_GEMM_SPLIT") == "1" or w.n >= 2048
+
+
+def split_blocks(m):
+    """Column blocks of one split product (the library's rule): widths 16,
+    32, 48 or 64 for m <= 64, two blocks of 48 for 64 < m <= 96."""
+    npad = 16 if m <= 16 else 32 if m <= 32 else 48 if m <= 48 else 64 if m <= 64 else 48
+    return npad, -(-m // npad)
+
+
 def split_ax_roofline(w, per_launch_s, launches):
-    """A X by error-free splitting on the bf16 tensor cores (MPL_AX_SPLIT=1):
-    per product 28 slice-pair MMAs over the padded tile grid (3 products for
-    complex A, 3M), A's row slices (7 bf16 digits) streamed from HBM once.
-    The bound is whichever of the tensor and HBM times is larger."""
+    """A X by error-free splitting on the bf16 tensor cores: per real product
+    36 slice-pair MMAs (8 digits, pairs i + j <= 7) over the padded tile grid
+    (3 real products for complex A, 3M); algorithmic bytes are A's eight
+    slices streamed from HBM once.  The bound is whichever of the tensor and
+    HBM times is larger at the measured peaks."""
     import math
     peaks = {}
     try:
@@ -476,12 +503,12 @@ def split_ax_roofline(w, per_launch_s, launches):
     hbm = peaks.get("hbm_gbs", 6800.0) * 1e9
     nprod = 3 if w.kind == "dense_complex" else 1
     rows = math.ceil(w.n / 128) * 128
-    depth = math.ceil(w.n / 64) * 64
-    cols = sum(32 if c <= 32 else 64 if c <= 64 else 96 for c in
-               [min(96, w.m - c0) for c0 in range(0, w.m, 96)])
-    flops = nprod * 28 * 2.0 * rows * cols * depth
-    nblk = math.ceil(w.m / 96)
-    bytes_ = nprod * nblk * 7 * rows * depth * 2.0
+    depth = math.ceil(w.n / 32) * 32
+    flops = bytes_ = 0.0
+    for c0 in range(0, w.m, 96):
+        npad, ncb = split_blocks(min(96, w.m - c0))
+        flops += nprod * 36 * 2.0 * rows * npad * ncb * depth
+        bytes_ += nprod * 8 * rows * depth * 2.0
     t_tensor, t_hbm = flops / bf16, bytes_ / hbm
     if t_tensor >= t_hbm:
         ach, peak, unit, bound = flops / per_launch_s / 1e12, bf16 / 1e12, "TFLOP/s", "tensor"
@@ -589,6 +616,89 @@ def kernel_probe(args, w, h, X0, stream, torch):
         flops *= tries
     if flops:
         out["gflops"] = flops / (min(ts) / 1e3) / 1e9
+    print(json.dumps(out))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# differentiable solve (adjoint)
+# ---------------------------------------------------------------------------
+def run_adjoint(args, w, M, dev, stream, torch, rank, dist):
+    """One step = c -> fv_values (finite-volume assembly) -> eigsh_csr
+    (Algorithm 3) -> loss = sum of the k eigenvalues + ||x_1 - x_ref||^2 (sign
+    of x_1 fixed by x_1 . x_ref > 0) -> backward to c (mpl_adjoint: the
+    eigenvalue part on A's pattern and the projected shifted CG solve of the
+    eigenvector part, then the chain rule through the assembly), all on the
+    GPU.  After the timed steps a directional central difference of the
+    same pipeline checks the gradient at full size."""
+    rp, ci, v, c = W.diffusion_csr(w.dims, w.seed, w.ell, w.sigma)
+    n = w.n
+    rpt, cit = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
+    c0 = torch.from_numpy(np.ascontiguousarray(c.reshape(-1))).to(dev)
+    X0 = torch.from_numpy(W.start_block(n, w.m, w.seed + 1)).to(dev)
+    Om = W.sketch(n, 8, w.seed + 2)
+    rng = np.random.default_rng(w.seed + 3)
+    xr = rng.standard_normal(n)
+    xref = torch.from_numpy(xr / np.linalg.norm(xr)).to(dev)
+
+    def loss_of(cvec, eig_only=False, grad=True):
+        cc = cvec.detach().clone().requires_grad_(grad)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        vals = M.fv_values(cc, w.dims, rpt, cit)
+        lam, X = M.eigsh_csr(vals, rpt, cit, w.k, w.m, X0, Om, tol=w.tol, policy=args.policy, grid_dims=w.dims,
+                             maxit=args.maxit)
+        L = lam.sum()
+        if not eig_only:
+            x1 = X[:, 0]
+            sgn = torch.sign(torch.dot(x1.detach(), xref))
+            L = L + ((sgn * x1 - xref) ** 2).sum()
+        e1.record(stream)
+        if grad:
+            L.backward()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        return (float(L.item()), cc.grad if grad else None, e0.elapsed_time(e1) / 1e3,
+                e1.elapsed_time(e2) / 1e3 if grad else 0.0)
+
+    for _ in range(args.warmup):
+        loss_of(c0)
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.synchronize()
+    clocks.start()
+    tf = tb = 0.0
+    Lval, g = None, None
+    for _ in range(args.steps):
+        Lval, g, a, b_ = loss_of(c0)
+        tf += a
+        tb += b_
+    ck = clocks.stop()
+    tf /= args.steps
+    tb /= args.steps
+    cg = dict(M.binding.last_adjoint)
+    # directional central differences: c(1 + eps r), r ~ N(0, 1)
+    r = torch.from_numpy(np.random.default_rng(w.seed + 4).standard_normal(n)).to(dev)
+    d = c0 * r
+    fd = {}
+    for name, eig_only in (("eigenvalue_sum", True), ("full_loss", False)):
+        _, gi, _, _ = loss_of(c0, eig_only=eig_only)
+        eps = 1e-5
+        lp = loss_of(c0 + eps * d, eig_only=eig_only, grad=False)[0]
+        lm = loss_of(c0 - eps * d, eig_only=eig_only, grad=False)[0]
+        num = (lp - lm) / (2 * eps)
+        ana = float(torch.dot(gi, d).item())
+        fd[name] = {"directional_fd": num, "adjoint": ana, "rel_err": abs(num - ana) / max(abs(num), 1e-300),
+                    "eps_rel": eps}
+    out = {"metric": "time of one forward + backward pass: k smallest eigenpairs (Algorithm 3) and their adjoint "
+                     "to the coefficient field",
+           "value": tf + tb, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": (tf + tb) * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64+f32", "data": "synthetic (seeded generators of workloads/)",
+           "config": {"workload": w.name, "n": n, "k": w.k, "m": w.m, "tol": w.tol, "sigma": w.sigma,
+                      "policy": args.policy, "loss": "sum(lambda_1..k) + ||x_1 - x_ref||^2"},
+           "adjoint": {"forward_s": tf, "backward_s": tb, "loss": Lval, **cg, "fd_check": fd}}
+    if ck:
+        out["clocks"] = ck
     print(json.dumps(out))
     return 0
 

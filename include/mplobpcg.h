@@ -39,7 +39,8 @@ typedef enum {
   MPL_ENOT_HPD = 2,        /* lower-precision Cholesky failed for every shift (info = column) */
   MPL_ERANK = 3,           /* Algorithm 2 broke down even in working precision          */
   MPL_ENOT_CONVERGED = 4,  /* maxit reached; best Lambda, X are still returned          */
-  MPL_ENUMERICAL = 5,      /* NaN/Inf met in the iteration                              */
+  MPL_ENUMERICAL = 5,      /* NaN/Inf: in A (create), in X0 (solve; info = its column), or
+                              met in the iteration                                     */
   MPL_ENOMEM = 6,          /* device allocation failed                                  */
   MPL_ECUDA = 7,           /* CUDA runtime error (message has the CUDA string)          */
   MPL_ESTATE = 8           /* call out of order (e.g. solve before factor)              */

@@ -131,12 +131,16 @@ mpl_status mpl_step_split_gemm(int is_complex, int trans_a, int64_t n, int64_t k
  * values of it), products accumulated in FP32 by tcgen05.mma (kind::f16).
  * Storage is column-major FP32, complex interleaved (re, im) with ld in
  * complex elements.  round_out != 0: the updated entries are rounded to the
- * format.  The strictly upper part of C is not touched.  Device pointers;
+ * format.  The strictly upper part of C is not touched.  wait_polls: the
+ * limit of the wait for the MMAs' completion in mbarrier polls (0: the
+ * library's limit, 4,194,304; smaller values let a test make the wait run
+ * out -- the kernel then waits, at the normal limit, for the MMAs it issued,
+ * leaves C untouched and frees its tensor memory).  Device pointers;
  * synchronous on stream.  Errors: MPL_EINVAL (sizes, fmt), MPL_ENOMEM,
  * MPL_ECUDA (launch error, or the wait for the MMAs' completion gave up).
  */
 mpl_status mpl_step_lowp_syrk(int fmt, int is_complex, int64_t n, int64_t k, const void* A, int64_t lda, void* C,
-                              int64_t ldc, int round_out, void* stream);
+                              int64_t ldc, int round_out, int64_t wait_polls, void* stream);
 
 /*
  * The start block mpl_solve draws when it is given X0 == NULL (Algorithm 3

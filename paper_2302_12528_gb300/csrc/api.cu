@@ -21,7 +21,7 @@ void spmm_csr(cudaStream_t st, int n, int m, const long long* rowptr, const int*
 // ---- operators ---------------------------------------------------------
 // Working-precision A X by error-free splitting on the bf16 tensor cores
 // (oz_gemm.cu): A's row slices are made once, X's column slices per product
-// (blocks of <= 96 columns).  Opt-in with MPL_AX_SPLIT=1 (or MPL_GEMM_SPLIT=1).
+// (blocks of <= 96 columns).
 struct SplitAX {
   bool cx = false;
   int n = 0, np = 1;
@@ -50,7 +50,7 @@ struct SplitAX {
     for (int c0 = 0; c0 < ncols; c0 += OZ_MAXM) {
       const int mc = std::min(OZ_MAXM, ncols - c0);
       const size_t tt = oz_t_elems(n, mc);
-      MPL_CUDA(cudaMemsetAsync(T.ptr(), 0, sizeof(long long) * np * tt, st));
+      if (oz_mma_accumulates(n, n, mc)) MPL_CUDA(cudaMemsetAsync(T.ptr(), 0, sizeof(long long) * np * tt, st));
       for (int p = 0; p < np; ++p)
         oz_split_b(st, cx ? p + 1 : 0, n, mc, X + (size_t)elt * c0 * ldx, ldx, f.as<int>() + p * OZ_MAXM,
                    P.as<uint16_t>() + p * pb);
@@ -71,14 +71,22 @@ struct SplitAX {
   }
 };
 
-// MPL_GEMM_SPLIT=1 (every large FP64 product split) implies it: A's slices
-// are made once instead of at every product.
-inline bool ax_split_requested() {
-  static const bool on = [] {
+// Whether the dense working-precision A X runs as the split product.  It is
+// at least as accurate as the FP64 GEMM (exact for the 64-bit digits, one
+// rounding at the end) and an order of magnitude faster for large n, so it is
+// the default from n = 2048 on; MPL_AX_SPLIT=0 selects the FP64 GEMM (DFMA)
+// at every n, MPL_AX_SPLIT=1 (or MPL_GEMM_SPLIT=1) the split product at every
+// n.  A's slices are made once, at create.  (The other large FP64 products of
+// the loop -- Grams, projections, updates -- take the split route in gemm()
+// unless MPL_GEMM_SPLIT=0.)
+inline bool ax_split_enabled(long long n) {
+  static const int mode = [] {
     const char* v = std::getenv("MPL_AX_SPLIT");
-    return (v && v[0] == '1') || oz_gemm_requested();
+    if (v && v[0] == '0') return 0;
+    if ((v && v[0] == '1') || oz_gemm_mode() == 1) return 1;
+    return 2;
   }();
-  return on;
+  return mode == 1 || (mode == 2 && n >= 2048);
 }
 
 template <typename T>
@@ -233,7 +241,7 @@ class Engine : public EngineBase {
     dense_op_.lda = n;
     dense_op_.n = (int)n;
     dense_op_.scr = scr_;
-    if (sizeof(real_t<TW>) == 8 && ax_split_requested() && n <= (1LL << 21)) {
+    if (sizeof(real_t<TW>) == 8 && ax_split_enabled(n) && n <= (1LL << 21)) {
       split_ax_ = std::make_unique<SplitAX>();
       split_ax_->prepare(st, tr<TW>::cx, (int)n, reinterpret_cast<const double*>(Aw_.ptr()), n);
       dense_op_.split = split_ax_.get();
@@ -277,6 +285,8 @@ class Engine : public EngineBase {
     for (int j = 0; j < mo; ++j) { sa += a[j]; sb += b[j]; }
     c_->norm_est = std::sqrt(sa / sb);
     c_->stats.norm_est = c_->norm_est;
+    if (!std::isfinite(c_->norm_est))
+      throw MplError{MPL_ENUMERICAL, "non-finite norm estimate: A (or Omega) holds NaN or Inf", 0};
   }
 
   // ---- factor ----
@@ -459,6 +469,15 @@ class Engine : public EngineBase {
     if (X0) {
       MPL_CUDA(cudaMemcpyAsync(dst, X0, sizeof(TW) * n * m,
                                x0_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+      // a NaN or Inf in the start block would reach every kernel of the loop:
+      // refuse it here (the column norms' sum is finite exactly when it is)
+      DevMem part(sizeof(double) * (ceil_div(n, 2048) + 1) * m), out(sizeof(double) * m);
+      std::vector<double> nrm(m);
+      col_norms2<TW>(st, (int)n, m, dst, n, part.as<double>(), out.as<double>());
+      MPL_CUDA(cudaMemcpyAsync(nrm.data(), out.ptr(), sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+      MPL_CUDA(cudaStreamSynchronize(st));
+      for (int j = 0; j < m; ++j)
+        if (!std::isfinite(nrm[j])) throw MplError{MPL_ENUMERICAL, "non-finite entry in the start block X0", j};
     } else {
       start_block(st, tr<TW>::cx, n, m, seed, reinterpret_cast<double*>(dst));
       check_launch("seeded start block");
@@ -1006,7 +1025,12 @@ extern "C" mpl_status mpl_create_csr(mpl_handle* h, int64_t n, int64_t nnz, cons
 
 extern "C" mpl_status mpl_factor(mpl_handle h) {
   if (!h) return MPL_EINVAL;
-  return guarded(h, [&]() { h->eng->factor(); return MPL_OK; });
+  return guarded(h, [&]() {
+    h->eng->factor();
+    if (mpl::oz_gemm_enabled() && mpl::oz_take_error(h->stream))
+      throw mpl::MplError{MPL_ECUDA, "split FP64 product: a completion wait gave up", 0};
+    return MPL_OK;
+  });
 }
 
 extern "C" mpl_status mpl_solve(mpl_handle h, const void* X0, int x0_is_device, uint64_t seed, int maxit,
@@ -1016,8 +1040,10 @@ extern "C" mpl_status mpl_solve(mpl_handle h, const void* X0, int x0_is_device, 
   mpl_status s = guarded(h, [&]() {
     const mpl_status r = h->eng->solve(X0, x0_is_device, seed, maxit, lambda, X, x_is_device, resid_hist, hist_cap,
                                        hist_len, iters);
-    if (mpl::oz_gemm_requested() && mpl::oz_take_error(h->stream))
+    if (mpl::oz_gemm_enabled() && mpl::oz_take_error(h->stream))
       throw mpl::MplError{MPL_ECUDA, "split FP64 product: a completion wait gave up", 0};
+    if (mpl::sweep_take_error(h->stream))
+      throw mpl::MplError{MPL_ECUDA, "triangular sweep: a dependency wait gave up", 0};
     return r;
   });
   if (s == MPL_ENOT_CONVERGED) h->err = "maximum number of iterations reached";
@@ -1029,8 +1055,13 @@ extern "C" mpl_status mpl_solve_pinvit(mpl_handle h, const void* X0, int x0_is_d
                                        int* hist_len, int* iters) {
   if (!h || maxit < 0 || (rho_hist && hist_cap < 0)) return MPL_EINVAL;
   mpl_status s = guarded(h, [&]() {
-    return h->eng->solve_pinvit(X0, x0_is_device, seed, maxit, lambda, X, x_is_device, rho_hist, hist_cap,
-                                hist_len, iters);
+    const mpl_status r = h->eng->solve_pinvit(X0, x0_is_device, seed, maxit, lambda, X, x_is_device, rho_hist,
+                                              hist_cap, hist_len, iters);
+    if (mpl::oz_gemm_enabled() && mpl::oz_take_error(h->stream))
+      throw mpl::MplError{MPL_ECUDA, "split FP64 product: a completion wait gave up", 0};
+    if (mpl::sweep_take_error(h->stream))
+      throw mpl::MplError{MPL_ECUDA, "triangular sweep: a dependency wait gave up", 0};
+    return r;
   });
   if (s == MPL_ENOT_CONVERGED) h->err = "maximum number of iterations reached";
   return s;

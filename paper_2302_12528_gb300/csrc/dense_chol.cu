@@ -8,15 +8,18 @@
 // panel L_ik = A_ik Dinv_k^* and the lower-triangular trailing update
 // A_ij -= L_ik L_jk^* are GEMMs.  Dinv is kept for the sweeps.
 //
-// Sweeps: one launch per sweep block row (NBS rows, NBS dividing NB).
-// Forward step k subtracts L_ik Y_k from every block row i > k (CT
-// right-hand sides per CTA, staged in shared memory) and the CTAs that own
-// block row k+1 finish Y_{k+1} = Dinv_{k+1} B_{k+1} in the same launch.  The
-// backward sweep does the same with (L_ki)^* and Dinv^*.
+// Sweeps: one persistent launch per sweep over work items (block row of NBS
+// rows, tile of right-hand sides), claimed in dependency order; the owner of
+// a block row accumulates its updates from the finished rows above it
+// (left-looking), applies the inverse diagonal block and publishes the row
+// through a flag.  The backward sweep does the same with (L_ji)^* and Dinv^*.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <new>
 
 #include "dense_chol.cuh"
 
@@ -222,88 +225,135 @@ void scale_rows(cudaStream_t st, int n, int m, T* B, long long ldb, const float*
 // ------------------------------------------------------------------------
 // triangular sweeps
 // ------------------------------------------------------------------------
-// Sweep geometry.  A step of the sweep is one launch whose latency is that of
-// a single CTA (the one that also finishes the next diagonal block), so the
-// sweep block NBS is smaller than the factor block: the diagonal NBS x NBS
-// sub-blocks of the stored Dinv_k are the inverses of the diagonal
-// sub-blocks of the triangular L_kk.  FP32 types use NBS = 64, FP64 types
-// 32 (their FMA rate is 1/64 of FP32, so the per-CTA critical path is kept
-// short); every CTA handles CT = 32 right-hand sides with a 16 x 16 thread
-// grid, each thread owning an (NBS/16) x 2 register tile.
+// Sweep geometry.  One persistent launch per sweep: work items are (sweep
+// block row i, tile of CT right-hand sides), claimed in dependency order
+// from an atomic counter.  The CTA that owns item (i, c) accumulates
+// B_i - sum_j L_ij Y_j over the finished blocks j in a fixed order (so the
+// result is bitwise reproducible), waiting on block j's flag before reading
+// Y_j, then applies the inverse diagonal sub-block and publishes Y_i with a
+// release store of its flag.  Items are claimed in order, so every item an
+// owner waits for was claimed earlier by a CTA that is already running: the
+// launch makes progress without co-residency guarantees.  The diagonal
+// NBS x NBS sub-blocks of the stored Dinv_k are the inverses of the diagonal
+// sub-blocks of the triangular L_kk.  FP32 types use NBS = 64, FP64 types 32;
+// every CTA works on CT = 32 right-hand sides with a 16 x 16 thread grid,
+// each thread owning an (NBS/16) x 2 register tile.  Each flag wait has an
+// iteration limit; a CTA that gives up records an error word (read by the
+// host after the solve) and still publishes its block, so no wait runs on
+// indefinitely.
 template <typename T> struct Sweep { static constexpr int NBS = 32, CT = 32; };
 template <> struct Sweep<float> { static constexpr int NBS = 64, CT = 32; };
 template <> struct Sweep<zf> { static constexpr int NBS = 64, CT = 32; };
 
+constexpr long long SWEEP_WAIT_LIMIT = 1LL << 24;  // flag polls (with a short sleep) before giving up
+
+// Loads that bypass L1 (another CTA wrote the value; L1 is not coherent).
+__device__ __forceinline__ float ldcg_(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ double ldcg_(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ zf ldcg_(const zf* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return {v.x, v.y};
+}
+__device__ __forceinline__ zd ldcg_(const zd* p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return {v.x, v.y};
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// sync: [0] claim counter (zeroed before the launch), [1] error word,
+// [2 + i * nct + c] the flag of item (i, c) (= epoch once published).
 template <typename T, int NBS, int CT, bool BACK>
 __global__ void __launch_bounds__(256)
-trsm_step_kernel(int n, int nsb, int k, const T* __restrict__ L, long long ldl, const T* __restrict__ Dinv,
-                 int dnb, T* B, long long ldb, int m, int only_diag) {
+trsm_sweep_kernel(int n, int nsb, int nct, const T* __restrict__ L, long long ldl, const T* __restrict__ Dinv,
+                  int dnb, T* B, long long ldb, int m, unsigned* sync, unsigned epoch) {
   constexpr int LDS = NBS + 1;
   constexpr int TM = NBS / 16, TN = CT / 16;
   extern __shared__ unsigned char sm[];
   T* Ls = reinterpret_cast<T*>(sm);  // Ls[kk * LDS + r]
   T* Ys = Ls + NBS * LDS;            // Ys[kk * CT + c]
+  __shared__ int item, gave_up;
   const int tid = threadIdx.x;
-  int i;
-  if (only_diag) i = BACK ? nsb - 1 : 0;
-  else i = BACK ? (k - 1 - (int)blockIdx.x) : (k + 1 + (int)blockIdx.x);
-  const int ct0 = blockIdx.y * CT;
-  const int cw = min(CT, m - ct0);
-  const int r0 = i * NBS, rb = min(NBS, n - r0);
   const int tr = tid & 15, tc = tid >> 4;
+  unsigned* flags = sync + 2;
+  const int nitems = nsb * nct;
+  for (;;) {
+    if (tid == 0) {
+      item = (int)atomicAdd(sync, 1u);
+      gave_up = 0;
+    }
+    __syncthreads();
+    const int t = item;
+    if (t >= nitems) break;
+    const int step = t / nct, c = t % nct;
+    const int i = BACK ? nsb - 1 - step : step;
+    const int ct0 = c * CT, cw = min(CT, m - ct0);
+    const int r0 = i * NBS, rb = min(NBS, n - r0);
 
-  // Programmatic dependent launch: the next step may be scheduled now; the
-  // factor tile L_ik is final before the sweep starts, so it is staged
-  // before waiting for the previous step's B to be complete and visible.
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  const int rk0 = k * NBS, kb = min(NBS, n - rk0);
-  if (!only_diag) {
-    for (int e = tid; e < NBS * NBS; e += 256) {
-      const int a = e % NBS, b = e / NBS;
-      if (!BACK) {  // L_ik(r = a, kk = b)
-        Ls[b * LDS + a] = (a < rb && b < kb) ? L[(r0 + a) + (long long)(rk0 + b) * ldl] : zero_<T>();
-      } else {      // (L_ki)^*(r = b, kk = a) = conj(L_ki(a, b))
-        Ls[a * LDS + b] = (a < kb && b < rb) ? conj_(L[(rk0 + a) + (long long)(r0 + b) * ldl]) : zero_<T>();
+    T acc[TM][TN];
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TN; ++b) {
+        const int r = tr + 16 * a, cc = tc + 16 * b;
+        acc[a][b] = (r < rb && cc < cw) ? ldcg_(B + (r0 + r) + (long long)(ct0 + cc) * ldb) : zero_<T>();
       }
-    }
-  }
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-
-  T acc[TM][TN];
-#pragma unroll
-  for (int a = 0; a < TM; ++a)
-#pragma unroll
-    for (int b = 0; b < TN; ++b) {
-      const int r = tr + 16 * a, c = tc + 16 * b;
-      acc[a][b] = (r < rb && c < cw) ? B[(r0 + r) + (long long)(ct0 + c) * ldb] : zero_<T>();
-    }
-  if (!only_diag) {
-    for (int e = tid; e < NBS * CT; e += 256) {
-      const int kk = e % NBS, c = e / NBS;
-      Ys[kk * CT + c] = (kk < kb && c < cw) ? B[(rk0 + kk) + (long long)(ct0 + c) * ldb] : zero_<T>();
-    }
-    __syncthreads();
+    for (int s2 = 0; s2 < step; ++s2) {
+      const int j = BACK ? nsb - 1 - s2 : s2;
+      const int rk0 = j * NBS, kb = min(NBS, n - rk0);
+      // the factor tile is final: stage it before waiting for Y_j
+      for (int e = tid; e < NBS * NBS; e += 256) {
+        const int a = e % NBS, b = e / NBS;
+        if (!BACK) {  // L_ij(r = a, kk = b)
+          Ls[b * LDS + a] = (a < rb && b < kb) ? L[(r0 + a) + (long long)(rk0 + b) * ldl] : zero_<T>();
+        } else {      // (L_ji)^*(r = b, kk = a) = conj(L_ji(a, b))
+          Ls[a * LDS + b] = (a < kb && b < rb) ? conj_(L[(rk0 + a) + (long long)(r0 + b) * ldl]) : zero_<T>();
+        }
+      }
+      if (tid == 0 && !gave_up) {
+        const unsigned* f = flags + (size_t)j * nct + c;
+        long long it = 0;
+        while (ld_acquire(f) != epoch) {
+          if (++it >= SWEEP_WAIT_LIMIT) {
+            gave_up = 1;
+            atomicExch(sync + 1, 1u);
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      __syncthreads();
+      for (int e = tid; e < NBS * CT; e += 256) {
+        const int kk = e % NBS, cc = e / NBS;
+        Ys[kk * CT + cc] = (kk < kb && cc < cw) ? ldcg_(B + (rk0 + kk) + (long long)(ct0 + cc) * ldb) : zero_<T>();
+      }
+      __syncthreads();
 #pragma unroll 4
-    for (int kk = 0; kk < NBS; ++kk) {
-      T av[TM], bv[TN];
+      for (int kk = 0; kk < NBS; ++kk) {
+        T av[TM], bv[TN];
 #pragma unroll
-      for (int a = 0; a < TM; ++a) av[a] = -Ls[kk * LDS + tr + 16 * a];
+        for (int a = 0; a < TM; ++a) av[a] = -Ls[kk * LDS + tr + 16 * a];
 #pragma unroll
-      for (int b = 0; b < TN; ++b) bv[b] = Ys[kk * CT + tc + 16 * b];
+        for (int b = 0; b < TN; ++b) bv[b] = Ys[kk * CT + tc + 16 * b];
 #pragma unroll
-      for (int a = 0; a < TM; ++a)
+        for (int a = 0; a < TM; ++a)
 #pragma unroll
-        for (int b = 0; b < TN; ++b) fma_(acc[a][b], av[a], bv[b]);
+          for (int b = 0; b < TN; ++b) fma_(acc[a][b], av[a], bv[b]);
+      }
+      __syncthreads();
     }
-    __syncthreads();
-  }
-  const bool diag = only_diag || (BACK ? (i == k - 1) : (i == k + 1));
-  if (diag) {
+    // Y_i = Dinv_ii (B_i - sum_j L_ij Y_j)   (backward: the conjugate transpose)
 #pragma unroll
     for (int a = 0; a < TM; ++a)
 #pragma unroll
       for (int b = 0; b < TN; ++b) Ys[(tr + 16 * a) * CT + tc + 16 * b] = acc[a][b];
-    // diagonal sub-block of Dinv for sweep block i (ld dnb)
     const int fb = r0 / dnb, off = r0 % dnb;
     const T* Di = Dinv + (size_t)fb * dnb * dnb + off + (size_t)off * dnb;
     for (int e = tid; e < NBS * NBS; e += 256) {
@@ -329,14 +379,17 @@ trsm_step_kernel(int n, int nsb, int k, const T* __restrict__ L, long long ldl, 
 #pragma unroll
         for (int b = 0; b < TN; ++b) fma_(acc[a][b], av[a], bv[b]);
     }
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TN; ++b) {
+        const int r = tr + 16 * a, cc = tc + 16 * b;
+        if (r < rb && cc < cw) B[(r0 + r) + (long long)(ct0 + cc) * ldb] = acc[a][b];
+      }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) st_release(flags + (size_t)i * nct + c, epoch);
   }
-#pragma unroll
-  for (int a = 0; a < TM; ++a)
-#pragma unroll
-    for (int b = 0; b < TN; ++b) {
-      const int r = tr + 16 * a, c = tc + 16 * b;
-      if (r < rb && c < cw) B[(r0 + r) + (long long)(ct0 + c) * ldb] = acc[a][b];
-    }
 }
 
 template <typename T>
@@ -345,37 +398,95 @@ static size_t sweep_smem() {
   return ((size_t)NBS * (NBS + 1) + (size_t)NBS * CT) * sizeof(T);
 }
 
+// Per-stream synchronisation words of the persistent sweeps (claim counter,
+// error word, item flags) and the epoch that marks a flag as published in
+// the current launch; sweeps on one stream run in order, so one area per
+// stream suffices.
+namespace {
+struct SweepSync {
+  unsigned* d = nullptr;
+  size_t words = 0;
+  unsigned epoch = 0;
+};
+std::mutex& sweep_mutex() {
+  static std::mutex mtx;
+  return mtx;
+}
+std::map<cudaStream_t, SweepSync>& sweep_syncs() {
+  static std::map<cudaStream_t, SweepSync> m;
+  return m;
+}
+}  // namespace
+
 template <typename T, bool BACK>
 static void dense_sweep(cudaStream_t st, const DenseFactor<T>& F, T* B, long long ldb, int m) {
   constexpr int NB = CholBlock<T>::NB, NBS = Sweep<T>::NBS, CT = Sweep<T>::CT;
   static_assert(NB % NBS == 0, "sweep block must divide the factor block");
-  const int n = F.n, nsb = ceil_div(n, NBS);
+  const int n = F.n, nsb = ceil_div(n, NBS), nct = ceil_div(m, CT);
+  if (n <= 0 || m <= 0) return;
   const size_t sm = sweep_smem<T>();
-  auto kern = trsm_step_kernel<T, NBS, CT, BACK>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  const int cty = ceil_div(m, CT);
-  count_launch();
-  kern<<<dim3(1, cty), 256, sm, st>>>(n, nsb, BACK ? nsb : -1, F.L, F.ldl, F.Dinv, NB, B, ldb, m, 1);
-  // FP32 sweeps: the remaining steps are programmatic dependent launches of
-  // one another (a step is latency-bound).  FP64 steps are bound by the FP64
-  // pipe; early-scheduled CTAs would share SMs with running ones, so they are
-  // ordinary stream-ordered launches (griddepcontrol is then a no-op).
-  constexpr bool kPDL = sizeof(real_t<T>) == 4;
-  cudaLaunchConfig_t cfg = {};
-  cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = sm;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = kPDL ? 1 : 0;
-  for (int s = 1; s < nsb; ++s) {
-    const int k = BACK ? nsb - s : s - 1;  // forward: rows > k; backward: rows < k
-    cfg.gridDim = dim3(BACK ? k : nsb - 1 - k, cty);
-    count_launch();
-    cudaLaunchKernelEx(&cfg, kern, n, nsb, k, (const T*)F.L, (long long)F.ldl, (const T*)F.Dinv, NB, B, ldb, m, 0);
+  auto kern = trsm_sweep_kernel<T, NBS, CT, BACK>;
+  // as many CTAs as fit at once (measured: faster than one per SM -- the
+  // off-chain updates need the throughput more than the chain needs an SM
+  // of its own)
+  static const int resident = [&] {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm) != cudaSuccess || per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    return per_sm * NUM_SMS;
+  }();
+  unsigned* sync;
+  unsigned epoch;
+  {
+    std::lock_guard<std::mutex> lock(sweep_mutex());
+    SweepSync& S = sweep_syncs()[st];
+    const size_t need = 2 + (size_t)nsb * nct;
+    if (need > S.words) {
+      if (S.d) {
+        cudaStreamSynchronize(st);
+        cudaFree(S.d);
+      }
+      S.d = nullptr;
+      S.words = 0;
+      if (cudaMalloc(&S.d, sizeof(unsigned) * need) != cudaSuccess) {
+        cudaGetLastError();
+        S.d = nullptr;
+        throw std::bad_alloc();
+      }
+      cudaMemsetAsync(S.d, 0, sizeof(unsigned) * need, st);
+      S.words = need;
+      S.epoch = 0;
+    }
+    if (++S.epoch == 0) {  // wrapped: clear the flags once
+      cudaMemsetAsync(S.d + 2, 0, sizeof(unsigned) * (S.words - 2), st);
+      S.epoch = 1;
+    }
+    sync = S.d;
+    epoch = S.epoch;
   }
+  cudaMemsetAsync(sync, 0, sizeof(unsigned), st);  // claim counter (launch errors surface at the caller's check)
+  const int grid = std::max(1, std::min(nsb * nct, resident));
+  count_launch();
+  kern<<<grid, 256, sm, st>>>(n, nsb, nct, F.L, F.ldl, F.Dinv, NB, B, ldb, m, sync, epoch);
+}
+
+int sweep_take_error(cudaStream_t st) {
+  std::lock_guard<std::mutex> lock(sweep_mutex());
+  cudaStreamSynchronize(st);
+  int any = 0;
+  for (auto& kv : sweep_syncs()) {
+    if (!kv.second.d) continue;
+    unsigned h = 0;
+    cudaMemcpy(&h, kv.second.d + 1, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (h) {
+      cudaMemset(kv.second.d + 1, 0, sizeof(unsigned));
+      any = 1;
+    }
+  }
+  return any;
 }
 
 template <typename T>

@@ -42,7 +42,7 @@ void dense_cholesky(cudaStream_t st, DenseFactor<T>& F, T* tmp, int* info, Scrat
 // format fmt: 1 fp16, 2 bf16), the result rounded to the format when
 // round_out.  False when k or fmt is out of range.
 bool tc_syrk(cudaStream_t st, int fmt, bool cx, int n, int k, const float* A, long long lda, float* C,
-             long long ldc, bool round_out, int* err);
+             long long ldc, bool round_out, int* err, long long wait_polls = 0);
 
 // Round a rows x cols block (ld lda; lower triangle only if lower_only) to
 // the 16-bit format fmt (1 fp16, 2 bf16; 0: no-op).
@@ -60,6 +60,10 @@ void scale_rows(cudaStream_t st, int n, int m, T* B, long long ldb, const float*
 // B <- L^-* L^-1 B for B n x m (ld ldb), in place, two blocked sweeps.
 template <typename T>
 void dense_precond(cudaStream_t st, const DenseFactor<T>& F, T* B, long long ldb, int m);
+
+// Returns 1 (and clears it) if a dependency wait of a triangular sweep gave
+// up since the last call, on any stream; synchronises with st first.
+int sweep_take_error(cudaStream_t st);
 
 // The two halves: B <- L^-1 B and B <- L^-* B (F.n rows).
 template <typename T>

@@ -104,10 +104,16 @@ __device__ __forceinline__ double pick(const double* A, long long idx, int mode)
   }
 }
 
-__device__ __forceinline__ int exp_of(double amax) {
-  if (!(amax > 0.0)) return INT_MIN;
+
+// Exponent of |x| as frexp gives it (|x| < 2^e, |x| >= 2^(e-1)); INT_MIN for
+// zero.  From the bit pattern except for subnormal numbers.
+__device__ __forceinline__ int exp_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFULL;
+  if (b == 0) return INT_MIN;
+  const int E = (int)(b >> 52);
+  if (E) return E - 1022;
   int e;
-  frexp(amax, &e);  // amax = f 2^e, f in [0.5, 1): |x| <= amax < 2^e
+  frexp(x, &e);
   return e;
 }
 
@@ -121,28 +127,24 @@ __global__ void row_exp_kernel(int n, int k, const double* __restrict__ A, long 
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const int k0 = blockIdx.y * 256, k1 = min(k, k0 + 256);
-  double m = 0.0;
-  for (int kk = k0; kk < k1; ++kk) m = fmax(m, fabs(pick(A, r + (long long)kk * lda, mode)));
-  const int ex = exp_of(m);
-  if (ex != INT_MIN) atomicMax(e + r, ex);
+  int m = INT_MIN;
+  for (int kk = k0; kk < k1; ++kk) m = max(m, exp_bits(pick(A, r + (long long)kk * lda, mode)));
+  if (m != INT_MIN) atomicMax(e + r, m);
 }
 
 // f[c] = max over k of the exponent of |B(k, c)| (one block per column)
 __global__ void col_exp_kernel(int k, const double* __restrict__ B, long long ldb, int mode, int* __restrict__ f) {
-  __shared__ double red[256];
+  __shared__ int red[256];
   const int c = blockIdx.x;
-  double m = 0.0;
-  for (int kk = threadIdx.x; kk < k; kk += blockDim.x) m = fmax(m, fabs(pick(B, kk + (long long)c * ldb, mode)));
+  int m = INT_MIN;
+  for (int kk = threadIdx.x; kk < k; kk += blockDim.x) m = max(m, exp_bits(pick(B, kk + (long long)c * ldb, mode)));
   red[threadIdx.x] = m;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+    if (threadIdx.x < s) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + s]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    const int ex = exp_of(red[0]);
-    f[c] = ex == INT_MIN ? 0 : ex;
-  }
+  if (threadIdx.x == 0) f[c] = red[0] == INT_MIN ? 0 : red[0];
 }
 
 __global__ void clamp_exp_kernel(int n, int* e) {
@@ -151,16 +153,34 @@ __global__ void clamp_exp_kernel(int n, int* e) {
 }
 
 // The OZ_S balanced digits of x below the exponent ex (|x| < 2^ex), as bf16
-// bit patterns of the integers q_i (|q_i| <= 128: exact in bf16).
+// bit patterns of the integers q_i (|q_i| <= 128: exact in bf16), on the
+// integer pipes (GB300 runs FP64 at 1/64 of the FP32 rate): x is taken from
+// its bit pattern to the 64-bit fixed point U = round(x 2^(63 - ex)),
+// |U| < 2^63, and U = sum_i q_i 2^(56 - 8i) exactly, each q_i the nearest
+// integer (half up) of what remains above 2^(56 - 8i).  Same value as
+// x 2^(7 - ex) = sum_i q_i 2^(-8i) up to 2^(ex - 64).
 __device__ __forceinline__ void digits(double x, int ex, uint16_t out[OZ_S]) {
-  double u = ldexp(x, 7 - ex);
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  const long long frac = (long long)(bits & 0xFFFFFFFFFFFFFULL);
+  const long long M = E ? (frac | (1LL << 52)) : frac;  // |x| = M 2^(max(E, 1) - 1075)
+  const int sft = (E ? E : 1) - 1075 + 63 - ex;          // U = M 2^sft
+  long long U;
+  if (M == 0 || sft <= -64) U = 0;
+  else if (sft >= 0) U = M << sft;                       // below 2^63 because |x| < 2^ex
+  else U = (M >> (-sft)) + ((M >> (-sft - 1)) & 1);      // nearest, half up
+  if (bits >> 63) U = -U;
 #pragma unroll
   for (int i = 0; i < OZ_S; ++i) {
-    const double q = rint(u);
+    const int sh = 56 - 8 * i;
+    const long long q = sh ? (U >> sh) + ((U >> (sh - 1)) & 1) : U;  // |q| <= 128
+    // the remainder fits (|U - q 2^sh| <= 2^(sh-1)); the product may not:
+    // subtract modulo 2^64
+    U = (long long)((unsigned long long)U - ((unsigned long long)q << sh));
     out[i] = __bfloat16_as_ushort(__float2bfloat16_rn((float)q));
-    u = (u - q) * 256.0;
   }
 }
+
 
 __device__ __forceinline__ void store8(uint16_t* dst, const uint16_t v[8]) {
   uint4 w;
@@ -282,7 +302,8 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 template <int NPAD>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 oz_mma_kernel(int ncb, int nchunk, int chunks_per_split, const uint16_t* __restrict__ QA,
-              const uint16_t* __restrict__ PB, long long* __restrict__ T, long long ldt, long long tlo, int* err) {
+              const uint16_t* __restrict__ PB, long long* __restrict__ T, long long ldt, long long tlo, int* err,
+              int single_split) {
   static_assert(NPAD % 16 == 0 && NPAD >= 16 && NPAD <= 64, "N of the tile");
   constexpr int A_BYTES = OZ_S * OZ_TILE_A * 2;          // the 8 slices of one chunk of the row tile
   constexpr int B_BYTES = OZ_S * NPAD * OZ_BK * 2;       // the 8 slices of one chunk of the column block
@@ -351,26 +372,28 @@ oz_mma_kernel(int ncb, int nchunk, int chunks_per_split, const uint16_t* __restr
     if (lane == 0) {
       constexpr uint32_t LBO = 128, SBO = (OZ_BK / 8) * 128;
       constexpr uint32_t idesc = idesc_bf16(OZ_BM, NPAD);
-      uint32_t fresh = 0;
       for (int s = 0; s < nst; ++s) {
         const int b = s & 1, r = s >> 1, w = s / OZ_STAGES_PER_WIN;
         const bool first = (s % OZ_STAGES_PER_WIN) == 0;
         if (first && w > 0 && !mbar_wait(smem_u32(&bar_acce), (w - 1) & 1, &abort_flag)) break;
         if (!mbar_wait(smem_u32(&bar_full[b]), r & 1, &abort_flag)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (first) fresh = 0xFFu;
+        // the first MMA of each group in a window overwrites its accumulator
+        const uint32_t acc0 = first ? 0u : 1u;
         const uint32_t sa = sbase + b * STAGE, sb = sa + A_BYTES;
-#pragma unroll 1
+        // descriptors of slice 0 / depth step 0; the others differ only in the
+        // start address field (bytes >> 4), so constant offsets are added
+        const uint64_t da0 = smem_desc(sa, LBO, SBO), db0 = smem_desc(sb, LBO, SBO);
+#pragma unroll
         for (int g = 0; g < OZ_S; ++g) {
           const uint32_t d_tmem = tmem + (uint32_t)(g * NPAD);
-#pragma unroll 1
+#pragma unroll
           for (int i = 0; i <= g; ++i) {
-            const int j = g - i;
 #pragma unroll
             for (int kk = 0; kk < OZ_BK / 16; ++kk) {
-              const uint64_t da = smem_desc(sa + i * (OZ_TILE_A * 2) + kk * 256, LBO, SBO);
-              const uint64_t db = smem_desc(sb + j * (NPAD * OZ_BK * 2) + kk * 256, LBO, SBO);
-              const uint32_t accum = ((fresh >> g) & 1u) ? 0u : 1u;
+              const uint64_t da = da0 + (uint64_t)((i * (OZ_TILE_A * 2) + kk * 256) >> 4);
+              const uint64_t db = db0 + (uint64_t)(((g - i) * (NPAD * OZ_BK * 2) + kk * 256) >> 4);
+              const uint32_t accum = (i == 0 && kk == 0) ? acc0 : 1u;
               asm volatile(
                   "{\n\t.reg .pred p;\n\t"
                   "setp.ne.b32 p, %4, 0;\n\t"
@@ -378,7 +401,6 @@ oz_mma_kernel(int ncb, int nchunk, int chunks_per_split, const uint16_t* __restr
                   "}" ::"r"(d_tmem),
                   "l"(da), "l"(db), "r"(idesc), "r"(accum)
                   : "memory");
-              fresh &= ~(1u << g);
             }
           }
         }
@@ -400,26 +422,38 @@ oz_mma_kernel(int ncb, int nchunk, int chunks_per_split, const uint16_t* __restr
     for (int q = 0; q < QC; ++q) hi[q] = lo[q] = 0;
     bool ok = true;
     for (int w = 0; w < nwin && ok; ++w) {
-      ok = mbar_wait(smem_u32(&bar_accf), w & 1, &abort_flag);
-      ok = __all_sync(0xffffffffu, ok);
+      // one lane polls (the others would compete with the MMAs' shared-memory reads)
+      int got = 1;
+      if (lane == 0) got = mbar_wait(smem_u32(&bar_accf), w & 1, &abort_flag) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, got, 0) != 0;
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
       for (int c4 = 0; c4 < QC; c4 += 4) {
+        // the eight groups' values of 4 columns: all loads in flight, one wait
+        uint32_t v[OZ_S][4];
 #pragma unroll
         for (int g = 0; g < OZ_S; ++g) {
-          uint32_t v[4];
           const uint32_t taddr = tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(g * NPAD + ch * QC + c4);
           asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-                       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                       : "=r"(v[g][0]), "=r"(v[g][1]), "=r"(v[g][2]), "=r"(v[g][3])
                        : "r"(taddr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const long long I = __float2ll_rn(__uint_as_float(v[q]));  // an integer below 2^24: exact
-            if (g < 4) hi[c4 + q] += I * (1LL << (24 - 8 * g));
-            else lo[c4 + q] += I * (1LL << (56 - 8 * g));
-          }
+        for (int g = 0; g < OZ_S; ++g)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) asm volatile("" : "+r"(v[g][q]));  // uses stay after the wait
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          // integers below 2^24 in magnitude: exact FP32 -> int32 conversions
+          long long h = 0, l = 0;
+#pragma unroll
+          for (int g = 0; g < 4; ++g) h += (long long)__float2int_rn(__uint_as_float(v[g][q])) * (1LL << (24 - 8 * g));
+#pragma unroll
+          for (int g = 4; g < OZ_S; ++g) l += (long long)__float2int_rn(__uint_as_float(v[g][q])) * (1LL << (56 - 8 * g));
+          hi[c4 + q] += h;
+          lo[c4 + q] += l;
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -431,8 +465,13 @@ oz_mma_kernel(int ncb, int nchunk, int chunks_per_split, const uint16_t* __restr
 #pragma unroll
       for (int q = 0; q < QC; ++q) {
         const long long col = (long long)cb * NPAD + ch * QC + q;
-        atomicAdd(reinterpret_cast<unsigned long long*>(T + row + col * ldt), (unsigned long long)hi[q]);
-        atomicAdd(reinterpret_cast<unsigned long long*>(T + tlo + row + col * ldt), (unsigned long long)lo[q]);
+        if (single_split) {  // the only writer of this tile: no zeroing, no atomics
+          T[row + col * ldt] = hi[q];
+          T[tlo + row + col * ldt] = lo[q];
+        } else {
+          atomicAdd(reinterpret_cast<unsigned long long*>(T + row + col * ldt), (unsigned long long)hi[q]);
+          atomicAdd(reinterpret_cast<unsigned long long*>(T + tlo + row + col * ldt), (unsigned long long)lo[q]);
+        }
       }
     }
   }
@@ -507,7 +546,7 @@ inline int grid_for(long long tot) { return (int)std::min<long long>((tot + 255)
 
 }  // namespace
 
-int oz_npad(int m) { return m <= 16 ? 16 : m <= 32 ? 32 : m <= 48 ? 48 : m <= 64 ? 64 : 48; }
+int oz_npad(int m) { return m <= 16 ? 16 : m <= 32 ? 32 : m <= 48 ? 48 : m <= 64 ? 64 : m <= 96 ? 48 : 64; }
 int oz_ncb(int m) { return (m + oz_npad(m) - 1) / oz_npad(m); }
 long long oz_t_rows(int n) { return (long long)((n + OZ_BM - 1) / OZ_BM) * OZ_BM; }
 size_t oz_t_elems(int n, int m) { return (size_t)2 * oz_t_rows(n) * oz_ncb(m) * oz_npad(m); }
@@ -557,6 +596,23 @@ void oz_split_b(cudaStream_t st, int mode, int k, int m, const double* B, long l
   split_cols_kernel<false><<<grid_for(tot), 256, 0, st>>>(k, m, B, ldb, mode, f, nchunk, npad, ncb, P);
 }
 
+// Depth splits of whole windows: about 8 waves of one CTA per SM per launch.
+static void oz_plan(int n, int k, int m, int* nsp, int* cps) {
+  const int ntile = (n + OZ_BM - 1) / OZ_BM, nchunk = (k + OZ_BK - 1) / OZ_BK;
+  const int tiles = ntile * oz_ncb(m);
+  const int want = std::max(1, (8 * NUM_SMS + tiles - 1) / tiles);
+  const int nwin = (nchunk + OZ_STAGES_PER_WIN - 1) / OZ_STAGES_PER_WIN;
+  const int nsplit = std::min(want, nwin);
+  *cps = ((nwin + nsplit - 1) / nsplit) * OZ_STAGES_PER_WIN;
+  *nsp = (nchunk + *cps - 1) / *cps;
+}
+
+bool oz_mma_accumulates(int n, int k, int m) {
+  int nsp, cps;
+  oz_plan(n, k, m, &nsp, &cps);
+  return nsp > 1;
+}
+
 template <int NPAD>
 static void launch_mma(cudaStream_t st, int ntile, int ncb, int nchunk, int nsplit, int cps, const uint16_t* Q,
                        const uint16_t* P, long long* T, long long ldt, long long tlo, int* err) {
@@ -567,19 +623,15 @@ static void launch_mma(cudaStream_t st, int ntile, int ncb, int nchunk, int nspl
       cudaSuccess;
   (void)opened;
   count_launch();
-  oz_mma_kernel<NPAD><<<dim3(ntile * ncb, nsplit), OZ_THREADS, sm, st>>>(ncb, nchunk, cps, Q, P, T, ldt, tlo, err);
+  oz_mma_kernel<NPAD><<<dim3(ntile * ncb, nsplit), OZ_THREADS, sm, st>>>(ncb, nchunk, cps, Q, P, T, ldt, tlo, err,
+                                                                          nsplit == 1 ? 1 : 0);
 }
 
 void oz_mma(cudaStream_t st, int n, int k, int m, const uint16_t* Q, const uint16_t* P, long long* T, int* err) {
   const int ntile = (n + OZ_BM - 1) / OZ_BM, nchunk = (k + OZ_BK - 1) / OZ_BK;
   const int npad = oz_npad(m), ncb = oz_ncb(m);
-  // depth splits of whole windows: about 8 waves of one CTA per SM per launch
-  const int tiles = ntile * ncb;
-  const int want = std::max(1, (8 * NUM_SMS + tiles - 1) / tiles);
-  const int nwin = (nchunk + OZ_STAGES_PER_WIN - 1) / OZ_STAGES_PER_WIN;
-  const int nsplit = std::min(want, nwin);
-  const int cps = ((nwin + nsplit - 1) / nsplit) * OZ_STAGES_PER_WIN;
-  const int nsp = (nchunk + cps - 1) / cps;
+  int nsp, cps;
+  oz_plan(n, k, m, &nsp, &cps);
   const long long ldt = oz_t_rows(n), tlo = ldt * ncb * npad;
   switch (npad) {
     case 16: launch_mma<16>(st, ntile, ncb, nchunk, nsp, cps, Q, P, T, ldt, tlo, err); break;
@@ -637,13 +689,15 @@ std::map<cudaStream_t, OzPool>& pools() {
 }
 }  // namespace
 
-bool oz_gemm_requested() {
-  static const bool on = [] {
+int oz_gemm_mode() {
+  static const int mode = [] {
     const char* v = std::getenv("MPL_GEMM_SPLIT");
-    return v && v[0] == '1';
+    if (v && v[0] == '0') return 0;
+    return (v && v[0] == '1') ? 1 : 2;
   }();
-  return on;
+  return mode;
 }
+bool oz_gemm_enabled() { return oz_gemm_mode() != 0; }
 
 bool oz_gemm_fp64(cudaStream_t st, bool cx, bool ta, bool tb, int M, int N, int K, double alpha, const double* A,
                   long long lda, const double* B, long long ldb, double beta, double* C, long long ldc,
@@ -652,7 +706,9 @@ bool oz_gemm_fp64(cudaStream_t st, bool cx, bool ta, bool tb, int M, int N, int 
   std::lock_guard<std::mutex> lock(pool_mutex());
   OzPool& P = pools()[st];
   const int np = cx ? 3 : 1, elt = cx ? 2 : 1;
-  const size_t qa = oz_a_elems(M, K), pb = oz_b_elems(K, OZ_MAXM), tmax = oz_t_elems(M, OZ_MAXM);
+  // column chunks: <= 96 as one call, wider products in chunks of 1536 (24 blocks of 64)
+  const int CW = N <= OZ_MAXM ? N : std::min(N, 1536);
+  const size_t qa = oz_a_elems(M, K), pb = oz_b_elems(K, CW), tmax = oz_t_elems(M, CW);
   if (!P.err) {
     if (cudaMalloc(&P.err, sizeof(int)) != cudaSuccess) {
       cudaGetLastError();
@@ -661,7 +717,7 @@ bool oz_gemm_fp64(cudaStream_t st, bool cx, bool ta, bool tb, int M, int N, int 
     }
     cudaMemsetAsync(P.err, 0, sizeof(int), st);
   }
-  if (!P.grow(0, sizeof(int) * np * M) || !P.grow(1, sizeof(int) * np * OZ_MAXM) || !P.grow(2, 2 * np * qa) ||
+  if (!P.grow(0, sizeof(int) * np * M) || !P.grow(1, sizeof(int) * np * CW) || !P.grow(2, 2 * np * qa) ||
       !P.grow(3, 2 * np * pb) || !P.grow(4, sizeof(long long) * np * tmax))
     return false;
   int* e = static_cast<int*>(P.p[0]);
@@ -672,31 +728,38 @@ bool oz_gemm_fp64(cudaStream_t st, bool cx, bool ta, bool tb, int M, int N, int 
   // 3M operands: re, im, re + im; of a conjugate transpose: re, -im, re - im
   auto mode_of = [&](int p, bool t) { return !cx ? 0 : !t ? p + 1 : (p == 0 ? 1 : p == 1 ? 4 : 5); };
   for (int p = 0; p < np; ++p) oz_split_a(st, mode_of(p, ta), M, K, A, lda, e + p * M, Q + p * qa, ta);
-  for (int c0 = 0; c0 < N; c0 += OZ_MAXM) {
-    const int nb = std::min(OZ_MAXM, N - c0);
+  for (int c0 = 0; c0 < N; c0 += CW) {
+    const int nb = std::min(CW, N - c0);
     const size_t tt = oz_t_elems(M, nb);
     // columns c0.. of op(B): stored columns (no transpose) or stored rows
     const double* Bc = B + (size_t)elt * (tb ? (size_t)c0 : (size_t)c0 * ldb);
-    cudaMemsetAsync(T, 0, sizeof(long long) * np * tt, st);
-    for (int p = 0; p < np; ++p)
-      oz_split_b(st, mode_of(p, tb), K, nb, Bc, ldb, f + p * OZ_MAXM, Pb + p * pb, tb);
+    if (oz_mma_accumulates(M, K, nb)) cudaMemsetAsync(T, 0, sizeof(long long) * np * tt, st);
+    for (int p = 0; p < np; ++p) oz_split_b(st, mode_of(p, tb), K, nb, Bc, ldb, f + p * CW, Pb + p * pb, tb);
     for (int p = 0; p < np; ++p) oz_mma(st, M, K, nb, Q + p * qa, Pb + p * pb, T + p * tt, P.err);
     double* Cc = C + (size_t)elt * c0 * ldc;
-    if (cx) oz_combine_3m(st, M, nb, T, e, M, f, OZ_MAXM, Cc, ldc, alpha, beta, lower_only, c0);
+    if (cx) oz_combine_3m(st, M, nb, T, e, M, f, CW, Cc, ldc, alpha, beta, lower_only, c0);
     else oz_combine_real(st, M, nb, T, e, f, Cc, ldc, alpha, beta, lower_only, c0);
   }
   return true;
 }
 
+// Every stream's flag (the sparse factorisation runs fronts on auxiliary
+// streams joined into the caller's): read after synchronising with the
+// caller's stream, cleared when set.
 int oz_take_error(cudaStream_t st) {
   std::lock_guard<std::mutex> lock(pool_mutex());
-  auto it = pools().find(st);
-  if (it == pools().end() || !it->second.err) return 0;
-  int h = 0;
-  cudaMemcpyAsync(&h, it->second.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  int any = 0;
   cudaStreamSynchronize(st);
-  if (h) cudaMemsetAsync(it->second.err, 0, sizeof(int), st);
-  return h;
+  for (auto& kv : pools()) {
+    if (!kv.second.err) continue;
+    int h = 0;
+    cudaMemcpy(&h, kv.second.err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (h) {
+      cudaMemset(kv.second.err, 0, sizeof(int));
+      any = 1;
+    }
+  }
+  return any;
 }
 
 }  // namespace mpl
@@ -737,7 +800,7 @@ extern "C" mpl_status mpl_step_split_gemm(int is_complex, int trans_a, int64_t n
     const double* a = static_cast<const double*>(A);
     const double* b = static_cast<const double*>(B);
     cudaMemsetAsync(err, 0, sizeof(int), st);
-    cudaMemsetAsync(T, 0, sizeof(long long) * np * tt, st);
+    if (mpl::oz_mma_accumulates((int)n, (int)k, (int)m)) cudaMemsetAsync(T, 0, sizeof(long long) * np * tt, st);
     for (int p = 0; p < np; ++p) {
       const int mode = is_complex ? p + 1 : 0;  // 3M: re, im, re + im
       // op(A) = A^H: re, -im, re - im of the stored matrix

@@ -238,18 +238,26 @@ void trinv_upper_ct(cudaStream_t st, int m, const TI* R, long long ldr, TO* Linv
 }
 
 // Cholesky (lower, in place) of an n x n Hermitian matrix held by one CTA.
-// Returns 0 or the 1-based column of the first pivot that is not positive.
+// Returns 0 or the 1-based column of the first pivot that is not positive
+// within rounding: at or below n u max_i A_ii (u the unit roundoff of the
+// type), or not finite -- the numerically rank-deficient V^* V of Algorithm 2.
 template <typename T>
 __device__ int chol_lower_cta(int n, T* A, long long ld) {
   using R = real_t<T>;
   __shared__ int bad;
-  __shared__ R piv;
-  if (threadIdx.x == 0) bad = 0;
+  __shared__ R piv, thr;
+  if (threadIdx.x == 0) {
+    bad = 0;
+    R mx = R(0);
+    for (int i = 0; i < n; ++i) mx = fmax(mx, re_(A[i + i * ld]));
+    const R u = sizeof(R) == 8 ? R(1.1102230246251565e-16) : R(5.9604645e-08);  // 2^-53, 2^-24
+    thr = R(n) * u * mx;
+  }
   __syncthreads();
   for (int j = 0; j < n; ++j) {
     if (threadIdx.x == 0) {
       R d = re_(A[j + j * ld]);
-      if (!(d > R(0)) || !isfinite((double)d)) {
+      if (!(d > thr) || !isfinite((double)d)) {
         if (bad == 0) bad = j + 1;
         d = R(1);
       }

@@ -23,7 +23,7 @@ namespace mpl {
 
 constexpr int TC_M = 128, TC_N = 128, TC_KMAX = 128;
 constexpr int TC_THREADS = 256;  // two warpgroups: both stage operands, each reads half the columns
-constexpr long long TC_WAIT_LIMIT = 1LL << 22;  // mbarrier polls before giving up
+constexpr long long TC_WAIT_LIMIT = 1LL << 22;  // mbarrier polls before giving up (tens of ns each)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -74,7 +74,7 @@ __device__ __forceinline__ int core_off(int r, int kc) {
 template <int FMT, bool CX>
 __global__ void __launch_bounds__(TC_THREADS)
 tc_syrk_kernel(int n, int k, const float* __restrict__ A, long long lda, float* __restrict__ C, long long ldc,
-               int round_out, int* err) {
+               int round_out, int* err, long long wait_limit) {
   constexpr int NACC = CX ? 2 : 1;
   constexpr int TILE_BYTES = TC_M * TC_KMAX * 2;
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -169,12 +169,12 @@ tc_syrk_kernel(int n, int k, const float* __restrict__ A, long long lda, float* 
                      smem_u32(&mbar))
                  : "memory");
   }
-  // wait for the MMAs (bounded)
+  // wait for the MMAs: at most wait_limit non-blocking polls
   uint32_t done = 0;
-  for (long long it = 0; it < TC_WAIT_LIMIT && !done; ++it) {
+  for (long long it = 0; it < wait_limit && !done; ++it) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t"
         "}"
         : "=r"(done)
@@ -182,7 +182,22 @@ tc_syrk_kernel(int n, int k, const float* __restrict__ A, long long lda, float* 
         : "memory");
   }
   done = __syncthreads_and(done);  // uniform: the epilogue's tcgen05.ld is warp-synchronous
-  if (!done && tid == 0) atomicExch(err, 1);
+  if (!done && tid == 0) {
+    atomicExch(err, 1);
+    // the wait gave up: let the MMAs that were issued finish (bounded, at the
+    // normal limit) before their tensor memory is released
+    uint32_t drained = 0;
+    for (long long it = 0; it < TC_WAIT_LIMIT && !drained; ++it) {
+      asm volatile(
+          "{\n\t.reg .pred p;\n\t"
+          "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t"
+          "}"
+          : "=r"(drained)
+          : "r"(smem_u32(&mbar)), "r"(0u)
+          : "memory");
+    }
+  }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (done) {
     // warp w may read accumulator lanes (rows) 32 (w % 4) .. + 31 only; the
@@ -231,7 +246,7 @@ tc_syrk_kernel(int n, int k, const float* __restrict__ A, long long lda, float* 
 
 template <int FMT, bool CX>
 static void launch_tc(cudaStream_t st, int tiles, int n, int k, const float* A, long long lda, float* C,
-                      long long ldc, int round_out, int* err) {
+                      long long ldc, int round_out, int* err, long long wait_limit) {
   const size_t sm = (size_t)(CX ? 3 : 2) * TC_M * TC_KMAX * 2;
   // one attribute call per instantiation (thread-safe static initialisation)
   static const bool opened =
@@ -239,7 +254,7 @@ static void launch_tc(cudaStream_t st, int tiles, int n, int k, const float* A, 
       cudaSuccess;
   (void)opened;
   count_launch();
-  tc_syrk_kernel<FMT, CX><<<tiles, TC_THREADS, sm, st>>>(n, k, A, lda, C, ldc, round_out, err);
+  tc_syrk_kernel<FMT, CX><<<tiles, TC_THREADS, sm, st>>>(n, k, A, lda, C, ldc, round_out, err, wait_limit);
 }
 
 // C (n x n, ld ldc, lower triangle) -= A A^T (A A^H when cx: A, C complex
@@ -248,18 +263,19 @@ static void launch_tc(cudaStream_t st, int tiles, int n, int k, const float* A, 
 // entries to the format.  Returns false when k or fmt is out of range (the
 // caller then uses the CUDA-core GEMM).
 bool tc_syrk(cudaStream_t st, int fmt, bool cx, int n, int k, const float* A, long long lda, float* C,
-             long long ldc, bool round_out, int* err) {
+             long long ldc, bool round_out, int* err, long long wait_polls) {
+  const long long wl = wait_polls > 0 ? std::min(wait_polls, TC_WAIT_LIMIT) : TC_WAIT_LIMIT;
   if (n <= 0 || k <= 0) return true;
   if ((cx ? 2 * k : k) > TC_KMAX || (fmt != 1 && fmt != 2)) return false;
   const int nt = (n + TC_M - 1) / TC_M;
   const int tiles = nt * (nt + 1) / 2;
   const int r = round_out ? 1 : 0;
   if (fmt == 1) {
-    if (cx) launch_tc<0, true>(st, tiles, n, k, A, lda, C, ldc, r, err);
-    else launch_tc<0, false>(st, tiles, n, k, A, lda, C, ldc, r, err);
+    if (cx) launch_tc<0, true>(st, tiles, n, k, A, lda, C, ldc, r, err, wl);
+    else launch_tc<0, false>(st, tiles, n, k, A, lda, C, ldc, r, err, wl);
   } else {
-    if (cx) launch_tc<1, true>(st, tiles, n, k, A, lda, C, ldc, r, err);
-    else launch_tc<1, false>(st, tiles, n, k, A, lda, C, ldc, r, err);
+    if (cx) launch_tc<1, true>(st, tiles, n, k, A, lda, C, ldc, r, err, wl);
+    else launch_tc<1, false>(st, tiles, n, k, A, lda, C, ldc, r, err, wl);
   }
   return true;
 }
@@ -270,7 +286,7 @@ bool tc_syrk(cudaStream_t st, int fmt, bool cx, int n, int k, const float* A, lo
 #include "mplobpcg_steps.h"
 
 extern "C" mpl_status mpl_step_lowp_syrk(int fmt, int is_complex, int64_t n, int64_t k, const void* A, int64_t lda,
-                                         void* C, int64_t ldc, int round_out, void* stream) {
+                                         void* C, int64_t ldc, int round_out, int64_t wait_polls, void* stream) {
   const int64_t kmax = is_complex ? mpl::TC_KMAX / 2 : mpl::TC_KMAX;
   if ((fmt != 1 && fmt != 2) || n < 0 || k < 1 || k > kmax || !A || !C || lda < n || ldc < n ||
       n > (1LL << 31) - 1)
@@ -286,7 +302,7 @@ extern "C" mpl_status mpl_step_lowp_syrk(int fmt, int is_complex, int64_t n, int
   if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) s = MPL_ECUDA;
   if (s == MPL_OK)
     mpl::tc_syrk(st, fmt, is_complex != 0, (int)n, (int)k, static_cast<const float*>(A), lda,
-                 static_cast<float*>(C), ldc, round_out != 0, err);
+                 static_cast<float*>(C), ldc, round_out != 0, err, wait_polls);
   if (s == MPL_OK && cudaGetLastError() != cudaSuccess) s = MPL_ECUDA;
   if (s == MPL_OK && (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                       cudaStreamSynchronize(st) != cudaSuccess))

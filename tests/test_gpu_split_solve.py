@@ -1,7 +1,9 @@
 """The dense solve with its FP64 products on the tensor cores by error-free
-splitting (MPL_GEMM_SPLIT=1: A X and the large Gram / projection / update
-products) reaches the same eigenpairs as LAPACK at the requested tolerance.
-The switch is read once per process, so the solve runs in a child process."""
+splitting (MPL_GEMM_SPLIT=1: A X at every order and the large Gram /
+projection / update products) reaches the same eigenpairs as LAPACK at the
+requested tolerance, and so does the solve with every FP64 product on the
+DFMA pipe (MPL_GEMM_SPLIT=0 MPL_AX_SPLIT=0).  The switches are read once per
+process, so each solve runs in a child process."""
 import json
 import os
 import subprocess
@@ -42,9 +44,11 @@ print(json.dumps({"lam": [float(x) for x in lam], "its": list(map(int, its))}))
 """
 
 
+@pytest.mark.parametrize("switches", [{"MPL_GEMM_SPLIT": "1"}, {"MPL_GEMM_SPLIT": "0", "MPL_AX_SPLIT": "0"}],
+                         ids=["split", "dfma"])
 @pytest.mark.parametrize("cx,n,k,m", [(True, 4096, 16, 96), (False, 3000, 8, 96)])
-def test_split_product_solve_matches_eigh(cx, n, k, m, tmp_path):
-    env = dict(os.environ, MPL_GEMM_SPLIT="1")
+def test_split_product_solve_matches_eigh(cx, n, k, m, switches, tmp_path):
+    env = dict(os.environ, **switches)
     xfile = str(tmp_path / "X.npy")
     r = subprocess.run([sys.executable, "-c", CHILD, ROOT, str(n), str(k), str(m), "1" if cx else "0", xfile],
                        env=env, capture_output=True, text=True, timeout=600)

@@ -78,5 +78,22 @@ def test_lowp_syrk_rejects_bad_arguments():
     A = torch.zeros((8, 16), dtype=torch.float32, device="cuda:0")
     C = torch.zeros((16, 16), dtype=torch.float32, device="cuda:0")
     for fmt_code, cx, k in ((3, 0, 8), (1, 0, 0), (1, 0, 129), (2, 1, 65)):
-        st = M.binding._lowp_syrk(fmt_code, cx, 16, k, M.binding._ptr(A), 16, M.binding._ptr(C), 16, 0, None)
+        st = M.binding._lowp_syrk(fmt_code, cx, 16, k, M.binding._ptr(A), 16, M.binding._ptr(C), 16, 0, 0, None)
         assert st == 1
+
+
+def test_lowp_syrk_wait_that_runs_out_reports_error():
+    """A completion wait limited to one poll gives up before the MMAs finish:
+    the kernel records the error, waits for its MMAs at the normal limit,
+    leaves C untouched and frees its tensor memory; the call returns
+    MPL_ECUDA and the context stays usable."""
+    n, k = 512, 128
+    A, C = _case("bf16", n, k, False, 5)
+    Ad = torch_dev(np.ascontiguousarray(A.T))
+    Cd = torch_dev(np.ascontiguousarray(C.T))
+    with pytest.raises(M.MplError) as e:
+        M.lowp_syrk("bf16", Ad, Cd, wait_polls=1)
+    assert e.value.status == 7                       # MPL_ECUDA
+    torch.cuda.synchronize()
+    assert np.array_equal(Cd.cpu().numpy().T, C)    # the epilogue did not run
+    assert np.array_equal(_run("bf16", A, C), _run("bf16", A, C))   # and the next call works
