@@ -12,7 +12,7 @@ complex Gaussian).  Prints one JSON line.
                   [--workload NAME] [--policy mp] [--no-fp64] [--no-e2e]
                   [--no-cpu-baseline]
   profiling helpers (their lines are marked as not bench values):
-                  [--profile-iters I] [--n N] [--kernel-probe apply|precond|eig|factor]
+                  [--profile-iters I] [--n N] [--kernel-probe apply|precond|eig|factor|fma]
   With MPL_PROFILE_RANGE=a:b set, the library brackets working-precision
   iterations a..b with cudaProfilerStart/Stop (for ncu --profile-from-start off).
 
@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--adjoint", action="store_true",
                     help="sparse workloads: one step = forward (finite-volume assembly + Algorithm 3) and backward "
                          "(the adjoint to the coefficient field) through the autograd wrappers")
-    ap.add_argument("--kernel-probe", default="", choices=["", "apply", "precond", "eig", "factor"],
+    ap.add_argument("--kernel-probe", default="", choices=["", "apply", "precond", "eig", "factor", "fma"],
                     help="profiling runs only: time one step entry point (A X, T R, or the "
                          "3m x 3m eigensolver) K times after W warm-ups instead of full solves")
     return ap.parse_args()
@@ -312,6 +312,13 @@ def main():
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
+    if args.kernel_probe == "fma":
+        # measured CUDA-core FMA rates (the FP64 and FP32 roofline denominators)
+        r64 = [M.probe_fma_rate(64, 1 << 16, stream) for _ in range(3)]
+        r32 = [M.probe_fma_rate(32, 1 << 20, stream) for _ in range(3)]
+        print(json.dumps({"kernel_probe": "fma", "dfma_tflops": max(r64), "ffma_tflops": max(r32),
+                          "runs": {"dfma": r64, "ffma": r32}, "note": "profiling helper; not a bench value"}))
+        return 0
     if w.kind == "batch":
         return run_batch(args, w, M, dev, stream, torch, rank, dist)
     if args.adjoint:

@@ -129,6 +129,9 @@ mpl_status mpl_step_split_gemm(int is_complex, int trans_a, int64_t n, int64_t k
  * (n x k, ld lda; 1 <= k <= 128 real, <= 64 complex) whose values are
  * converted to the format fmt (1 fp16, 2 bf16; exact when they already are
  * values of it), products accumulated in FP32 by tcgen05.mma (kind::f16).
+ * fmt = 3: the FP32 factor's update by 3xTF32 products (each FP32 value cut
+ * into a TF32 part and a TF32 remainder; the three leading products
+ * accumulated in FP32 by tcgen05.mma kind::tf32; round_out is ignored).
  * Storage is column-major FP32, complex interleaved (re, im) with ld in
  * complex elements.  round_out != 0: the updated entries are rounded to the
  * format.  The strictly upper part of C is not touched.  wait_polls: the
@@ -157,6 +160,21 @@ mpl_status mpl_step_lowp_syrk(int fmt, int is_complex, int64_t n, int64_t k, con
  * MPL_ECUDA.
  */
 mpl_status mpl_start_block(int dtype, int64_t n, int m, uint64_t seed, void* X, void* stream);
+
+/* Measured rate of the CUDA-core fused multiply-add pipe, the denominator
+ * of the rooflines of the FP64 kernels on the CUDA cores (the FP64 block
+ * product below the split product's threshold, DLOBPCG's fallbacks) and of
+ * the FP32 factor and sweeps (Section 5.1's lower-precision Cholesky and
+ * triangular solves).  Not a step of Algorithm 3.
+ *
+ * precision: 64 (DFMA) or 32 (FFMA).  iters: fused multiply-adds per chain
+ * (1 .. 2^24; 2^16 takes tens of milliseconds in FP64).  tflops: host
+ * pointer, receives 2 x FMAs / second / 1e12 of the second of two
+ * identical launches (8 x SMs blocks of 256 threads, 8 independent chains
+ * per thread), timed with CUDA events on stream.  Synchronous.  Allocates
+ * one element of device memory.  Errors: MPL_EINVAL (precision, iters, NULL
+ * tflops), MPL_ECUDA. */
+mpl_status mpl_probe_fma_rate(int precision, int64_t iters, double* tflops, void* stream);
 
 /* Residual without device allocation (the paper has no counterpart).
  *

@@ -11,5 +11,5 @@ Import fails loudly when the CUDA library has not been built
 from .binding import (  # noqa: F401
     LIB_PATH, Batch, MPL_C128, MPL_D_DCHOL, MPL_D_SCHOL, MPL_MP_SCHOL, MPL_R64, POLICIES, MplError,
     Stats, Handle, analyze_host, create_csr, create_dense, eigsh_csr, fv_assemble, fv_assemble_adjoint,
-    fv_values, lib, lowp_syrk, residual_noalloc, split_gemm,
+    fv_values, lib, lowp_syrk, probe_fma_rate, residual_noalloc, split_gemm, start_block,
 )

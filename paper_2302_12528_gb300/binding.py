@@ -66,6 +66,7 @@ _factor = _sig("mpl_factor", _i, [_h])
 _solve = _sig("mpl_solve", _i, [_h, _p, _i, C.c_uint64, _i, _p, _p, _i, _p, _i, _p, _p])
 _pinvit = _sig("mpl_solve_pinvit", _i, [_h, _p, _i, C.c_uint64, _i, _p, _p, _i, _p, _i, _p, _p])
 _start_block = _sig("mpl_start_block", _i, [_i, _i64, _i, C.c_uint64, _p, _p])
+_probe_fma_rate = _sig("mpl_probe_fma_rate", _i, [_i, _i64, C.POINTER(C.c_double), _p])
 _adjoint = _sig("mpl_adjoint", _i, [_h, _p, _p, _p, _i, _d, _p, _p])
 _fv_assemble = _sig("mpl_fv_assemble", _i, [_i, _p, _p, _p, _p, _p, _p])
 _fv_assemble_adjoint = _sig("mpl_fv_assemble_adjoint", _i, [_i, _p, _p, _p, _p, _p, _p])
@@ -352,6 +353,16 @@ def start_block(X, seed, stream=None):
         raise MplError(st, "mpl_start_block", 0)
 
 
+def probe_fma_rate(precision, iters=1 << 16, stream=None):
+    """mpl_probe_fma_rate: measured TFLOP/s of the CUDA-core FMA pipe
+    (precision 64: DFMA, 32: FFMA)."""
+    out = C.c_double(0.0)
+    st = _probe_fma_rate(precision, iters, C.byref(out), _stream_ptr(stream))
+    if st != 0:
+        raise MplError(st, "mpl_probe_fma_rate", 0)
+    return out.value
+
+
 def residual_noalloc(dtype, n, m, AX, X, theta, R, norms2, stream=None):
     """mpl_residual_noalloc: every argument a device tensor (theta: m float64,
     norms2: 2m float64).  Allocates nothing on the device; see the header."""
@@ -529,12 +540,13 @@ class Batch:
 def lowp_syrk(fmt, A, C, round_out=False, stream=None, wait_polls=0):
     """mpl_step_lowp_syrk: C -= A A^H (lower) on the tensor cores.  A and C
     are column-major device tensors given as (k, n) / (n, n) row-major
-    arrays, float32 or complex64; fmt "fp16" or "bf16".  wait_polls: limit of
-    the MMA completion wait (0: the library's)."""
+    arrays, float32 or complex64; fmt "fp16", "bf16" or "tf32x3" (FP32
+    values, three TF32 products).  wait_polls: limit of the MMA completion
+    wait (0: the library's)."""
     k, n = A.shape
     cx = 1 if A.is_complex() else 0
-    st = _lowp_syrk({"fp16": 1, "bf16": 2}[fmt], cx, n, k, _ptr(A), n, _ptr(C), n, 1 if round_out else 0,
-                    int(wait_polls), _stream_ptr(stream))
+    st = _lowp_syrk({"fp16": 1, "bf16": 2, "tf32x3": 3}[fmt], cx, n, k, _ptr(A), n, _ptr(C), n,
+                    1 if round_out else 0, int(wait_polls), _stream_ptr(stream))
     if st != 0:
         raise MplError(st, "mpl_step_lowp_syrk failed", 0)
 

@@ -20,7 +20,8 @@ OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libmplobpcg.so")
 
 SOURCES = ["blas.cu", "small.cu", "eig_cluster.cu", "dense_chol.cu", "spmm.cu", "sparse.cu", "symbolic.cpp",
-           "api.cu", "noalloc.cu", "adjoint.cu", "batch.cu", "tc_syrk.cu", "oz_gemm.cu", "rng.cu"]
+           "api.cu", "noalloc.cu", "adjoint.cu", "batch.cu", "tc_syrk.cu", "oz_gemm.cu", "rng.cu",
+           "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + CSRC, "-I" + INCLUDE]

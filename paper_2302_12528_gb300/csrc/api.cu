@@ -143,6 +143,17 @@ inline bool mp_like(int policy) {
 }
 // 16-bit storage format of the factor: 0 none, 1 fp16, 2 bf16.
 inline int fmt16_of(int policy) { return policy == MPL_MP_HCHOL ? 1 : policy == MPL_MP_BCHOL ? 2 : 0; }
+// Explored stage (extension of Section 5.1's lower precision): the dense FP32
+// factor's trailing updates by 3xTF32 products on the tensor cores, with
+// MPL_FACTOR_TF32X3=1.  The factor stays FP32; each product carries an error
+// of about 2^-22 of its size instead of FP32's per-operation 2^-24.
+inline bool factor_tf32x3() {
+  static const bool on = [] {
+    const char* e = std::getenv("MPL_FACTOR_TF32X3");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
 // The real 16-bit factor's trailing update runs on the tensor cores unless
 // MPL_FMT16_TC=0 (then on the CUDA-core GEMM, for comparison).
 inline bool fmt16_tc() {
@@ -338,9 +349,11 @@ class Engine : public EngineBase {
       else cast<TF, TW>(st, (int)n, (int)n, Aw_.as<TW>(), n, F.L, n);
       if (sigma != 0.0) add_diag<TF>(st, (int)n, F.L, n, sigma);
       round_block<TF>(st, (int)n, (int)n, F.L, n, fmt, true);
-      int* tc_err = (fmt && fmt16_tc()) ? info_.as<int>() + 1 : nullptr;
+      // 3: the FP32 factor's trailing updates by 3xTF32 on the tensor cores
+      const int dfmt = fmt ? fmt : (sizeof(real_t<TF>) == 4 && factor_tf32x3()) ? 3 : 0;
+      int* tc_err = (dfmt == 3 || (dfmt && fmt16_tc())) ? info_.as<int>() + 1 : nullptr;
       if (tc_err) MPL_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int), st));
-      dense_cholesky<TF>(st, F, tmp_.as<TF>(), info_.as<int>(), scr_, -1, 0, true, fmt, tc_err);
+      dense_cholesky<TF>(st, F, tmp_.as<TF>(), info_.as<int>(), scr_, -1, 0, true, dfmt, tc_err);
       int info[2] = {0, 0};
       MPL_CUDA(cudaMemcpyAsync(info, info_.ptr(), 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
       MPL_CUDA(cudaStreamSynchronize(st));
@@ -568,6 +581,14 @@ class Engine : public EngineBase {
       cudaStream_t st = c_->stream;
       const long long n = c_->n;
       const int k = c_->k;
+      // split-K partials of the k x k products X_k^T V over the n rows (a
+      // sparse handle has no scratch of its own; without it one CTA would
+      // stream all n rows)
+      if (scr_.bytes < ((size_t)48 << 20)) {
+        scr_mem_.alloc((size_t)48 << 20);
+        scr_.ptr = scr_mem_.ptr();
+        scr_.bytes = scr_mem_.bytes();
+      }
       const size_t blk = sizeof(double) * n * k;
       adj_.ensure(blk * 8 + sizeof(double) * ((size_t)ceil_div(n, 4096) * k + 8 * (size_t)k * k + 16 * k));
       double* G = adj_.as<double>();

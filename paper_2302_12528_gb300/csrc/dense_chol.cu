@@ -122,7 +122,7 @@ __global__ void round_block_kernel(int rows, int cols, T* A, long long lda, int 
 
 template <typename T>
 void round_block(cudaStream_t st, int rows, int cols, T* A, long long lda, int fmt, bool lower_only) {
-  if (fmt == 0 || rows <= 0 || cols <= 0) return;
+  if (fmt == 0 || fmt == 3 || rows <= 0 || cols <= 0) return;  // 3: FP32 storage, nothing to round
   const long long tot = (long long)rows * cols;
   count_launch();
   round_block_kernel<T><<<(int)std::min<long long>((tot + 255) / 256, 8 * NUM_SMS), 256, 0, st>>>(
@@ -241,9 +241,14 @@ void scale_rows(cudaStream_t st, int n, int m, T* B, long long ldb, const float*
 // iteration limit; a CTA that gives up records an error word (read by the
 // host after the solve) and still publishes its block, so no wait runs on
 // indefinitely.
-template <typename T> struct Sweep { static constexpr int NBS = 32, CT = 32; };
-template <> struct Sweep<float> { static constexpr int NBS = 64, CT = 32; };
-template <> struct Sweep<zf> { static constexpr int NBS = 64, CT = 32; };
+// NBS: rows of a block row; CT: right-hand sides per item; DB: two tile
+// buffers (the next tile is loaded while the current one is multiplied).
+// The FP32 sweeps wait on memory and take DB; the FP64 ones are bound by the
+// FP64 pipe, where twice the shared memory per CTA only lowers the number of
+// resident CTAs.
+template <typename T> struct Sweep { static constexpr int NBS = 32, CT = 32; static constexpr bool DB = false; };
+template <> struct Sweep<float> { static constexpr int NBS = 64, CT = 32; static constexpr bool DB = true; };
+template <> struct Sweep<zf> { static constexpr int NBS = 64, CT = 32; static constexpr bool DB = true; };
 
 constexpr long long SWEEP_WAIT_LIMIT = 1LL << 24;  // flag polls (with a short sleep) before giving up
 
@@ -268,27 +273,46 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Asynchronous element copies global -> shared (cp.async; 4, 8 or 16 bytes,
+// the element's own alignment, so any leading dimension works).  The factor
+// is read-only during a sweep, so L1-cached copies are fine for it.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  if constexpr (sizeof(T) == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"((int)sizeof(T)) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // sync: [0] claim counter (zeroed before the launch), [1] error word,
 // [2 + i * nct + c] the flag of item (i, c) (= epoch once published).
-template <typename T, int NBS, int CT, bool BACK>
-__global__ void __launch_bounds__(256)
+// Per tile update one barrier: the next factor tile is copied asynchronously
+// and the next Y block read into registers (each thread acquires the row's
+// flag itself) while the current tile is multiplied; two buffers alternate.
+template <typename T, int NBS, int CT, bool BACK, bool DB>
+__global__ void __launch_bounds__(256, DB ? 2 : 4)
 trsm_sweep_kernel(int n, int nsb, int nct, const T* __restrict__ L, long long ldl, const T* __restrict__ Dinv,
                   int dnb, T* B, long long ldb, int m, unsigned* sync, unsigned epoch) {
   constexpr int LDS = NBS + 1;
   constexpr int TM = NBS / 16, TN = CT / 16;
+  constexpr int YPT = NBS * CT / 256;  // elements of a Y block per thread
+  static_assert(NBS * CT % 256 == 0, "whole Y block per thread");
   extern __shared__ unsigned char sm[];
-  T* Ls = reinterpret_cast<T*>(sm);  // Ls[kk * LDS + r]
-  T* Ys = Ls + NBS * LDS;            // Ys[kk * CT + c]
-  __shared__ int item, gave_up;
+  // buffer q: factor tile at L0 + q NBS LDS (forward [kk * LDS + r];
+  // backward [r * LDS + kk], the raw L_ji), Y block at Y0 + q NBS CT ([kk * CT + c])
+  T* const L0 = reinterpret_cast<T*>(sm);
+  T* const Y0 = L0 + (DB ? 2 : 1) * NBS * LDS;
+  __shared__ int item;
   const int tid = threadIdx.x;
   const int tr = tid & 15, tc = tid >> 4;
   unsigned* flags = sync + 2;
   const int nitems = nsb * nct;
+  bool gave_up = false;
   for (;;) {
-    if (tid == 0) {
-      item = (int)atomicAdd(sync, 1u);
-      gave_up = 0;
-    }
+    if (tid == 0) item = (int)atomicAdd(sync, 1u);
     __syncthreads();
     const int t = item;
     if (t >= nitems) break;
@@ -296,6 +320,54 @@ trsm_sweep_kernel(int n, int nsb, int nct, const T* __restrict__ L, long long ld
     const int i = BACK ? nsb - 1 - step : step;
     const int ct0 = c * CT, cw = min(CT, m - ct0);
     const int r0 = i * NBS, rb = min(NBS, n - r0);
+    auto jof = [&](int s2) { return BACK ? nsb - 1 - s2 : s2; };
+    // the factor tile (i, j) into buffer q, asynchronously
+    auto stage_L = [&](int q, int j) {
+      const int rk0 = j * NBS, kb = min(NBS, n - rk0);
+      T* Ls = L0 + q * NBS * LDS;
+      for (int e = tid; e < NBS * NBS; e += 256) {
+        if (!BACK) {  // L_ij(r, kk) at [kk * LDS + r]
+          const int r = e % NBS, kk = e / NBS;
+          if (r < rb && kk < kb) cp_async_elem(Ls + kk * LDS + r, L + (r0 + r) + (long long)(rk0 + kk) * ldl);
+          else Ls[kk * LDS + r] = zero_<T>();
+        } else {      // L_ji(kk, r) at [r * LDS + kk]; conjugated when read
+          const int kk = e % NBS, r = e / NBS;
+          if (r < rb && kk < kb) cp_async_elem(Ls + r * LDS + kk, L + (rk0 + kk) + (long long)(r0 + r) * ldl);
+          else Ls[r * LDS + kk] = zero_<T>();
+        }
+      }
+      cp_async_commit();
+    };
+    // Y_j's flag: poll once, or wait (bounded) for it
+    auto flag_ready = [&](int j) { return gave_up || ld_acquire(flags + (size_t)j * nct + c) == epoch; };
+    auto wait_flag = [&](int j) {
+      long long it = 0;
+      while (!flag_ready(j)) {
+        if (++it >= SWEEP_WAIT_LIMIT) {
+          gave_up = true;
+          atomicExch(sync + 1, 1u);
+          break;
+        }
+        __nanosleep(32);
+      }
+    };
+    // this thread's elements of Y_j into registers (after its flag was seen)
+    T yr[YPT];
+    auto load_Y = [&](int j) {
+      const int rk0 = j * NBS, kb = min(NBS, n - rk0);
+#pragma unroll
+      for (int q = 0; q < YPT; ++q) {
+        const int e = tid + 256 * q, kk = e % NBS, cc = e / NBS;
+        yr[q] = (kk < kb && cc < cw) ? ldcg_(B + (rk0 + kk) + (long long)(ct0 + cc) * ldb) : zero_<T>();
+      }
+    };
+    auto put_Y = [&](int q) {
+#pragma unroll
+      for (int u = 0; u < YPT; ++u) {
+        const int e = tid + 256 * u, kk = e % NBS, cc = e / NBS;
+        Y0[q * NBS * CT + kk * CT + cc] = yr[u];
+      }
+    };
 
     T acc[TM][TN];
 #pragma unroll
@@ -305,51 +377,66 @@ trsm_sweep_kernel(int n, int nsb, int nct, const T* __restrict__ L, long long ld
         const int r = tr + 16 * a, cc = tc + 16 * b;
         acc[a][b] = (r < rb && cc < cw) ? ldcg_(B + (r0 + r) + (long long)(ct0 + cc) * ldb) : zero_<T>();
       }
-    for (int s2 = 0; s2 < step; ++s2) {
-      const int j = BACK ? nsb - 1 - s2 : s2;
-      const int rk0 = j * NBS, kb = min(NBS, n - rk0);
-      // the factor tile is final: stage it before waiting for Y_j
-      for (int e = tid; e < NBS * NBS; e += 256) {
-        const int a = e % NBS, b = e / NBS;
-        if (!BACK) {  // L_ij(r = a, kk = b)
-          Ls[b * LDS + a] = (a < rb && b < kb) ? L[(r0 + a) + (long long)(rk0 + b) * ldl] : zero_<T>();
-        } else {      // (L_ji)^*(r = b, kk = a) = conj(L_ji(a, b))
-          Ls[a * LDS + b] = (a < kb && b < rb) ? conj_(L[(rk0 + a) + (long long)(r0 + b) * ldl]) : zero_<T>();
-        }
-      }
-      if (tid == 0 && !gave_up) {
-        const unsigned* f = flags + (size_t)j * nct + c;
-        long long it = 0;
-        while (ld_acquire(f) != epoch) {
-          if (++it >= SWEEP_WAIT_LIMIT) {
-            gave_up = 1;
-            atomicExch(sync + 1, 1u);
-            break;
-          }
-          __nanosleep(32);
-        }
-      }
+    if (step > 0) {
+      stage_L(0, jof(0));
+      wait_flag(jof(0));
+      load_Y(jof(0));
+      put_Y(0);
+      cp_async_wait_all();
       __syncthreads();
-      for (int e = tid; e < NBS * CT; e += 256) {
-        const int kk = e % NBS, cc = e / NBS;
-        Ys[kk * CT + cc] = (kk < kb && cc < cw) ? ldcg_(B + (rk0 + kk) + (long long)(ct0 + cc) * ldb) : zero_<T>();
-      }
-      __syncthreads();
+      for (int s2 = 0; s2 < step; ++s2) {
+        const int q = DB ? (s2 & 1) : 0;
+        const bool more = s2 + 1 < step;
+        // DB: the next tile's factor part is always prefetched; its Y part
+        // only when already published (else read after this tile's product,
+        // so that a row still in flight does not hold up the product)
+        bool early = false;
+        if (DB && more) {
+          stage_L(q ^ 1, jof(s2 + 1));
+          early = flag_ready(jof(s2 + 1));
+          if (early) load_Y(jof(s2 + 1));
+        }
+        const T* Ls = L0 + q * NBS * LDS;
+        const T* Ys = Y0 + q * NBS * CT;
 #pragma unroll 4
-      for (int kk = 0; kk < NBS; ++kk) {
-        T av[TM], bv[TN];
+        for (int kk = 0; kk < NBS; ++kk) {
+          T av[TM], bv[TN];
 #pragma unroll
-        for (int a = 0; a < TM; ++a) av[a] = -Ls[kk * LDS + tr + 16 * a];
+          for (int a = 0; a < TM; ++a)
+            av[a] = BACK ? -conj_(Ls[(tr + 16 * a) * LDS + kk]) : -Ls[kk * LDS + tr + 16 * a];
 #pragma unroll
-        for (int b = 0; b < TN; ++b) bv[b] = Ys[kk * CT + tc + 16 * b];
+          for (int b = 0; b < TN; ++b) bv[b] = Ys[kk * CT + tc + 16 * b];
 #pragma unroll
-        for (int a = 0; a < TM; ++a)
+          for (int a = 0; a < TM; ++a)
 #pragma unroll
-          for (int b = 0; b < TN; ++b) fma_(acc[a][b], av[a], bv[b]);
+            for (int b = 0; b < TN; ++b) fma_(acc[a][b], av[a], bv[b]);
+        }
+        if (DB) {
+          if (more) {
+            if (!early) {
+              wait_flag(jof(s2 + 1));
+              load_Y(jof(s2 + 1));
+            }
+            put_Y(q ^ 1);
+          }
+          cp_async_wait_all();
+          __syncthreads();
+        } else {  // one buffer: refill it after everyone has read it
+          __syncthreads();
+          if (more) {
+            stage_L(0, jof(s2 + 1));
+            wait_flag(jof(s2 + 1));
+            load_Y(jof(s2 + 1));
+            put_Y(0);
+            cp_async_wait_all();
+            __syncthreads();
+          }
+        }
       }
-      __syncthreads();
     }
     // Y_i = Dinv_ii (B_i - sum_j L_ij Y_j)   (backward: the conjugate transpose)
+    T* Ls = L0;
+    T* Ys = Y0;
 #pragma unroll
     for (int a = 0; a < TM; ++a)
 #pragma unroll
@@ -395,7 +482,7 @@ trsm_sweep_kernel(int n, int nsb, int nct, const T* __restrict__ L, long long ld
 template <typename T>
 static size_t sweep_smem() {
   constexpr int NBS = Sweep<T>::NBS, CT = Sweep<T>::CT;
-  return ((size_t)NBS * (NBS + 1) + (size_t)NBS * CT) * sizeof(T);
+  return (Sweep<T>::DB ? 2 : 1) * ((size_t)NBS * (NBS + 1) + (size_t)NBS * CT) * sizeof(T);
 }
 
 // Per-stream synchronisation words of the persistent sweeps (claim counter,
@@ -425,7 +512,7 @@ static void dense_sweep(cudaStream_t st, const DenseFactor<T>& F, T* B, long lon
   const int n = F.n, nsb = ceil_div(n, NBS), nct = ceil_div(m, CT);
   if (n <= 0 || m <= 0) return;
   const size_t sm = sweep_smem<T>();
-  auto kern = trsm_sweep_kernel<T, NBS, CT, BACK>;
+  auto kern = trsm_sweep_kernel<T, NBS, CT, BACK, Sweep<T>::DB>;
   // as many CTAs as fit at once (measured: faster than one per SM -- the
   // off-chain updates need the throughput more than the chain needs an SM
   // of its own)

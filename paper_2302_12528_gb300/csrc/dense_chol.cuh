@@ -28,6 +28,8 @@ struct DenseFactor {
 // fmt16 (0 none, 1 fp16, 2 bf16): the matrix is stored in that 16-bit
 // format -- the diagonal block, the panel and the trailing update are
 // rounded to it after each step (arithmetic in T; FP32 types only).
+// fmt16 = 3 (FP32 types): FP32 storage, the trailing update by 3xTF32
+// products on the tensor cores (needs tc_err).
 // tc_err (FP32 types with fmt16 only): when given, the trailing update runs
 // on the tensor cores (tcgen05, 16-bit operands exact, FP32 accumulation,
 // rounded to the format in its epilogue) and *tc_err becomes nonzero if an

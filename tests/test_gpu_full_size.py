@@ -114,3 +114,44 @@ def test_diffusion3d_64_full_size():
         o1, o2 = ref["mp"]["iters"]
         assert abs(its[1] - o2) <= max(3, o2 // 4), (its, ref["mp"]["iters"])
         assert np.allclose(lam, ref["mp"]["theta"], rtol=1e-10, atol=0)
+
+
+def test_diffusion2d_512_adjoint_directional_differences():
+    """The differentiable solve at the 512^2 workload's size (n = 262144,
+    k = 16, m = 24, sigma = 0.5): the adjoint's gradient with respect to the
+    coefficient field, along a seeded direction, against central
+    differences of the same GPU pipeline (eigenvalue sum and the loss with
+    ||x_1 - x_ref||^2); 32^2 checks against the dense eigh gradient are in
+    test_gpu_adjoint.py."""
+    w = W.WORKLOADS["diffusion2d_512"]
+    rp, ci, v, c = W.diffusion_csr(w.dims, w.seed, w.ell, w.sigma)
+    n = w.n
+    rpt, cit = torch_dev(rp), torch_dev(ci)
+    c0 = torch_dev(np.ascontiguousarray(c.reshape(-1)))
+    X0 = torch_dev(W.start_block(n, w.m, w.seed + 1))
+    Om = W.sketch(n, 8, w.seed + 2)
+    xr = np.random.default_rng(w.seed + 3).standard_normal(n)
+    xref = torch_dev(xr / np.linalg.norm(xr))
+
+    def loss(cvec, eig_only, grad):
+        cc = cvec.detach().clone().requires_grad_(grad)
+        vals = M.fv_values(cc, w.dims, rpt, cit)
+        lam, X = M.eigsh_csr(vals, rpt, cit, w.k, w.m, X0, Om, tol=w.tol, policy="mp", grid_dims=w.dims)
+        L = lam.sum()
+        if not eig_only:
+            x1 = X[:, 0]
+            L = L + ((torch.sign(torch.dot(x1.detach(), xref)) * x1 - xref) ** 2).sum()
+        if grad:
+            L.backward()
+        return float(L.item()), (cc.grad if grad else None)
+
+    d = c0 * torch_dev(np.random.default_rng(w.seed + 4).standard_normal(n))
+    for eig_only in (True, False):
+        _, g = loss(c0, eig_only, True)
+        if not eig_only:   # the eigenvector term's projected shifted solve (none for the eigenvalue sum)
+            assert 0 < M.binding.last_adjoint["cg_iterations"] <= 500
+            assert M.binding.last_adjoint["cg_rel_resid"] <= 1e-10
+        eps = 1e-5
+        fd = (loss(c0 + eps * d, eig_only, False)[0] - loss(c0 - eps * d, eig_only, False)[0]) / (2 * eps)
+        ana = float(torch.dot(g, d).item())
+        assert abs(fd - ana) <= 1e-5 * abs(fd), (eig_only, fd, ana)

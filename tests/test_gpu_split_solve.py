@@ -1,8 +1,10 @@
 """The dense solve with its FP64 products on the tensor cores by error-free
 splitting (MPL_GEMM_SPLIT=1: A X at every order and the large Gram /
 projection / update products) reaches the same eigenpairs as LAPACK at the
-requested tolerance, and so does the solve with every FP64 product on the
-DFMA pipe (MPL_GEMM_SPLIT=0 MPL_AX_SPLIT=0).  The switches are read once per
+requested tolerance, and so do the solve with every FP64 product on the
+DFMA pipe (MPL_GEMM_SPLIT=0 MPL_AX_SPLIT=0) and the solve whose FP32
+factor takes its trailing updates from 3xTF32 tensor-core products
+(MPL_FACTOR_TF32X3=1).  The switches are read once per
 process, so each solve runs in a child process."""
 import json
 import os
@@ -44,8 +46,9 @@ print(json.dumps({"lam": [float(x) for x in lam], "its": list(map(int, its))}))
 """
 
 
-@pytest.mark.parametrize("switches", [{"MPL_GEMM_SPLIT": "1"}, {"MPL_GEMM_SPLIT": "0", "MPL_AX_SPLIT": "0"}],
-                         ids=["split", "dfma"])
+@pytest.mark.parametrize("switches", [{"MPL_GEMM_SPLIT": "1"}, {"MPL_GEMM_SPLIT": "0", "MPL_AX_SPLIT": "0"},
+                                      {"MPL_FACTOR_TF32X3": "1"}],
+                         ids=["split", "dfma", "tf32x3-factor"])
 @pytest.mark.parametrize("cx,n,k,m", [(True, 4096, 16, 96), (False, 3000, 8, 96)])
 def test_split_product_solve_matches_eigh(cx, n, k, m, switches, tmp_path):
     env = dict(os.environ, **switches)

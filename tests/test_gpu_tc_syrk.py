@@ -77,7 +77,7 @@ def test_lowp_syrk_rounded_epilogue(fmt, cx):
 def test_lowp_syrk_rejects_bad_arguments():
     A = torch.zeros((8, 16), dtype=torch.float32, device="cuda:0")
     C = torch.zeros((16, 16), dtype=torch.float32, device="cuda:0")
-    for fmt_code, cx, k in ((3, 0, 8), (1, 0, 0), (1, 0, 129), (2, 1, 65)):
+    for fmt_code, cx, k in ((4, 0, 8), (0, 0, 8), (1, 0, 0), (1, 0, 129), (2, 1, 65), (3, 1, 65)):
         st = M.binding._lowp_syrk(fmt_code, cx, 16, k, M.binding._ptr(A), 16, M.binding._ptr(C), 16, 0, 0, None)
         assert st == 1
 
@@ -97,3 +97,37 @@ def test_lowp_syrk_wait_that_runs_out_reports_error():
     torch.cuda.synchronize()
     assert np.array_equal(Cd.cpu().numpy().T, C)    # the epilogue did not run
     assert np.array_equal(_run("bf16", A, C), _run("bf16", A, C))   # and the next call works
+
+
+@pytest.mark.parametrize("cx,n,k", [(False, 300, 128), (False, 517, 97), (False, 1, 1), (True, 300, 64),
+                                    (True, 129, 7)])
+def test_tf32x3_update_has_fp32_class_accuracy(cx, n, k):
+    """fmt 3: FP32 values (not rounded to any format), three TF32 products
+    per product on the tensor cores; against the exact FP64 update the error
+    stays within a few 2^-22 of |A| |A|^T plus FP32 rounding of the
+    accumulation and of C (2^-24 per operation), far below a single TF32
+    product's 2^-11."""
+    rng = np.random.default_rng(7 * n + k)
+    A = rng.standard_normal((n, k))
+    C = rng.standard_normal((n, n))
+    if cx:
+        A = A + 1j * rng.standard_normal((n, k))
+        C = C + 1j * rng.standard_normal((n, n))
+    A = A.astype(np.complex64 if cx else np.float32)
+    C = C.astype(np.complex64 if cx else np.float32)
+    Ad = torch_dev(np.ascontiguousarray(A.T))
+    Cd = torch_dev(np.ascontiguousarray(C.T))
+    M.lowp_syrk("tf32x3", Ad, Cd)
+    torch.cuda.synchronize()
+    out = Cd.cpu().numpy().T
+    A64 = A.astype(np.complex128 if cx else np.float64)
+    exact = C.astype(A64.dtype) - A64 @ A64.conj().T
+    Aa = np.abs(A64.real) + np.abs(A64.imag) if cx else np.abs(A64)
+    depth = 2 * k if cx else k
+    bound = (8 * 2.0 ** -22 + 2 * (depth + 2) * U32) * (Aa @ Aa.T) + 2 * U32 * np.abs(C)
+    lo = np.tril(np.ones((n, n), dtype=bool))
+    err = np.maximum(np.abs((out - exact).real), np.abs((out - exact).imag))
+    assert np.all(err[lo] <= bound[lo]), np.max((err - bound)[lo])
+    assert np.array_equal(out[~lo], C[~lo])
+    # a single TF32 product would be off by ~2^-11 |A||A|^T: the split is doing its work
+    assert np.max(err[lo] / (Aa @ Aa.T)[lo]) < 2.0 ** -16

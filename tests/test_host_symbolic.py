@@ -191,7 +191,7 @@ def test_step_entries_validate_arguments_before_any_device_work():
                              (1, 8, 16, 8, 8)):   # transposed storage needs lda >= k
         assert b._split_gemm(0, tr, n, k, m, dummy, lda, dummy, max(k, 1), dummy, max(n, 1), None) == 1
     # mpl_step_lowp_syrk(fmt, is_complex, n, k, A, lda, C, ldc, round_out, wait_polls, stream)
-    for fmt, cx, k in ((3, 0, 8), (1, 0, 0), (1, 0, 129), (2, 1, 65)):
+    for fmt, cx, k in ((4, 0, 8), (0, 0, 8), (1, 0, 0), (1, 0, 129), (2, 1, 65), (3, 1, 65)):
         assert b._lowp_syrk(fmt, cx, 16, k, dummy, 16, dummy, 16, 0, 0, None) == 1
 
 
