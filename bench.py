@@ -42,7 +42,7 @@ sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
 
-FP64_PEAK_GFLOPS = 1250.0     # nominal GB300 FP64 (152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz ~ 1.26e3)
+FP64_PEAK_GFLOPS = 1058.0     # measured DFMA rate of this GB300 pool (bench.py --kernel-probe fma; nominal ~1.25e3)
 CACHE_DIR = os.path.join(tempfile.gettempdir(), "mplobpcg_bench_cache")
 
 
@@ -413,9 +413,9 @@ def main():
                            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic_per_launch(w),
                            "flops_per_launch": apply_flops / apply_calls, "launches": apply_calls,
                            "avg_launch_ms": per_launch_s * 1e3,
-                           "peak_note": "nominal FP64 of the recipe table, 152 SMs x 2 DFMA/clk x 2 flop x "
-                                        "2.07 GHz (DFMA microbenchmark: 1190); achieved counts the FP64 flops "
-                                        "the pipe executes"}
+                           "peak_note": "measured DFMA rate (mpl_probe_fma_rate through bench.py --kernel-probe "
+                                        "fma: 8 independent FMA chains per thread on every SM); achieved counts "
+                                        "the FP64 flops the pipe executes"}
         if cplx:
             out["roofline"]["complex_equivalent_gflops"] = achieved * 8.0 / 6.0
         if split_ax_active(w):
@@ -804,7 +804,7 @@ def run_batch(args, w, M, dev, stream, torch, rank, dist):
                      "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                      "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
                      "flops_per_launch": flops64, "launches": args.steps, "avg_launch_ms": ms,
-                     "peak_note": "nominal FP64; achieved counts only the FP64 products with A (the "
+                     "peak_note": "measured DFMA rate; achieved counts only the FP64 products with A (the "
                                   "Gram, projection and update flops and all FP32 work are extra)"},
     }
     if ck:

@@ -74,6 +74,16 @@ template <typename R> __device__ __forceinline__ void fma_(cplx<R>& acc, cplx<R>
   acc.y = fma(a.x, b.y, acc.y);
   acc.y = fma(a.y, b.x, acc.y);
 }
+// acc -= a * b  (negations folded into the fused operations)
+__device__ __forceinline__ void fms_(float& acc, float a, float b) { acc = fmaf(-a, b, acc); }
+__device__ __forceinline__ void fms_(double& acc, double a, double b) { acc = fma(-a, b, acc); }
+template <typename R> __device__ __forceinline__ void fms_(cplx<R>& acc, cplx<R> a, cplx<R> b) {
+  acc.x = fma(-a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(-a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+
 // acc += conj(a) * b
 __device__ __forceinline__ void fmac_(float& acc, float a, float b) { acc = fmaf(a, b, acc); }
 __device__ __forceinline__ void fmac_(double& acc, double a, double b) { acc = fma(a, b, acc); }

@@ -246,9 +246,23 @@ void scale_rows(cudaStream_t st, int n, int m, T* B, long long ldb, const float*
 // The FP32 sweeps wait on memory and take DB; the FP64 ones are bound by the
 // FP64 pipe, where twice the shared memory per CTA only lowers the number of
 // resident CTAs.
-template <typename T> struct Sweep { static constexpr int NBS = 32, CT = 32; static constexpr bool DB = false; };
-template <> struct Sweep<float> { static constexpr int NBS = 64, CT = 32; static constexpr bool DB = true; };
-template <> struct Sweep<zf> { static constexpr int NBS = 64, CT = 32; static constexpr bool DB = true; };
+// MINB: CTAs per SM the register allocation must allow.
+template <typename T> struct Sweep {
+  static constexpr int NBS = 32, CT = 32, MINB = 6;
+  static constexpr bool DB = false;
+};
+template <> struct Sweep<zd> {
+  static constexpr int NBS = 32, CT = 32, MINB = 4;
+  static constexpr bool DB = false;
+};
+template <> struct Sweep<float> {
+  static constexpr int NBS = 64, CT = 32, MINB = 2;
+  static constexpr bool DB = true;
+};
+template <> struct Sweep<zf> {
+  static constexpr int NBS = 64, CT = 32, MINB = 2;
+  static constexpr bool DB = true;
+};
 
 constexpr long long SWEEP_WAIT_LIMIT = 1LL << 24;  // flag polls (with a short sleep) before giving up
 
@@ -293,7 +307,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // and the next Y block read into registers (each thread acquires the row's
 // flag itself) while the current tile is multiplied; two buffers alternate.
 template <typename T, int NBS, int CT, bool BACK, bool DB>
-__global__ void __launch_bounds__(256, DB ? 2 : 4)
+__global__ void __launch_bounds__(256, Sweep<T>::MINB)
 trsm_sweep_kernel(int n, int nsb, int nct, const T* __restrict__ L, long long ldl, const T* __restrict__ Dinv,
                   int dnb, T* B, long long ldb, int m, unsigned* sync, unsigned epoch) {
   constexpr int LDS = NBS + 1;
@@ -301,12 +315,11 @@ trsm_sweep_kernel(int n, int nsb, int nct, const T* __restrict__ L, long long ld
   constexpr int YPT = NBS * CT / 256;  // elements of a Y block per thread
   static_assert(NBS * CT % 256 == 0, "whole Y block per thread");
   extern __shared__ unsigned char sm[];
-  // buffer q: factor tile at L0 + q NBS LDS (forward [kk * LDS + r];
-  // backward [r * LDS + kk], the raw L_ji), Y block at Y0 + q NBS CT ([kk * CT + c])
+  // buffer q: factor tile at L0 + q NBS LDS, Y block at Y0 + q NBS CT ([kk * CT + c])
   T* const L0 = reinterpret_cast<T*>(sm);
   T* const Y0 = L0 + (DB ? 2 : 1) * NBS * LDS;
   __shared__ int item;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
   const int tr = tid & 15, tc = tid >> 4;
   unsigned* flags = sync + 2;
   const int nitems = nsb * nct;
@@ -321,35 +334,61 @@ trsm_sweep_kernel(int n, int nsb, int nct, const T* __restrict__ L, long long ld
     const int ct0 = c * CT, cw = min(CT, m - ct0);
     const int r0 = i * NBS, rb = min(NBS, n - r0);
     auto jof = [&](int s2) { return BACK ? nsb - 1 - s2 : s2; };
-    // the factor tile (i, j) into buffer q, asynchronously
+    // the factor tile (i, j) into buffer q.  DB: asynchronously, as stored
+    // (backward: L_ji(kk, r) at [r * LDS + kk], conjugated when read); one
+    // buffer: by plain loads, the backward tile conjugate-transposed so that
+    // both sweeps read [kk * LDS + r]
     auto stage_L = [&](int q, int j) {
       const int rk0 = j * NBS, kb = min(NBS, n - rk0);
       T* Ls = L0 + q * NBS * LDS;
       for (int e = tid; e < NBS * NBS; e += 256) {
         if (!BACK) {  // L_ij(r, kk) at [kk * LDS + r]
           const int r = e % NBS, kk = e / NBS;
-          if (r < rb && kk < kb) cp_async_elem(Ls + kk * LDS + r, L + (r0 + r) + (long long)(rk0 + kk) * ldl);
-          else Ls[kk * LDS + r] = zero_<T>();
-        } else {      // L_ji(kk, r) at [r * LDS + kk]; conjugated when read
+          if (r < rb && kk < kb) {
+            if (DB) cp_async_elem(Ls + kk * LDS + r, L + (r0 + r) + (long long)(rk0 + kk) * ldl);
+            else Ls[kk * LDS + r] = L[(r0 + r) + (long long)(rk0 + kk) * ldl];
+          } else {
+            Ls[kk * LDS + r] = zero_<T>();
+          }
+        } else {
           const int kk = e % NBS, r = e / NBS;
-          if (r < rb && kk < kb) cp_async_elem(Ls + r * LDS + kk, L + (rk0 + kk) + (long long)(r0 + r) * ldl);
-          else Ls[r * LDS + kk] = zero_<T>();
+          const int dst = DB ? r * LDS + kk : kk * LDS + r;
+          if (r < rb && kk < kb) {
+            if (DB) cp_async_elem(Ls + dst, L + (rk0 + kk) + (long long)(r0 + r) * ldl);
+            else Ls[dst] = conj_(L[(rk0 + kk) + (long long)(r0 + r) * ldl]);
+          } else {
+            Ls[dst] = zero_<T>();
+          }
         }
       }
-      cp_async_commit();
+      if (DB) cp_async_commit();
     };
-    // Y_j's flag: poll once, or wait (bounded) for it
-    auto flag_ready = [&](int j) { return gave_up || ld_acquire(flags + (size_t)j * nct + c) == epoch; };
+    // Y_j's flag, read by lane 0 of each warp (one poller per warp keeps the
+    // polling traffic off the L2 slices that hold the flags) and passed on
+    // with a warp barrier, which orders lane 0's acquire before the other
+    // lanes' loads: poll once, or wait (bounded) for it
+    auto flag_ready = [&](int j) {
+      int r = 1;
+      if (lane == 0 && !gave_up) r = ld_acquire(flags + (size_t)j * nct + c) == epoch;
+      r = __shfl_sync(0xffffffffu, r, 0);
+      __syncwarp();
+      return r != 0;
+    };
     auto wait_flag = [&](int j) {
-      long long it = 0;
-      while (!flag_ready(j)) {
-        if (++it >= SWEEP_WAIT_LIMIT) {
-          gave_up = true;
-          atomicExch(sync + 1, 1u);
-          break;
+      int g = gave_up ? 1 : 0;
+      if (lane == 0 && !g) {
+        long long it = 0;
+        while (ld_acquire(flags + (size_t)j * nct + c) != epoch) {
+          if (++it >= SWEEP_WAIT_LIMIT) {
+            g = 1;
+            atomicExch(sync + 1, 1u);
+            break;
+          }
+          __nanosleep(32);
         }
-        __nanosleep(32);
       }
+      gave_up = __shfl_sync(0xffffffffu, g, 0) != 0;
+      __syncwarp();
     };
     // this thread's elements of Y_j into registers (after its flag was seen)
     T yr[YPT];
@@ -403,7 +442,7 @@ trsm_sweep_kernel(int n, int nsb, int nct, const T* __restrict__ L, long long ld
           T av[TM], bv[TN];
 #pragma unroll
           for (int a = 0; a < TM; ++a)
-            av[a] = BACK ? -conj_(Ls[(tr + 16 * a) * LDS + kk]) : -Ls[kk * LDS + tr + 16 * a];
+            av[a] = (BACK && DB) ? -conj_(Ls[(tr + 16 * a) * LDS + kk]) : -Ls[kk * LDS + tr + 16 * a];
 #pragma unroll
           for (int b = 0; b < TN; ++b) bv[b] = Ys[kk * CT + tc + 16 * b];
 #pragma unroll

@@ -5,13 +5,17 @@
 // complex Hermitian eigendecomposition on a single CTA takes ~100 ms.  Here
 // the N x N matrix is distributed column-cyclically over the shared memory of
 // a cluster of CL CTAs (CL = 16, or 8) and every Householder step of the
-// reduction to tridiagonal form runs on all of them:
-//   * the owner of column j builds the reflector u_j and publishes it in its
-//     shared memory; the others read it through distributed shared memory;
-//   * each CTA forms the partial product of its own columns with u_j; the
-//     partials are summed by reading every peer's buffer (fixed rank order:
-//     deterministic); each CTA applies the rank-2 update to its own columns.
-// Two cluster barriers per step order the publication and the reads.  The
+// reduction to tridiagonal form runs on all of them.  Every exchange is a
+// push: a CTA writes into its peers' shared memory and the next cluster
+// barrier makes the writes visible, so no step waits on a remote load:
+//   * the owner of column j builds the reflector u_j and stores it into every
+//     CTA's reflector buffer (two buffers, alternating by step);
+//   * each CTA forms p_c = t (B u)_c for its own columns c as the dot product
+//     of column c with u (B is Hermitian), and stores p_c and its partial
+//     u^* p into every CTA (fixed rank order in the sum: deterministic);
+//   * each CTA applies the rank-2 update to its own columns; the owner of
+//     column j + 1 updates that column first and builds u_{j+1}.
+// Two cluster barriers per step order the exchanges.  The
 // tridiagonal eigenproblem is then solved for the m wanted pairs by
 // Sturm-sequence multisection and inverse iteration (one warp per pair),
 // followed by two Cholesky-QR passes over the m vectors (they are orthogonal
@@ -37,7 +41,7 @@ constexpr int CLUSTER_THREADS = 512;
 // Householder tridiagonalisation on a cluster
 // ------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(CLUSTER_THREADS)
+__global__ void __launch_bounds__(CLUSTER_THREADS, 1)
 tridiag_cluster_kernel(int N, const T* __restrict__ Ag, T* __restrict__ U, T* __restrict__ uhead,
                        real_t<T>* __restrict__ tau, real_t<T>* __restrict__ dout, T* __restrict__ eout) {
   using R = real_t<T>;
@@ -48,93 +52,176 @@ tridiag_cluster_kernel(int N, const T* __restrict__ Ag, T* __restrict__ U, T* __
   const int nloc = (N + CL - 1) / CL;
   extern __shared__ __align__(16) unsigned char smem[];
   T* Aloc = reinterpret_cast<T*>(smem);  // owned columns c = rank + CL q, column-major
-  T* u = Aloc + (size_t)nloc * N;
-  T* p = u + N;
-  T* ppart = p + N;
-  R* scal = reinterpret_cast<R*>(ppart + N);
-  __shared__ R red[32];
+  T* ub = Aloc + (size_t)nloc * N;       // two reflector buffers (step j uses ub + (j & 1) N)
+  T* pv = ub + 2 * (size_t)N;            // p = t B u, then w = p - K u (entries pushed by their owners)
+  R* tb = reinterpret_cast<R*>(pv + N);  // t of the two reflector buffers
+  R* sp = tb + 2;                        // per-rank partial sums u^* p
+  __shared__ T part[32];                 // per-warp partial dot products
+  __shared__ T sh_u0, sh_beta;
+  __shared__ R sh_t;
 
+  int nown = 0;  // owned columns
   for (int q = 0; q < nloc; ++q) {
     const int c = rank + CL * q;
     if (c >= N) break;
+    ++nown;
     for (int i = tid; i < N; i += nt) Aloc[(size_t)q * N + i] = Ag[i + (size_t)c * N];
   }
   __syncthreads();
-  cluster.sync();
+
+  // Reflector of step j from the owner's column j (rows j+1..N-1): warp 0
+  // forms the scalars, then the whole CTA stores it for the
+  // back-transformation and pushes it into every rank's buffer (j & 1).
+  auto reflect = [&](int j) {
+    const int r0 = j + 1;
+    const T* col = Aloc + (size_t)(j / CL) * N;
+    if (wid == 0) {
+      R s2 = R(0);
+      for (int i = r0 + 1 + lane; i < N; i += 32) s2 += abs2_(col[i]);
+      s2 = warp_sum(s2);
+      if (lane == 0) {
+        const T x0 = col[r0];
+        R t = R(0);
+        T u0 = zero_<T>(), beta = x0;
+        if (s2 != R(0)) {
+          const R ax0 = sqrt_(abs2_(x0));
+          const R alpha = sqrt_(s2 + ax0 * ax0);
+          const T ph = ax0 > R(0) ? x0 * (R(1) / ax0) : from_real<T>(R(1));
+          beta = ph * (-alpha);
+          u0 = x0 - beta;
+          t = R(1) / (alpha * (alpha + ax0));
+        }
+        sh_t = t;
+        sh_u0 = u0;
+        sh_beta = beta;
+      }
+    }
+    __syncthreads();
+    const R t = sh_t;
+    const T u0 = sh_u0;
+    if (tid == 0) { tau[j] = t; uhead[j] = u0; eout[j] = sh_beta; }
+    const int len = N - r0, b = j & 1;
+    if (t != R(0)) {
+      for (int i = r0 + 1 + tid; i < N; i += nt) U[i + (size_t)j * N] = col[i];
+      for (int e = tid; e < len * CL; e += nt) {
+        const int rr = e / len, i = r0 + e % len;
+        cluster.map_shared_rank(ub, rr)[(size_t)b * N + i] = (i == r0) ? u0 : col[i];
+      }
+    }
+    if (tid < CL) cluster.map_shared_rank(tb, tid)[b] = t;
+  };
+
+  if (N > 2 && rank == 0) reflect(0);
+  __syncthreads();
+  cluster.sync();  // reflector 0 is in every rank's buffer
   for (int j = 0; j + 2 < N; ++j) {
     const int r0 = j + 1;
-    const int owner = j % CL;
-    if (rank == owner) {
-      T* col = Aloc + (size_t)(j / CL) * N;
-      R s2 = R(0);
-      for (int i = r0 + 1 + tid; i < N; i += nt) s2 += abs2_(col[i]);
-      s2 = block_sum(s2, red);
-      const T x0 = col[r0];
-      if (s2 == R(0)) {
-        if (tid == 0) { scal[0] = R(0); tau[j] = R(0); uhead[j] = zero_<T>(); eout[j] = x0; }
-      } else {
-        const R ax0 = sqrt_(abs2_(x0));
-        const R alpha = sqrt_(s2 + ax0 * ax0);
-        const T ph = ax0 > R(0) ? x0 * (R(1) / ax0) : from_real<T>(R(1));
-        const T beta = ph * (-alpha);
-        const T u0 = x0 - beta;
-        const R t = R(1) / (alpha * (alpha + ax0));
-        for (int i = r0 + tid; i < N; i += nt) u[i] = (i == r0) ? u0 : col[i];
-        for (int i = r0 + 1 + tid; i < N; i += nt) U[i + (size_t)j * N] = col[i];
-        if (tid == 0) { scal[0] = t; tau[j] = t; uhead[j] = u0; eout[j] = beta; }
-      }
-    }
-    __syncthreads();
-    cluster.sync();  // the owner's u_j and t are published
-    const R t = *cluster.map_shared_rank(scal, owner);
+    const int b = j & 1;
+    const R t = tb[b];
+    const T* u = ub + (size_t)b * N;
     const int q0 = (r0 > rank) ? (r0 - rank + CL - 1) / CL : 0;  // first owned column >= r0
-    if (t != R(0)) {
-      if (rank != owner) {
-        const T* uo = cluster.map_shared_rank(u, owner);
-        for (int i = r0 + tid; i < N; i += nt) u[i] = uo[i];
+    const int ncols = nown - q0;  // owned columns >= r0
+    const int len = N - r0;
+    if (t != R(0) && ncols > 0) {
+      // p_c = t (B u)_c = t sum_i conj(B_ic) u_i for the owned columns (B is
+      // Hermitian): each column's rows split over nw / ncols warps
+      const int wpc = max(1, nw / ncols);  // warps per column
+      const int chunk = (len + wpc - 1) / wpc;
+      const int qq = wid / wpc, piece = wid % wpc;
+      T acc = zero_<T>();
+      if (qq < ncols) {
+        const T* col = Aloc + (size_t)(q0 + qq) * N;
+        const int i0 = r0 + piece * chunk, i1 = min(N, i0 + chunk);
+        for (int i = i0 + lane; i < i1; i += 32) fmac_(acc, col[i], u[i]);  // += conj(B_ic) u_i
+        acc = warp_sum(acc);
+      }
+      // columns beyond nw (only when ncols > nw): one warp each, in turn
+      for (int q = q0 + nw + wid; q < nloc && wpc == 1; q += nw) {
+        const int c = rank + CL * q;
+        if (c >= N) break;
+        const T* col = Aloc + (size_t)q * N;
+        T a2 = zero_<T>();
+        for (int i = r0 + lane; i < N; i += 32) fmac_(a2, col[i], u[i]);
+        a2 = warp_sum(a2) * t;
+        if (lane < CL) cluster.map_shared_rank(pv, lane)[c] = a2;
+      }
+      if (lane == 0) part[wid] = acc;
+      __syncthreads();
+      if (wid == 0) {
+        R sacc = R(0);
+        for (int q = lane; q < min(ncols, nw); q += 32) {
+          T pc = zero_<T>();
+          for (int k = 0; k < wpc; ++k) pc = pc + part[q * wpc + k];
+          pc = pc * t;
+          const int c = rank + CL * (q0 + q);
+          for (int rr = 0; rr < CL; ++rr) cluster.map_shared_rank(pv, rr)[c] = pc;
+          sacc += re_(conj_(u[c]) * pc);
+        }
+        sacc = warp_sum(sacc);
+        // the columns taken one warp each above (ncols > nw) add to the sum
+        // after the barrier below, read back from this rank's own buffer
+        part[0] = from_real<T>(sacc);
       }
       __syncthreads();
-      for (int i = r0 + tid; i < N; i += nt) {  // partial B u over the owned columns
-        T acc0 = zero_<T>(), acc1 = zero_<T>();
-        int q = q0;
-        for (; q + 1 < nloc; q += 2) {
-          const int c0 = rank + CL * q, c1 = c0 + CL;
-          if (c0 < N) fma_(acc0, Aloc[(size_t)q * N + i], u[c0]);
-          if (c1 < N) fma_(acc1, Aloc[(size_t)(q + 1) * N + i], u[c1]);
+      if (tid == 0) {
+        R s0 = re_(part[0]);
+        for (int q = q0 + nw; q < nloc; ++q) {
+          const int c = rank + CL * q;
+          if (c >= N) break;
+          s0 += re_(conj_(u[c]) * pv[c]);
         }
-        if (q < nloc && rank + CL * q < N) fma_(acc0, Aloc[(size_t)q * N + i], u[rank + CL * q]);
-        ppart[i] = acc0 + acc1;
+        part[0] = from_real<T>(s0);
       }
+      __syncthreads();
+      if (tid < CL) cluster.map_shared_rank(sp, tid)[rank] = re_(part[0]);
+    } else if (t != R(0)) {
+      if (tid < CL) cluster.map_shared_rank(sp, tid)[rank] = R(0);
     }
     __syncthreads();
-    cluster.sync();  // every partial product is ready
+    cluster.sync();  // p and the partial sums are in every rank's buffers
+    const int nj = j + 1;  // the next step, when there is one
+    const bool next = nj + 2 < N;
+    const int nowner = nj % CL;
     if (t != R(0)) {
-      for (int i = r0 + tid; i < N; i += nt) {
-        T acc = zero_<T>();
-        for (int rk = 0; rk < CL; ++rk) acc = acc + cluster.map_shared_rank(ppart, rk)[i];
-        p[i] = acc * t;
-      }
+      R s = R(0);
+      for (int rr = 0; rr < CL; ++rr) s += sp[rr];
+      const R K = s * t * R(0.5);
+      for (int i = r0 + tid; i < N; i += nt) pv[i] = pv[i] - K * u[i];
       __syncthreads();
-      R up = R(0);
-      for (int i = r0 + tid; i < N; i += nt) up += re_(conj_(u[i]) * p[i]);
-      up = block_sum(up, red);
-      const R K = up * t * R(0.5);
-      for (int i = r0 + tid; i < N; i += nt) p[i] = p[i] - K * u[i];
-      __syncthreads();
-      for (int q = q0 + wid; q < nloc; q += nw) {  // rank-2 update of the owned columns
-        const int c = rank + CL * q;
-        if (c >= N) continue;
-        const T pc = conj_(p[c]), uc = conj_(u[c]);
-        T* col = Aloc + (size_t)q * N;
-        for (int i = r0 + lane; i < N; i += 32) {
+      // rank-2 update B -= u w^* + w u^* of the owned columns, element-wise
+      // over the CTA; the owner of the next pivot column updates that column
+      // first and reflects it
+      const int qn = (next && rank == nowner) ? nj / CL : -1;
+      if (qn >= 0) {
+        T* col = Aloc + (size_t)qn * N;
+        const T wc = conj_(pv[nj]), uc = conj_(u[nj]);
+        for (int i = r0 + tid; i < N; i += nt) {
           T v = col[i];
-          v = v - u[i] * pc;
-          v = v - p[i] * uc;
+          fms_(v, u[i], wc);
+          fms_(v, pv[i], uc);
           col[i] = v;
         }
+        __syncthreads();
+        reflect(nj);
       }
+      const int skip = (qn >= 0) ? qn - q0 : -1;  // that column is done
+      const int nupd = ncols - (skip >= 0 ? 1 : 0);
+      for (int e = tid; e < nupd * len; e += nt) {
+        int k = e / len;
+        if (skip >= 0 && k >= skip) ++k;
+        const int q = q0 + k, i = r0 + e % len;
+        const int c = rank + CL * q;
+        T* col = Aloc + (size_t)q * N;
+        T v = col[i];
+        fms_(v, u[i], conj_(pv[c]));
+        fms_(v, pv[i], conj_(u[c]));
+        col[i] = v;
+      }
+    } else if (next && rank == nowner) {
+      reflect(nj);
     }
     __syncthreads();
+    cluster.sync();  // the updates are done and the next reflector is pushed
   }
   for (int q = 0; q < nloc; ++q) {
     const int c = rank + CL * q;
@@ -144,7 +231,7 @@ tridiag_cluster_kernel(int N, const T* __restrict__ Ag, T* __restrict__ U, T* __
       if (c == N - 2) eout[N - 2] = Aloc[(size_t)q * N + N - 1];
     }
   }
-  cluster.sync();  // no CTA leaves while a peer may still read its shared memory
+  cluster.sync();  // no CTA leaves while a peer may still write its shared memory
 }
 
 // ------------------------------------------------------------------------
@@ -152,30 +239,60 @@ tridiag_cluster_kernel(int N, const T* __restrict__ Ag, T* __restrict__ U, T* __
 // ------------------------------------------------------------------------
 // Real symmetric tridiagonal (d, f) from the Hermitian one (d, e) by the
 // diagonal unitary similarity delta (delta_0 = 1, delta_{i+1} = delta_i e_i/|e_i|).
+// One warp: each lane takes a contiguous run of the phases, forms its
+// running products, and the lanes' totals are combined by a warp scan.
+template <typename R> __device__ __forceinline__ R shfl_up_(R v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+template <typename R> __device__ __forceinline__ cplx<R> shfl_up_(cplx<R> v, int o) {
+  return {__shfl_up_sync(0xffffffffu, v.x, o), __shfl_up_sync(0xffffffffu, v.y, o)};
+}
 template <typename T>
-__global__ void tri_real_kernel(int N, const T* __restrict__ e_in, T* delta, real_t<T>* f) {
+__global__ void __launch_bounds__(32, 1) tri_real_kernel(int N, const T* __restrict__ e_in, T* delta, real_t<T>* f) {
   using R = real_t<T>;
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  delta[0] = from_real<T>(R(1));
-  for (int i = 0; i + 1 < N; ++i) {
+  const int lane = threadIdx.x;
+  const int per = (N - 1 + 31) / 32;
+  const int i0 = min(N - 1, lane * per), i1 = min(N - 1, i0 + per);
+  T run = from_real<T>(R(1));
+  for (int i = i0; i < i1; ++i) {
     const T e = e_in[i];
     const R ae = sqrt_(abs2_(e));
     f[i] = ae;
     const T ph = ae > R(0) ? e * (R(1) / ae) : from_real<T>(R(1));
-    delta[i + 1] = delta[i] * ph;
+    run = run * ph;
+    delta[i + 1] = run;  // this lane's partial product, completed below
   }
-  f[N - 1] = R(0);
+  T pre = run;  // inclusive scan of the lanes' products
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T other = shfl_up_(pre, o);
+    if (lane >= o) pre = other * pre;
+  }
+  T excl = shfl_up_(pre, 1);
+  if (lane == 0) excl = from_real<T>(R(1));
+  for (int i = i0; i < i1; ++i) delta[i + 1] = excl * delta[i + 1];
+  if (lane == 0) {
+    delta[0] = from_real<T>(R(1));
+    f[N - 1] = R(0);
+  }
 }
 
 // One warp per wanted eigenvalue: multisection (the 32 lanes evaluate the
 // Sturm count at 32 interior points, shrinking the bracket 33-fold per round)
 // followed by inverse iteration on lane 0.
 template <typename R>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(32, 1)
 tri_multisect_kernel(int N, int m, const R* __restrict__ d, const R* __restrict__ f, R* lamv, R* z, R* lu,
-                     int* piv) {
+                     int* piv, int* bad) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  R* sd = reinterpret_cast<R*>(smem);  // d, then f_i^2 (the Sturm recurrence's only use of f)
+  R* sf2 = sd + N;
   const int lane = threadIdx.x & 31;
-  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int k = blockIdx.x;  // one warp (block) per wanted eigenvalue: each on its own SM's FP64 pipe
+  if (k == 0 && lane == 0) *bad = 0;  // the Cholesky-QR passes that follow report breakdown here
+  for (int i = lane; i < N; i += 32) {
+    sd[i] = d[i];
+    sf2[i] = f[i] * f[i];
+  }
+  __syncwarp();
   if (k >= m) return;
   R glo = d[0], ghi = d[0], tnorm = R(0);
   for (int i = 0; i < N; ++i) {
@@ -192,7 +309,7 @@ tri_multisect_kernel(int N, int m, const R* __restrict__ d, const R* __restrict_
   for (int round = 0; round < 64; ++round) {
     if (hi - lo <= R(2) * eps * fmax((R)fabs((double)lo), (R)fabs((double)hi)) + pivmin) break;
     const R x = lo + (hi - lo) * (R)(lane + 1) / R(33);
-    const bool above = (x > lo && x < hi) && sturm_count(N, d, f, x, pivmin) > k;
+    const bool above = (x > lo && x < hi) && sturm_count_f2(N, sd, sf2, x, pivmin) > k;
     const unsigned mask = __ballot_sync(0xffffffffu, above);
     // counts are monotone in x: the first lane with count > k bounds from above
     R nlo = lo, nhi = hi;
@@ -223,54 +340,103 @@ tri_multisect_kernel(int N, int m, const R* __restrict__ d, const R* __restrict_
   }
 }
 
-// Two Cholesky-QR passes over the m vectors (Z <- Z L^-T, Z^T Z = L L^T);
-// Gram-Schmidt inside eigenvalue clusters if the Cholesky breaks down.
+// Two Cholesky-QR passes over the m vectors (Z <- Z L^-T, Z^T Z = L L^T),
+// each as three launches over many SMs: the Gram matrix (a block per
+// column), its Cholesky factor (one block), the triangular solve (a warp per
+// row).  A breakdown sets *bad and the remaining passes skip; the finishing
+// kernel then orthogonalises inside eigenvalue clusters by Gram-Schmidt.
 template <typename R>
-__global__ void __launch_bounds__(1024)
-cholqr_vectors_kernel(int N, int m, const R* __restrict__ d, const R* __restrict__ f, const R* lamv, R* z,
-                      R* lu, int* piv, R* G, double* lam_out, int* fail) {
-  __shared__ int bad;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) bad = 0;
+__global__ void __launch_bounds__(256) gram_lower_kernel(int N, int m, const R* __restrict__ z, R* G,
+                                                         const int* bad) {
+  if (*bad) return;
+  const int b = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const R* zb = z + (size_t)b * N;
+  for (int a = b + w; a < m; a += 8) {
+    const R* za = z + (size_t)a * N;
+    R sacc = R(0);
+    for (int i = lane; i < N; i += 32) sacc += za[i] * zb[i];
+    sacc = warp_sum(sacc);
+    if (lane == 0) G[a + (size_t)b * m] = sacc;
+  }
+}
+
+// Left-looking Cholesky of the Gram matrix (lower triangle of G); the factor
+// is also written transposed into the upper triangle for the row solves.
+template <typename R>
+__global__ void __launch_bounds__(1024) chol_gram_kernel(int m, R* G, R* rdiag, int* bad) {
+  __shared__ int sbad;
+  __shared__ R rpiv;  // 1 / L_jj: one division per column, a product per entry
+  if (*bad) return;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  if (tid == 0) sbad = 0;
   __syncthreads();
-  for (int pass = 0; pass < 2 && m > 1; ++pass) {
-    for (int e = tid; e < m * m; e += nt) {
-      const int a = e % m, b = e / m;
-      if (a < b) continue;
-      const R* za = z + (size_t)a * N;
-      const R* zb = z + (size_t)b * N;
-      R s = R(0);
-      for (int i = 0; i < N; ++i) s += za[i] * zb[i];
-      G[a + (size_t)b * m] = s;
+  for (int jj = 0; jj < m; ++jj) {
+    if (wid == 0) {
+      R sacc = R(0);
+      for (int l = lane; l < jj; l += 32) sacc += G[jj + (size_t)l * m] * G[jj + (size_t)l * m];
+      sacc = warp_sum(sacc);
+      if (lane == 0) {
+        const R sj = G[jj + (size_t)jj * m] - sacc;
+        if (!(sj > R(0))) {
+          sbad = 1;
+        } else {
+          const R pd = sqrt_(sj);
+          G[jj + (size_t)jj * m] = pd;
+          rpiv = R(1) / pd;
+          rdiag[jj] = rpiv;
+        }
+      }
     }
     __syncthreads();
-    for (int jj = 0; jj < m; ++jj) {
-      if (tid == 0) {
-        R s = G[jj + (size_t)jj * m];
-        for (int l = 0; l < jj; ++l) s -= G[jj + (size_t)l * m] * G[jj + (size_t)l * m];
-        if (!(s > R(0)) || bad) bad = 1;
-        else G[jj + (size_t)jj * m] = sqrt_(s);
-      }
-      __syncthreads();
-      if (bad) break;
-      const R piv_d = G[jj + (size_t)jj * m];
-      for (int i = jj + 1 + tid; i < m; i += nt) {
-        R v = G[i + (size_t)jj * m];
-        for (int l = 0; l < jj; ++l) v -= G[i + (size_t)l * m] * G[jj + (size_t)l * m];
-        G[i + (size_t)jj * m] = v / piv_d;
-      }
-      __syncthreads();
-    }
-    if (bad) break;
-    for (int i = tid; i < N; i += nt) {
-      for (int b = 0; b < m; ++b) {
-        R v = z[(size_t)b * N + i];
-        for (int a = 0; a < b; ++a) v -= z[(size_t)a * N + i] * G[b + (size_t)a * m];
-        z[(size_t)b * N + i] = v / G[b + (size_t)b * m];
+    if (sbad) break;
+    const R rp = rpiv;
+    for (int i = jj + 1 + wid; i < m; i += nw) {
+      R sacc = R(0);
+      for (int l = lane; l < jj; l += 32) sacc += G[i + (size_t)l * m] * G[jj + (size_t)l * m];
+      sacc = warp_sum(sacc);
+      if (lane == 0) {
+        const R v = (G[i + (size_t)jj * m] - sacc) * rp;
+        G[i + (size_t)jj * m] = v;
+        G[jj + (size_t)i * m] = v;  // the transpose, for the row solves
       }
     }
     __syncthreads();
   }
+  if (tid == 0 && sbad) *bad = 1;
+}
+
+// Z <- Z L^-T: row i solves v L^T = z_i (v_b = (z_ib - sum_{a<b} v_a L_ba) / L_bb),
+// one warp per row, the row staged in shared memory.
+template <typename R>
+__global__ void __launch_bounds__(128) trsolve_rows_kernel(int N, int m, R* z, const R* __restrict__ G,
+                                                           const R* __restrict__ rdiag, const int* bad) {
+  if (*bad) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x * 4 + w;
+  if (i >= N) return;
+  R* v = reinterpret_cast<R*>(smem) + (size_t)w * m;
+  for (int b = lane; b < m; b += 32) v[b] = z[(size_t)b * N + i];
+  __syncwarp();
+  for (int b = 0; b < m; ++b) {
+    const R* Lb = G + (size_t)b * m;  // upper triangle: L_ba at Lb[a], a < b
+    R sacc = R(0);
+    for (int a = lane; a < b; a += 32) sacc += v[a] * Lb[a];
+    sacc = warp_sum(sacc);
+    if (lane == 0) v[b] = (v[b] - sacc) * rdiag[b];
+    __syncwarp();
+  }
+  for (int b = lane; b < m; b += 32) z[(size_t)b * N + i] = v[b];
+}
+
+// Breakdown fallback (Gram-Schmidt inside eigenvalue clusters) and the
+// eigenvalues out.
+template <typename R>
+__global__ void __launch_bounds__(1024)
+cholqr_finish_kernel(int N, int m, const R* __restrict__ d, const R* __restrict__ f, const R* lamv, R* z, R* lu,
+                     int* piv, R* G, double* lam_out, int* fail, const int* badp) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int bad = *badp;
   if (bad) {
     R tnorm = R(0);
     for (int i = 0; i < N; ++i) tnorm = fmax(tnorm, (R)fabs((double)d[i]) + (i > 0 ? f[i - 1] : R(0)) + f[i]);
@@ -318,7 +484,7 @@ cholqr_vectors_kernel(int N, int m, const R* __restrict__ d, const R* __restrict
 // Back-transformation: one warp per eigenvector
 // ------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(32, 1)
 backtransform_kernel(int N, int m, const real_t<T>* __restrict__ z, const T* __restrict__ delta,
                      const T* __restrict__ U, const T* __restrict__ uhead, const real_t<T>* __restrict__ tau,
                      T* C1) {
@@ -348,7 +514,7 @@ backtransform_kernel(int N, int m, const real_t<T>* __restrict__ z, const T* __r
 // Householder QR on a cluster (reflectors kept below the diagonal of Y)
 // ------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(CLUSTER_THREADS)
+__global__ void __launch_bounds__(CLUSTER_THREADS, 1)
 qr_cluster_kernel(int N, int q, T* Y, T* uhead, real_t<T>* tau) {
   using R = real_t<T>;
   cg::cluster_group cluster = cg::this_cluster();
@@ -357,53 +523,69 @@ qr_cluster_kernel(int N, int q, T* Y, T* uhead, real_t<T>* tau) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   const int nloc = (q + CL - 1) / CL;
   extern __shared__ __align__(16) unsigned char smem[];
-  T* Aloc = reinterpret_cast<T*>(smem);
-  T* u = Aloc + (size_t)nloc * N;
-  R* scal = reinterpret_cast<R*>(u + N);
+  T* Aloc = reinterpret_cast<T*>(smem);  // owned columns c = rank + CL qq
+  T* ub = Aloc + (size_t)nloc * N;       // two reflector buffers (step j uses ub + (j & 1) N)
+  R* tb = reinterpret_cast<R*>(ub + 2 * (size_t)N);
   __shared__ R red[32];
+  __shared__ T redc[32];
   for (int qq = 0; qq < nloc; ++qq) {
     const int c = rank + CL * qq;
     if (c >= q) break;
     for (int i = tid; i < N; i += nt) Aloc[(size_t)qq * N + i] = Y[i + (size_t)c * N];
   }
   __syncthreads();
-  cluster.sync();
-  const int jmax = q < N ? q : N;
-  for (int j = 0; j < jmax; ++j) {
-    const int owner = j % CL;
-    if (rank == owner) {
-      T* col = Aloc + (size_t)(j / CL) * N;
-      R s2 = R(0);
-      for (int i = j + 1 + tid; i < N; i += nt) s2 += abs2_(col[i]);
-      s2 = block_sum(s2, red);
-      const T x0 = col[j];
-      if (s2 == R(0)) {
-        if (tid == 0) { scal[0] = R(0); tau[j] = R(0); uhead[j] = zero_<T>(); }
-      } else {
-        const R ax0 = sqrt_(abs2_(x0));
-        const R alpha = sqrt_(s2 + ax0 * ax0);
-        const T ph = ax0 > R(0) ? x0 * (R(1) / ax0) : from_real<T>(R(1));
-        const T beta = ph * (-alpha);
-        const T u0 = x0 - beta;
-        const R t = R(1) / (alpha * (alpha + ax0));
-        for (int i = j + tid; i < N; i += nt) u[i] = (i == j) ? u0 : col[i];
-        __syncthreads();
-        if (tid == 0) { scal[0] = t; tau[j] = t; uhead[j] = u0; col[j] = beta; }
+  // reflector j from the owner's column j (rows j..N-1), pushed into every
+  // rank's buffer (j & 1); R_jj = beta replaces the column's head
+  auto reflect = [&](int j) {
+    T* col = Aloc + (size_t)(j / CL) * N;
+    const T x0 = col[j];
+    R s2 = R(0);
+    for (int i = j + 1 + tid; i < N; i += nt) s2 += abs2_(col[i]);
+    s2 = block_sum(s2, red);  // (its barriers also order every read of x0 before the write below)
+    R t = R(0);
+    T u0 = zero_<T>(), beta = x0;
+    if (s2 != R(0)) {
+      const R ax0 = sqrt_(abs2_(x0));
+      const R alpha = sqrt_(s2 + ax0 * ax0);
+      const T ph = ax0 > R(0) ? x0 * (R(1) / ax0) : from_real<T>(R(1));
+      beta = ph * (-alpha);
+      u0 = x0 - beta;
+      t = R(1) / (alpha * (alpha + ax0));
+      const int len = N - j, b = j & 1;
+      for (int e = tid; e < len * CL; e += nt) {
+        const int rr = e / len, i = j + e % len;
+        cluster.map_shared_rank(ub, rr)[(size_t)b * N + i] = (i == j) ? u0 : col[i];
       }
     }
-    __syncthreads();
-    cluster.sync();  // the owner's reflector is published
-    const R t = *cluster.map_shared_rank(scal, owner);
+    if (tid < CL) cluster.map_shared_rank(tb, tid)[j & 1] = t;
+    if (tid == 0) { tau[j] = t; uhead[j] = u0; col[j] = beta; }
+  };
+  const int jmax = q < N ? q : N;
+  if (jmax > 0 && rank == 0) reflect(0);
+  __syncthreads();
+  cluster.sync();  // reflector 0 is in every rank's buffer
+  for (int j = 0; j < jmax; ++j) {
+    const R t = tb[j & 1];
+    const T* u = ub + (size_t)(j & 1) * N;
+    const int nj = j + 1;
+    const bool next = nj < jmax;
+    const int qn = (next && rank == nj % CL) ? nj / CL : -1;
+    const int q0 = (j + 1 > rank) ? (j + 1 - rank + CL - 1) / CL : 0;  // first owned column > j
     if (t != R(0)) {
-      if (rank != owner) {
-        const T* uo = cluster.map_shared_rank(u, owner);
-        for (int i = j + tid; i < N; i += nt) u[i] = uo[i];
+      if (qn >= 0) {  // the next pivot column first, then its reflector
+        T* col = Aloc + (size_t)qn * N;
+        T dsum = zero_<T>();
+        for (int i = j + tid; i < N; i += nt) fmac_(dsum, u[i], col[i]);
+        dsum = block_sum(dsum, redc);
+        const T g = dsum * t;
+        for (int i = j + tid; i < N; i += nt) col[i] = col[i] - g * u[i];
+        __syncthreads();
+        reflect(nj);
       }
-      __syncthreads();
-      const int q0 = (j + 1 > rank) ? (j + 1 - rank + CL - 1) / CL : 0;
       for (int qq = q0 + wid; qq < nloc; qq += nw) {
+        if (qq == qn) continue;
         const int c = rank + CL * qq;
-        if (c >= q) continue;
+        if (c >= q) break;
         T* col = Aloc + (size_t)qq * N;
         T dsum = zero_<T>();
         for (int i = j + lane; i < N; i += 32) fmac_(dsum, u[i], col[i]);
@@ -411,20 +593,22 @@ qr_cluster_kernel(int N, int q, T* Y, T* uhead, real_t<T>* tau) {
         const T g = dsum * t;
         for (int i = j + lane; i < N; i += 32) col[i] = col[i] - g * u[i];
       }
+    } else if (qn >= 0) {
+      reflect(nj);
     }
     __syncthreads();
+    cluster.sync();  // the updates are done and the next reflector is pushed
   }
   for (int qq = 0; qq < nloc; ++qq) {
     const int c = rank + CL * qq;
     if (c >= q) break;
     for (int i = tid; i < N; i += nt) Y[i + (size_t)c * N] = Aloc[(size_t)qq * N + i];
   }
-  cluster.sync();
 }
 
 // Columns c0 .. c0+nq-1 of Q = H_0 ... H_{q-1}: one warp per column.
 template <typename T>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(32, 1)
 qform_kernel(int N, int q, const T* __restrict__ Y, const T* __restrict__ uhead,
              const real_t<T>* __restrict__ tau, int c0, int nq, T* Q) {
   using R = real_t<T>;
@@ -552,15 +736,15 @@ static int pick_cluster(K kernel, size_t smem_of_cl(int), int* out_cl, size_t* o
 template <typename T>
 struct ClusterSizes {
   static int N_, q_;
-  static size_t tri(int CL) { return ((size_t)((N_ + CL - 1) / CL) * N_ + 3 * (size_t)N_) * sizeof(T) + 64; }
-  static size_t qr(int CL) { return ((size_t)((q_ + CL - 1) / CL) * N_ + (size_t)N_) * sizeof(T) + 64; }
+  static size_t tri(int CL) { return ((size_t)((N_ + CL - 1) / CL) * N_ + 3 * (size_t)N_) * sizeof(T) + 512; }
+  static size_t qr(int CL) { return ((size_t)((q_ + CL - 1) / CL) * N_ + 2 * (size_t)N_) * sizeof(T) + 64; }
 };
 template <typename T> int ClusterSizes<T>::N_ = 0;
 template <typename T> int ClusterSizes<T>::q_ = 0;
 
 size_t eig_fast_ws_bytes(int N, int m, size_t elem) {
   return (size_t)N * N * elem + 5 * (size_t)N * elem + 4 * (size_t)N * 8 + 5 * (size_t)N * m * 8 +
-         (size_t)N * m * 4 + (size_t)m * m * 8 + (size_t)m * 8 + 1024;
+         (size_t)N * m * 4 + (size_t)m * m * 8 + 2 * (size_t)m * 8 + 1024;
 }
 
 template <typename T>
@@ -612,12 +796,20 @@ bool eig_small_fast(cudaStream_t st, int N, int m, T* Ap, double* lam, T* C1, vo
   R* lamv = f + N;                          // m reals
   count_launch();
   tri_real_kernel<T><<<1, 32, 0, st>>>(N, e, delta, f);
+  int* bad = piv + (size_t)N * m;
+  R* rdiag = reinterpret_cast<R*>(piv + (((size_t)N * m + 2) & ~(size_t)1));  // past bad, 8-byte aligned
   count_launch();
-  tri_multisect_kernel<R><<<ceil_div(m, 4), 128, 0, st>>>(N, m, d, f, lamv, z, lu, piv);
+  tri_multisect_kernel<R><<<m, 32, 2 * (size_t)N * sizeof(R), st>>>(N, m, d, f, lamv, z, lu, piv, bad);
+  for (int pass = 0; pass < 2 && m > 1; ++pass) {
+    count_launch(3);
+    gram_lower_kernel<R><<<m, 256, 0, st>>>(N, m, z, G, bad);
+    chol_gram_kernel<R><<<1, 1024, 0, st>>>(m, G, rdiag, bad);
+    trsolve_rows_kernel<R><<<ceil_div(N, 4), 128, 4 * (size_t)m * sizeof(R), st>>>(N, m, z, G, rdiag, bad);
+  }
   count_launch();
-  cholqr_vectors_kernel<R><<<1, 1024, 0, st>>>(N, m, d, f, lamv, z, lu, piv, G, lam, fail_dev);
+  cholqr_finish_kernel<R><<<1, 1024, 0, st>>>(N, m, d, f, lamv, z, lu, piv, G, lam, fail_dev, bad);
   count_launch();
-  backtransform_kernel<T><<<ceil_div(m, 4), 128, 0, st>>>(N, m, z, delta, U, uh, tau, C1);
+  backtransform_kernel<T><<<m, 32, 0, st>>>(N, m, z, delta, U, uh, tau, C1);
   return true;
 }
 
@@ -651,44 +843,13 @@ bool thin_q_fast(cudaStream_t st, int N, int q, T* Y, int c0, int nq, T* Q, T* h
     return false;
   }
   count_launch();
-  qform_kernel<T><<<ceil_div(nq, 4), 128, 0, st>>>(N, q, Y, uh, tau, c0, nq, Q);
-  return true;
-}
-
-template <typename T>
-bool qr_cluster_inplace(cudaStream_t st, int N, int q, T* Y, T* hb) {
-  using R = real_t<T>;
-  ClusterSizes<T>::N_ = N;
-  ClusterSizes<T>::q_ = q;
-  int CL = 0;
-  size_t sm = 0;
-  if (!pick_cluster(qr_cluster_kernel<T>, &ClusterSizes<T>::qr, &CL, &sm)) return false;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(CL);
-  cfg.blockDim = dim3(CLUSTER_THREADS);
-  cfg.dynamicSmemBytes = sm;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = CL;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  count_launch();
-  const cudaError_t e = cudaLaunchKernelEx(&cfg, qr_cluster_kernel<T>, N, q, Y, hb, reinterpret_cast<R*>(hb + q));
-  if (e != cudaSuccess) {
-    note_cluster_fallback(6000 + (int)e);
-    cudaGetLastError();
-    return false;
-  }
+  qform_kernel<T><<<nq, 32, 0, st>>>(N, q, Y, uh, tau, c0, nq, Q);
   return true;
 }
 
 #define MPL_INST_FAST(T)                                                                          \
   template bool eig_small_fast<T>(cudaStream_t, int, int, T*, double*, T*, void*, int*);          \
-  template bool thin_q_fast<T>(cudaStream_t, int, int, T*, int, int, T*, T*);                     \
-  template bool qr_cluster_inplace<T>(cudaStream_t, int, int, T*, T*);
+  template bool thin_q_fast<T>(cudaStream_t, int, int, T*, int, int, T*, T*);
 MPL_INST_FAST(float)
 MPL_INST_FAST(double)
 MPL_INST_FAST(zf)

@@ -2,10 +2,14 @@
 // tall-skinny QR of Algorithm 2.
 //
 //  * tsqr_r         Householder QR of single(W) (n x m) by a tree of per-CTA
-//                   Householder factorisations (leaves of 128+ rows, merges of
-//                   4 stacked R factors); only R is formed (Algorithm 2's Householder QR step).
-//  * trinv_upper_ct (R^*)^-1 for the triangular solves of the triangular solve of Algorithm 2.
-//  * chol_inv       V^* V = L L^* and L^-1 (the Cholesky and back-substitution steps of Algorithm 2).
+//                   Householder factorisations (leaves of 128+ rows in shared
+//                   memory, then merges of up to 4 stacked R factors by
+//                   structure-aware reflections in packed shared storage);
+//                   only R is formed (Algorithm 2's Householder QR step).
+//  * trinv_upper_ct (R^*)^-1 for the triangular solve of Algorithm 2 (V = W R_l^-1),
+//                   one warp (and block) per column.
+//  * chol_inv       V^* V = L L^* on one CTA and L^-1 one warp per column (the
+//                   Cholesky and back-substitution steps of Algorithm 2).
 //  * eig_small      the m smallest eigenpairs of A_p = S^* A S (the small
 //                   eigenproblem of Algorithm 3).
 //  * thin_q         orth(C(1:m, m+1:end)^*) of the Hetmaniuk-Lehoucq step.
@@ -18,6 +22,9 @@
 // (clusters: gaps below 1e-3 ||T||_1), and back-transformation through the
 // reflectors.  Only the m wanted eigenvectors are formed.
 #include <algorithm>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "small.cuh"
 #include "small_dev.cuh"
@@ -111,6 +118,99 @@ tsqr_leaf_kernel(int n, int m, const T* __restrict__ W, long long ldw, int b, TQ
   }
 }
 
+// Leaf factorisation with the block in shared memory (when it fits).
+template <typename T, typename TQ>
+__global__ void __launch_bounds__(256, 1)
+tsqr_leaf_smem_kernel(int n, int m, const T* __restrict__ W, long long ldw, int b, TQ* Rout, TQ* hbuf) {
+  __shared__ real_t<TQ> red[32];
+  extern __shared__ __align__(16) unsigned char smem_l[];
+  TQ* A = reinterpret_cast<TQ*>(smem_l);
+  const int l = blockIdx.x;
+  const int r0 = l * b;
+  const int rb = min(b, n - r0);
+  for (long long e = threadIdx.x; e < (long long)rb * m; e += blockDim.x) {
+    const int i = (int)(e % rb), c = (int)(e / rb);
+    A[i + (long long)c * rb] = cvt<TQ, T>(W[r0 + i + (long long)c * ldw]);
+  }
+  __syncthreads();
+  TQ* uh = hbuf + (size_t)l * 2 * m;
+  hh_qr_cta<TQ>(rb, m, A, rb, uh, reinterpret_cast<real_t<TQ>*>(uh + m), red);
+  TQ* Ro = Rout + (size_t)l * m * m;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e % m, c = e / m;
+    Ro[e] = (i <= c && i < rb) ? A[i + (long long)c * rb] : zero_<TQ>();
+  }
+}
+
+// Merge of k <= 4 stacked upper-triangular factors [R_0; ...; R_{k-1}] by
+// Householder reflections that use their structure: the reflector of
+// column j has nonzeros only in row j of R_0 and rows 0..j of the others, and
+// the update keeps every factor upper triangular.  The factors are held in
+// shared memory packed by columns (column c: rows 0..c at c (c + 1) / 2).
+// Only R (the new R_0) is formed.
+template <typename TQ>
+__global__ void __launch_bounds__(512)
+tsqr_merge_packed_kernel(int cnt, int G, int m, const TQ* __restrict__ Rin, TQ* Rout) {
+  using R = real_t<TQ>;
+  __shared__ R red[32];
+  __shared__ TQ redc[32];
+  extern __shared__ __align__(16) unsigned char smem_m[];
+  TQ* P = reinterpret_cast<TQ*>(smem_m);
+  const size_t tri = (size_t)m * (m + 1) / 2;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int q0 = blockIdx.x * G;
+  const int k = min(G, cnt - q0);
+  for (size_t e = tid; e < (size_t)k * m * m; e += nt) {
+    const int q = (int)(e / ((size_t)m * m)), r = (int)(e % ((size_t)m * m));
+    const int i = r % m, c = r / m;
+    if (i <= c) P[q * tri + (size_t)c * (c + 1) / 2 + i] = Rin[(size_t)(q0 + q) * m * m + r];
+  }
+  __syncthreads();
+  for (int j = 0; j < m; ++j) {
+    const size_t cj = (size_t)j * (j + 1) / 2;
+    R s2 = R(0);
+    for (int e = tid; e < (k - 1) * (j + 1); e += nt) {
+      const int q = 1 + e / (j + 1), i = e % (j + 1);
+      s2 += abs2_(P[q * tri + cj + i]);
+    }
+    s2 = block_sum(s2, red);
+    const TQ x0 = P[cj + j];
+    if (s2 == R(0)) continue;  // H_j = I (block-uniform)
+    const R ax0 = sqrt_(abs2_(x0));
+    const R alpha = sqrt_(s2 + ax0 * ax0);
+    const TQ ph = ax0 > R(0) ? x0 * (R(1) / ax0) : from_real<TQ>(R(1));
+    const TQ beta = ph * (-alpha);
+    const TQ u0 = x0 - beta;
+    const R t = R(1) / (alpha * (alpha + ax0));
+    // u = [u0 (row j of R_0); R_q(0..j, j), q >= 1]; apply to columns c > j
+    for (int c = j + 1 + wid; c < m; c += nw) {
+      const size_t cc = (size_t)c * (c + 1) / 2;
+      TQ d = zero_<TQ>();
+      for (int e = lane; e < (k - 1) * (j + 1); e += 32) {
+        const int q = 1 + e / (j + 1), i = e % (j + 1);
+        fmac_(d, P[q * tri + cj + i], P[q * tri + cc + i]);
+      }
+      d = warp_sum(d);
+      const TQ a0 = P[cc + j];
+      fmac_(d, u0, a0);
+      const TQ f = d * t;
+      for (int e = lane; e < (k - 1) * (j + 1); e += 32) {
+        const int q = 1 + e / (j + 1), i = e % (j + 1);
+        P[q * tri + cc + i] = P[q * tri + cc + i] - f * P[q * tri + cj + i];
+      }
+      if (lane == 0) P[cc + j] = a0 - f * u0;
+    }
+    __syncthreads();
+    if (tid == 0) P[cj + j] = beta;
+    __syncthreads();
+  }
+  TQ* Ro = Rout + (size_t)blockIdx.x * m * m;
+  for (int e = tid; e < m * m; e += nt) {
+    const int i = e % m, c = e / m;
+    Ro[e] = (i <= c) ? P[(size_t)c * (c + 1) / 2 + i] : zero_<TQ>();
+  }
+}
+
 template <typename TQ>
 __global__ void __launch_bounds__(256)
 tsqr_merge_kernel(int cnt, int m, const TQ* __restrict__ Rin, TQ* Rout, TQ* slots, size_t slot,
@@ -136,29 +236,20 @@ tsqr_merge_kernel(int cnt, int m, const TQ* __restrict__ Rin, TQ* Rout, TQ* slot
   }
 }
 
-// Stack cnt R factors (m x m each, consecutive) into a (cnt m) x m matrix.
-template <typename TQ>
-__global__ void stack_r_kernel(int cnt, int m, const TQ* __restrict__ Rin, TQ* Y) {
-  const long long rows = (long long)cnt * m;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < rows * m;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long i = e % rows;
-    const int c = (int)(e / rows);
-    const long long q = i / m, ii = i % m;
-    Y[e] = Rin[q * m * m + ii + (long long)c * m];
-  }
-}
+constexpr size_t TSQR_SMEM_MAX = 200 * 1024;  // shared memory a leaf or a packed merge may take
 
-// Upper triangle of the leading m x m block of Y (ld ldy) into R (m x m).
-template <typename TQ>
-__global__ void extract_r_kernel(int m, const TQ* __restrict__ Y, long long ldy, TQ* R) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
-    const int i = e % m, c = e / m;
-    R[e] = (i <= c) ? Y[i + (long long)c * ldy] : zero_<TQ>();
-  }
+// Raise a kernel's dynamic shared-memory limit once per device.
+template <typename K>
+static void open_smem(K kernel) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> opened;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if (opened.insert({dev, reinterpret_cast<const void*>(kernel)}).second &&
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TSQR_SMEM_MAX) != cudaSuccess)
+    cudaGetLastError();
 }
-
-constexpr int TSQR_CLUSTER_MAX = 16;  // R factors stacked for the cluster QR
 
 template <typename T, typename TQ>
 void tsqr_r(cudaStream_t st, int n, int m, const T* W, long long ldw, TQ* R, TQ* ws) {
@@ -171,70 +262,94 @@ void tsqr_r(cudaStream_t st, int n, int m, const T* W, long long ldw, TQ* R, TQ*
   TQ* Rb = Ra + (size_t)nleaf * m * m;
   TQ* hbuf = Rb + (size_t)nleaf * m * m;
   count_launch();
-  tsqr_leaf_kernel<T, TQ><<<nleaf, 256, 0, st>>>(n, m, W, ldw, b, slots, slot, Ra, hbuf);
+  const size_t leaf_bytes = (size_t)b * m * sizeof(TQ);
+  if (leaf_bytes <= TSQR_SMEM_MAX) {
+    open_smem(tsqr_leaf_smem_kernel<T, TQ>);
+    tsqr_leaf_smem_kernel<T, TQ><<<nleaf, 256, leaf_bytes, st>>>(n, m, W, ldw, b, Ra, hbuf);
+  } else {
+    tsqr_leaf_kernel<T, TQ><<<nleaf, 256, 0, st>>>(n, m, W, ldw, b, slots, slot, Ra, hbuf);
+  }
   int cnt = nleaf;
   TQ* src = Ra;
   TQ* dst = Rb;
-  while (cnt > TSQR_CLUSTER_MAX) {
-    const int groups = ceil_div(cnt, TSQR_G);
-    count_launch();
-    tsqr_merge_kernel<TQ><<<groups, 256, 0, st>>>(cnt, m, src, dst, slots, slot, hbuf);
-    cnt = groups;
-    TQ* t = src;
-    src = dst;
-    dst = t;
-  }
-  if (cnt == 1) {
-    cudaMemcpyAsync(R, src, sizeof(TQ) * m * m, cudaMemcpyDeviceToDevice, st);
-    return;
-  }
-  // the last <= 16 factors: one Householder QR of the stacked matrix on a
-  // thread-block cluster (the slots area holds cnt m x m >= the stack)
-  TQ* Y = slots;
-  const long long tot = (long long)cnt * m * m;
-  count_launch();
-  stack_r_kernel<TQ><<<(int)std::min<long long>((tot + 255) / 256, 4 * NUM_SMS), 256, 0, st>>>(cnt, m, src, Y);
-  if (qr_cluster_inplace<TQ>(st, cnt * m, m, Y, hbuf)) {
-    count_launch();
-    extract_r_kernel<TQ><<<ceil_div((long long)m * m, 256), 256, 0, st>>>(m, Y, (long long)cnt * m, R);
-    return;
-  }
-  while (cnt > 1) {  // no cluster: single-CTA merges
-    const int groups = ceil_div(cnt, TSQR_G);
+  // factors per packed merge: as many as fit in shared memory, at most 4
+  const size_t tri_bytes = (size_t)m * (m + 1) / 2 * sizeof(TQ);
+  const int G = (int)std::min<size_t>(4, TSQR_SMEM_MAX / tri_bytes);
+  while (cnt > 1) {
+    const int g = G >= 2 ? G : TSQR_G;
+    const int groups = ceil_div(cnt, g);
     TQ* out = (groups == 1) ? R : dst;
     count_launch();
-    tsqr_merge_kernel<TQ><<<groups, 256, 0, st>>>(cnt, m, src, out, slots, slot, hbuf);
+    if (G >= 2) {
+      open_smem(tsqr_merge_packed_kernel<TQ>);
+      tsqr_merge_packed_kernel<TQ><<<groups, 512, (size_t)G * tri_bytes, st>>>(cnt, G, m, src, out);
+    } else {
+      tsqr_merge_kernel<TQ><<<groups, 256, 0, st>>>(cnt, m, src, out, slots, slot, hbuf);
+    }
     cnt = groups;
     TQ* t = src;
     src = dst;
     dst = t;
   }
+  if (nleaf == 1) cudaMemcpyAsync(R, Ra, sizeof(TQ) * m * m, cudaMemcpyDeviceToDevice, st);
 }
 
 // ------------------------------------------------------------------------
 // Triangular inverses and the small Cholesky
 // ------------------------------------------------------------------------
+// Column c of Linv = (R^*)^-1 (lower triangular): the column sweep for
+// R^* x = e_c, x_l = b_l / conj(R_ll), b_i -= conj(R_li) x_l (i > l), one
+// warp per column and one column per block, so the m dependent chains run
+// on m SMs' FP64 pipes side by side.
 template <typename TI, typename TO>
-__global__ void trinv_upper_ct_kernel(int m, const TI* __restrict__ R, long long ldr, TO* Linv) {
-  // Linv = (R^*)^-1 ; (R^*)(i, l) = conj(R(l, i)), lower triangular
-  for (int c = threadIdx.x; c < m; c += blockDim.x) {
-    for (int i = 0; i < c; ++i) Linv[i + (size_t)c * m] = zero_<TO>();
-    for (int i = c; i < m; ++i) {
-      TO s = (i == c) ? from_real<TO>(real_t<TO>(1)) : zero_<TO>();
-      for (int l = c; l < i; ++l) {
-        const TO a = conj_(cvt<TO, TI>(R[l + (long long)i * ldr]));
-        s = s - a * Linv[l + (size_t)c * m];
-      }
-      const TO d = conj_(cvt<TO, TI>(R[i + (long long)i * ldr]));
-      Linv[i + (size_t)c * m] = div_(s, d);
-    }
+__global__ void __launch_bounds__(32, 1)
+trinv_upper_ct_kernel(int m, const TI* __restrict__ R, long long ldr, TO* Linv) {
+  extern __shared__ __align__(16) unsigned char smem_t[];
+  TO* b = reinterpret_cast<TO*>(smem_t);  // right-hand side, then the solution
+  TO* dinv = b + m;                        // 1 / conj(R_ll)
+  const int c = blockIdx.x, lane = threadIdx.x;
+  for (int i = lane; i < m; i += 32) {
+    b[i] = (i == c) ? from_real<TO>(real_t<TO>(1)) : zero_<TO>();
+    dinv[i] = div_(from_real<TO>(real_t<TO>(1)), conj_(cvt<TO, TI>(R[i + (long long)i * ldr])));
   }
+  __syncwarp();
+  for (int l = c; l < m; ++l) {
+    const TO xl = b[l] * dinv[l];
+    for (int i = l + 1 + lane; i < m; i += 32) b[i] = b[i] - conj_(cvt<TO, TI>(R[l + (long long)i * ldr])) * xl;
+    __syncwarp();
+    if (lane == 0) b[l] = xl;
+    __syncwarp();
+  }
+  for (int i = lane; i < m; i += 32) Linv[i + (size_t)c * m] = (i < c) ? zero_<TO>() : b[i];
 }
 
 template <typename TI, typename TO>
 void trinv_upper_ct(cudaStream_t st, int m, const TI* R, long long ldr, TO* Linv) {
   count_launch();
-  trinv_upper_ct_kernel<TI, TO><<<1, 256, 0, st>>>(m, R, ldr, Linv);
+  trinv_upper_ct_kernel<TI, TO><<<m, 32, 2 * (size_t)m * sizeof(TO), st>>>(m, R, ldr, Linv);
+}
+
+// Column c of L^-1 for lower triangular L (ld ld): x_l = b_l / L_ll,
+// b_i -= L_il x_l (i > l); one warp per column, one column per block.
+template <typename T>
+__global__ void __launch_bounds__(32, 1) trinv_lower_kernel(int n, const T* __restrict__ L, long long ld, T* Li) {
+  extern __shared__ __align__(16) unsigned char smem_t[];
+  T* b = reinterpret_cast<T*>(smem_t);
+  T* dinv = b + n;
+  const int c = blockIdx.x, lane = threadIdx.x;
+  for (int i = lane; i < n; i += 32) {
+    b[i] = (i == c) ? from_real<T>(real_t<T>(1)) : zero_<T>();
+    dinv[i] = div_(from_real<T>(real_t<T>(1)), L[i + (long long)i * ld]);
+  }
+  __syncwarp();
+  for (int l = c; l < n; ++l) {
+    const T xl = b[l] * dinv[l];
+    for (int i = l + 1 + lane; i < n; i += 32) b[i] = b[i] - L[i + (long long)l * ld] * xl;
+    __syncwarp();
+    if (lane == 0) b[l] = xl;
+    __syncwarp();
+  }
+  for (int i = lane; i < n; i += 32) Li[i + (size_t)c * n] = (i < c) ? zero_<T>() : b[i];
 }
 
 // Cholesky (lower, in place) of an n x n Hermitian matrix held by one CTA.
@@ -280,29 +395,16 @@ __device__ int chol_lower_cta(int n, T* A, long long ld) {
 }
 
 template <typename T>
-__device__ void trinv_lower_cta(int n, const T* L, long long ld, T* Li, long long ldi) {
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
-    for (int i = 0; i < c; ++i) Li[i + c * ldi] = zero_<T>();
-    for (int i = c; i < n; ++i) {
-      T s = (i == c) ? from_real<T>(real_t<T>(1)) : zero_<T>();
-      for (int l = c; l < i; ++l) s = s - L[i + l * ld] * Li[l + c * ldi];
-      Li[i + c * ldi] = div_(s, L[i + i * ld]);
-    }
-  }
-  __syncthreads();
-}
-
-template <typename T>
-__global__ void chol_inv_kernel(int m, T* G, long long ldg, T* Linv, int* info) {
+__global__ void chol_kernel(int m, T* G, long long ldg, int* info) {
   const int bad = chol_lower_cta<T>(m, G, ldg);
   if (threadIdx.x == 0) info[0] = bad;
-  trinv_lower_cta<T>(m, G, ldg, Linv, m);
 }
 
 template <typename T>
 void chol_inv(cudaStream_t st, int m, T* G, long long ldg, T* Linv, int* info) {
-  count_launch();
-  chol_inv_kernel<T><<<1, 256, 0, st>>>(m, G, ldg, Linv, info);
+  count_launch(2);
+  chol_kernel<T><<<1, 256, 0, st>>>(m, G, ldg, info);
+  trinv_lower_kernel<T><<<m, 32, 2 * (size_t)m * sizeof(T), st>>>(m, G, ldg, Linv);
 }
 
 // ------------------------------------------------------------------------

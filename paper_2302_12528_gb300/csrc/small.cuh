@@ -53,9 +53,5 @@ template <typename T>
 bool eig_small_fast(cudaStream_t st, int N, int m, T* Ap, double* lam, T* C1, void* ws, int* fail_dev);
 template <typename T>
 bool thin_q_fast(cudaStream_t st, int N, int q, T* Y, int c0, int nq, T* Q, T* ws);
-// Householder QR of Y (N x q, ld N) in place on a cluster: R in the upper
-// triangle, reflectors below it, uhead/tau in hb (2q elements).
-template <typename T>
-bool qr_cluster_inplace(cudaStream_t st, int N, int q, T* Y, T* hb);
 
 }  // namespace mpl

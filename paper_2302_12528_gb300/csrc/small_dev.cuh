@@ -37,6 +37,21 @@ __device__ int sturm_count(int N, const R* d, const R* f, R x, R pivmin) {
   return cnt;
 }
 
+// The same count with the squares f_i^2 precomputed (f2[i] = f[i] * f[i]).
+template <typename R>
+__device__ int sturm_count_f2(int N, const R* d, const R* f2, R x, R pivmin) {
+  int cnt = 0;
+  R q = d[0] - x;
+  if (fabs((double)q) < (double)pivmin) q = -pivmin;
+  if (q < R(0)) ++cnt;
+  for (int i = 1; i < N; ++i) {
+    q = d[i] - x - f2[i - 1] / q;
+    if (fabs((double)q) < (double)pivmin) q = -pivmin;
+    if (q < R(0)) ++cnt;
+  }
+  return cnt;
+}
+
 // LU with partial pivoting of the tridiagonal (T - lam I): on return dl holds
 // the multipliers, dd/du/du2 the three diagonals of U, piv[i] = 1 if rows i
 // and i+1 were interchanged.  Zero pivots are replaced by ``tiny``.
