@@ -420,7 +420,7 @@ def main():
             out["roofline"]["complex_equivalent_gflops"] = achieved * 8.0 / 6.0
         if split_ax_active(w):
             out["roofline"] = split_ax_roofline(w, per_launch_s, apply_calls)
-            out["config"]["fp64_products"] = ("A X and products >= 2^28 FMAs" if os.environ.get("MPL_GEMM_SPLIT") != "0"
+            out["config"]["fp64_products"] = ("A X and products >= 2^25 FMAs" if os.environ.get("MPL_GEMM_SPLIT") != "0"
                                               else "A X") + " by error-free bf16 splitting on the tensor cores " \
                                                             "(exact for 64-bit digits, one rounding)"
     if ck:

@@ -325,6 +325,7 @@ class Engine : public EngineBase {
     constexpr int NB = CholBlock<TF>::NB;
     const int nblk = ceil_div(n, NB);
     DenseFactor<TF>& F = FS.F;
+    F.Mf = F.Mb = nullptr;  // the look-ahead products belong to the factor being replaced
     if (!F.L) {
       Lbuf_.alloc(sizeof(TF) * n * n);
       Dbuf_.alloc(sizeof(TF) * (size_t)nblk * NB * NB);
@@ -363,6 +364,12 @@ class Engine : public EngineBase {
       if (info[0] == 0) {
         c_->stats.factor_shift = sigma;
         c_->stats.nnz_L = n * (n + 1) / 2;
+        const size_t la = dense_lookahead_elems<TF>((int)n);
+        if (la) {
+          Mbuf_.ensure(sizeof(TF) * la);
+          dense_sweep_lookahead<TF>(st, F, Mbuf_.as<TF>());
+          check_launch("sweep look-ahead products");
+        }
         return;
       }
       c_->info = info[0];
@@ -848,7 +855,7 @@ class Engine : public EngineBase {
   void make_low_op();
 
   mpl_ctx* c_;
-  DevMem Aw_, Al_, Lbuf_, Dbuf_, tmp_, info_, scr_mem_, X0_, x0l_, tmpx_, eigws_, perm_dev_;
+  DevMem Aw_, Al_, Lbuf_, Dbuf_, Mbuf_, tmp_, info_, scr_mem_, X0_, x0l_, tmpx_, eigws_, perm_dev_;
   DevMem rp_, ci_, vw_, vl_, orig_rp_, orig_ci_, adj_, dscale_;
   const TW* last_X_ = nullptr;       // Ritz block of the last solve (internal ordering)
   std::vector<double> last_theta_;   // its Ritz values

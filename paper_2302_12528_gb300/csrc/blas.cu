@@ -246,7 +246,7 @@ void gemm(cudaStream_t st, bool opA, bool opB, int M, int N, int K, real_t<T> al
   if constexpr (sizeof(real_t<T>) == 8) {
     // large FP64 products on the tensor cores by error-free splitting (exact
     // for the 64-bit digits, one rounding: at least as accurate as this GEMM)
-    if (oz_gemm_enabled() && (long long)M * N * K >= (1LL << 28) &&
+    if (oz_gemm_enabled() && (long long)M * N * K >= (1LL << 25) &&
         oz_gemm_fp64(st, tr<T>::cx, opA, opB, M, N, K, (double)alpha, reinterpret_cast<const double*>(A), lda,
                      reinterpret_cast<const double*>(B), ldb, (double)beta, reinterpret_cast<double*>(C), ldc,
                      lower_only))

@@ -246,23 +246,9 @@ void scale_rows(cudaStream_t st, int n, int m, T* B, long long ldb, const float*
 // The FP32 sweeps wait on memory and take DB; the FP64 ones are bound by the
 // FP64 pipe, where twice the shared memory per CTA only lowers the number of
 // resident CTAs.
-// MINB: CTAs per SM the register allocation must allow.
-template <typename T> struct Sweep {
-  static constexpr int NBS = 32, CT = 32, MINB = 6;
-  static constexpr bool DB = false;
-};
-template <> struct Sweep<zd> {
-  static constexpr int NBS = 32, CT = 32, MINB = 4;
-  static constexpr bool DB = false;
-};
-template <> struct Sweep<float> {
-  static constexpr int NBS = 64, CT = 32, MINB = 2;
-  static constexpr bool DB = true;
-};
-template <> struct Sweep<zf> {
-  static constexpr int NBS = 64, CT = 32, MINB = 2;
-  static constexpr bool DB = true;
-};
+template <typename T> struct Sweep { static constexpr int NBS = 32, CT = 32; static constexpr bool DB = false; };
+template <> struct Sweep<float> { static constexpr int NBS = 64, CT = 32; static constexpr bool DB = true; };
+template <> struct Sweep<zf> { static constexpr int NBS = 64, CT = 32; static constexpr bool DB = true; };
 
 constexpr long long SWEEP_WAIT_LIMIT = 1LL << 24;  // flag polls (with a short sleep) before giving up
 
@@ -306,10 +292,137 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Per tile update one barrier: the next factor tile is copied asynchronously
 // and the next Y block read into registers (each thread acquires the row's
 // flag itself) while the current tile is multiplied; two buffers alternate.
-template <typename T, int NBS, int CT, bool BACK, bool DB>
-__global__ void __launch_bounds__(256, Sweep<T>::MINB)
-trsm_sweep_kernel(int n, int nsb, int nct, const T* __restrict__ L, long long ldl, const T* __restrict__ Dinv,
+// The single-buffer form (the FP64 sweeps): the factor tile is staged by
+// plain loads (the backward tile conjugate-transposed) before waiting for
+// Y_j, thread 0 waits, and three barriers bracket each tile.  Bound by the
+// FP64 pipe, it gains nothing from overlapping the loads and keeps more
+// CTAs resident.
+template <typename T, int NBS, int CT, bool BACK>
+__global__ void __launch_bounds__(256)
+trsm_sweep_1buf_kernel(int n, int nsb, int nct, const T* __restrict__ L, long long ldl, const T* __restrict__ Dinv,
                   int dnb, T* B, long long ldb, int m, unsigned* sync, unsigned epoch) {
+  constexpr int LDS = NBS + 1;
+  constexpr int TM = NBS / 16, TN = CT / 16;
+  extern __shared__ unsigned char sm[];
+  T* Ls = reinterpret_cast<T*>(sm);  // Ls[kk * LDS + r]
+  T* Ys = Ls + NBS * LDS;            // Ys[kk * CT + c]
+  __shared__ int item, gave_up;
+  const int tid = threadIdx.x;
+  const int tr = tid & 15, tc = tid >> 4;
+  unsigned* flags = sync + 2;
+  const int nitems = nsb * nct;
+  for (;;) {
+    if (tid == 0) {
+      item = (int)atomicAdd(sync, 1u);
+      gave_up = 0;
+    }
+    __syncthreads();
+    const int t = item;
+    if (t >= nitems) break;
+    const int step = t / nct, c = t % nct;
+    const int i = BACK ? nsb - 1 - step : step;
+    const int ct0 = c * CT, cw = min(CT, m - ct0);
+    const int r0 = i * NBS, rb = min(NBS, n - r0);
+
+    T acc[TM][TN];
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TN; ++b) {
+        const int r = tr + 16 * a, cc = tc + 16 * b;
+        acc[a][b] = (r < rb && cc < cw) ? ldcg_(B + (r0 + r) + (long long)(ct0 + cc) * ldb) : zero_<T>();
+      }
+    for (int s2 = 0; s2 < step; ++s2) {
+      const int j = BACK ? nsb - 1 - s2 : s2;
+      const int rk0 = j * NBS, kb = min(NBS, n - rk0);
+      // the factor tile is final: stage it before waiting for Y_j
+      for (int e = tid; e < NBS * NBS; e += 256) {
+        const int a = e % NBS, b = e / NBS;
+        if (!BACK) {  // L_ij(r = a, kk = b)
+          Ls[b * LDS + a] = (a < rb && b < kb) ? L[(r0 + a) + (long long)(rk0 + b) * ldl] : zero_<T>();
+        } else {      // (L_ji)^*(r = b, kk = a) = conj(L_ji(a, b))
+          Ls[a * LDS + b] = (a < kb && b < rb) ? conj_(L[(rk0 + a) + (long long)(r0 + b) * ldl]) : zero_<T>();
+        }
+      }
+      if (tid == 0 && !gave_up) {
+        const unsigned* f = flags + (size_t)j * nct + c;
+        long long it = 0;
+        while (ld_acquire(f) != epoch) {
+          if (++it >= SWEEP_WAIT_LIMIT) {
+            gave_up = 1;
+            atomicExch(sync + 1, 1u);
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      __syncthreads();
+      for (int e = tid; e < NBS * CT; e += 256) {
+        const int kk = e % NBS, cc = e / NBS;
+        Ys[kk * CT + cc] = (kk < kb && cc < cw) ? ldcg_(B + (rk0 + kk) + (long long)(ct0 + cc) * ldb) : zero_<T>();
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < NBS; ++kk) {
+        T av[TM], bv[TN];
+#pragma unroll
+        for (int a = 0; a < TM; ++a) av[a] = -Ls[kk * LDS + tr + 16 * a];
+#pragma unroll
+        for (int b = 0; b < TN; ++b) bv[b] = Ys[kk * CT + tc + 16 * b];
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+          for (int b = 0; b < TN; ++b) fma_(acc[a][b], av[a], bv[b]);
+      }
+      __syncthreads();
+    }
+    // Y_i = Dinv_ii (B_i - sum_j L_ij Y_j)   (backward: the conjugate transpose)
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TN; ++b) Ys[(tr + 16 * a) * CT + tc + 16 * b] = acc[a][b];
+    const int fb = r0 / dnb, off = r0 % dnb;
+    const T* Di = Dinv + (size_t)fb * dnb * dnb + off + (size_t)off * dnb;
+    for (int e = tid; e < NBS * NBS; e += 256) {
+      const int a = e % NBS, b = e / NBS;
+      const T v = (a < rb && b < rb) ? Di[a + (size_t)b * dnb] : zero_<T>();
+      if (!BACK) Ls[b * LDS + a] = v;           // Dinv(r = a, kk = b)
+      else Ls[a * LDS + b] = conj_(v);          // Dinv^*(r = b, kk = a)
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TN; ++b) acc[a][b] = zero_<T>();
+#pragma unroll 4
+    for (int kk = 0; kk < NBS; ++kk) {
+      T av[TM], bv[TN];
+#pragma unroll
+      for (int a = 0; a < TM; ++a) av[a] = Ls[kk * LDS + tr + 16 * a];
+#pragma unroll
+      for (int b = 0; b < TN; ++b) bv[b] = Ys[kk * CT + tc + 16 * b];
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TN; ++b) fma_(acc[a][b], av[a], bv[b]);
+    }
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TN; ++b) {
+        const int r = tr + 16 * a, cc = tc + 16 * b;
+        if (r < rb && cc < cw) B[(r0 + r) + (long long)(ct0 + cc) * ldb] = acc[a][b];
+      }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) st_release(flags + (size_t)i * nct + c, epoch);
+  }
+}
+
+template <typename T, int NBS, int CT, bool BACK>
+__global__ void __launch_bounds__(256, 2)
+trsm_sweep_kernel(int n, int nsb, int nct, const T* __restrict__ L, long long ldl, const T* __restrict__ Dinv,
+                  int dnb, const T* __restrict__ Mla, T* B, long long ldb, int m, unsigned* sync, unsigned epoch) {
   constexpr int LDS = NBS + 1;
   constexpr int TM = NBS / 16, TN = CT / 16;
   constexpr int YPT = NBS * CT / 256;  // elements of a Y block per thread
@@ -317,7 +430,7 @@ trsm_sweep_kernel(int n, int nsb, int nct, const T* __restrict__ L, long long ld
   extern __shared__ unsigned char sm[];
   // buffer q: factor tile at L0 + q NBS LDS, Y block at Y0 + q NBS CT ([kk * CT + c])
   T* const L0 = reinterpret_cast<T*>(sm);
-  T* const Y0 = L0 + (DB ? 2 : 1) * NBS * LDS;
+  T* const Y0 = L0 + 2 * NBS * LDS;
   __shared__ int item;
   const int tid = threadIdx.x, lane = tid & 31;
   const int tr = tid & 15, tc = tid >> 4;
@@ -334,34 +447,23 @@ trsm_sweep_kernel(int n, int nsb, int nct, const T* __restrict__ L, long long ld
     const int ct0 = c * CT, cw = min(CT, m - ct0);
     const int r0 = i * NBS, rb = min(NBS, n - r0);
     auto jof = [&](int s2) { return BACK ? nsb - 1 - s2 : s2; };
-    // the factor tile (i, j) into buffer q.  DB: asynchronously, as stored
-    // (backward: L_ji(kk, r) at [r * LDS + kk], conjugated when read); one
-    // buffer: by plain loads, the backward tile conjugate-transposed so that
-    // both sweeps read [kk * LDS + r]
+    // the factor tile (i, j) into buffer q, asynchronously and as stored
+    // (backward: L_ji(kk, r) at [r * LDS + kk], conjugated when read)
     auto stage_L = [&](int q, int j) {
       const int rk0 = j * NBS, kb = min(NBS, n - rk0);
       T* Ls = L0 + q * NBS * LDS;
       for (int e = tid; e < NBS * NBS; e += 256) {
         if (!BACK) {  // L_ij(r, kk) at [kk * LDS + r]
           const int r = e % NBS, kk = e / NBS;
-          if (r < rb && kk < kb) {
-            if (DB) cp_async_elem(Ls + kk * LDS + r, L + (r0 + r) + (long long)(rk0 + kk) * ldl);
-            else Ls[kk * LDS + r] = L[(r0 + r) + (long long)(rk0 + kk) * ldl];
-          } else {
-            Ls[kk * LDS + r] = zero_<T>();
-          }
+          if (r < rb && kk < kb) cp_async_elem(Ls + kk * LDS + r, L + (r0 + r) + (long long)(rk0 + kk) * ldl);
+          else Ls[kk * LDS + r] = zero_<T>();
         } else {
           const int kk = e % NBS, r = e / NBS;
-          const int dst = DB ? r * LDS + kk : kk * LDS + r;
-          if (r < rb && kk < kb) {
-            if (DB) cp_async_elem(Ls + dst, L + (rk0 + kk) + (long long)(r0 + r) * ldl);
-            else Ls[dst] = conj_(L[(rk0 + kk) + (long long)(r0 + r) * ldl]);
-          } else {
-            Ls[dst] = zero_<T>();
-          }
+          if (r < rb && kk < kb) cp_async_elem(Ls + r * LDS + kk, L + (rk0 + kk) + (long long)(r0 + r) * ldl);
+          else Ls[r * LDS + kk] = zero_<T>();
         }
       }
-      if (DB) cp_async_commit();
+      cp_async_commit();
     };
     // Y_j's flag, read by lane 0 of each warp (one poller per warp keeps the
     // polling traffic off the L2 slices that hold the flags) and passed on
@@ -416,21 +518,27 @@ trsm_sweep_kernel(int n, int nsb, int nct, const T* __restrict__ L, long long ld
         const int r = tr + 16 * a, cc = tc + 16 * b;
         acc[a][b] = (r < rb && cc < cw) ? ldcg_(B + (r0 + r) + (long long)(ct0 + cc) * ldb) : zero_<T>();
       }
-    if (step > 0) {
+    // with the look-ahead products M_i (Mla), the last tile (the row that
+    // finishes just before this one) is left out of the accumulation:
+    // Y_i = Dinv_ii (B_i - sum_{j < last} L_ij Y_j) - M_i Y_last, so only one
+    // product follows the wait for Y_last
+    const bool la = Mla != nullptr && step > 0;
+    const int nacc = la ? step - 1 : step;
+    if (nacc > 0) {
       stage_L(0, jof(0));
       wait_flag(jof(0));
       load_Y(jof(0));
       put_Y(0);
       cp_async_wait_all();
       __syncthreads();
-      for (int s2 = 0; s2 < step; ++s2) {
-        const int q = DB ? (s2 & 1) : 0;
-        const bool more = s2 + 1 < step;
-        // DB: the next tile's factor part is always prefetched; its Y part
-        // only when already published (else read after this tile's product,
-        // so that a row still in flight does not hold up the product)
+      for (int s2 = 0; s2 < nacc; ++s2) {
+        const int q = s2 & 1;
+        const bool more = s2 + 1 < nacc;
+        // the next tile's factor part is always prefetched; its Y part only
+        // when already published (else read after this tile's product, so
+        // that a row still in flight does not hold up the product)
         bool early = false;
-        if (DB && more) {
+        if (more) {
           stage_L(q ^ 1, jof(s2 + 1));
           early = flag_ready(jof(s2 + 1));
           if (early) load_Y(jof(s2 + 1));
@@ -442,7 +550,7 @@ trsm_sweep_kernel(int n, int nsb, int nct, const T* __restrict__ L, long long ld
           T av[TM], bv[TN];
 #pragma unroll
           for (int a = 0; a < TM; ++a)
-            av[a] = (BACK && DB) ? -conj_(Ls[(tr + 16 * a) * LDS + kk]) : -Ls[kk * LDS + tr + 16 * a];
+            av[a] = BACK ? -conj_(Ls[(tr + 16 * a) * LDS + kk]) : -Ls[kk * LDS + tr + 16 * a];
 #pragma unroll
           for (int b = 0; b < TN; ++b) bv[b] = Ys[kk * CT + tc + 16 * b];
 #pragma unroll
@@ -450,28 +558,25 @@ trsm_sweep_kernel(int n, int nsb, int nct, const T* __restrict__ L, long long ld
 #pragma unroll
             for (int b = 0; b < TN; ++b) fma_(acc[a][b], av[a], bv[b]);
         }
-        if (DB) {
-          if (more) {
-            if (!early) {
-              wait_flag(jof(s2 + 1));
-              load_Y(jof(s2 + 1));
-            }
-            put_Y(q ^ 1);
-          }
-          cp_async_wait_all();
-          __syncthreads();
-        } else {  // one buffer: refill it after everyone has read it
-          __syncthreads();
-          if (more) {
-            stage_L(0, jof(s2 + 1));
+        if (more) {
+          if (!early) {
             wait_flag(jof(s2 + 1));
             load_Y(jof(s2 + 1));
-            put_Y(0);
-            cp_async_wait_all();
-            __syncthreads();
           }
+          put_Y(q ^ 1);
         }
+        cp_async_wait_all();
+        __syncthreads();
       }
+    }
+    if (la) {  // M_i into buffer 1 while the diagonal product runs
+      const T* Mi = Mla + (size_t)i * NBS * NBS;
+      T* Lm = L0 + NBS * LDS;
+      for (int e = tid; e < NBS * NBS; e += 256) {
+        const int r = e % NBS, kk = e / NBS;
+        cp_async_elem(Lm + kk * LDS + r, Mi + e);
+      }
+      cp_async_commit();
     }
     // Y_i = Dinv_ii (B_i - sum_j L_ij Y_j)   (backward: the conjugate transpose)
     T* Ls = L0;
@@ -504,6 +609,28 @@ trsm_sweep_kernel(int n, int nsb, int nct, const T* __restrict__ L, long long ld
       for (int a = 0; a < TM; ++a)
 #pragma unroll
         for (int b = 0; b < TN; ++b) fma_(acc[a][b], av[a], bv[b]);
+    }
+    if (la) {  // - M_i Y_last, after Y_last is published
+      const int jl = jof(step - 1);
+      wait_flag(jl);
+      load_Y(jl);
+      put_Y(1);
+      cp_async_wait_all();
+      __syncthreads();
+      const T* Lm = L0 + NBS * LDS;
+      const T* Ym = Y0 + NBS * CT;
+#pragma unroll 4
+      for (int kk = 0; kk < NBS; ++kk) {
+        T av[TM], bv[TN];
+#pragma unroll
+        for (int a = 0; a < TM; ++a) av[a] = Lm[kk * LDS + tr + 16 * a];
+#pragma unroll
+        for (int b = 0; b < TN; ++b) bv[b] = Ym[kk * CT + tc + 16 * b];
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+          for (int b = 0; b < TN; ++b) fms_(acc[a][b], av[a], bv[b]);
+      }
     }
 #pragma unroll
     for (int a = 0; a < TM; ++a)
@@ -544,6 +671,75 @@ std::map<cudaStream_t, SweepSync>& sweep_syncs() {
 }
 }  // namespace
 
+// Look-ahead products of the double-buffered sweeps: for block row i,
+// forward M_i = Dinv_ii L_{i,i-1}, backward M_i = Dinv_ii^* L_{i+1,i}^*
+// (NBS x NBS, column-major at M + i NBS^2; zero where the neighbour does not
+// exist).  Computed once per factorisation, in the factor's precision.
+template <typename T, int NBS, bool BACK>
+__global__ void __launch_bounds__(256) sweep_lookahead_kernel(int n, int nsb, const T* __restrict__ L, long long ldl,
+                                                              const T* __restrict__ Dinv, int dnb, T* M) {
+  constexpr int LDS = NBS + 1;
+  extern __shared__ unsigned char sm[];
+  T* Ds = reinterpret_cast<T*>(sm);  // Ds[t * LDS + r] = (Dinv or Dinv^*)(r, t)
+  T* Ls = Ds + NBS * LDS;            // Ls[kk * LDS + t] = (L_{i,i-1} or L_{i+1,i}^*)(t, kk)
+  const int i = blockIdx.x, tid = threadIdx.x;
+  const int jl = BACK ? i + 1 : i - 1;
+  T* Mi = M + (size_t)i * NBS * NBS;
+  if (jl < 0 || jl >= nsb) {
+    for (int e = tid; e < NBS * NBS; e += 256) Mi[e] = zero_<T>();
+    return;
+  }
+  const int r0 = i * NBS, rb = min(NBS, n - r0);
+  const int rk0 = jl * NBS, kb = min(NBS, n - rk0);
+  const int fb = r0 / dnb, off = r0 % dnb;
+  const T* Di = Dinv + (size_t)fb * dnb * dnb + off + (size_t)off * dnb;
+  for (int e = tid; e < NBS * NBS; e += 256) {
+    const int a = e % NBS, b = e / NBS;
+    if (!BACK) {
+      Ds[b * LDS + a] = (a < rb && b < rb) ? Di[a + (size_t)b * dnb] : zero_<T>();                  // Dinv(a, b)
+      Ls[b * LDS + a] = (a < rb && b < kb) ? L[(r0 + a) + (long long)(rk0 + b) * ldl] : zero_<T>();  // L(r0+a, rk0+b)
+    } else {
+      Ds[a * LDS + b] = (a < rb && b < rb) ? conj_(Di[a + (size_t)b * dnb]) : zero_<T>();           // Dinv^*(b, a)
+      Ls[a * LDS + b] = (a < kb && b < rb) ? conj_(L[(rk0 + a) + (long long)(r0 + b) * ldl]) : zero_<T>();  // L^*(b, a)
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < NBS * NBS; e += 256) {
+    const int r = e % NBS, kk = e / NBS;
+    T acc = zero_<T>();
+    for (int t = 0; t < NBS; ++t) fma_(acc, Ds[t * LDS + r], Ls[kk * LDS + t]);
+    Mi[e] = acc;
+  }
+}
+
+template <typename T>
+size_t dense_lookahead_elems(int n) {
+  constexpr int NBS = Sweep<T>::NBS;
+  return Sweep<T>::DB ? 2 * (size_t)ceil_div(n, NBS) * NBS * NBS : 0;
+}
+
+template <typename T>
+void dense_sweep_lookahead(cudaStream_t st, DenseFactor<T>& F, T* ws) {
+  F.Mf = F.Mb = nullptr;
+  if constexpr (Sweep<T>::DB) {
+    constexpr int NBS = Sweep<T>::NBS, NB = CholBlock<T>::NB;
+    const int nsb = ceil_div(F.n, NBS);
+    if (!ws || nsb < 2) return;
+    const size_t sm = 2 * (size_t)NBS * (NBS + 1) * sizeof(T);
+    static const bool opened = [&] {
+      cudaFuncSetAttribute(sweep_lookahead_kernel<T, NBS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaFuncSetAttribute(sweep_lookahead_kernel<T, NBS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      return true;
+    }();
+    (void)opened;
+    count_launch(2);
+    sweep_lookahead_kernel<T, NBS, false><<<nsb, 256, sm, st>>>(F.n, nsb, F.L, F.ldl, F.Dinv, NB, ws);
+    sweep_lookahead_kernel<T, NBS, true><<<nsb, 256, sm, st>>>(F.n, nsb, F.L, F.ldl, F.Dinv, NB, ws + (size_t)nsb * NBS * NBS);
+    F.Mf = ws;
+    F.Mb = ws + (size_t)nsb * NBS * NBS;
+  }
+}
+
 template <typename T, bool BACK>
 static void dense_sweep(cudaStream_t st, const DenseFactor<T>& F, T* B, long long ldb, int m) {
   constexpr int NB = CholBlock<T>::NB, NBS = Sweep<T>::NBS, CT = Sweep<T>::CT;
@@ -551,7 +747,11 @@ static void dense_sweep(cudaStream_t st, const DenseFactor<T>& F, T* B, long lon
   const int n = F.n, nsb = ceil_div(n, NBS), nct = ceil_div(m, CT);
   if (n <= 0 || m <= 0) return;
   const size_t sm = sweep_smem<T>();
-  auto kern = trsm_sweep_kernel<T, NBS, CT, BACK, Sweep<T>::DB>;
+  auto kern = [] {
+    if constexpr (Sweep<T>::DB) return trsm_sweep_kernel<T, NBS, CT, BACK>;
+    else return trsm_sweep_1buf_kernel<T, NBS, CT, BACK>;
+  }();
+  const T* Mla = BACK ? F.Mb : F.Mf;
   // as many CTAs as fit at once (measured: faster than one per SM -- the
   // off-chain updates need the throughput more than the chain needs an SM
   // of its own)
@@ -596,7 +796,8 @@ static void dense_sweep(cudaStream_t st, const DenseFactor<T>& F, T* B, long lon
   cudaMemsetAsync(sync, 0, sizeof(unsigned), st);  // claim counter (launch errors surface at the caller's check)
   const int grid = std::max(1, std::min(nsb * nct, resident));
   count_launch();
-  kern<<<grid, 256, sm, st>>>(n, nsb, nct, F.L, F.ldl, F.Dinv, NB, B, ldb, m, sync, epoch);
+  if constexpr (Sweep<T>::DB) kern<<<grid, 256, sm, st>>>(n, nsb, nct, F.L, F.ldl, F.Dinv, NB, Mla, B, ldb, m, sync, epoch);
+  else kern<<<grid, 256, sm, st>>>(n, nsb, nct, F.L, F.ldl, F.Dinv, NB, B, ldb, m, sync, epoch);
 }
 
 int sweep_take_error(cudaStream_t st) {
@@ -638,7 +839,9 @@ void dense_precond(cudaStream_t st, const DenseFactor<T>& F, T* B, long long ldb
   template void round_block<T>(cudaStream_t, int, int, T*, long long, int, bool);           \
   template void dense_precond<T>(cudaStream_t, const DenseFactor<T>&, T*, long long, int);   \
   template void dense_trsm_fwd<T>(cudaStream_t, const DenseFactor<T>&, T*, long long, int);  \
-  template void dense_trsm_bwd<T>(cudaStream_t, const DenseFactor<T>&, T*, long long, int);
+  template void dense_trsm_bwd<T>(cudaStream_t, const DenseFactor<T>&, T*, long long, int);  \
+  template size_t dense_lookahead_elems<T>(int);                                             \
+  template void dense_sweep_lookahead<T>(cudaStream_t, DenseFactor<T>&, T*);
 MPL_INST_CHOL(float)
 MPL_INST_CHOL(double)
 MPL_INST_CHOL(zf)

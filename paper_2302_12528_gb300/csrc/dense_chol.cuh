@@ -16,6 +16,8 @@ struct DenseFactor {
   long long ldl = 0;
   T* Dinv = nullptr;
   int n = 0, nb = 0, nblk = 0;
+  T* Mf = nullptr;  // look-ahead products of the forward / backward sweeps
+  T* Mb = nullptr;  // (dense_sweep_lookahead), or none
 };
 
 // In-place blocked Cholesky of the lower triangle of F.L.  Only the first
@@ -62,6 +64,15 @@ void scale_rows(cudaStream_t st, int n, int m, T* B, long long ldb, const float*
 // B <- L^-* L^-1 B for B n x m (ld ldb), in place, two blocked sweeps.
 template <typename T>
 void dense_precond(cudaStream_t st, const DenseFactor<T>& F, T* B, long long ldb, int m);
+// The sweeps' look-ahead products of a finished factor (FP32 types; a no-op
+// returning 0 elements otherwise): ws holds dense_lookahead_elems<T>(n)
+// elements and must live as long as F is used; sets F.Mf, F.Mb.  Without
+// them the sweeps compute the same solves with both products of a block row
+// after the wait for its predecessor.
+template <typename T>
+size_t dense_lookahead_elems(int n);
+template <typename T>
+void dense_sweep_lookahead(cudaStream_t st, DenseFactor<T>& F, T* ws);
 
 // Returns 1 (and clears it) if a dependency wait of a triangular sweep gave
 // up since the last call, on any stream; synchronises with st first.

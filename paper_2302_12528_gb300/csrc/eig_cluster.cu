@@ -69,34 +69,36 @@ tridiag_cluster_kernel(int N, const T* __restrict__ Ag, T* __restrict__ U, T* __
   }
   __syncthreads();
 
-  // Reflector of step j from the owner's column j (rows j+1..N-1): warp 0
-  // forms the scalars, then the whole CTA stores it for the
-  // back-transformation and pushes it into every rank's buffer (j & 1).
-  auto reflect = [&](int j) {
+  // Reflector of step j from the owner's column j (rows j+1..N-1).
+  // reflect_scalars: warp 0 alone; reflect_push: the whole CTA (after a
+  // barrier) stores the reflector for the back-transformation and pushes it
+  // into every rank's buffer (j & 1).
+  auto reflect_scalars = [&](int j) {  // called by warp 0
     const int r0 = j + 1;
     const T* col = Aloc + (size_t)(j / CL) * N;
-    if (wid == 0) {
-      R s2 = R(0);
-      for (int i = r0 + 1 + lane; i < N; i += 32) s2 += abs2_(col[i]);
-      s2 = warp_sum(s2);
-      if (lane == 0) {
-        const T x0 = col[r0];
-        R t = R(0);
-        T u0 = zero_<T>(), beta = x0;
-        if (s2 != R(0)) {
-          const R ax0 = sqrt_(abs2_(x0));
-          const R alpha = sqrt_(s2 + ax0 * ax0);
-          const T ph = ax0 > R(0) ? x0 * (R(1) / ax0) : from_real<T>(R(1));
-          beta = ph * (-alpha);
-          u0 = x0 - beta;
-          t = R(1) / (alpha * (alpha + ax0));
-        }
-        sh_t = t;
-        sh_u0 = u0;
-        sh_beta = beta;
+    R s2 = R(0);
+    for (int i = r0 + 1 + lane; i < N; i += 32) s2 += abs2_(col[i]);
+    s2 = warp_sum(s2);
+    if (lane == 0) {
+      const T x0 = col[r0];
+      R t = R(0);
+      T u0 = zero_<T>(), beta = x0;
+      if (s2 != R(0)) {
+        const R ax0 = sqrt_(abs2_(x0));
+        const R alpha = sqrt_(s2 + ax0 * ax0);
+        const T ph = ax0 > R(0) ? x0 * (R(1) / ax0) : from_real<T>(R(1));
+        beta = ph * (-alpha);
+        u0 = x0 - beta;
+        t = R(1) / (alpha * (alpha + ax0));
       }
+      sh_t = t;
+      sh_u0 = u0;
+      sh_beta = beta;
     }
-    __syncthreads();
+  };
+  auto reflect_push = [&](int j) {  // all threads, after a barrier
+    const int r0 = j + 1;
+    const T* col = Aloc + (size_t)(j / CL) * N;
     const R t = sh_t;
     const T u0 = sh_u0;
     if (tid == 0) { tau[j] = t; uhead[j] = u0; eout[j] = sh_beta; }
@@ -111,7 +113,11 @@ tridiag_cluster_kernel(int N, const T* __restrict__ Ag, T* __restrict__ U, T* __
     if (tid < CL) cluster.map_shared_rank(tb, tid)[b] = t;
   };
 
-  if (N > 2 && rank == 0) reflect(0);
+  if (N > 2 && rank == 0) {
+    if (wid == 0) reflect_scalars(0);
+    __syncthreads();
+    reflect_push(0);
+  }
   __syncthreads();
   cluster.sync();  // reflector 0 is in every rank's buffer
   for (int j = 0; j + 2 < N; ++j) {
@@ -189,24 +195,26 @@ tridiag_cluster_kernel(int N, const T* __restrict__ Ag, T* __restrict__ U, T* __
       for (int i = r0 + tid; i < N; i += nt) pv[i] = pv[i] - K * u[i];
       __syncthreads();
       // rank-2 update B -= u w^* + w u^* of the owned columns, element-wise
-      // over the CTA; the owner of the next pivot column updates that column
-      // first and reflects it
+      // over the CTA; on the owner of the next pivot column, warp 0 updates
+      // that column and forms its reflector while the other warps update
+      // the rest
       const int qn = (next && rank == nowner) ? nj / CL : -1;
-      if (qn >= 0) {
+      if (qn >= 0 && wid == 0) {
         T* col = Aloc + (size_t)qn * N;
         const T wc = conj_(pv[nj]), uc = conj_(u[nj]);
-        for (int i = r0 + tid; i < N; i += nt) {
+        for (int i = r0 + lane; i < N; i += 32) {
           T v = col[i];
           fms_(v, u[i], wc);
           fms_(v, pv[i], uc);
           col[i] = v;
         }
-        __syncthreads();
-        reflect(nj);
+        __syncwarp();
+        reflect_scalars(nj);
       }
-      const int skip = (qn >= 0) ? qn - q0 : -1;  // that column is done
+      const int skip = (qn >= 0) ? qn - q0 : -1;  // that column is warp 0's
       const int nupd = ncols - (skip >= 0 ? 1 : 0);
-      for (int e = tid; e < nupd * len; e += nt) {
+      const int t0 = (qn >= 0) ? 32 : 0;           // the threads of the rest
+      for (int e = tid - t0; e >= 0 && e < nupd * len; e += nt - t0) {
         int k = e / len;
         if (skip >= 0 && k >= skip) ++k;
         const int q = q0 + k, i = r0 + e % len;
@@ -217,8 +225,14 @@ tridiag_cluster_kernel(int N, const T* __restrict__ Ag, T* __restrict__ U, T* __
         fms_(v, pv[i], conj_(u[c]));
         col[i] = v;
       }
+      if (qn >= 0) {
+        __syncthreads();
+        reflect_push(nj);
+      }
     } else if (next && rank == nowner) {
-      reflect(nj);
+      if (wid == 0) reflect_scalars(nj);
+      __syncthreads();
+      reflect_push(nj);
     }
     __syncthreads();
     cluster.sync();  // the updates are done and the next reflector is pushed
@@ -275,68 +289,94 @@ __global__ void __launch_bounds__(32, 1) tri_real_kernel(int N, const T* __restr
   }
 }
 
-// One warp per wanted eigenvalue: multisection (the 32 lanes evaluate the
-// Sturm count at 32 interior points, shrinking the bracket 33-fold per round)
-// followed by inverse iteration on lane 0.
+// One block of MS_PTS threads per wanted eigenvalue (each on its own SM):
+// multisection -- the threads evaluate the Sturm count at MS_PTS interior
+// points, shrinking the bracket (MS_PTS + 1)-fold per round; a dependent FP64
+// division costs about ten fused multiply-adds here, so the Sturm recurrence
+// is latency-bound and four warps share an SM's FP64 pipe at no cost --
+// followed by inverse iteration (warp 0).
+constexpr int MS_PTS = 128;
 template <typename R>
-__global__ void __launch_bounds__(32, 1)
+__global__ void __launch_bounds__(MS_PTS, 1)
 tri_multisect_kernel(int N, int m, const R* __restrict__ d, const R* __restrict__ f, R* lamv, R* z, R* lu,
                      int* piv, int* bad) {
   extern __shared__ __align__(16) unsigned char smem[];
   R* sd = reinterpret_cast<R*>(smem);  // d, then f_i^2 (the Sturm recurrence's only use of f)
   R* sf2 = sd + N;
-  const int lane = threadIdx.x & 31;
-  const int k = blockIdx.x;  // one warp (block) per wanted eigenvalue: each on its own SM's FP64 pipe
-  if (k == 0 && lane == 0) *bad = 0;  // the Cholesky-QR passes that follow report breakdown here
-  for (int i = lane; i < N; i += 32) {
+  __shared__ unsigned masks[MS_PTS / 32];
+  __shared__ R rlo[MS_PTS / 32], rhi[MS_PTS / 32], rnorm[MS_PTS / 32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int k = blockIdx.x;
+  if (k == 0 && tid == 0) *bad = 0;  // the Cholesky-QR passes that follow report breakdown here
+  // Gershgorin bounds and ||T||, reduced over the block
+  R glo = d[0], ghi = d[0], tnorm = R(0);
+  for (int i = tid; i < N; i += MS_PTS) {
     sd[i] = d[i];
     sf2[i] = f[i] * f[i];
-  }
-  __syncwarp();
-  if (k >= m) return;
-  R glo = d[0], ghi = d[0], tnorm = R(0);
-  for (int i = 0; i < N; ++i) {
     const R r = (i > 0 ? f[i - 1] : R(0)) + f[i];
     glo = fmin(glo, d[i] - r);
     ghi = fmax(ghi, d[i] + r);
     tnorm = fmax(tnorm, (R)fabs((double)d[i]) + r);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    glo = fmin(glo, __shfl_xor_sync(0xffffffffu, glo, o));
+    ghi = fmax(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
+    tnorm = fmax(tnorm, __shfl_xor_sync(0xffffffffu, tnorm, o));
+  }
+  if (lane == 0) { rlo[wid] = glo; rhi[wid] = ghi; rnorm[wid] = tnorm; }
+  __syncthreads();
+  for (int w = 0; w < MS_PTS / 32; ++w) {
+    glo = fmin(glo, rlo[w]);
+    ghi = fmax(ghi, rhi[w]);
+    tnorm = fmax(tnorm, rnorm[w]);
+  }
+  if (k >= m) return;  // block-uniform
   const R eps = (sizeof(R) == 8) ? R(1.1102230246251565e-16) : R(5.9604645e-08);
   const R pivmin = (sizeof(R) == 8 ? R(1e-290) : R(1e-35)) + tnorm * eps * eps;
   const R spread = fmax(ghi - glo, tnorm * eps);
   R lo = glo - (spread * eps * R(4) + pivmin);
   R hi = ghi + (spread * eps * R(4) + pivmin);
+  const R NP1 = R(MS_PTS + 1);
   for (int round = 0; round < 64; ++round) {
     if (hi - lo <= R(2) * eps * fmax((R)fabs((double)lo), (R)fabs((double)hi)) + pivmin) break;
-    const R x = lo + (hi - lo) * (R)(lane + 1) / R(33);
+    const R x = lo + (hi - lo) * (R)(tid + 1) / NP1;
     const bool above = (x > lo && x < hi) && sturm_count_f2(N, sd, sf2, x, pivmin) > k;
-    const unsigned mask = __ballot_sync(0xffffffffu, above);
-    // counts are monotone in x: the first lane with count > k bounds from above
+    const unsigned mk = __ballot_sync(0xffffffffu, above);
+    if (lane == 0) masks[wid] = mk;
+    __syncthreads();
+    // counts are monotone in x: the first point with count > k bounds from above
+    int l = -1;
+    for (int w = 0; w < MS_PTS / 32 && l < 0; ++w)
+      if (masks[w]) l = 32 * w + __ffs(masks[w]) - 1;
+    __syncthreads();  // masks are rewritten next round
     R nlo = lo, nhi = hi;
-    if (mask) {
-      const int l = __ffs(mask) - 1;
-      nhi = lo + (hi - lo) * (R)(l + 1) / R(33);
-      if (l > 0) nlo = lo + (hi - lo) * (R)l / R(33);
+    if (l >= 0) {
+      nhi = lo + (hi - lo) * (R)(l + 1) / NP1;
+      if (l > 0) nlo = lo + (hi - lo) * (R)l / NP1;
     } else {
-      nlo = lo + (hi - lo) * R(32) / R(33);
+      nlo = lo + (hi - lo) * R(MS_PTS) / NP1;
     }
     if (!(nhi < hi || nlo > lo)) break;  // no progress (rounding): converged
     lo = nlo;
     hi = nhi;
   }
+  if (wid != 0) return;
   const R lam = R(0.5) * (lo + hi);
+  const R tiny = eps * tnorm + pivmin;
+  R* zk = z + (size_t)k * N;
+  R* dl = lu + (size_t)k * 4 * N;
+  int* pv = piv + (size_t)k * N;
+  for (int i = lane; i < N; i += 32) zk[i] = R(1) + R(0.25) * (R)(((i + 1) * 7919 + (k + 1) * 104729) % 101) / R(101);
   if (lane == 0) {
     lamv[k] = lam;
-    const R tiny = eps * tnorm + pivmin;
-    R* zk = z + (size_t)k * N;
-    R* dl = lu + (size_t)k * 4 * N;
-    int* pv = piv + (size_t)k * N;
     tri_lu(N, d, f, lam, tiny, dl, dl + N, dl + 2 * N, dl + 3 * N, pv);
-    for (int i = 0; i < N; ++i) zk[i] = R(1) + R(0.25) * (R)(((i + 1) * 7919 + (k + 1) * 104729) % 101) / R(101);
-    for (int it = 0; it < 3; ++it) {
-      tri_solve(N, dl, dl + N, dl + 2 * N, dl + 3 * N, pv, zk);
-      scale_unit(N, zk);
-    }
+  }
+  __syncwarp();
+  for (int it = 0; it < 3; ++it) {
+    if (lane == 0) tri_solve(N, dl, dl + N, dl + 2 * N, dl + 3 * N, pv, zk);
+    __syncwarp();
+    scale_unit_warp(N, zk);
   }
 }
 
@@ -526,42 +566,59 @@ qr_cluster_kernel(int N, int q, T* Y, T* uhead, real_t<T>* tau) {
   T* Aloc = reinterpret_cast<T*>(smem);  // owned columns c = rank + CL qq
   T* ub = Aloc + (size_t)nloc * N;       // two reflector buffers (step j uses ub + (j & 1) N)
   R* tb = reinterpret_cast<R*>(ub + 2 * (size_t)N);
-  __shared__ R red[32];
-  __shared__ T redc[32];
+  __shared__ T sh_u0;
+  __shared__ R sh_t;
   for (int qq = 0; qq < nloc; ++qq) {
     const int c = rank + CL * qq;
     if (c >= q) break;
     for (int i = tid; i < N; i += nt) Aloc[(size_t)qq * N + i] = Y[i + (size_t)c * N];
   }
   __syncthreads();
-  // reflector j from the owner's column j (rows j..N-1), pushed into every
-  // rank's buffer (j & 1); R_jj = beta replaces the column's head
-  auto reflect = [&](int j) {
+  // Reflector j from the owner's column j (rows j..N-1).  Scalars by warp 0
+  // (R_jj = beta replaces the column's head); the push into every rank's
+  // buffer (j & 1) by the whole CTA after a barrier.
+  auto reflect_scalars = [&](int j) {  // warp 0
     T* col = Aloc + (size_t)(j / CL) * N;
-    const T x0 = col[j];
     R s2 = R(0);
-    for (int i = j + 1 + tid; i < N; i += nt) s2 += abs2_(col[i]);
-    s2 = block_sum(s2, red);  // (its barriers also order every read of x0 before the write below)
-    R t = R(0);
-    T u0 = zero_<T>(), beta = x0;
-    if (s2 != R(0)) {
-      const R ax0 = sqrt_(abs2_(x0));
-      const R alpha = sqrt_(s2 + ax0 * ax0);
-      const T ph = ax0 > R(0) ? x0 * (R(1) / ax0) : from_real<T>(R(1));
-      beta = ph * (-alpha);
-      u0 = x0 - beta;
-      t = R(1) / (alpha * (alpha + ax0));
-      const int len = N - j, b = j & 1;
+    for (int i = j + 1 + lane; i < N; i += 32) s2 += abs2_(col[i]);
+    s2 = warp_sum(s2);
+    if (lane == 0) {
+      const T x0 = col[j];
+      R t = R(0);
+      T u0 = zero_<T>(), beta = x0;
+      if (s2 != R(0)) {
+        const R ax0 = sqrt_(abs2_(x0));
+        const R alpha = sqrt_(s2 + ax0 * ax0);
+        const T ph = ax0 > R(0) ? x0 * (R(1) / ax0) : from_real<T>(R(1));
+        beta = ph * (-alpha);
+        u0 = x0 - beta;
+        t = R(1) / (alpha * (alpha + ax0));
+      }
+      sh_t = t;
+      sh_u0 = u0;
+      tau[j] = t;
+      uhead[j] = u0;
+      col[j] = beta;  // read as x0 above by this lane only
+    }
+  };
+  auto reflect_push = [&](int j) {  // all threads, after a barrier
+    const T* col = Aloc + (size_t)(j / CL) * N;
+    const R t = sh_t;
+    const T u0 = sh_u0;
+    const int len = N - j, b = j & 1;
+    if (t != R(0))
       for (int e = tid; e < len * CL; e += nt) {
         const int rr = e / len, i = j + e % len;
         cluster.map_shared_rank(ub, rr)[(size_t)b * N + i] = (i == j) ? u0 : col[i];
       }
-    }
-    if (tid < CL) cluster.map_shared_rank(tb, tid)[j & 1] = t;
-    if (tid == 0) { tau[j] = t; uhead[j] = u0; col[j] = beta; }
+    if (tid < CL) cluster.map_shared_rank(tb, tid)[b] = t;
   };
   const int jmax = q < N ? q : N;
-  if (jmax > 0 && rank == 0) reflect(0);
+  if (jmax > 0 && rank == 0) {
+    if (wid == 0) reflect_scalars(0);
+    __syncthreads();
+    reflect_push(0);
+  }
   __syncthreads();
   cluster.sync();  // reflector 0 is in every rank's buffer
   for (int j = 0; j < jmax; ++j) {
@@ -572,17 +629,20 @@ qr_cluster_kernel(int N, int q, T* Y, T* uhead, real_t<T>* tau) {
     const int qn = (next && rank == nj % CL) ? nj / CL : -1;
     const int q0 = (j + 1 > rank) ? (j + 1 - rank + CL - 1) / CL : 0;  // first owned column > j
     if (t != R(0)) {
-      if (qn >= 0) {  // the next pivot column first, then its reflector
+      // warp 0 of the next pivot column's owner: that column first, then its
+      // reflector; the other warps take the other owned columns meanwhile
+      if (qn >= 0 && wid == 0) {
         T* col = Aloc + (size_t)qn * N;
         T dsum = zero_<T>();
-        for (int i = j + tid; i < N; i += nt) fmac_(dsum, u[i], col[i]);
-        dsum = block_sum(dsum, redc);
+        for (int i = j + lane; i < N; i += 32) fmac_(dsum, u[i], col[i]);
+        dsum = warp_sum(dsum);
         const T g = dsum * t;
-        for (int i = j + tid; i < N; i += nt) col[i] = col[i] - g * u[i];
-        __syncthreads();
-        reflect(nj);
+        for (int i = j + lane; i < N; i += 32) fms_(col[i], g, u[i]);
+        __syncwarp();
+        reflect_scalars(nj);
       }
-      for (int qq = q0 + wid; qq < nloc; qq += nw) {
+      const int w0 = (qn >= 0) ? 1 : 0;
+      for (int qq = q0 + wid - w0; wid >= w0 && qq < nloc; qq += nw - w0) {
         if (qq == qn) continue;
         const int c = rank + CL * qq;
         if (c >= q) break;
@@ -591,10 +651,16 @@ qr_cluster_kernel(int N, int q, T* Y, T* uhead, real_t<T>* tau) {
         for (int i = j + lane; i < N; i += 32) fmac_(dsum, u[i], col[i]);
         dsum = warp_sum(dsum);
         const T g = dsum * t;
-        for (int i = j + lane; i < N; i += 32) col[i] = col[i] - g * u[i];
+        for (int i = j + lane; i < N; i += 32) fms_(col[i], g, u[i]);
+      }
+      if (qn >= 0) {
+        __syncthreads();
+        reflect_push(nj);
       }
     } else if (qn >= 0) {
-      reflect(nj);
+      if (wid == 0) reflect_scalars(nj);
+      __syncthreads();
+      reflect_push(nj);
     }
     __syncthreads();
     cluster.sync();  // the updates are done and the next reflector is pushed
@@ -799,7 +865,7 @@ bool eig_small_fast(cudaStream_t st, int N, int m, T* Ap, double* lam, T* C1, vo
   int* bad = piv + (size_t)N * m;
   R* rdiag = reinterpret_cast<R*>(piv + (((size_t)N * m + 2) & ~(size_t)1));  // past bad, 8-byte aligned
   count_launch();
-  tri_multisect_kernel<R><<<m, 32, 2 * (size_t)N * sizeof(R), st>>>(N, m, d, f, lamv, z, lu, piv, bad);
+  tri_multisect_kernel<R><<<m, MS_PTS, 2 * (size_t)N * sizeof(R), st>>>(N, m, d, f, lamv, z, lu, piv, bad);
   for (int pass = 0; pass < 2 && m > 1; ++pass) {
     count_launch(3);
     gram_lower_kernel<R><<<m, 256, 0, st>>>(N, m, z, G, bad);

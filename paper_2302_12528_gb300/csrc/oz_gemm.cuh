@@ -49,7 +49,7 @@ void oz_combine_3m(cudaStream_t st, int n, int m, const long long* T, const int*
 // conjugate transpose when ta / tb) through the split product, with a
 // per-stream workspace; false when the shape or beta is not supported (the
 // caller computes it otherwise).  The FP64 GEMM takes this route for products
-// of >= 2^28 multiply-adds unless MPL_GEMM_SPLIT=0: oz_gemm_mode() is 0 (off),
+// of >= 2^25 multiply-adds unless MPL_GEMM_SPLIT=0: oz_gemm_mode() is 0 (off),
 // 1 (MPL_GEMM_SPLIT=1: on, and the dense A X split at every order) or 2 (the
 // default: on).  oz_take_error() returns and clears the stream's
 // completion-wait error flag (synchronising).

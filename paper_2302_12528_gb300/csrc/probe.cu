@@ -1,7 +1,7 @@
 // Peak rate of the CUDA-core fused multiply-add pipes (FP64 and FP32), the
 // denominators of the FP64 and FP32 kernels' rooflines (the FP64 block
 // product below the split product's threshold, the FP32 factor and sweeps).
-// Every thread runs CH independent chains acc = acc * a_c + b_c, so the pipe,
+// Every thread runs CH independent chains acc = acc * a + b, so the pipe,
 // not the dependency latency, is the limit; the grid covers every SM several
 // times over.  Rate = 2 x (threads x CH x iterations) / the second launch's
 // CUDA-event time (the first launch warms up).
@@ -19,16 +19,12 @@ constexpr int CH = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(256) fma_rate_kernel(long long iters, T a, T b, T* out) {
-  T acc[CH], ma[CH], mb[CH];  // every chain with its own operand registers
+  T acc[CH];
 #pragma unroll
-  for (int c = 0; c < CH; ++c) {
-    acc[c] = (T)(threadIdx.x + c);
-    ma[c] = a - (T)c * (T)1e-9;
-    mb[c] = b + (T)c * (T)1e-9;
-  }
+  for (int c = 0; c < CH; ++c) acc[c] = (T)(threadIdx.x + c);
   for (long long it = 0; it < iters; ++it) {
 #pragma unroll
-    for (int c = 0; c < CH; ++c) acc[c] = fma(acc[c], ma[c], mb[c]);
+    for (int c = 0; c < CH; ++c) acc[c] = fma(acc[c], a, b);
   }
   T s = 0;
 #pragma unroll

@@ -53,8 +53,10 @@ __device__ int sturm_count_f2(int N, const R* d, const R* f2, R x, R pivmin) {
 }
 
 // LU with partial pivoting of the tridiagonal (T - lam I): on return dl holds
-// the multipliers, dd/du/du2 the three diagonals of U, piv[i] = 1 if rows i
-// and i+1 were interchanged.  Zero pivots are replaced by ``tiny``.
+// the multipliers, dd the reciprocals of U's diagonal, du/du2 U's two upper
+// diagonals, piv[i] = 1 if rows i and i+1 were interchanged.  Zero pivots are
+// replaced by ``tiny``.  One division per row (the pivot's reciprocal serves
+// the multiplier and the later solves).
 template <typename R>
 __device__ void tri_lu(int N, const R* d, const R* f, R lam, R tiny, R* dl, R* dd, R* du, R* du2,
                        int* piv) {
@@ -64,17 +66,20 @@ __device__ void tri_lu(int N, const R* d, const R* f, R lam, R tiny, R* dl, R* d
     if (fabs((double)dd[i]) >= fabs((double)dl[i])) {
       piv[i] = 0;
       if (dd[i] == R(0)) dd[i] = tiny;
-      const R fac = dl[i] / dd[i];
+      const R r = R(1) / dd[i];
+      const R fac = dl[i] * r;
       dl[i] = fac;
       dd[i + 1] -= fac * du[i];
+      dd[i] = r;
     } else {
       piv[i] = 1;
-      const R fac = dd[i] / dl[i];
-      dd[i] = dl[i];
+      const R r = R(1) / dl[i];
+      const R fac = dd[i] * r;
       dl[i] = fac;
       const R tmp = du[i];
       du[i] = dd[i + 1];
       dd[i + 1] = tmp - fac * dd[i + 1];
+      dd[i] = r;
       if (i + 2 < N) {
         du2[i] = du[i + 1];
         du[i + 1] = -fac * du[i + 1];
@@ -82,9 +87,11 @@ __device__ void tri_lu(int N, const R* d, const R* f, R lam, R tiny, R* dl, R* d
     }
   }
   if (dd[N - 1] == R(0)) dd[N - 1] = tiny;
+  dd[N - 1] = R(1) / dd[N - 1];
 }
 
-// Solve (T - lam I) x = b with the factors of tri_lu, in place in b.
+// Solve (T - lam I) x = b with the factors of tri_lu (dd: reciprocal pivots),
+// in place in b.
 template <typename R>
 __device__ void tri_solve(int N, const R* dl, const R* dd, const R* du, const R* du2,
                           const int* piv, R* b) {
@@ -97,9 +104,35 @@ __device__ void tri_solve(int N, const R* dl, const R* dd, const R* du, const R*
       b[i + 1] = t - dl[i] * b[i];
     }
   }
-  b[N - 1] /= dd[N - 1];
-  if (N > 1) b[N - 2] = (b[N - 2] - du[N - 2] * b[N - 1]) / dd[N - 2];
-  for (int i = N - 3; i >= 0; --i) b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) / dd[i];
+  b[N - 1] *= dd[N - 1];
+  if (N > 1) b[N - 2] = (b[N - 2] - du[N - 2] * b[N - 1]) * dd[N - 2];
+  for (int i = N - 3; i >= 0; --i) b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) * dd[i];
+}
+
+// z / ||z|| by one warp (after a prescaling by max |z_i| against overflow);
+// a zero or non-finite z becomes the normalised vector of ones.
+template <typename R>
+__device__ void scale_unit_warp(int N, R* z) {
+  const int lane = threadIdx.x & 31;
+  R mx = R(0);
+  for (int i = lane; i < N; i += 32) mx = fmax(mx, (R)fabs((double)z[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (!(mx > R(0)) || !isfinite((double)mx)) {
+    for (int i = lane; i < N; i += 32) z[i] = R(1);
+    mx = R(1);
+  }
+  const R rm = R(1) / mx;
+  R sq = R(0);
+  for (int i = lane; i < N; i += 32) {
+    const R v = z[i] * rm;
+    z[i] = v;
+    sq += v * v;
+  }
+  sq = warp_sum(sq);
+  const R sc = R(1) / sqrt_(sq);
+  for (int i = lane; i < N; i += 32) z[i] *= sc;
+  __syncwarp();
 }
 
 template <typename R>
@@ -110,8 +143,9 @@ __device__ void scale_unit(int N, R* z) {
     for (int i = 0; i < N; ++i) z[i] = R(1);
     mx = R(1);
   }
+  const R rm = R(1) / mx;
   R s = R(0);
-  for (int i = 0; i < N; ++i) { z[i] /= mx; s += z[i] * z[i]; }
+  for (int i = 0; i < N; ++i) { z[i] *= rm; s += z[i] * z[i]; }
   s = R(1) / sqrt_(s);
   for (int i = 0; i < N; ++i) z[i] *= s;
 }
