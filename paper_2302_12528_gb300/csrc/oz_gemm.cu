@@ -33,8 +33,12 @@
 // 32-deep chunk in the canonical no-swizzle K-major core-matrix layout, the
 // eight slices of a chunk contiguous, so one bulk copy brings a chunk of A
 // (64 KB) and one a chunk of B.  Warp roles: warp 0 copies (two stages in
-// flight), warp 1 issues the 36 x 2 tcgen05.mma of a stage and commits
-// their completion, warps 2-17 fold the accumulators after each window.
+// flight), warp 1 issues the 36 x 2 tcgen05.mma of a stage (ordered by A
+// slice, so that each block of A is read from shared memory once and kept
+// in the tensor core's collector buffer for its 8 - i products) and commits
+// their completion, warps 2-17 fold the accumulators after each window
+// (one lane polls the accumulator barrier, the other warps sleep on a
+// hardware barrier).
 // Every wait has an iteration limit; a role that gives up records an error
 // and raises the CTA's abort flag, the others leave their waits, and the CTA
 // waits (bounded) for the copies and MMAs it issued before it frees its
@@ -299,7 +303,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // T (hi at T, lo at T + tlo; column-major, ld ldt) += the exact fixed-point
 // product of row tile blockIdx.x / ncb with column block blockIdx.x % ncb
 // over the chunks of split blockIdx.y.
-template <int NPAD>
+template <int NPAD, bool COLLECT>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 oz_mma_kernel(int ncb, int nchunk, int chunks_per_split, const uint16_t* __restrict__ QA,
               const uint16_t* __restrict__ PB, long long* __restrict__ T, long long ldt, long long tlo, int* err,
@@ -314,6 +318,7 @@ oz_mma_kernel(int ncb, int nchunk, int chunks_per_split, const uint16_t* __restr
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   __shared__ int issued, committed;                      // stages copied / whose MMAs were committed
+  __shared__ volatile int fold_go[2];                     // the accumulator poll's answer, by window parity
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
   const int tile = blockIdx.x / ncb, cb = blockIdx.x % ncb;
   const int c0 = blockIdx.y * chunks_per_split, c1 = min(nchunk, c0 + chunks_per_split);
@@ -384,23 +389,57 @@ oz_mma_kernel(int ncb, int nchunk, int chunks_per_split, const uint16_t* __restr
         // descriptors of slice 0 / depth step 0; the others differ only in the
         // start address field (bytes >> 4), so constant offsets are added
         const uint64_t da0 = smem_desc(sa, LBO, SBO), db0 = smem_desc(sb, LBO, SBO);
+        // A slice i at depth step kk feeds the groups g = i..7 with B slices
+        // g - i: with COLLECT the consecutive MMAs of one (i, kk) keep A in
+        // the tensor core's collector buffer (filled by the first, released
+        // by the last), so each 128 x 16 block of A is read from shared
+        // memory once per stage instead of 8 - i times (the operand reads of
+        // small-N MMAs otherwise saturate shared memory before the tensor
+        // pipe).  The first MMA into every accumulator is still
+        // (i = 0, kk = 0).
 #pragma unroll
-        for (int g = 0; g < OZ_S; ++g) {
-          const uint32_t d_tmem = tmem + (uint32_t)(g * NPAD);
+        for (int i = 0; i < OZ_S; ++i) {
 #pragma unroll
-          for (int i = 0; i <= g; ++i) {
+          for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+            const uint64_t da = da0 + (uint64_t)((i * (OZ_TILE_A * 2) + kk * 256) >> 4);
 #pragma unroll
-            for (int kk = 0; kk < OZ_BK / 16; ++kk) {
-              const uint64_t da = da0 + (uint64_t)((i * (OZ_TILE_A * 2) + kk * 256) >> 4);
+            for (int g = i; g < OZ_S; ++g) {
+              const uint32_t d_tmem = tmem + (uint32_t)(g * NPAD);
               const uint64_t db = db0 + (uint64_t)(((g - i) * (NPAD * OZ_BK * 2) + kk * 256) >> 4);
               const uint32_t accum = (i == 0 && kk == 0) ? acc0 : 1u;
-              asm volatile(
-                  "{\n\t.reg .pred p;\n\t"
-                  "setp.ne.b32 p, %4, 0;\n\t"
-                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t"
-                  "}" ::"r"(d_tmem),
-                  "l"(da), "l"(db), "r"(idesc), "r"(accum)
-                  : "memory");
+              if (!COLLECT || i == OZ_S - 1) {
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "setp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t"
+                    "}" ::"r"(d_tmem),
+                    "l"(da), "l"(db), "r"(idesc), "r"(accum)
+                    : "memory");
+              } else if (g == i) {
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "setp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n\t"
+                    "}" ::"r"(d_tmem),
+                    "l"(da), "l"(db), "r"(idesc), "r"(accum)
+                    : "memory");
+              } else if (g == OZ_S - 1) {
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "setp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n\t"
+                    "}" ::"r"(d_tmem),
+                    "l"(da), "l"(db), "r"(idesc), "r"(accum)
+                    : "memory");
+              } else {
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "setp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n\t"
+                    "}" ::"r"(d_tmem),
+                    "l"(da), "l"(db), "r"(idesc), "r"(accum)
+                    : "memory");
+              }
             }
           }
         }
@@ -422,10 +461,15 @@ oz_mma_kernel(int ncb, int nchunk, int chunks_per_split, const uint16_t* __restr
     for (int q = 0; q < QC; ++q) hi[q] = lo[q] = 0;
     bool ok = true;
     for (int w = 0; w < nwin && ok; ++w) {
-      // one lane polls (the others would compete with the MMAs' shared-memory reads)
-      int got = 1;
-      if (lane == 0) got = mbar_wait(smem_u32(&bar_accf), w & 1, &abort_flag) ? 1 : 0;
-      ok = __shfl_sync(0xffffffffu, got, 0) != 0;
+      // one lane of one fold warp polls the accumulator barrier (every poll
+      // is a shared-memory access that competes with the MMAs' operand
+      // reads); the other fold warps sleep on hardware barrier 1 until it
+      // has the answer.  The answer is double-buffered by window so that a
+      // late reader of window w never sees window w + 1's: the poller
+      // cannot pass the next barrier before every fold warp has.
+      if (wid == 2 && lane == 0) fold_go[w & 1] = mbar_wait(smem_u32(&bar_accf), w & 1, &abort_flag) ? 1 : 0;
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * OZ_FOLD_WARPS) : "memory");
+      ok = fold_go[w & 1] != 0;
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
@@ -596,14 +640,28 @@ void oz_split_b(cudaStream_t st, int mode, int k, int m, const double* B, long l
   split_cols_kernel<false><<<grid_for(tot), 256, 0, st>>>(k, m, B, ldb, mode, f, nchunk, npad, ncb, P);
 }
 
-// Depth splits of whole windows: about 8 waves of one CTA per SM per launch.
+// Depth splits of whole windows.  One CTA fits an SM (tensor memory and
+// shared memory), so a launch of C CTAs of w windows each takes about
+// ceil(C / NUM_SMS) rounds of w windows plus a fixed start (first copies,
+// tensor-memory allocation; about half a window): the split count with the
+// fewest half-window units wins, ties to fewer splits (fewer atomics).
 static void oz_plan(int n, int k, int m, int* nsp, int* cps) {
   const int ntile = (n + OZ_BM - 1) / OZ_BM, nchunk = (k + OZ_BK - 1) / OZ_BK;
-  const int tiles = ntile * oz_ncb(m);
-  const int want = std::max(1, (8 * NUM_SMS + tiles - 1) / tiles);
+  const long long tiles = (long long)ntile * oz_ncb(m);
   const int nwin = (nchunk + OZ_STAGES_PER_WIN - 1) / OZ_STAGES_PER_WIN;
-  const int nsplit = std::min(want, nwin);
-  *cps = ((nwin + nsplit - 1) / nsplit) * OZ_STAGES_PER_WIN;
+  const int maxsp = (int)std::min<long long>(nwin, std::max<long long>(1, (32LL * NUM_SMS + tiles - 1) / tiles));
+  int best_cw = nwin;
+  long long best = LLONG_MAX;
+  for (int s = 1; s <= maxsp; ++s) {
+    const int cw = (nwin + s - 1) / s;                 // windows per split
+    const long long ctas = tiles * ((nwin + cw - 1) / cw);
+    const long long cost = ((ctas + NUM_SMS - 1) / NUM_SMS) * (2LL * cw + 1);
+    if (cost < best) {
+      best = cost;
+      best_cw = cw;
+    }
+  }
+  *cps = best_cw * OZ_STAGES_PER_WIN;
   *nsp = (nchunk + *cps - 1) / *cps;
 }
 
@@ -613,18 +671,35 @@ bool oz_mma_accumulates(int n, int k, int m) {
   return nsp > 1;
 }
 
-template <int NPAD>
-static void launch_mma(cudaStream_t st, int ntile, int ncb, int nchunk, int nsplit, int cps, const uint16_t* Q,
-                       const uint16_t* P, long long* T, long long ldt, long long tlo, int* err) {
+// MPL_OZ_COLLECTOR=0 issues every MMA with its A operand read from shared
+// memory (no collector-buffer reuse); same products, for comparison.
+static bool oz_collector() {
+  static const bool on = [] {
+    const char* v = std::getenv("MPL_OZ_COLLECTOR");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
+template <int NPAD, bool COLLECT>
+static void launch_mma_as(cudaStream_t st, int ntile, int ncb, int nchunk, int nsplit, int cps, const uint16_t* Q,
+                          const uint16_t* P, long long* T, long long ldt, long long tlo, int* err) {
   const size_t sm = (size_t)2 * (OZ_S * OZ_TILE_A * 2 + OZ_S * NPAD * OZ_BK * 2);
   // one attribute call per instantiation (thread-safe static initialisation)
   static const bool opened =
-      cudaFuncSetAttribute(oz_mma_kernel<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) ==
+      cudaFuncSetAttribute(oz_mma_kernel<NPAD, COLLECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) ==
       cudaSuccess;
   (void)opened;
   count_launch();
-  oz_mma_kernel<NPAD><<<dim3(ntile * ncb, nsplit), OZ_THREADS, sm, st>>>(ncb, nchunk, cps, Q, P, T, ldt, tlo, err,
-                                                                          nsplit == 1 ? 1 : 0);
+  oz_mma_kernel<NPAD, COLLECT><<<dim3(ntile * ncb, nsplit), OZ_THREADS, sm, st>>>(ncb, nchunk, cps, Q, P, T, ldt,
+                                                                                   tlo, err, nsplit == 1 ? 1 : 0);
+}
+
+template <int NPAD>
+static void launch_mma(cudaStream_t st, int ntile, int ncb, int nchunk, int nsplit, int cps, const uint16_t* Q,
+                       const uint16_t* P, long long* T, long long ldt, long long tlo, int* err) {
+  if (oz_collector()) launch_mma_as<NPAD, true>(st, ntile, ncb, nchunk, nsplit, cps, Q, P, T, ldt, tlo, err);
+  else launch_mma_as<NPAD, false>(st, ntile, ncb, nchunk, nsplit, cps, Q, P, T, ldt, tlo, err);
 }
 
 void oz_mma(cudaStream_t st, int n, int k, int m, const uint16_t* Q, const uint16_t* P, long long* T, int* err) {
