@@ -41,8 +41,8 @@ struct SplitAX {
     T.alloc(sizeof(long long) * np * tmax);
     err.alloc(sizeof(int));
     MPL_CUDA(cudaMemsetAsync(err.ptr(), 0, sizeof(int), st));
-    for (int p = 0; p < np; ++p)
-      oz_split_a(st, cx ? p + 1 : 0, n, n, A, lda, e.as<int>() + (size_t)p * n, Q.as<uint16_t>() + p * qa);
+    if (cx) oz_split_a_3m(st, false, n, n, A, lda, e.as<int>(), n, Q.as<uint16_t>(), (long long)qa);
+    else oz_split_a(st, 0, n, n, A, lda, e.as<int>(), Q.as<uint16_t>());
     check_launch("split A");
   }
   void apply(cudaStream_t st, const double* X, long long ldx, double* Y, long long ldy, int ncols) {
@@ -51,9 +51,11 @@ struct SplitAX {
       const int mc = std::min(OZ_MAXM, ncols - c0);
       const size_t tt = oz_t_elems(n, mc);
       if (oz_mma_accumulates(n, n, mc)) MPL_CUDA(cudaMemsetAsync(T.ptr(), 0, sizeof(long long) * np * tt, st));
-      for (int p = 0; p < np; ++p)
-        oz_split_b(st, cx ? p + 1 : 0, n, mc, X + (size_t)elt * c0 * ldx, ldx, f.as<int>() + p * OZ_MAXM,
-                   P.as<uint16_t>() + p * pb);
+      if (cx)
+        oz_split_b_3m(st, false, n, mc, X + (size_t)elt * c0 * ldx, ldx, f.as<int>(), OZ_MAXM, P.as<uint16_t>(),
+                      (long long)pb);
+      else
+        oz_split_b(st, 0, n, mc, X + (size_t)elt * c0 * ldx, ldx, f.as<int>(), P.as<uint16_t>());
       for (int p = 0; p < np; ++p)
         oz_mma(st, n, n, mc, Q.as<uint16_t>() + p * qa, P.as<uint16_t>() + p * pb, T.as<long long>() + p * tt,
                err.as<int>());

@@ -30,15 +30,26 @@
 // (8 accumulators x NPAD <= 512 tensor-memory columns) and a range of depth.
 // Two column blocks of one row tile run as adjacent CTAs, so the second
 // read of A's slices is served by L2.  The slices are stored pre-blocked per
-// 32-deep chunk in the canonical no-swizzle K-major core-matrix layout, the
-// eight slices of a chunk contiguous, so one bulk copy brings a chunk of A
-// (64 KB) and one a chunk of B.  Warp roles: warp 0 copies (two stages in
+// OZ_BK-deep chunk in the canonical no-swizzle K-major core-matrix layout,
+// the eight slices of a chunk contiguous, so one bulk copy brings a chunk of
+// A (64 KB) and one a chunk of B.  Warp roles: warp 0 copies (two stages in
 // flight), warp 1 issues the 36 x 2 tcgen05.mma of a stage (ordered by A
 // slice, so that each block of A is read from shared memory once and kept
 // in the tensor core's collector buffer for its 8 - i products) and commits
 // their completion, warps 2-17 fold the accumulators after each window
 // (one lane polls the accumulator barrier, the other warps sleep on a
 // hardware barrier).
+//
+// What bounds it (ncu, one real product at n = 8192, N = 48): the tensor
+// pipe is active a third of the time, about 80 cycles per M = 128, N = 48,
+// K = 16 MMA against about 24 of tensor work, and neither halving the
+// shared-memory operand reads (collector reuse: tensor-core shared-memory
+// wavefronts 61 % -> 28 %), nor four copies in flight instead of one, nor
+// fewer launch waves changes the time; DRAM runs at 28 %, L2 at 17 %.  The
+// product is bound by the number of MMA instructions, which the eight
+// shift-group accumulators (8 x N <= 512 tensor-memory columns) cap at
+// 128 x 64 outputs each; a CTA pair (cta_group::2, M = 256) would double
+// the work per instruction.
 // Every wait has an iteration limit; a role that gives up records an error
 // and raises the CTA's abort flag, the others leave their waits, and the CTA
 // waits (bounded) for the copies and MMAs it issued before it frees its
@@ -66,13 +77,29 @@ constexpr int OZ_THREADS = 32 * (2 + OZ_FOLD_WARPS);
 constexpr int OZ_TILE_A = OZ_BM * OZ_BK;           // elements of one slice block of A
 constexpr long long OZ_WAIT_LIMIT = 1LL << 22;     // mbarrier polls before giving up
 static_assert(OZ_WIN % OZ_BK == 0, "window of whole stages");
+static_assert(OZ_BK % 16 == 0, "whole MMA depth steps per stage");
+
+// The stage ring of the product kernel for a column block of NPAD: NST
+// stages of OZ_BK depth (A's and B's eight slices).  Two 32-deep stages:
+// a ring of five 16-deep stages (four copies in flight instead of one)
+// measured 11 % slower -- the product is bound by the issue of its small
+// MMAs, not by operand delivery (see the header).
+template <int NPAD>
+struct OzRing {
+  static constexpr int A_BYTES = OZ_S * OZ_TILE_A * 2;      // the 8 slices of one chunk of the row tile
+  static constexpr int B_BYTES = OZ_S * NPAD * OZ_BK * 2;   // the 8 slices of one chunk of the column block
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int NST = 2;
+  static_assert(NST * STAGE <= 227 * 1024, "the ring fits the shared memory of a CTA");
+  static_assert(STAGE % 1024 == 0, "stages keep the 1024-byte alignment of the buffer");
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// element offset of (r, kc) in a rows x 32 block, K-major core matrices
-// (8 rows x 8 elements = 128 bytes; 4 of them along the chunk's depth)
+// element offset of (r, kc) in a rows x OZ_BK block, K-major core matrices
+// (8 rows x 8 elements = 128 bytes; OZ_BK / 8 of them along the chunk's depth)
 __host__ __device__ __forceinline__ int core_off32(int r, int kc) {
   return (((r >> 3) * (OZ_BK / 8) + (kc >> 3)) << 6) + ((r & 7) << 3) + (kc & 7);
 }
@@ -121,39 +148,107 @@ __device__ __forceinline__ int exp_bits(double x) {
   return e;
 }
 
-__global__ void fill_int_kernel(int n, int* p, int v) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+// The NP real operands one stored entry feeds: NP = 1, the value `pick`
+// selects by mode; NP = 3, the 3M operands of complex storage, (re, im,
+// re + im) for mode 0 and those of the conjugate (re, -im, re - im) for
+// mode 1.  One read of the entry serves all three.
+template <int NP>
+__device__ __forceinline__ void operands(const double* A, long long idx, int mode, double v[NP]) {
+  if constexpr (NP == 1) {
+    v[0] = pick(A, idx, mode);
+  } else {
+    const double re = A[2 * idx], im = A[2 * idx + 1];
+    v[0] = re;
+    v[1] = mode ? -im : im;
+    v[2] = mode ? re - im : re + im;
+  }
 }
 
-// e[r] = max over k of the exponent of |A(r, k)| (rows: threads, depth: grid y)
+// exponent slots of NP operands (slot p of entry r at e[p * estride + r]):
+// "no nonzero entry yet" before the maxima, 0 for all-zero rows after them
+__global__ void fill_exp_kernel(int n, int* e, long long estride) {
+  int* ep = e + blockIdx.y * estride;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) ep[i] = INT_MIN;
+}
+
+__global__ void clamp_exp_kernel(int n, int* e, long long estride) {
+  int* ep = e + blockIdx.y * estride;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    if (ep[i] == INT_MIN) ep[i] = 0;
+}
+
+// e[p][r] = max over k of the exponent of operand p of A(r, k) (rows:
+// threads, depth: grid y)
+template <int NP>
 __global__ void row_exp_kernel(int n, int k, const double* __restrict__ A, long long lda, int mode,
-                               int* __restrict__ e) {
+                               int* __restrict__ e, long long estride) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const int k0 = blockIdx.y * 256, k1 = min(k, k0 + 256);
-  int m = INT_MIN;
-  for (int kk = k0; kk < k1; ++kk) m = max(m, exp_bits(pick(A, r + (long long)kk * lda, mode)));
-  if (m != INT_MIN) atomicMax(e + r, m);
-}
-
-// f[c] = max over k of the exponent of |B(k, c)| (one block per column)
-__global__ void col_exp_kernel(int k, const double* __restrict__ B, long long ldb, int mode, int* __restrict__ f) {
-  __shared__ int red[256];
-  const int c = blockIdx.x;
-  int m = INT_MIN;
-  for (int kk = threadIdx.x; kk < k; kk += blockDim.x) m = max(m, exp_bits(pick(B, kk + (long long)c * ldb, mode)));
-  red[threadIdx.x] = m;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + s]);
-    __syncthreads();
+  int m[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) m[p] = INT_MIN;
+#pragma unroll 4
+  for (int kk = k0; kk < k1; ++kk) {
+    double v[NP];
+    operands<NP>(A, r + (long long)kk * lda, mode, v);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) m[p] = max(m[p], exp_bits(v[p]));
   }
-  if (threadIdx.x == 0) f[c] = red[0] == INT_MIN ? 0 : red[0];
+#pragma unroll
+  for (int p = 0; p < NP; ++p)
+    if (m[p] != INT_MIN) atomicMax(e + p * estride + r, m[p]);
 }
 
-__global__ void clamp_exp_kernel(int n, int* e) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    if (e[i] == INT_MIN) e[i] = 0;
+// f[p][c] = max over k of the exponent of operand p of B(k, c): grid x
+// columns, grid y chunks of OZ_EXP_CHUNK depth (256 threads x 8 independent
+// loads each), a block reduction and one atomic per operand
+constexpr int OZ_EXP_CHUNK = 2048;
+template <int NP>
+__global__ void __launch_bounds__(256) col_exp_kernel(int k, const double* __restrict__ B, long long ldb, int mode,
+                                                      int* __restrict__ f, long long fstride) {
+  __shared__ int red[NP][8];
+  const int c = blockIdx.x, k0 = blockIdx.y * OZ_EXP_CHUNK;
+  int m[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) m[p] = INT_MIN;
+#pragma unroll
+  for (int j = 0; j < OZ_EXP_CHUNK / 256; ++j) {
+    const int kk = k0 + j * 256 + threadIdx.x;
+    if (kk < k) {
+      double v[NP];
+      operands<NP>(B, kk + (long long)c * ldb, mode, v);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) m[p] = max(m[p], exp_bits(v[p]));
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m[p] = max(m[p], __shfl_xor_sync(0xffffffffu, m[p], o));
+    if ((threadIdx.x & 31) == 0) red[p][threadIdx.x >> 5] = m[p];
+  }
+  __syncthreads();
+  if (threadIdx.x < NP) {
+    int mm = INT_MIN;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) mm = max(mm, red[threadIdx.x][w]);
+    if (mm != INT_MIN) atomicMax(f + threadIdx.x * fstride + c, mm);
+  }
+}
+
+// Signed field of len bits of x starting at bit pos.
+__host__ __device__ __forceinline__ int sext_field(uint32_t x, int pos, int len) {
+  return ((int)(x << (32 - pos - len))) >> (32 - len);
+}
+
+// bf16 bit pattern of an integer |q| <= 256 (at most 8 significant bits, so
+// exact): 1.5 2^23 + q is exact in FP32, removing 1.5 2^23 leaves q, and
+// the upper half of q's FP32 pattern is its bf16 pattern.  Two full-rate
+// operations instead of an integer-to-float conversion.
+__device__ __forceinline__ uint16_t bf16_of_small_int(int q) {
+  const float fq = __int_as_float(0x4B400000 + q) - 12582912.0f;
+  return (uint16_t)(__float_as_uint(fq) >> 16);
 }
 
 // The OZ_S balanced digits of x below the exponent ex (|x| < 2^ex), as bf16
@@ -163,6 +258,13 @@ __global__ void clamp_exp_kernel(int n, int* e) {
 // |U| < 2^63, and U = sum_i q_i 2^(56 - 8i) exactly, each q_i the nearest
 // integer (half up) of what remains above 2^(56 - 8i).  Same value as
 // x 2^(7 - ex) = sum_i q_i 2^(-8i) up to 2^(ex - 64).
+//
+// What remains above 2^(56 - 8i) after the digits before it is the low
+// 64 - 8i bits of U read as a two's-complement number (each half-up digit
+// leaves a remainder in [-2^(s-1), 2^(s-1)), s = 64 - 8i), so
+// q_i = floor(t_i / 2 + 1/2) with t_i the signed 9-bit field of U at bits
+// 63 - 8i .. 55 - 8i, and the last digit is the signed low byte: eight
+// 32-bit field extractions, no 64-bit shifts or subtractions.
 __device__ __forceinline__ void digits(double x, int ex, uint16_t out[OZ_S]) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const int E = (int)((bits >> 52) & 0x7FF);
@@ -174,15 +276,16 @@ __device__ __forceinline__ void digits(double x, int ex, uint16_t out[OZ_S]) {
   else if (sft >= 0) U = M << sft;                       // below 2^63 because |x| < 2^ex
   else U = (M >> (-sft)) + ((M >> (-sft - 1)) & 1);      // nearest, half up
   if (bits >> 63) U = -U;
-#pragma unroll
-  for (int i = 0; i < OZ_S; ++i) {
-    const int sh = 56 - 8 * i;
-    const long long q = sh ? (U >> sh) + ((U >> (sh - 1)) & 1) : U;  // |q| <= 128
-    // the remainder fits (|U - q 2^sh| <= 2^(sh-1)); the product may not:
-    // subtract modulo 2^64
-    U = (long long)((unsigned long long)U - ((unsigned long long)q << sh));
-    out[i] = __bfloat16_as_ushort(__float2bfloat16_rn((float)q));
-  }
+  const uint32_t lo = (uint32_t)(unsigned long long)U, hi = (uint32_t)((unsigned long long)U >> 32);
+  const uint32_t mid = (hi << 1) | (lo >> 31);           // bits 62 .. 31 of U
+  out[0] = bf16_of_small_int((sext_field(hi, 23, 9) + 1) >> 1);
+  out[1] = bf16_of_small_int((sext_field(hi, 15, 9) + 1) >> 1);
+  out[2] = bf16_of_small_int((sext_field(hi, 7, 9) + 1) >> 1);
+  out[3] = bf16_of_small_int((sext_field(mid, 0, 9) + 1) >> 1);
+  out[4] = bf16_of_small_int((sext_field(lo, 23, 9) + 1) >> 1);
+  out[5] = bf16_of_small_int((sext_field(lo, 15, 9) + 1) >> 1);
+  out[6] = bf16_of_small_int((sext_field(lo, 7, 9) + 1) >> 1);
+  out[7] = bf16_of_small_int(sext_field(lo, 0, 8));
 }
 
 
@@ -196,13 +299,17 @@ __device__ __forceinline__ void store8(uint16_t* dst, const uint16_t v[8]) {
 }
 
 // Row slices of op(A) (n x k; rows padded to ntile * 128, depth to
-// nchunk * 32, zeros outside): slice i of tile t, chunk c is the 128 x 32
-// block at ((t * nchunk + c) * OZ_S + i) * 4096.  One thread per row and 8
-// consecutive depth indices (16-byte stores into one core-matrix row); trans:
-// op(A) = A^T (A^H through the conjugate modes) from storage k x n.
-template <bool TRANS>
+// nchunk * OZ_BK, zeros outside) for each of the NP operands (slices of operand
+// p at Q + p * qstride, exponents at e + p * estride): slice i of tile t,
+// chunk c is the 128 x OZ_BK block at ((t * nchunk + c) * OZ_S + i) * 128 OZ_BK.
+// One thread per row and 8 consecutive depth indices (one read of the
+// stored entries for all operands; 16-byte stores into one core-matrix
+// row); trans: op(A) = A^T (A^H through the conjugate modes) from storage
+// k x n.
+template <bool TRANS, int NP>
 __global__ void split_rows_kernel(int n, int k, const double* __restrict__ A, long long lda, int mode,
-                                  const int* __restrict__ e, int ntile, int nchunk, uint16_t* __restrict__ Q) {
+                                  const int* __restrict__ e, long long estride, int ntile, int nchunk,
+                                  uint16_t* __restrict__ Q, long long qstride) {
   const long long rows = (long long)ntile * OZ_BM, k8 = (long long)nchunk * (OZ_BK / 8);
   const long long tot = rows * k8;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot;
@@ -210,53 +317,79 @@ __global__ void split_rows_kernel(int n, int k, const double* __restrict__ A, lo
     int r, kb;
     if (TRANS) { kb = (int)(id % k8); r = (int)(id / k8); }
     else { r = (int)(id % rows); kb = (int)(id / rows); }
-    const int ex = r < n ? e[r] : 0;
-    uint16_t d[OZ_S][8];
+    double x[8][NP];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int kk = kb * 8 + q;
-      double x = 0.0;
-      if (r < n && kk < k) x = TRANS ? pick(A, kk + (long long)r * lda, mode) : pick(A, r + (long long)kk * lda, mode);
-      uint16_t dq[OZ_S];
-      digits(x, ex, dq);
+      if (r < n && kk < k) {
+        operands<NP>(A, TRANS ? kk + (long long)r * lda : r + (long long)kk * lda, mode, x[q]);
+      } else {
 #pragma unroll
-      for (int i = 0; i < OZ_S; ++i) d[i][q] = dq[i];
+        for (int p = 0; p < NP; ++p) x[q][p] = 0.0;
+      }
     }
     const int t = r / OZ_BM, c = (kb * 8) / OZ_BK;
     const int off = core_off32(r % OZ_BM, (kb * 8) % OZ_BK);
 #pragma unroll
-    for (int i = 0; i < OZ_S; ++i) store8(Q + (((long long)t * nchunk + c) * OZ_S + i) * OZ_TILE_A + off, d[i]);
+    for (int p = 0; p < NP; ++p) {
+      const int ex = r < n ? e[p * estride + r] : 0;
+      uint16_t d[OZ_S][8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        uint16_t dq[OZ_S];
+        digits(x[q][p], ex, dq);
+#pragma unroll
+        for (int i = 0; i < OZ_S; ++i) d[i][q] = dq[i];
+      }
+#pragma unroll
+      for (int i = 0; i < OZ_S; ++i)
+        store8(Q + p * qstride + (((long long)t * nchunk + c) * OZ_S + i) * OZ_TILE_A + off, d[i]);
+    }
   }
 }
 
 // Column slices of op(B) (k x m; columns padded to ncb * npad, depth to
-// nchunk * 32): slice j of column block b, chunk c is the npad x 32 block at
-// ((b * nchunk + c) * OZ_S + j) * npad * 32.  One thread per column and 8
-// consecutive depth indices; trans: op(B) = B^T (B^H) from storage m x k.
-template <bool TRANS>
+// nchunk * OZ_BK) for each of the NP operands (at P + p * pstride, exponents
+// at f + p * fstride): slice j of column block b, chunk c is the npad x OZ_BK
+// block at ((b * nchunk + c) * OZ_S + j) * npad * OZ_BK.  One thread per
+// column and 8 consecutive depth indices; trans: op(B) = B^T (B^H) from
+// storage m x k.
+template <bool TRANS, int NP>
 __global__ void split_cols_kernel(int k, int m, const double* __restrict__ B, long long ldb, int mode,
-                                  const int* __restrict__ f, int nchunk, int npad, int ncb, uint16_t* __restrict__ P) {
+                                  const int* __restrict__ f, long long fstride, int nchunk, int npad, int ncb,
+                                  uint16_t* __restrict__ P, long long pstride) {
   const long long k8 = (long long)nchunk * (OZ_BK / 8), tot = (long long)ncb * npad * k8;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot;
        id += (long long)gridDim.x * blockDim.x) {
     const int kb = (int)(id % k8), c = (int)(id / k8);
-    const int ex = c < m ? f[c] : 0;
-    uint16_t d[OZ_S][8];
+    double x[8][NP];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int kk = kb * 8 + q;
-      double x = 0.0;
-      if (c < m && kk < k) x = TRANS ? pick(B, c + (long long)kk * ldb, mode) : pick(B, kk + (long long)c * ldb, mode);
-      uint16_t dq[OZ_S];
-      digits(x, ex, dq);
+      if (c < m && kk < k) {
+        operands<NP>(B, TRANS ? c + (long long)kk * ldb : kk + (long long)c * ldb, mode, x[q]);
+      } else {
 #pragma unroll
-      for (int j = 0; j < OZ_S; ++j) d[j][q] = dq[j];
+        for (int p = 0; p < NP; ++p) x[q][p] = 0.0;
+      }
     }
     const int b = c / npad, cc = c % npad, ch = (kb * 8) / OZ_BK;
     const int off = core_off32(cc, (kb * 8) % OZ_BK);
 #pragma unroll
-    for (int j = 0; j < OZ_S; ++j)
-      store8(P + (((long long)b * nchunk + ch) * OZ_S + j) * npad * OZ_BK + off, d[j]);
+    for (int p = 0; p < NP; ++p) {
+      const int ex = c < m ? f[p * fstride + c] : 0;
+      uint16_t d[OZ_S][8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        uint16_t dq[OZ_S];
+        digits(x[q][p], ex, dq);
+#pragma unroll
+        for (int j = 0; j < OZ_S; ++j) d[j][q] = dq[j];
+      }
+#pragma unroll
+      for (int j = 0; j < OZ_S; ++j)
+        store8(P + p * pstride + (((long long)b * nchunk + ch) * OZ_S + j) * npad * OZ_BK + off, d[j]);
+    }
   }
 }
 
@@ -309,12 +442,13 @@ oz_mma_kernel(int ncb, int nchunk, int chunks_per_split, const uint16_t* __restr
               const uint16_t* __restrict__ PB, long long* __restrict__ T, long long ldt, long long tlo, int* err,
               int single_split) {
   static_assert(NPAD % 16 == 0 && NPAD >= 16 && NPAD <= 64, "N of the tile");
-  constexpr int A_BYTES = OZ_S * OZ_TILE_A * 2;          // the 8 slices of one chunk of the row tile
-  constexpr int B_BYTES = OZ_S * NPAD * OZ_BK * 2;       // the 8 slices of one chunk of the column block
-  constexpr int STAGE = A_BYTES + B_BYTES;
+  constexpr int A_BYTES = OzRing<NPAD>::A_BYTES;
+  constexpr int B_BYTES = OzRing<NPAD>::B_BYTES;
+  constexpr int STAGE = OzRing<NPAD>::STAGE;
+  constexpr int NST = OzRing<NPAD>::NST;                 // stages in the ring
   constexpr int QC = NPAD / 4;                           // columns a fold warp reads back
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) uint64_t bar_full[2], bar_empty[2], bar_accf, bar_acce;
+  __shared__ __align__(8) uint64_t bar_full[NST], bar_empty[NST], bar_accf, bar_acce;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   __shared__ int issued, committed;                      // stages copied / whose MMAs were committed
@@ -326,7 +460,7 @@ oz_mma_kernel(int ncb, int nchunk, int chunks_per_split, const uint16_t* __restr
   const int nwin = (nst + OZ_STAGES_PER_WIN - 1) / OZ_STAGES_PER_WIN;
 
   if (tid == 0) {
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NST; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_full[b])), "r"(1));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_empty[b])), "r"(1));
     }
@@ -352,7 +486,7 @@ oz_mma_kernel(int ncb, int nchunk, int chunks_per_split, const uint16_t* __restr
     // ---- producer: one bulk copy of A's and one of B's slices per stage
     if (lane == 0) {
       for (int s = 0; s < nst; ++s) {
-        const int b = s & 1, r = s >> 1;
+        const int b = s % NST, r = s / NST;
         if (r > 0 && !mbar_wait(smem_u32(&bar_empty[b]), (r - 1) & 1, &abort_flag)) break;
         const uint32_t fb = smem_u32(&bar_full[b]);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"((uint32_t)STAGE)
@@ -378,7 +512,7 @@ oz_mma_kernel(int ncb, int nchunk, int chunks_per_split, const uint16_t* __restr
       constexpr uint32_t LBO = 128, SBO = (OZ_BK / 8) * 128;
       constexpr uint32_t idesc = idesc_bf16(OZ_BM, NPAD);
       for (int s = 0; s < nst; ++s) {
-        const int b = s & 1, r = s >> 1, w = s / OZ_STAGES_PER_WIN;
+        const int b = s % NST, r = s / NST, w = s / OZ_STAGES_PER_WIN;
         const bool first = (s % OZ_STAGES_PER_WIN) == 0;
         if (first && w > 0 && !mbar_wait(smem_u32(&bar_acce), (w - 1) & 1, &abort_flag)) break;
         if (!mbar_wait(smem_u32(&bar_full[b]), r & 1, &abort_flag)) break;
@@ -525,8 +659,9 @@ oz_mma_kernel(int ncb, int nchunk, int chunks_per_split, const uint16_t* __restr
       atomicExch(err, 1);
       // let the copies and MMAs that were issued finish (bounded) before the
       // shared and tensor memory are released
-      for (int s = max(0, issued - 2); s < issued; ++s) mbar_drain(smem_u32(&bar_full[s & 1]), (s >> 1) & 1);
-      for (int s = max(0, committed - 2); s < committed; ++s) mbar_drain(smem_u32(&bar_empty[s & 1]), (s >> 1) & 1);
+      for (int s = max(0, issued - NST); s < issued; ++s) mbar_drain(smem_u32(&bar_full[s % NST]), (s / NST) & 1);
+      for (int s = max(0, committed - NST); s < committed; ++s)
+        mbar_drain(smem_u32(&bar_empty[s % NST]), (s / NST) & 1);
     }
     __syncthreads();
   }
@@ -535,26 +670,35 @@ oz_mma_kernel(int ncb, int nchunk, int chunks_per_split, const uint16_t* __restr
   if (wid == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
+// x 2^k: a multiplication by the power of two when 2^k is a normal double
+// (exact, or rounded once like ldexp when the result is subnormal), ldexp
+// otherwise -- the same value as ldexp(x, k) without its FP64 sequence
+__device__ __forceinline__ double scale2(double x, int k) {
+  if (k >= -1022 && k <= 1023) return x * __longlong_as_double((long long)(k + 1023) << 52);
+  return ldexp(x, k);
+}
+
 // value of one accumulator pair in units of the leading digit product:
 // hi 2^-24 + lo 2^-56, from an exact split into a 53-bit-safe part and the
 // low 32 bits of lo, times 2^ex
 __device__ __forceinline__ double fixed_value(long long hi, long long lo, int ex) {
   const long long top = hi + (lo >> 32);            // lo = (lo >> 32) 2^32 + (lo & 0xffffffff)
   const long long low = lo & 0xFFFFFFFFLL;
-  return ldexp((double)top, ex - 24) + ldexp((double)low, ex - 56);
+  return scale2((double)top, ex - 24) + scale2((double)low, ex - 56);
 }
 
-// C(r, c) = alpha 2^(e_r + f_c - 14) (hi 2^-24 + lo 2^-56) (+ beta C)
+// C(r, c) = alpha 2^(e_r + f_c - 14) (hi 2^-24 + lo 2^-56) (+ beta C); rows
+// by grid x (grid-stride), columns by grid y
 __global__ void combine_real_kernel(int n, int m, const long long* __restrict__ T, long long ldt, long long tlo,
                                     const int* __restrict__ e, const int* __restrict__ f, double alpha, double beta,
                                     int lower_only, int col0, double* __restrict__ C, long long ldc) {
-  const long long tot = (long long)n * m;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot;
-       id += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(id % n), c = (int)(id / n);
+  const int c = blockIdx.y;
+  const int fc = f[c] - 14;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     if (lower_only && r < col0 + c) continue;
     const long long t = r + c * ldt;
-    double v = alpha * fixed_value(T[t], T[tlo + t], e[r] + f[c] - 14);
+    double v = fixed_value(T[t], T[tlo + t], e[r] + fc);
+    if (alpha != 1.0) v *= alpha;
     if (beta != 0.0) v += beta * C[r + c * ldc];
     C[r + c * ldc] = v;
   }
@@ -565,18 +709,23 @@ __global__ void combine_3m_kernel(int n, int m, const long long* __restrict__ T,
                                   long long tstride, const int* __restrict__ e, int estride,
                                   const int* __restrict__ f, int fstride, double alpha, double beta, int lower_only,
                                   int col0, double* __restrict__ C, long long ldc) {
-  const long long tot = (long long)n * m;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot;
-       id += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(id % n), c = (int)(id / n);
+  const int c = blockIdx.y;
+  int fc[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) fc[q] = f[q * fstride + c] - 14;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     if (lower_only && r < col0 + c) continue;
     double p[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       const long long t = q * tstride + r + c * ldt;
-      p[q] = fixed_value(T[t], T[tlo + t], e[q * estride + r] + f[q * fstride + c] - 14);
+      p[q] = fixed_value(T[t], T[tlo + t], e[q * estride + r] + fc[q]);
     }
-    double re = alpha * (p[0] - p[1]), im = alpha * (p[2] - p[0] - p[1]);
+    double re = p[0] - p[1], im = p[2] - p[0] - p[1];
+    if (alpha != 1.0) {
+      re *= alpha;
+      im *= alpha;
+    }
     if (beta != 0.0) {
       re += beta * C[2 * (r + c * ldc)];
       im += beta * C[2 * (r + c * ldc) + 1];
@@ -604,40 +753,70 @@ size_t oz_b_elems(int k, int m) {
   return (size_t)OZ_S * oz_ncb(m) * oz_npad(m) * nchunk * OZ_BK;
 }
 
-void oz_split_a(cudaStream_t st, int mode, int n, int k, const double* A, long long lda, int* e, uint16_t* Q,
-                bool trans) {
+namespace {
+// exponents of the NP operands: every stored entry is read once per pass
+// (maxima, then digits); four launches whatever NP is
+template <int NP>
+void split_a_np(cudaStream_t st, int mode, int n, int k, const double* A, long long lda, int* e, long long estride,
+                uint16_t* Q, long long qstride, bool trans) {
   const int ntile = (n + OZ_BM - 1) / OZ_BM, nchunk = (k + OZ_BK - 1) / OZ_BK;
   const long long tot = (long long)ntile * OZ_BM * nchunk * (OZ_BK / 8);
-  if (trans) {
-    // row r of op(A) is stored column r: one block per row reduces its exponent
-    count_launch(2);
-    col_exp_kernel<<<n, 256, 0, st>>>(k, A, lda, mode, e);
-    split_rows_kernel<true><<<grid_for(tot), 256, 0, st>>>(n, k, A, lda, mode, e, ntile, nchunk, Q);
-    return;
-  }
+  const int gx = std::min((n + 255) / 256, 4 * NUM_SMS);
   count_launch(4);
-  fill_int_kernel<<<grid_for(n), 256, 0, st>>>(n, e, INT_MIN);
-  row_exp_kernel<<<dim3((n + 255) / 256, (k + 255) / 256), 256, 0, st>>>(n, k, A, lda, mode, e);
-  clamp_exp_kernel<<<grid_for(n), 256, 0, st>>>(n, e);
-  split_rows_kernel<false><<<grid_for(tot), 256, 0, st>>>(n, k, A, lda, mode, e, ntile, nchunk, Q);
+  fill_exp_kernel<<<dim3(gx, NP), 256, 0, st>>>(n, e, estride);
+  if (trans)  // row r of op(A) is stored column r (contiguous along the depth)
+    col_exp_kernel<NP><<<dim3(n, (k + OZ_EXP_CHUNK - 1) / OZ_EXP_CHUNK), 256, 0, st>>>(k, A, lda, mode, e, estride);
+  else
+    row_exp_kernel<NP><<<dim3((n + 255) / 256, (k + 255) / 256), 256, 0, st>>>(n, k, A, lda, mode, e, estride);
+  clamp_exp_kernel<<<dim3(gx, NP), 256, 0, st>>>(n, e, estride);
+  if (trans)
+    split_rows_kernel<true, NP><<<grid_for(tot), 256, 0, st>>>(n, k, A, lda, mode, e, estride, ntile, nchunk, Q,
+                                                               qstride);
+  else
+    split_rows_kernel<false, NP><<<grid_for(tot), 256, 0, st>>>(n, k, A, lda, mode, e, estride, ntile, nchunk, Q,
+                                                                qstride);
+}
+
+template <int NP>
+void split_b_np(cudaStream_t st, int mode, int k, int m, const double* B, long long ldb, int* f, long long fstride,
+                uint16_t* P, long long pstride, bool trans) {
+  const int npad = oz_npad(m), ncb = oz_ncb(m), nchunk = (k + OZ_BK - 1) / OZ_BK;
+  const long long tot = (long long)ncb * npad * nchunk * (OZ_BK / 8);
+  const int gx = std::min((m + 255) / 256, 4 * NUM_SMS);
+  count_launch(4);
+  fill_exp_kernel<<<dim3(gx, NP), 256, 0, st>>>(m, f, fstride);
+  if (trans)  // column c of op(B) is stored row c
+    row_exp_kernel<NP><<<dim3((m + 255) / 256, (k + 255) / 256), 256, 0, st>>>(m, k, B, ldb, mode, f, fstride);
+  else
+    col_exp_kernel<NP><<<dim3(m, (k + OZ_EXP_CHUNK - 1) / OZ_EXP_CHUNK), 256, 0, st>>>(k, B, ldb, mode, f, fstride);
+  clamp_exp_kernel<<<dim3(gx, NP), 256, 0, st>>>(m, f, fstride);
+  if (trans)
+    split_cols_kernel<true, NP><<<grid_for(tot), 256, 0, st>>>(k, m, B, ldb, mode, f, fstride, nchunk, npad, ncb, P,
+                                                               pstride);
+  else
+    split_cols_kernel<false, NP><<<grid_for(tot), 256, 0, st>>>(k, m, B, ldb, mode, f, fstride, nchunk, npad, ncb,
+                                                                P, pstride);
+}
+}  // namespace
+
+void oz_split_a(cudaStream_t st, int mode, int n, int k, const double* A, long long lda, int* e, uint16_t* Q,
+                bool trans) {
+  split_a_np<1>(st, mode, n, k, A, lda, e, 0, Q, 0, trans);
 }
 
 void oz_split_b(cudaStream_t st, int mode, int k, int m, const double* B, long long ldb, int* f, uint16_t* P,
                 bool trans) {
-  const int npad = oz_npad(m), ncb = oz_ncb(m), nchunk = (k + OZ_BK - 1) / OZ_BK;
-  const long long tot = (long long)ncb * npad * nchunk * (OZ_BK / 8);
-  if (trans) {
-    // column c of op(B) is stored row c: row maxima by atomics
-    count_launch(4);
-    fill_int_kernel<<<grid_for(m), 256, 0, st>>>(m, f, INT_MIN);
-    row_exp_kernel<<<dim3((m + 255) / 256, (k + 255) / 256), 256, 0, st>>>(m, k, B, ldb, mode, f);
-    clamp_exp_kernel<<<grid_for(m), 256, 0, st>>>(m, f);
-    split_cols_kernel<true><<<grid_for(tot), 256, 0, st>>>(k, m, B, ldb, mode, f, nchunk, npad, ncb, P);
-    return;
-  }
-  count_launch(2);
-  col_exp_kernel<<<m, 256, 0, st>>>(k, B, ldb, mode, f);
-  split_cols_kernel<false><<<grid_for(tot), 256, 0, st>>>(k, m, B, ldb, mode, f, nchunk, npad, ncb, P);
+  split_b_np<1>(st, mode, k, m, B, ldb, f, 0, P, 0, trans);
+}
+
+void oz_split_a_3m(cudaStream_t st, bool conj, int n, int k, const double* A, long long lda, int* e,
+                   long long estride, uint16_t* Q, long long qstride, bool trans) {
+  split_a_np<3>(st, conj ? 1 : 0, n, k, A, lda, e, estride, Q, qstride, trans);
+}
+
+void oz_split_b_3m(cudaStream_t st, bool conj, int k, int m, const double* B, long long ldb, int* f,
+                   long long fstride, uint16_t* P, long long pstride, bool trans) {
+  split_b_np<3>(st, conj ? 1 : 0, k, m, B, ldb, f, fstride, P, pstride, trans);
 }
 
 // Depth splits of whole windows.  One CTA fits an SM (tensor memory and
@@ -684,7 +863,7 @@ static bool oz_collector() {
 template <int NPAD, bool COLLECT>
 static void launch_mma_as(cudaStream_t st, int ntile, int ncb, int nchunk, int nsplit, int cps, const uint16_t* Q,
                           const uint16_t* P, long long* T, long long ldt, long long tlo, int* err) {
-  const size_t sm = (size_t)2 * (OZ_S * OZ_TILE_A * 2 + OZ_S * NPAD * OZ_BK * 2);
+  const size_t sm = (size_t)OzRing<NPAD>::NST * OzRing<NPAD>::STAGE;
   // one attribute call per instantiation (thread-safe static initialisation)
   static const bool opened =
       cudaFuncSetAttribute(oz_mma_kernel<NPAD, COLLECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) ==
@@ -720,16 +899,17 @@ void oz_combine_real(cudaStream_t st, int n, int m, const long long* T, const in
                      long long ldc, double alpha, double beta, bool lower_only, int col0) {
   const long long ldt = oz_t_rows(n), tlo = (long long)oz_t_elems(n, m) / 2;
   count_launch();
-  combine_real_kernel<<<grid_for((long long)n * m), 256, 0, st>>>(n, m, T, ldt, tlo, e, f, alpha, beta,
-                                                                   lower_only ? 1 : 0, col0, C, ldc);
+  const dim3 grid(std::min((n + 255) / 256, 64), m);  // columns by grid y: no index division
+  combine_real_kernel<<<grid, 256, 0, st>>>(n, m, T, ldt, tlo, e, f, alpha, beta, lower_only ? 1 : 0, col0, C, ldc);
 }
 
 void oz_combine_3m(cudaStream_t st, int n, int m, const long long* T, const int* e, int estride, const int* f,
                    int fstride, double* C, long long ldc, double alpha, double beta, bool lower_only, int col0) {
   const long long ldt = oz_t_rows(n), tt = (long long)oz_t_elems(n, m), tlo = tt / 2;
   count_launch();
-  combine_3m_kernel<<<grid_for((long long)n * m), 256, 0, st>>>(n, m, T, ldt, tlo, tt, e, estride, f, fstride,
-                                                                 alpha, beta, lower_only ? 1 : 0, col0, C, ldc);
+  const dim3 grid(std::min((n + 255) / 256, 64), m);
+  combine_3m_kernel<<<grid, 256, 0, st>>>(n, m, T, ldt, tlo, tt, e, estride, f, fstride, alpha, beta,
+                                          lower_only ? 1 : 0, col0, C, ldc);
 }
 
 }  // namespace mpl
@@ -801,15 +981,16 @@ bool oz_gemm_fp64(cudaStream_t st, bool cx, bool ta, bool tb, int M, int N, int 
   uint16_t* Pb = static_cast<uint16_t*>(P.p[3]);
   long long* T = static_cast<long long*>(P.p[4]);
   // 3M operands: re, im, re + im; of a conjugate transpose: re, -im, re - im
-  auto mode_of = [&](int p, bool t) { return !cx ? 0 : !t ? p + 1 : (p == 0 ? 1 : p == 1 ? 4 : 5); };
-  for (int p = 0; p < np; ++p) oz_split_a(st, mode_of(p, ta), M, K, A, lda, e + p * M, Q + p * qa, ta);
+  if (cx) oz_split_a_3m(st, ta, M, K, A, lda, e, M, Q, (long long)qa, ta);
+  else oz_split_a(st, 0, M, K, A, lda, e, Q, ta);
   for (int c0 = 0; c0 < N; c0 += CW) {
     const int nb = std::min(CW, N - c0);
     const size_t tt = oz_t_elems(M, nb);
     // columns c0.. of op(B): stored columns (no transpose) or stored rows
     const double* Bc = B + (size_t)elt * (tb ? (size_t)c0 : (size_t)c0 * ldb);
     if (oz_mma_accumulates(M, K, nb)) cudaMemsetAsync(T, 0, sizeof(long long) * np * tt, st);
-    for (int p = 0; p < np; ++p) oz_split_b(st, mode_of(p, tb), K, nb, Bc, ldb, f + p * CW, Pb + p * pb, tb);
+    if (cx) oz_split_b_3m(st, tb, K, nb, Bc, ldb, f, CW, Pb, (long long)pb, tb);
+    else oz_split_b(st, 0, K, nb, Bc, ldb, f, Pb, tb);
     for (int p = 0; p < np; ++p) oz_mma(st, M, K, nb, Q + p * qa, Pb + p * pb, T + p * tt, P.err);
     double* Cc = C + (size_t)elt * c0 * ldc;
     if (cx) oz_combine_3m(st, M, nb, T, e, M, f, CW, Cc, ldc, alpha, beta, lower_only, c0);

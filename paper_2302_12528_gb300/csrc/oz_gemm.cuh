@@ -28,6 +28,14 @@ void oz_split_a(cudaStream_t st, int mode, int n, int k, const double* A, long l
 // trans: B is stored m x k and op(B) = its transpose (conjugate modes: B^H)
 void oz_split_b(cudaStream_t st, int mode, int k, int m, const double* B, long long ldb, int* f, uint16_t* P,
                 bool trans = false);
+// The three 3M operands of complex storage at once (re, im, re + im; with
+// conj those of the conjugate: re, -im, re - im), each stored entry read
+// once: operand p's exponents at e + p * estride, its slices at
+// Q + p * qstride -- the same values as three single-mode calls.
+void oz_split_a_3m(cudaStream_t st, bool conj, int n, int k, const double* A, long long lda, int* e,
+                   long long estride, uint16_t* Q, long long qstride, bool trans = false);
+void oz_split_b_3m(cudaStream_t st, bool conj, int k, int m, const double* B, long long ldb, int* f,
+                   long long fstride, uint16_t* P, long long pstride, bool trans = false);
 // The exact fixed-point product of the slices into T (oz_t_elems(n, m)
 // int64: hi at T, lo at T + oz_t_elems(n, m) / 2).  When
 // oz_mma_accumulates(n, k, m) the depth is split over several CTAs per tile
