@@ -517,13 +517,18 @@ def split_ax_roofline(w, per_launch_s, launches):
         flops += nprod * 36 * 2.0 * rows * npad * ncb * depth
         bytes_ += nprod * 8 * rows * depth * 2.0
     t_tensor, t_hbm = flops / bf16, bytes_ / hbm
+    # DRAM bytes of one whole product, measured by ncu on the dense complex
+    # product at n = 8192, m = 96 (profiles/oz_mma_dense_complex_n8192.txt:
+    # 3.84 GB; A's slices dominate) and scaled by n^2; other shapes were not
+    # captured
+    traffic = 3.84e9 * (w.n / 8192.0) ** 2 if (w.kind == "dense_complex" and w.m == 96) else None
     if t_tensor >= t_hbm:
         ach, peak, unit, bound = flops / per_launch_s / 1e12, bf16 / 1e12, "TFLOP/s", "tensor"
     else:
         ach, peak, unit, bound = bytes_ / per_launch_s / 1e9, hbm / 1e9, "GB/s", "hbm"
     return {"kernel": "oz_mma_kernel (FP64-accurate A X by error-free bf16 splitting, tcgen05) with its "
                       "split and combine kernels", "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
-            "frac": ach / peak, "traffic": None, "bf16_flops_per_launch": flops, "slice_bytes_per_launch": bytes_,
+            "frac": ach / peak, "traffic": traffic, "bf16_flops_per_launch": flops, "slice_bytes_per_launch": bytes_,
             "launches": launches, "avg_launch_ms": per_launch_s * 1e3,
             "peak_note": "measured sustained bf16 (cuBLAS) and copy bandwidth of this pool; the launch time "
                          "covers the whole product (X's slices, the three products, the combination)"}
