@@ -178,13 +178,16 @@ __global__ void clamp_exp_kernel(int n, int* e, long long estride) {
 }
 
 // e[p][r] = max over k of the exponent of operand p of A(r, k) (rows:
-// threads, depth: grid y)
+// threads, depth: grid y in chunks of kc -- 32 unless the grid would exceed
+// its y limit -- enough blocks to keep many loads in flight on the thin
+// operands of the basis updates)
+inline int row_exp_chunk(int k) { return std::max(32, (k + 65534) / 65535); }
 template <int NP>
-__global__ void row_exp_kernel(int n, int k, const double* __restrict__ A, long long lda, int mode,
+__global__ void row_exp_kernel(int n, int k, int kc, const double* __restrict__ A, long long lda, int mode,
                                int* __restrict__ e, long long estride) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
-  const int k0 = blockIdx.y * 256, k1 = min(k, k0 + 256);
+  const int k0 = blockIdx.y * kc, k1 = min(k, k0 + kc);
   int m[NP];
 #pragma unroll
   for (int p = 0; p < NP; ++p) m[p] = INT_MIN;
@@ -304,8 +307,9 @@ __device__ __forceinline__ void store8(uint16_t* dst, const uint16_t v[8]) {
 // chunk c is the 128 x OZ_BK block at ((t * nchunk + c) * OZ_S + i) * 128 OZ_BK.
 // One thread per row and 8 consecutive depth indices (one read of the
 // stored entries for all operands; 16-byte stores into one core-matrix
-// row); trans: op(A) = A^T (A^H through the conjugate modes) from storage
-// k x n.
+// row), rows fastest across threads so that 8 neighbours fill a 128-byte
+// core-matrix row group; trans: op(A) = A^T (A^H through the conjugate
+// modes) from storage k x n (each thread then reads 128 contiguous bytes).
 template <bool TRANS, int NP>
 __global__ void split_rows_kernel(int n, int k, const double* __restrict__ A, long long lda, int mode,
                                   const int* __restrict__ e, long long estride, int ntile, int nchunk,
@@ -314,9 +318,7 @@ __global__ void split_rows_kernel(int n, int k, const double* __restrict__ A, lo
   const long long tot = rows * k8;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot;
        id += (long long)gridDim.x * blockDim.x) {
-    int r, kb;
-    if (TRANS) { kb = (int)(id % k8); r = (int)(id / k8); }
-    else { r = (int)(id % rows); kb = (int)(id / rows); }
+    const int r = (int)(id % rows), kb = (int)(id / rows);
     double x[8][NP];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -352,16 +354,17 @@ __global__ void split_rows_kernel(int n, int k, const double* __restrict__ A, lo
 // nchunk * OZ_BK) for each of the NP operands (at P + p * pstride, exponents
 // at f + p * fstride): slice j of column block b, chunk c is the npad x OZ_BK
 // block at ((b * nchunk + c) * OZ_S + j) * npad * OZ_BK.  One thread per
-// column and 8 consecutive depth indices; trans: op(B) = B^T (B^H) from
-// storage m x k.
+// column and 8 consecutive depth indices, columns fastest across threads
+// (8 neighbours fill a 128-byte core-matrix row group; with trans their
+// loads are contiguous too); trans: op(B) = B^T (B^H) from storage m x k.
 template <bool TRANS, int NP>
 __global__ void split_cols_kernel(int k, int m, const double* __restrict__ B, long long ldb, int mode,
                                   const int* __restrict__ f, long long fstride, int nchunk, int npad, int ncb,
                                   uint16_t* __restrict__ P, long long pstride) {
-  const long long k8 = (long long)nchunk * (OZ_BK / 8), tot = (long long)ncb * npad * k8;
+  const long long k8 = (long long)nchunk * (OZ_BK / 8), cols = (long long)ncb * npad, tot = cols * k8;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot;
        id += (long long)gridDim.x * blockDim.x) {
-    const int kb = (int)(id % k8), c = (int)(id / k8);
+    const int c = (int)(id % cols), kb = (int)(id / cols);
     double x[8][NP];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -767,7 +770,8 @@ void split_a_np(cudaStream_t st, int mode, int n, int k, const double* A, long l
   if (trans)  // row r of op(A) is stored column r (contiguous along the depth)
     col_exp_kernel<NP><<<dim3(n, (k + OZ_EXP_CHUNK - 1) / OZ_EXP_CHUNK), 256, 0, st>>>(k, A, lda, mode, e, estride);
   else
-    row_exp_kernel<NP><<<dim3((n + 255) / 256, (k + 255) / 256), 256, 0, st>>>(n, k, A, lda, mode, e, estride);
+    row_exp_kernel<NP><<<dim3((n + 255) / 256, (k + row_exp_chunk(k) - 1) / row_exp_chunk(k)), 256, 0, st>>>(
+        n, k, row_exp_chunk(k), A, lda, mode, e, estride);
   clamp_exp_kernel<<<dim3(gx, NP), 256, 0, st>>>(n, e, estride);
   if (trans)
     split_rows_kernel<true, NP><<<grid_for(tot), 256, 0, st>>>(n, k, A, lda, mode, e, estride, ntile, nchunk, Q,
@@ -786,7 +790,8 @@ void split_b_np(cudaStream_t st, int mode, int k, int m, const double* B, long l
   count_launch(4);
   fill_exp_kernel<<<dim3(gx, NP), 256, 0, st>>>(m, f, fstride);
   if (trans)  // column c of op(B) is stored row c
-    row_exp_kernel<NP><<<dim3((m + 255) / 256, (k + 255) / 256), 256, 0, st>>>(m, k, B, ldb, mode, f, fstride);
+    row_exp_kernel<NP><<<dim3((m + 255) / 256, (k + row_exp_chunk(k) - 1) / row_exp_chunk(k)), 256, 0, st>>>(
+        m, k, row_exp_chunk(k), B, ldb, mode, f, fstride);
   else
     col_exp_kernel<NP><<<dim3(m, (k + OZ_EXP_CHUNK - 1) / OZ_EXP_CHUNK), 256, 0, st>>>(k, B, ldb, mode, f, fstride);
   clamp_exp_kernel<<<dim3(gx, NP), 256, 0, st>>>(m, f, fstride);
