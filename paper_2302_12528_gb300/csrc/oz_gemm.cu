@@ -10,7 +10,9 @@
 //   u = A_rk 2^(7 - e_r),  q_i = rint(u),  u <- 256 (u - q_i),
 // so |q_i| <= 128 (exact in bf16) and A_rk = 2^(e_r - 7) sum_i q_i 2^(-8i)
 // up to 2^(e_r - 71).  Columns of B likewise with exponents f_c.  Every step
-// is exact in FP64 (u - rint(u) and the scaling by 256 round nothing).
+// is exact in FP64 (u - rint(u) and the scaling by 256 round nothing); the
+// kernels compute the same digits from the bit pattern on the integer pipes
+// (oz_digits.cuh).
 //
 // Products.  The slice pairs (i, j) with i + j = g <= 7 (36 pairs; the
 // dropped ones weigh <= 2^-64 of the leading product) are accumulated per
@@ -64,6 +66,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "oz_digits.cuh"
 #include "oz_gemm.cuh"
 
 namespace mpl {
@@ -240,58 +243,6 @@ __global__ void __launch_bounds__(256) col_exp_kernel(int k, const double* __res
   }
 }
 
-// Signed field of len bits of x starting at bit pos.
-__host__ __device__ __forceinline__ int sext_field(uint32_t x, int pos, int len) {
-  return ((int)(x << (32 - pos - len))) >> (32 - len);
-}
-
-// bf16 bit pattern of an integer |q| <= 256 (at most 8 significant bits, so
-// exact): 1.5 2^23 + q is exact in FP32, removing 1.5 2^23 leaves q, and
-// the upper half of q's FP32 pattern is its bf16 pattern.  Two full-rate
-// operations instead of an integer-to-float conversion.
-__device__ __forceinline__ uint16_t bf16_of_small_int(int q) {
-  const float fq = __int_as_float(0x4B400000 + q) - 12582912.0f;
-  return (uint16_t)(__float_as_uint(fq) >> 16);
-}
-
-// The OZ_S balanced digits of x below the exponent ex (|x| < 2^ex), as bf16
-// bit patterns of the integers q_i (|q_i| <= 128: exact in bf16), on the
-// integer pipes (GB300 runs FP64 at 1/64 of the FP32 rate): x is taken from
-// its bit pattern to the 64-bit fixed point U = round(x 2^(63 - ex)),
-// |U| < 2^63, and U = sum_i q_i 2^(56 - 8i) exactly, each q_i the nearest
-// integer (half up) of what remains above 2^(56 - 8i).  Same value as
-// x 2^(7 - ex) = sum_i q_i 2^(-8i) up to 2^(ex - 64).
-//
-// What remains above 2^(56 - 8i) after the digits before it is the low
-// 64 - 8i bits of U read as a two's-complement number (each half-up digit
-// leaves a remainder in [-2^(s-1), 2^(s-1)), s = 64 - 8i), so
-// q_i = floor(t_i / 2 + 1/2) with t_i the signed 9-bit field of U at bits
-// 63 - 8i .. 55 - 8i, and the last digit is the signed low byte: eight
-// 32-bit field extractions, no 64-bit shifts or subtractions.
-__device__ __forceinline__ void digits(double x, int ex, uint16_t out[OZ_S]) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-  const int E = (int)((bits >> 52) & 0x7FF);
-  const long long frac = (long long)(bits & 0xFFFFFFFFFFFFFULL);
-  const long long M = E ? (frac | (1LL << 52)) : frac;  // |x| = M 2^(max(E, 1) - 1075)
-  const int sft = (E ? E : 1) - 1075 + 63 - ex;          // U = M 2^sft
-  long long U;
-  if (M == 0 || sft <= -64) U = 0;
-  else if (sft >= 0) U = M << sft;                       // below 2^63 because |x| < 2^ex
-  else U = (M >> (-sft)) + ((M >> (-sft - 1)) & 1);      // nearest, half up
-  if (bits >> 63) U = -U;
-  const uint32_t lo = (uint32_t)(unsigned long long)U, hi = (uint32_t)((unsigned long long)U >> 32);
-  const uint32_t mid = (hi << 1) | (lo >> 31);           // bits 62 .. 31 of U
-  out[0] = bf16_of_small_int((sext_field(hi, 23, 9) + 1) >> 1);
-  out[1] = bf16_of_small_int((sext_field(hi, 15, 9) + 1) >> 1);
-  out[2] = bf16_of_small_int((sext_field(hi, 7, 9) + 1) >> 1);
-  out[3] = bf16_of_small_int((sext_field(mid, 0, 9) + 1) >> 1);
-  out[4] = bf16_of_small_int((sext_field(lo, 23, 9) + 1) >> 1);
-  out[5] = bf16_of_small_int((sext_field(lo, 15, 9) + 1) >> 1);
-  out[6] = bf16_of_small_int((sext_field(lo, 7, 9) + 1) >> 1);
-  out[7] = bf16_of_small_int(sext_field(lo, 0, 8));
-}
-
-
 __device__ __forceinline__ void store8(uint16_t* dst, const uint16_t v[8]) {
   uint4 w;
   w.x = (uint32_t)v[0] | ((uint32_t)v[1] << 16);
@@ -339,7 +290,7 @@ __global__ void split_rows_kernel(int n, int k, const double* __restrict__ A, lo
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         uint16_t dq[OZ_S];
-        digits(x[q][p], ex, dq);
+        oz_digits(x[q][p], ex, dq);
 #pragma unroll
         for (int i = 0; i < OZ_S; ++i) d[i][q] = dq[i];
       }
@@ -385,7 +336,7 @@ __global__ void split_cols_kernel(int k, int m, const double* __restrict__ B, lo
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         uint16_t dq[OZ_S];
-        digits(x[q][p], ex, dq);
+        oz_digits(x[q][p], ex, dq);
 #pragma unroll
         for (int j = 0; j < OZ_S; ++j) d[j][q] = dq[j];
       }
