@@ -43,3 +43,13 @@ def test_split_blocks_and_activation_rule(monkeypatch):
     assert not bench.split_ax_active(W.WORKLOADS["dense_complex_n16384"])
     monkeypatch.setenv("MPL_AX_SPLIT", "1")
     assert bench.split_ax_active(W.WORKLOADS["dense_real_n1000"])
+
+
+def test_split_roofline_traffic_only_where_measured():
+    """The DRAM traffic of the dense complex product was captured at n = 8192
+    (3.84 GB per product, slices of A dominate) and is scaled by n^2; shapes
+    never captured report no traffic."""
+    r = bench.split_ax_roofline(W.WORKLOADS["dense_complex_n16384"], 7e-3, 10)
+    assert abs(r["traffic"] - 4 * 3.84e9) < 1.0
+    assert 1.0 < r["traffic"] / r["slice_bytes_per_launch"] < 1.3   # re-reads on top of the algorithmic bytes
+    assert bench.split_ax_roofline(W.WORKLOADS["dense_real_n1000"], 1e-4, 10)["traffic"] is None
