@@ -1,6 +1,7 @@
-"""Section 4 pins (CPU): Lemma 2's bound on ||I - A^1/2 T_E A^1/2||, Theorem 1's
-per-step contraction of PINVIT, and the Remark's attainable-accuracy floor,
-on tiny dense instances where the hypotheses hold."""
+"""Section 4 pins (CPU): Lemma 1's rounding model of the computed residual,
+Lemma 2's bound on ||I - A^1/2 T_E A^1/2||, Theorem 1's per-step contraction
+of PINVIT, and the Remark's attainable-accuracy floor, on tiny dense
+instances where the hypotheses hold."""
 import numpy as np
 import pytest
 import scipy.linalg as sla
@@ -114,3 +115,52 @@ def test_pinvit_single_vector_rate():
         x = x - TE @ (A @ x - rho * x)
     ratios = [b / a for a, b in zip(qs[2:], qs[3:]) if a > 1e-13]
     assert ratios and max(ratios) <= rate * 1.01
+
+
+def _exact_residual_gap(A, R, x):
+    """||R - r||_2 and ||r||_2, r = A x - rho(x) x evaluated exactly in
+    rational arithmetic for the x the oracle used (rho = x^T A x / x^T x)."""
+    from fractions import Fraction
+    n = A.shape[0]
+    xf = [Fraction(float(v)) for v in x]
+    Af = [[Fraction(float(a)) for a in row] for row in A]
+    Ax = [sum(Af[i][j] * xf[j] for j in range(n)) for i in range(n)]
+    rho = sum(xf[i] * Ax[i] for i in range(n)) / sum(v * v for v in xf)
+    r = [Ax[i] - rho * xf[i] for i in range(n)]
+    gap = float(sum((Fraction(float(R[i])) - r[i]) ** 2 for i in range(n))) ** 0.5
+    rn = float(sum(v * v for v in r)) ** 0.5
+    return gap, rn
+
+
+def test_lemma1_residual_of_the_pinvit_step(monkeypatch):
+    """Lemma 1: the computed residual r^ of a PINVIT step is (I + E)(r + F x)
+    with ||E|| <= u_h and ||F|| <= eps_r ||A||, so
+    ||r^ - r|| <= u_h ||r|| + (1 + u_h) eps_r ||A|| ||x||, with r = A x - rho(x) x
+    exact.  Checked on the residuals the oracle's Algorithm 1 actually forms
+    (captured at its convergence test), against r in exact rationals."""
+    n = 24
+    A, lam = W.dense_spd(n, seed=11, kappa=1e3)
+    normA = float(lam[-1])
+    TE, _ = _factor_TE(A)
+    X0 = np.random.default_rng(5).standard_normal((n, 1))
+    seen = []
+    stop = D.stop_test
+
+    def spy(R, X, theta, nA, tol):
+        seen.append((np.array(R[:, 0]), np.array(X[:, 0])))
+        return stop(R, X, theta, nA, tol)
+
+    monkeypatch.setattr(D, "stop_test", spy)
+    L.pinvit(lambda X: A @ X, lambda R: TE @ R, X0, 1, 1e-300, 4, normA)
+    assert len(seen) == 4
+    er = B.eps_r(n)
+    for R, x in seen:
+        gap, rn = _exact_residual_gap(A, R, x)
+        bound = B.U_H * rn + (1 + B.U_H) * er * normA * float(np.linalg.norm(x))
+        assert gap <= bound, (gap, bound)
+    # not vacuous: the same step with rho(x) rounded to single precision (a
+    # precision slip in the Rayleigh quotient) breaks the bound
+    R, x = seen[-1]
+    rho32 = float(np.float32(x @ (A @ x) / (x @ x)))
+    gap, rn = _exact_residual_gap(A, A @ x - rho32 * x, x)
+    assert gap > B.U_H * rn + (1 + B.U_H) * er * normA * float(np.linalg.norm(x))
