@@ -1,10 +1,15 @@
-// Digits of the error-free splitting of the FP64-accurate products
-// (oz_gemm.cu; Ozaki, Ogita, Oishi & Rump 2012): one FP64 value x below a
-// given exponent ex (|x| < 2^ex) as OZ_S = 8 balanced signed 8-bit digits,
-// each returned as the bf16 bit pattern of the integer (|q| <= 128, exact in
-// bf16).  Host and device: the split kernels call it, and a CPU test
-// compiles it for the host and checks it against the definition.
+// Scalar fixed-point arithmetic of the FP64-accurate split products
+// (oz_gemm.cu; Ozaki, Ogita, Oishi & Rump 2012), host and device: the
+// kernels call it, and CPU tests compile it for the host and check it
+// against the definitions in exact arithmetic.
+//   oz_digits       one FP64 value x below a given exponent ex (|x| < 2^ex)
+//                   as OZ_S = 8 balanced signed 8-bit digits, each returned
+//                   as the bf16 bit pattern of the integer (|q| <= 128,
+//                   exact in bf16);
+//   oz_fixed_value  the exact int64 sums of a product back to FP64,
+//                   correctly rounded.
 #pragma once
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 
@@ -33,6 +38,16 @@ OZ_HD float oz_float_of_bits(uint32_t b) {
   float f;
   std::memcpy(&f, &b, sizeof f);
   return f;
+#endif
+}
+
+OZ_HD double oz_double_of_bits(unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double x;
+  std::memcpy(&x, &b, sizeof x);
+  return x;
 #endif
 }
 
@@ -94,6 +109,33 @@ OZ_HD void oz_digits(double x, int ex, uint16_t out[8]) {
   out[5] = oz_bf16_of_small_int((oz_sext_field(lo, 15, 9) + 1) >> 1);
   out[6] = oz_bf16_of_small_int((oz_sext_field(lo, 7, 9) + 1) >> 1);
   out[7] = oz_bf16_of_small_int(oz_sext_field(lo, 0, 8));
+}
+
+// x 2^k: a multiplication by the power of two when 2^k is a normal double
+// (exact unless the result is subnormal), ldexp otherwise -- the value of
+// ldexp(x, k) without its FP64 instruction sequence on the device.
+OZ_HD double oz_scale2(double x, int k) {
+  if (k >= -1022 && k <= 1023) return x * oz_double_of_bits((unsigned long long)(k + 1023) << 52);
+  return ldexp(x, k);
+}
+
+// The FP64 value of one accumulator pair of a product, 2^ex (hi 2^-24 +
+// lo 2^-56) = 2^(ex - 56) (top 2^32 + low) with top = hi + floor(lo / 2^32)
+// and low = lo mod 2^32 (|hi| < 2^59, |lo| < 2^62, so |top| < 2^60), rounded
+// once to nearest-even (while the result is normal):
+//   -2^53 <= top < 2^53: top and low are exact doubles, so the one addition
+//     is the only rounding;
+//   otherwise the exact value top + low 2^-32 has magnitude >= 2^53, its unit
+//     in the last place is >= 2 units of top, the rounding midpoints are
+//     integers, and low only decides on which side of a midpoint at top the
+//     value lies: 2 top + [low != 0] (a sticky bit below top, < 2^61) rounded
+//     once and halved gives the same double.
+OZ_HD double oz_fixed_value(long long hi, long long lo, int ex) {
+  const long long top = hi + (lo >> 32);
+  const long long low = lo & 0xFFFFFFFFLL;
+  if (top >= -(1LL << 53) && top < (1LL << 53))
+    return oz_scale2((double)top, ex - 24) + oz_scale2((double)low, ex - 56);
+  return oz_scale2((double)(2 * top + (low != 0 ? 1 : 0)), ex - 25);
 }
 
 }  // namespace mpl

@@ -12,7 +12,7 @@
 // up to 2^(e_r - 71).  Columns of B likewise with exponents f_c.  Every step
 // is exact in FP64 (u - rint(u) and the scaling by 256 round nothing); the
 // kernels compute the same digits from the bit pattern on the integer pipes
-// (oz_digits.cuh).
+// (oz_fixed.cuh).
 //
 // Products.  The slice pairs (i, j) with i + j = g <= 7 (36 pairs; the
 // dropped ones weigh <= 2^-64 of the leading product) are accumulated per
@@ -25,8 +25,8 @@
 // and the depth splits of a tile add theirs with exact, order-free int64
 // atomics.  The product is then exact for the truncated digits:
 //   C = 2^(e_r + f_c - 14) (hi 2^-24 + lo 2^-56),
-// rounded once to FP64 in the combination kernel -- no rounding inside the
-// dot product at all, unlike an FP64 GEMM.
+// rounded once to FP64 in the combination kernel (oz_fixed_value) -- no
+// rounding inside the dot product at all, unlike an FP64 GEMM.
 //
 // Tiles.  A CTA owns 128 rows of A, one block of NPAD <= 64 columns of B
 // (8 accumulators x NPAD <= 512 tensor-memory columns) and a range of depth.
@@ -52,6 +52,7 @@
 // shift-group accumulators (8 x N <= 512 tensor-memory columns) cap at
 // 128 x 64 outputs each; a CTA pair (cta_group::2, M = 256) would double
 // the work per instruction.
+//
 // Every wait has an iteration limit; a role that gives up records an error
 // and raises the CTA's abort flag, the others leave their waits, and the CTA
 // waits (bounded) for the copies and MMAs it issued before it frees its
@@ -66,7 +67,7 @@
 #include <mutex>
 
 #include "common.cuh"
-#include "oz_digits.cuh"
+#include "oz_fixed.cuh"
 #include "oz_gemm.cuh"
 
 namespace mpl {
@@ -624,23 +625,6 @@ oz_mma_kernel(int ncb, int nchunk, int chunks_per_split, const uint16_t* __restr
   if (wid == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
-// x 2^k: a multiplication by the power of two when 2^k is a normal double
-// (exact, or rounded once like ldexp when the result is subnormal), ldexp
-// otherwise -- the same value as ldexp(x, k) without its FP64 sequence
-__device__ __forceinline__ double scale2(double x, int k) {
-  if (k >= -1022 && k <= 1023) return x * __longlong_as_double((long long)(k + 1023) << 52);
-  return ldexp(x, k);
-}
-
-// value of one accumulator pair in units of the leading digit product:
-// hi 2^-24 + lo 2^-56, from an exact split into a 53-bit-safe part and the
-// low 32 bits of lo, times 2^ex
-__device__ __forceinline__ double fixed_value(long long hi, long long lo, int ex) {
-  const long long top = hi + (lo >> 32);            // lo = (lo >> 32) 2^32 + (lo & 0xffffffff)
-  const long long low = lo & 0xFFFFFFFFLL;
-  return scale2((double)top, ex - 24) + scale2((double)low, ex - 56);
-}
-
 // C(r, c) = alpha 2^(e_r + f_c - 14) (hi 2^-24 + lo 2^-56) (+ beta C); rows
 // by grid x (grid-stride), columns by grid y
 __global__ void combine_real_kernel(int n, int m, const long long* __restrict__ T, long long ldt, long long tlo,
@@ -651,7 +635,7 @@ __global__ void combine_real_kernel(int n, int m, const long long* __restrict__ 
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     if (lower_only && r < col0 + c) continue;
     const long long t = r + c * ldt;
-    double v = fixed_value(T[t], T[tlo + t], e[r] + fc);
+    double v = oz_fixed_value(T[t], T[tlo + t], e[r] + fc);
     if (alpha != 1.0) v *= alpha;
     if (beta != 0.0) v += beta * C[r + c * ldc];
     C[r + c * ldc] = v;
@@ -673,7 +657,7 @@ __global__ void combine_3m_kernel(int n, int m, const long long* __restrict__ T,
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       const long long t = q * tstride + r + c * ldt;
-      p[q] = fixed_value(T[t], T[tlo + t], e[q * estride + r] + fc[q]);
+      p[q] = oz_fixed_value(T[t], T[tlo + t], e[q * estride + r] + fc[q]);
     }
     double re = p[0] - p[1], im = p[2] - p[0] - p[1];
     if (alpha != 1.0) {

@@ -1,13 +1,17 @@
-"""Digits of the error-free splitting behind the FP64-accurate products
-(Ozaki, Ogita, Oishi & Rump 2012), checked on the CPU.
+"""Scalar arithmetic of the error-free splitting behind the FP64-accurate
+products (Ozaki, Ogita, Oishi & Rump 2012), checked on the CPU.
 
-The split kernels call mpl::oz_digits (csrc/oz_digits.cuh).  This test
-compiles that function for the host and compares it, value by value, with
-the splitting written out from its definition in Python integers: the
-64-bit fixed point U = round(x 2^(63 - ex)) (half away from zero), then the
-balanced digits taken from the top, each the nearest integer (half up) of
-what remains, and the bf16 pattern of each digit.  It also checks that the
-digits add back to U exactly and stay within |q| <= 128 (exact in bf16).
+The split kernels call mpl::oz_digits and mpl::oz_fixed_value
+(csrc/oz_fixed.cuh).  These tests compile both for the host and compare
+them, value by value, with their definitions in exact arithmetic:
+  * the digits: the 64-bit fixed point U = round(x 2^(63 - ex)) (half away
+    from zero), then the balanced digits taken from the top, each the
+    nearest integer (half up) of what remains, and the bf16 pattern of each
+    digit; the digits must also add back to U and stay within |q| <= 128;
+  * the value of an accumulator pair: 2^ex (hi 2^-24 + lo 2^-56) as a
+    rational number, rounded once to the nearest double (Python's
+    Fraction -> float rounds correctly), which the kernel must reproduce
+    bit for bit.
 """
 import math
 import os
@@ -24,17 +28,31 @@ CSRC = os.path.join(ROOT, "paper_2302_12528_gb300", "csrc")
 HARNESS = r"""
 #include <cstdio>
 #include <cstdlib>
-#include "oz_digits.cuh"
+#include <cstring>
+#include "oz_fixed.cuh"
+// argv[1] = d: lines "bits ex" -> the 8 digit patterns;
+// argv[1] = v: lines "hi lo ex" -> the bit pattern of oz_fixed_value
 int main(int argc, char** argv) {
-  FILE* f = std::fopen(argv[1], "r");
-  unsigned long long b;
-  int ex;
-  while (std::fscanf(f, "%llx %d", &b, &ex) == 2) {
-    double x;
-    std::memcpy(&x, &b, 8);
-    uint16_t d[8];
-    mpl::oz_digits(x, ex, d);
-    for (int i = 0; i < 8; ++i) std::printf("%04x%c", d[i], i == 7 ? '\n' : ' ');
+  FILE* f = std::fopen(argv[2], "r");
+  if (argv[1][0] == 'd') {
+    unsigned long long b;
+    int ex;
+    while (std::fscanf(f, "%llx %d", &b, &ex) == 2) {
+      double x;
+      std::memcpy(&x, &b, 8);
+      uint16_t d[8];
+      mpl::oz_digits(x, ex, d);
+      for (int i = 0; i < 8; ++i) std::printf("%04x%c", d[i], i == 7 ? '\n' : ' ');
+    }
+  } else {
+    long long hi, lo;
+    int ex;
+    while (std::fscanf(f, "%lld %lld %d", &hi, &lo, &ex) == 3) {
+      const double v = mpl::oz_fixed_value(hi, lo, ex);
+      unsigned long long b;
+      std::memcpy(&b, &v, 8);
+      std::printf("%016llx\n", b);
+    }
   }
   return 0;
 }
@@ -124,7 +142,7 @@ def test_digits_match_the_definition(harness, tmp_path):
     cs = cases()
     inp = tmp_path / "in.txt"
     inp.write_text("".join(f"{struct.unpack('<Q', struct.pack('<d', x))[0]:016x} {ex}\n" for x, ex in cs))
-    r = subprocess.run([str(harness), str(inp)], capture_output=True, text=True, check=True)
+    r = subprocess.run([str(harness), "d", str(inp)], capture_output=True, text=True, check=True)
     lines = r.stdout.strip().split("\n")
     assert len(lines) == len(cs)
     for (x, ex), line in zip(cs, lines):
@@ -143,3 +161,53 @@ def test_reference_worked_example():
     U, q = reference_digits(math.ldexp(float(U0), -63), 0)
     assert U == U0
     assert q == [0, 4, -128, 0, 0, 0, 0, 0]
+
+
+def value_cases():
+    """(hi, lo, ex) as the kernels produce them (|hi| < 2^59, |lo| < 2^62),
+    with ex keeping the result normal, plus the branch boundaries of
+    top = hi + floor(lo / 2^32) at +-2^53 and exact halves."""
+    rng = np.random.default_rng(1202)
+    out = []
+    for _ in range(6000):
+        hi = int(rng.integers(-(1 << 59) + 1, 1 << 59))
+        lo = int(rng.integers(-(1 << 62) + 1, 1 << 62))
+        out.append((hi, lo, int(rng.integers(-900, 900))))
+    for _ in range(3000):   # small hi: the exact branch, low word significant
+        hi = int(rng.integers(-(1 << 40), 1 << 40))
+        lo = int(rng.integers(-(1 << 62) + 1, 1 << 62))
+        out.append((hi, lo, int(rng.integers(-60, 60))))
+    for top in (1 << 53, (1 << 53) - 1, (1 << 53) + 1, -(1 << 53), -(1 << 53) + 1, -(1 << 53) - 1,
+                (1 << 54) + 1, -(1 << 54) - 1, (1 << 59) - 1, -(1 << 59) + 1, 0, 1, -1):
+        for low in (0, 1, (1 << 31) - 1, 1 << 31, (1 << 31) + 1, (1 << 32) - 1):
+            for lo_top in (0, 5, -5):   # split top between hi and lo's upper bits
+                hi = top - lo_top
+                lo = (lo_top << 32) + low
+                if abs(hi) < 1 << 59:
+                    out.append((hi, lo, 0))
+    return out
+
+
+def test_fixed_value_is_rounded_once(harness, tmp_path):
+    cs = value_cases()
+    inp = tmp_path / "vin.txt"
+    inp.write_text("".join(f"{hi} {lo} {ex}\n" for hi, lo, ex in cs))
+    r = subprocess.run([str(harness), "v", str(inp)], capture_output=True, text=True, check=True)
+    lines = r.stdout.strip().split("\n")
+    assert len(lines) == len(cs)
+    from fractions import Fraction
+    for (hi, lo, ex), line in zip(cs, lines):
+        exact = (Fraction(hi) / (1 << 24) + Fraction(lo) / (1 << 56)) * (Fraction(2) ** ex)
+        want = struct.unpack("<Q", struct.pack("<d", float(exact)))[0]
+        assert int(line, 16) == want, (hi, lo, ex, float(exact))
+
+
+def test_fixed_value_reference_catches_double_rounding():
+    """The exact reference is not the kernel's arithmetic: converting top
+    first and adding the low word afterwards (two roundings) differs from it
+    on a case where top is odd and above 2^53 and the low word breaks the tie."""
+    from fractions import Fraction
+    top, low = (1 << 53) + 1, 1            # exact value top + 2^-32: just above the midpoint
+    two_roundings = float(top) + math.ldexp(float(low), -32)
+    exact = float(Fraction(top) + Fraction(low, 1 << 32))
+    assert exact == float((1 << 53) + 2) and two_roundings == float(1 << 53)
